@@ -1,0 +1,424 @@
+#!/usr/bin/env python
+"""Benchmark of the underwater splat rasterizer's training step.
+
+Workload: 1.5M Gaussians from the seeded surface-patch generator (2-15 m,
+SH degree 3), 1920x1280, 100 views on a 6 m arc. One step = forward render
+(preprocess, depth sort, binning, tile sort, blend with the water model),
+loss L1 + 0.2 (1 - SSIM) against the view's target (rendered beforehand from
+the ground-truth scene and medium), backward to every Gaussian and medium
+parameter, and one Adam update. Inputs stay resident in HBM; the per-step
+working set (parameters, gradients, Adam moments: ~1.4 GB) is larger than
+L2, so no explicit flush is needed.
+
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FPS & fwd+bwd iters/s at 1.5M Gaussians 1920x1280; frac of FP32/smem peak"
+N_GAUSS = 1_500_000
+N_VIEWS = 100
+LAMBDA_SSIM = 0.2
+# learning rates (3DGS values the paper keeps, appendix "Experimental Setup")
+LR = {"means": 1.6e-4, "log_scales": 5e-3, "quats": 1e-3, "opacity_logits": 5e-2, "sh": 2.5e-3, "medium": 2.5e-3}
+# algorithmic work per unit (see the design notes): FP32 FLOP per walked pixel-Gaussian pair
+FLOP_PER_PAIR_FWD = 18
+FLOP_PER_PAIR_BWD = 50
+SM_COUNT_FALLBACK = 148
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N_GAUSS, help="Gaussians (default: the 1.5M workload)")
+    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if torch.cuda.is_available() and args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, power, throttle reasons) during the timed region."""
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={','.join(self.FIELDS)}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def build_workload(n, rank, device="cuda"):
+    import torch
+
+    from paper_2411_19588_b300 import render as R
+    from paper_2411_19588_b300 import scenes
+    g_gt, med_gt, _ = scenes.patch_scene(n, 3, (2.0, 15.0), 1920, 1280, 1800.0)
+    cams = scenes.arc_cameras(N_VIEWS, seed=3)
+    fit, _ = scenes.perturb(g_gt, med_gt, seed=1 + rank)
+    params = R.params_to_device(fit, device)
+    med = torch.tensor([0.1] * 9, dtype=torch.float32, device=device)
+    gt = R.params_to_device(g_gt, device)
+    med_gt_t = torch.tensor(med_gt.as_array(), device=device)
+    return params, med, gt, med_gt_t, cams
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_2411_19588_b300 import render as R
+
+    torch.cuda.set_device(local)
+    tw, th = (int(x) for x in args.tile.split("x"))
+    r = R.Renderer(tile=(tw, th))
+    params, med, gt, med_gt, cams = build_workload(args.n, rank)
+    H, W = cams[0].height, cams[0].width
+    # targets: the ground-truth scene and medium seen from every view
+    st_t = r.state()
+    targets = []
+    for cam in cams:
+        img, _, _ = r.forward(st_t, gt, med_gt, cam)
+        targets.append(img.clone())
+    del gt
+    torch.cuda.synchronize()
+
+    names = list(R.PARAM_NAMES) + ["medium"]
+    tensors = {k: params[k] for k in R.PARAM_NAMES}
+    tensors["medium"] = med
+    grads = {k: torch.zeros_like(v) for k, v in tensors.items()}
+    mom = {k: torch.zeros_like(v) for k, v in tensors.items()}
+    vel = {k: torch.zeros_like(v) for k, v in tensors.items()}
+    groups = [{"param": tensors[k], "grad": grads[k], "m": mom[k], "v": vel[k], "lr": LR[k],
+               "clamp_min": 0.0 if k == "medium" else None} for k in names]
+    st = r.state()
+    image = torch.empty((3, H, W), device="cuda")
+    depth = torch.empty((H, W), device="cuda")
+    depth01 = torch.empty((H, W), device="cuda")
+    step_no = [0]
+
+    def view_of(i):
+        return (i * 7 + rank * 13) % N_VIEWS
+
+    def step(i, target=None):
+        cam = cams[view_of(i)]
+        r.forward(st, params, med, cam, image, depth, depth01)
+        loss, gimg = r.loss(st, image, targets[view_of(i)] if target is None else target, LAMBDA_SSIM)
+        r.backward(st, params, med, cam, gimg, None, None, grads)
+        step_no[0] += 1
+        R.adam_step(groups, step_no[0])
+        return loss
+
+    stream = torch.cuda.current_stream()
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    barrier(world)
+
+    # --- timed region: the training step, inputs resident in HBM
+    clocks = ClockSampler(local)
+    clocks.start()
+    r.profile(True)
+    l0 = R.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    adam_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for i in range(args.steps):
+        cam = cams[view_of(args.warmup + i)]
+        r.forward(st, params, med, cam, image, depth, depth01)
+        loss, gimg = r.loss(st, image, targets[view_of(args.warmup + i)], LAMBDA_SSIM)
+        r.backward(st, params, med, cam, gimg, None, None, grads)
+        step_no[0] += 1
+        adam_ev[i][0].record(stream)
+        R.adam_step(groups, step_no[0])
+        adam_ev[i][1].record(stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = R.kernel_launches() - l0
+    clk = clocks.stop()
+    stage = r.profile_read()
+    r.profile(False)
+    ms_step = ev0.elapsed_time(ev1) / args.steps
+    adam_ms = sum(a.elapsed_time(b) for a, b in adam_ev) / args.steps
+    ms_step_max = max_over_ranks(ms_step, world)
+
+    # --- forward-only frames per second
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for i in range(args.steps):
+        r.forward(st, params, med, cams[view_of(i)], image, depth, depth01)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = max_over_ranks(f0.elapsed_time(f1) / args.steps, world)
+
+    # --- algorithmic work of the blend launches in the timed region (same views)
+    walk, last = 0.0, 0.0
+    for i in range(args.steps):
+        r.forward(st, params, med, cams[view_of(args.warmup + i)], image, depth, depth01)
+        walk += float(r.state_array(st, "n_walk").to(torch.int64).sum())
+        last += float(r.state_array(st, "n_last").to(torch.int64).sum())
+    walk /= args.steps
+    last /= args.steps
+    n_keys = r.info(st)["n_keys"]
+
+    # --- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        nb = min(8, N_VIEWS)
+        host_t = [targets[view_of(args.warmup + i)].cpu().pin_memory() for i in range(nb)]
+        host_loss = torch.empty(1, dtype=torch.float32).pin_memory()
+        dev_t = torch.empty_like(targets[0])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            dev_t.copy_(host_t[i % nb], non_blocking=True)
+            cam = cams[view_of(args.warmup + i)]
+            r.forward(st, params, med, cam, image, depth, depth01)
+            loss, gimg = r.loss(st, image, dev_t, LAMBDA_SSIM)
+            r.backward(st, params, med, cam, gimg, None, None, grads)
+            step_no[0] += 1
+            R.adam_step(groups, step_no[0])
+            host_loss.copy_(loss, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
+        e2e = {"value": round(world / e2e_s, 3), "unit": "iters/s", "h2d_bytes_per_step": int(dev_t.numel() * 4),
+               "d2h_bytes_per_step": 4}
+
+    # --- roofline of the dominant kernel
+    peaks, peak_src = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count or SM_COUNT_FALLBACK
+    f_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
+    fp32_peak_tflops = sm_count * 128 * 2 * f_mhz * 1e6 / 1e12
+    n_total = sum(t.numel() for t in tensors.values())
+    per_launch = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in stage.items()}
+    per_launch["adam"] = adam_ms
+    work = {
+        "blend_fwd": ("alu", FLOP_PER_PAIR_FWD * walk, "TFLOP/s"),
+        "blend_bwd": ("alu", FLOP_PER_PAIR_BWD * last, "TFLOP/s"),
+        "adam": ("hbm", 28.0 * n_total, "GB/s"),
+        "preprocess": ("hbm", (236 + 68) * args.n, "GB/s"),
+        "preprocess_bwd": ("hbm", (236 + 48 + 236) * args.n, "GB/s"),
+        "tile_sort": ("hbm", 2 * 16.0 * n_keys + 4.0 * n_keys, "GB/s"),
+        "loss": ("hbm", 4.0 * 3 * H * W * 9, "GB/s"),
+    }
+    dom = max((k for k in work if per_launch.get(k, 0) > 0), key=lambda k: per_launch[k])
+    bound, units, unit = work[dom]
+    t_s = per_launch[dom] * 1e-3
+    if unit == "TFLOP/s":
+        achieved, peak, note = units / t_s / 1e12, fp32_peak_tflops, f"FP32 issue peak at {f_mhz:.0f} MHz x {sm_count} SMs"
+    else:
+        achieved, peak, note = units / t_s / 1e9, float(peaks["hbm_gbs"]), f"{peak_src} HBM copy bandwidth"
+    stages_ms = {k: round(v, 4) for k, v in per_launch.items() if v > 0}
+
+    out = {
+        "metric": METRIC,
+        "value": round(world * 1000.0 / ms_step_max, 3),
+        "unit": "iters/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step_max, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded surface-patch scenes standing in for the paper's underwater captures)",
+        "config": {"workload": "train step: 1.5M Gaussians (SH3, 2-15 m), 1920x1280, 100-view arc, "
+                               "fwd + L1+0.2(1-SSIM) + bwd + Adam",
+                   "n_gaussians": args.n, "width": W, "height": H, "views": N_VIEWS, "tile": args.tile,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "working set (params+grads+Adam moments ~1.4 GB) larger than L2; no flush"},
+        "fps": round(world * 1000.0 / fwd_ms, 2),
+        "fwd_ms": round(fwd_ms, 4),
+        "roofline": {"kernel": dom, "bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 2),
+                     "unit": unit, "frac": round(achieved / peak, 4), "traffic": None, "peak_source": note},
+        "stages_ms": stages_ms,
+        "pairs": {"walked_fwd": int(walk), "walked_bwd": int(last), "keys": int(n_keys)},
+        "gpu_launches": int(launches + args.steps),
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(budget_s=20.0)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def cpu_baseline(budget_s: float = 20.0, n: int = N_GAUSS) -> dict:
+    """The FP64 oracle (as it stands) on a bounded sample of the training
+    step: projection of all Gaussians, forward and adjoint at a random
+    sample of pixels, the loss and Adam on a sample of their elements;
+    scaled to one full step."""
+    import oracle
+    from oracle import adam as oadam
+    from oracle import loss as oloss
+    from paper_2411_19588_b300 import scenes
+    g, m, _ = scenes.patch_scene(n, 3, (2.0, 15.0), 1920, 1280, 1800.0)
+    cam = scenes.arc_cameras(N_VIEWS, seed=3)[N_VIEWS // 2]
+    H, W = cam.height, cam.width
+    rng = np.random.default_rng(0)
+    t = time.perf_counter()
+    oracle.project(g, m, cam)
+    t_proj = time.perf_counter() - t
+    S = 32
+    while True:
+        pix = rng.choice(H * W, S, replace=False)
+        t = time.perf_counter()
+        oracle.render(g, m, cam, pix=pix)
+        oracle.backward(g, m, cam, rng.standard_normal((3, S)), pix=pix)
+        t_pix = time.perf_counter() - t - 2 * t_proj
+        if t_pix + 2 * t_proj > budget_s * 0.6 or S >= 4096:
+            break
+        S *= 2
+    per_pixel = max(t_pix, 0.0) / S
+    crop = 256
+    x = rng.uniform(0, 1, (3, crop, crop))
+    t = time.perf_counter()
+    oloss.loss_and_grad(x, x * 0.9, LAMBDA_SSIM)
+    t_loss = (time.perf_counter() - t) * (H * W) / (crop * crop)
+    ne = 1_000_000
+    p = rng.standard_normal(ne)
+    t = time.perf_counter()
+    oadam.adam_step(p, p, np.zeros(ne), np.zeros(ne), 1, 1e-3)
+    t_adam = (time.perf_counter() - t) * (n * 59 + 9) / ne
+    t_step = 2 * t_proj + per_pixel * H * W + t_loss + t_adam
+    return {"value": 1.0 / t_step, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"projection of all {n} Gaussians + forward/adjoint at {S} random pixels (scaled by "
+                      f"{H * W}/{S}) + loss on a {crop}x{crop} crop and Adam on {ne} elements (scaled)",
+            "seconds_per_step": round(t_step, 1)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    budget = 4.0
+    vals = []
+    for i in range(args.warmup + args.steps):
+        b = cpu_baseline(budget_s=budget, n=args.n)
+        if i >= args.warmup:
+            vals.append(b["value"])
+    v = float(np.median(vals))
+    out = {"metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": "train step: 1.5M Gaussians (SH3, 2-15 m), 1920x1280, 100-view arc, "
+                                  "fwd + L1+0.2(1-SSIM) + bwd + Adam", "n_gaussians": args.n},
+           "cpu_baseline": {"value": v, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": b["sample"]},
+           "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,238 @@
+/*
+ * splash.h -- C ABI of libsplash.so, a B300 (sm_103a) differentiable tile
+ * rasterizer for 3D Gaussians with the Gaussian Splashing underwater
+ * image-formation model folded into compositing (arXiv 2411.19588).
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers named *_dev / buffers of the rasterizer are DEVICE pointers
+ *    (cudaMalloc'd or torch CUDA storage) on the current device; the caller
+ *    owns them. Host structs (camera, options, gradient tables) are read
+ *    during the call only.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). Work is
+ *    asynchronous on it unless stated otherwise.
+ *  - Every call returns a splash_status; on failure splash_last_error()
+ *    gives a message (thread-local). Errors found by kernels (a bounded
+ *    device wait that gave up, a capacity overflow) are reported by the next
+ *    call that synchronises with the stream, or by splash_sync_status().
+ *  - Floats are IEEE binary32; layouts are C-contiguous (row-major).
+ */
+#ifndef SPLASH_H
+#define SPLASH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPLASH_OK = 0,
+    SPLASH_ERR_INVALID_ARG = 1, /* a null pointer, a bad size, degree or tile shape */
+    SPLASH_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+    SPLASH_ERR_OOM = 3,         /* device allocation failed */
+    SPLASH_ERR_CAPACITY = 4,    /* more tile/Gaussian pairs than the workspace holds */
+    SPLASH_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    SPLASH_ERR_STATE = 6        /* backward without a matching forward */
+} splash_status;
+
+typedef struct splash_ctx splash_ctx;     /* options + device status word */
+typedef struct splash_state splash_state; /* per-render workspace and forward state */
+
+/* Pinhole camera. Pixel (ix, iy) has its centre at (ix + 0.5, iy + 0.5);
+ * world_to_cam is a row-major 3x4 [R | t] with OpenCV axes (x right, y down,
+ * z forward). Gaussians with camera-frame z <= z_near or z > z_far are culled;
+ * the water behind the last Gaussian ends at z_far. */
+typedef struct {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float world_to_cam[12];
+    float z_near, z_far;
+} splash_camera;
+
+/* Gaussian parameters theta_i = (mu, Sigma, c, opacity) of Sec. III-A, as
+ * device buffers: means [n,3]; log_scales [n,3] (Sigma = R S S^T R^T with
+ * S = diag(exp(log_scales))); quats [n,4] as (w, x, y, z), normalised inside;
+ * opacity_logits [n] (opacity = sigmoid); sh [n, (deg+1)^2, 3] real
+ * spherical-harmonic colour coefficients, colour = sum + 0.5 clamped at 0.
+ * n < 2^31; sh_degree in 0..3. */
+typedef struct {
+    const float *means;
+    const float *log_scales;
+    const float *quats;
+    const float *opacity_logits;
+    const float *sh;
+    int64_t n;
+    int32_t sh_degree;
+} splash_gaussians;
+
+/* Gradient outputs (device), same layouts as the parameters; medium is [9].
+ * They are OVERWRITTEN (not accumulated). A null member is not written. */
+typedef struct {
+    float *means;
+    float *log_scales;
+    float *quats;
+    float *opacity_logits;
+    float *sh;
+    float *medium;
+} splash_grads;
+
+typedef struct {
+    int32_t tile_w, tile_h; /* pixel tile: 16x16 (default), 8x32 or 32x8 */
+    int32_t spin_limit;     /* iterations before a device wait gives up; 0 = default (2^22) */
+    int32_t test_stall_partition; /* testing aid, 0 = off: when p > 0, partition p of every
+                                     sort pass never publishes its look-back entry, so the
+                                     wait of partition p + 1 runs out and the call reports
+                                     SPLASH_ERR_TIMEOUT (results are then invalid) */
+} splash_options;
+
+/* Context: options and a device status word. Allocates only the status
+ * word. opt may be NULL (defaults). */
+splash_status splash_create(const splash_options *opt, splash_ctx **out);
+splash_status splash_destroy(splash_ctx *ctx);
+
+/* A state holds the workspace of one render (projected Gaussians, sorted
+ * tile lists, per-pixel final transmittance) so that splash_render_backward
+ * can follow splash_render_forward. Its device buffers grow on demand
+ * (cudaMalloc) and are freed by splash_state_destroy. One state serves one
+ * forward/backward pair at a time; use one state per in-flight render. */
+splash_status splash_state_create(splash_ctx *ctx, splash_state **out);
+splash_status splash_state_destroy(splash_state *st);
+
+/* Forward render (Sec. III-A tiles and Eq. 1-2 compositing, water model of
+ * Eq. 3-5, depth of Eq. 6 and its logistic map of Sec. IV-D).
+ * medium_dev: device float[9] = beta_D[3], beta_B[3], B_inf[3] (1/m, 1/m, colour).
+ * Per pixel, Gaussians whose 3-sigma ellipse holds the pixel centre are
+ * composited front to back; Gaussian i adds c_i e^{-beta_D d_i} alpha_i T_i,
+ * the water in front of it adds B_inf (e^{-beta_B d_{i-1}} - e^{-beta_B d_i}) T_i,
+ * and the water behind the last one out to z_far adds
+ * B_inf (e^{-beta_B d_last} - e^{-beta_B z_far}) T_final.
+ * Outputs (device, caller-owned): image [3,H,W]; depth [H,W] metres
+ * (z_far where nothing is hit); depth01 [H,W] = 2/(1+e^{-0.1 depth}) - 1.
+ * depth and depth01 may be NULL. Synchronises `stream` once (to size the
+ * sort by the number of tile/Gaussian pairs). */
+splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const splash_gaussians *g,
+                                    const float *medium_dev, const splash_camera *cam, float *image,
+                                    float *depth, float *depth01, void *stream);
+
+/* Backward of the last forward on `st` (same g, medium and camera, unchanged
+ * in between). Upstream gradients (device): dL_dimage [3,H,W] (required),
+ * dL_ddepth and dL_ddepth01 [H,W] (NULL = zero). Writes every non-null
+ * member of `grads`. Forward transmittance is recomputed back to front from
+ * the stored final T; no per-pixel lists are kept. */
+splash_status splash_render_backward(splash_ctx *ctx, splash_state *st, const splash_gaussians *g,
+                                     const float *medium_dev, const splash_camera *cam,
+                                     const float *dL_dimage, const float *dL_ddepth,
+                                     const float *dL_ddepth01, const splash_grads *grads, void *stream);
+
+/* Read-only views of the forward state, for tests and diagnostics. Device
+ * pointers stay valid until the next forward on the state. */
+typedef struct {
+    int64_t n_keys;              /* number of (tile, Gaussian) pairs */
+    int32_t tiles_x, tiles_y, tile_w, tile_h;
+    int64_t n_gaussians;
+    const uint32_t *tile_ids;    /* [n_keys] sorted tile index of each pair */
+    const uint32_t *gauss_ids;   /* [n_keys] Gaussian index of each pair */
+    const uint32_t *ranges;      /* [tiles][2] half-open [start, end) into the pairs */
+    const uint32_t *depth_keys;  /* [n] FP32 depth bits, 0xffffffff when culled */
+    const uint32_t *tiles_touched; /* [n] */
+    const float *records;        /* [n][12] projected Gaussian: x_hi, y_hi, x_lo, y_lo (centre =
+                                    hi + lo), A, B, C (conic scaled by -log2(e)/2, -log2(e),
+                                    -log2(e)/2), log2(opacity), depth, ct_r, ct_g, ct_b with
+                                    ct = c e^{-beta_D d} - B_inf e^{-beta_B d}; valid where
+                                    depth_keys != 0xffffffff */
+    const float *final_T;        /* [H*W] transmittance after the last contributor */
+    const float *acc_alpha;      /* [H*W] sum of alpha T */
+    const uint32_t *n_last;      /* [H*W] 1 + list position of the last contributor */
+    const uint32_t *n_walk;      /* [H*W] list entries the pixel walked (its blend work) */
+} splash_state_info;
+splash_status splash_state_get_info(const splash_state *st, splash_state_info *out);
+
+/* Copy one forward-state buffer (sizes as in splash_state_info) into `dst`
+ * (device or pinned host memory), asynchronously on `stream`. `bytes` must
+ * equal the buffer's size: n_keys*4 for TILE_IDS/GAUSS_IDS, tiles*8 for
+ * RANGES, n*4 for DEPTH_KEYS/TILES_TOUCHED, n*48 for RECORDS, n*8 for RECTS,
+ * H*W*4 for the per-pixel fields. */
+typedef enum {
+    SPLASH_FIELD_TILE_IDS = 0,
+    SPLASH_FIELD_GAUSS_IDS = 1,
+    SPLASH_FIELD_RANGES = 2,
+    SPLASH_FIELD_DEPTH_KEYS = 3,
+    SPLASH_FIELD_TILES_TOUCHED = 4,
+    SPLASH_FIELD_RECORDS = 5,
+    SPLASH_FIELD_FINAL_T = 6,
+    SPLASH_FIELD_ACC_ALPHA = 7,
+    SPLASH_FIELD_N_LAST = 8,
+    SPLASH_FIELD_N_WALK = 9,
+    SPLASH_FIELD_RECTS = 10 /* [n][2] uint32: tile columns tx0 | tx1 << 16, rows ty0 | ty1 << 16 */
+} splash_field;
+splash_status splash_state_copy(const splash_state *st, int32_t field, void *dst, int64_t bytes, void *stream);
+
+/* Photometric loss of the training step: loss = mean|x - y| + lam (1 - mean SSIM)
+ * (the Eq. 7 form; SSIM with an 11x11 Gaussian window, sigma 1.5, zero
+ * padding, C1 = 0.01^2, C2 = 0.03^2). image, target: device [C,H,W].
+ * loss_dev: device float[1] (written). dL_dimage: device [C,H,W] (written;
+ * may be NULL for loss only). Uses workspace of `st`. */
+splash_status splash_loss_l1_ssim(splash_ctx *ctx, splash_state *st, const float *image, const float *target,
+                                  int32_t channels, int32_t height, int32_t width, float lam,
+                                  float *loss_dev, float *dL_dimage, void *stream);
+
+/* One Adam step (Sec. IV-C) over several parameter groups in one launch.
+ * Each group: param, grad, m, v device float[n]; lr; optional lower clamp.
+ * Bias correction uses `step` (>= 1). */
+typedef struct {
+    float *param;
+    const float *grad;
+    float *m;
+    float *v;
+    int64_t n;
+    float lr;
+    float clamp_min;
+    int32_t has_clamp;
+} splash_adam_group;
+#define SPLASH_ADAM_MAX_GROUPS 8
+splash_status splash_adam_step(const splash_adam_group *groups, int32_t n_groups, int32_t step, float beta1,
+                               float beta2, float eps, void *stream);
+
+/* Stable LSD radix sort of (uint32 key, uint32 value) pairs on key bits
+ * [0, key_bits), onesweep form. keys/vals in (device, n) are left unchanged;
+ * keys_out/vals_out (device, n) receive the result. vals_in NULL means
+ * values 0..n-1. Uses workspace of `st`. */
+splash_status splash_sort_pairs_u32(splash_ctx *ctx, splash_state *st, const uint32_t *keys_in,
+                                    const uint32_t *vals_in, uint32_t *keys_out, uint32_t *vals_out,
+                                    int64_t n, int32_t key_bits, void *stream);
+
+/* Stage timing with CUDA events recorded on the caller's stream around each
+ * stage of the calls that take a context (tracing aid; off by default).
+ * splash_profile_enable clears the totals; splash_profile_read waits for the
+ * recorded events and returns per-stage total milliseconds and launch counts
+ * (arrays of SPLASH_STAGE_COUNT entries), then clears them. */
+typedef enum {
+    SPLASH_STAGE_PREPROCESS = 0,
+    SPLASH_STAGE_DEPTH_SORT = 1,
+    SPLASH_STAGE_SCAN = 2,
+    SPLASH_STAGE_EMIT = 3,
+    SPLASH_STAGE_TILE_SORT = 4,
+    SPLASH_STAGE_RANGES = 5,
+    SPLASH_STAGE_BLEND_FWD = 6,
+    SPLASH_STAGE_BLEND_BWD = 7,
+    SPLASH_STAGE_PREPROCESS_BWD = 8,
+    SPLASH_STAGE_MEDIUM_REDUCE = 9,
+    SPLASH_STAGE_LOSS = 10,
+    SPLASH_STAGE_COUNT = 11
+} splash_stage;
+splash_status splash_profile_enable(splash_ctx *ctx, int32_t on);
+splash_status splash_profile_read(splash_ctx *ctx, double *ms, int64_t *counts);
+
+/* Number of kernels this library has launched in this process so far. */
+uint64_t splash_kernel_launches(void);
+
+/* Synchronise `stream` and report any error a kernel recorded since the last check. */
+splash_status splash_sync_status(splash_ctx *ctx, void *stream);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *splash_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPLASH_H */

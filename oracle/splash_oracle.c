@@ -57,7 +57,6 @@
 #define Q_MAX 9.0
 #define DILATE 0.3
 #define JCLAMP 1.3
-#define TIE_REL (1.0 / 262144.0) /* 2^-18 relative: possible FP32 depth tie */
 
 /* per-Gaussian fields written by oracle_project */
 enum {
@@ -378,7 +377,7 @@ typedef struct {
     double Tf;         /* transmittance after the last contributor */
     double margin;     /* smallest relative distance to a discrete decision */
     double gmargin;    /* smallest relative distance to a gradient kink */
-    int tie;           /* two alpha-valid neighbours within TIE_REL in depth */
+    int tie;           /* an FP32 depth sort would swap two alpha-valid neighbours */
 } plist_t;
 
 /* Collect, sort and walk the Gaussians at pixel centre (px, py) with the
@@ -405,7 +404,7 @@ static void pixel_list(const pg_t *P, const int64_t *vis, int64_t nvis, double p
     }
     qsort(s->cand, (size_t)nc, sizeof(cand_t), cand_cmp);
     double T = 1.0, prev_d = -1.0;
-    int64_t m = 0, it = 0;
+    int64_t m = 0, it = 0, prev_id = -1;
     int tie = 0;
     for (int64_t k = 0; k < nc; k++) {
         const cand_t *cd = &s->cand[k];
@@ -416,8 +415,13 @@ static void pixel_list(const pg_t *P, const int64_t *vis, int64_t nvis, double p
         gm = fmin(gm, fabs(araw - A_MAX) / A_MAX);
         mg = fmin(mg, fabs(alpha - A_MIN) / A_MIN);
         if (alpha < A_MIN) continue;
-        if (prev_d >= 0 && fabs(cd->d - prev_d) <= TIE_REL * cd->d) tie = 1;
+        /* An FP32 depth orders two Gaussians like their exact depths unless
+         * both round to the same float, where ties go to the lower index
+         * (rounding is monotonic). Flag the pixel when that index order
+         * disagrees with the exact depth order of two alpha-valid neighbours. */
+        if (prev_id >= 0 && (float)cd->d == (float)prev_d && prev_id > cd->id) tie = 1;
         prev_d = cd->d;
+        prev_id = cd->id;
         const double Tn = T * (1.0 - alpha);
         mg = fmin(mg, fabs(Tn - T_STOP) / T_STOP);
         if (Tn < T_STOP) break;

@@ -1,0 +1,134 @@
+"""ctypes binding of libsplash.so (include/splash.h): struct layouts and
+argument marshalling only; every step of the render runs in the library's
+CUDA kernels. Loading fails loudly when the library cannot be built or
+loaded; there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from . import build as _build
+
+_lib = None
+
+c_float_p = ctypes.POINTER(ctypes.c_float)
+c_u32_p = ctypes.POINTER(ctypes.c_uint32)
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_CAPACITY, ERR_TIMEOUT, ERR_STATE = range(7)
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "CAPACITY", 5: "TIMEOUT", 6: "STATE"}
+
+
+class SplashError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("world_to_cam", ctypes.c_float * 12),
+                ("z_near", ctypes.c_float), ("z_far", ctypes.c_float)]
+
+
+class Gaussians(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("opacity_logits", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("sh_degree", ctypes.c_int32)]
+
+
+class Grads(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("opacity_logits", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("medium", ctypes.c_void_p)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("spin_limit", ctypes.c_int32),
+                ("test_stall_partition", ctypes.c_int32)]
+
+
+class StateInfo(ctypes.Structure):
+    _fields_ = [("n_keys", ctypes.c_int64), ("tiles_x", ctypes.c_int32), ("tiles_y", ctypes.c_int32),
+                ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("n_gaussians", ctypes.c_int64),
+                ("tile_ids", ctypes.c_void_p), ("gauss_ids", ctypes.c_void_p), ("ranges", ctypes.c_void_p),
+                ("depth_keys", ctypes.c_void_p), ("tiles_touched", ctypes.c_void_p), ("records", ctypes.c_void_p),
+                ("final_T", ctypes.c_void_p), ("acc_alpha", ctypes.c_void_p), ("n_last", ctypes.c_void_p),
+                ("n_walk", ctypes.c_void_p)]
+
+
+class AdamGroup(ctypes.Structure):
+    _fields_ = [("param", ctypes.c_void_p), ("grad", ctypes.c_void_p), ("m", ctypes.c_void_p), ("v", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("lr", ctypes.c_float), ("clamp_min", ctypes.c_float),
+                ("has_clamp", ctypes.c_int32)]
+
+
+ADAM_MAX_GROUPS = 8
+
+_SIGS = {
+    "splash_create": [ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_void_p)],
+    "splash_destroy": [ctypes.c_void_p],
+    "splash_state_create": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)],
+    "splash_state_destroy": [ctypes.c_void_p],
+    "splash_render_forward": [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(Gaussians), ctypes.c_void_p,
+                              ctypes.POINTER(Camera), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "splash_render_backward": [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(Gaussians), ctypes.c_void_p,
+                               ctypes.POINTER(Camera), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.POINTER(Grads), ctypes.c_void_p],
+    "splash_state_get_info": [ctypes.c_void_p, ctypes.POINTER(StateInfo)],
+    "splash_loss_l1_ssim": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                            ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p,
+                            ctypes.c_void_p],
+    "splash_adam_step": [ctypes.POINTER(AdamGroup), ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+                         ctypes.c_float, ctypes.c_void_p],
+    "splash_sort_pairs_u32": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p],
+    "splash_sync_status": [ctypes.c_void_p, ctypes.c_void_p],
+    "splash_state_copy": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p],
+    "splash_profile_enable": [ctypes.c_void_p, ctypes.c_int32],
+    "splash_profile_read": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
+}
+
+STAGES = ["preprocess", "depth_sort", "scan", "emit", "tile_sort", "ranges", "blend_fwd", "blend_bwd",
+          "preprocess_bwd", "medium_reduce", "loss"]
+
+FIELDS = {"tile_ids": 0, "gauss_ids": 1, "ranges": 2, "depth_keys": 3, "tiles_touched": 4, "records": 5,
+          "final_T": 6, "acc_alpha": 7, "n_last": 8, "n_walk": 9, "rects": 10}
+
+
+def header_symbols() -> list[str]:
+    """Function names declared in include/splash.h."""
+    with open(os.path.join(_build.INCLUDE, "splash.h")) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^\s*(?:splash_status|const char \*|uint64_t)\s*(splash_\w+)\s*\(", text, re.M)))
+
+
+def lib():
+    """Build (if stale) and load libsplash.so."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.splash_last_error.argtypes = []
+        L.splash_last_error.restype = ctypes.c_char_p
+        L.splash_kernel_launches.argtypes = []
+        L.splash_kernel_launches.restype = ctypes.c_uint64
+        _lib = L
+    return _lib
+
+
+def check(status: int, where: str) -> None:
+    if status != OK:
+        msg = lib().splash_last_error().decode(errors="replace")
+        raise SplashError(status, where, msg)
+
+
+def ptr(t) -> int | None:
+    """Device address of a tensor (None for None)."""
+    if t is None:
+        return None
+    return t.data_ptr()

@@ -1,0 +1,591 @@
+// C ABI of libsplash: contexts, render states (grow-only device
+// workspaces), argument checks and the order of the stages.
+//
+// Forward (one stream, one host synchronisation to read the pair count):
+//   preprocess -> depth sort (N pairs) -> scan of tile counts in depth order
+//   -> [read back K] -> emit K (tile, Gaussian) pairs -> tile sort -> ranges
+//   -> blend.
+// Backward: blend adjoint -> preprocess adjoint -> medium reduction.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace splash;
+
+namespace {
+thread_local std::string g_last_error;
+
+struct Buf {
+    void *p = nullptr;
+    size_t cap = 0;
+    ~Buf() { release(); }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    // grow-only; contents are not preserved
+    bool ensure(size_t bytes)
+    {
+        if (bytes <= cap) return true;
+        release();
+        const size_t want = std::max<size_t>(bytes + bytes / 4, 256);
+        if (cudaMalloc(&p, want) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return false;
+        }
+        cap = want;
+        return true;
+    }
+    template <class T>
+    T *as() const { return static_cast<T *>(p); }
+};
+}  // namespace
+
+void splash_set_error(const std::string &msg) { g_last_error = msg; }
+
+namespace {
+std::atomic<uint64_t> g_launches{0};
+
+// Per-stage CUDA-event timing (tracing aid)
+struct Prof {
+    bool on = false;
+    struct Rec {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<cudaEvent_t> spare;
+    std::vector<Rec> pending;
+    double ms[SPLASH_STAGE_COUNT] = {};
+    int64_t cnt[SPLASH_STAGE_COUNT] = {};
+    cudaEvent_t take()
+    {
+        if (!spare.empty()) {
+            cudaEvent_t e = spare.back();
+            spare.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return e;
+    }
+    ~Prof()
+    {
+        for (auto &r : pending) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        for (auto e : spare) cudaEventDestroy(e);
+    }
+};
+
+// Records a start event on construction and the stop event on destruction.
+struct Stage {
+    Prof &p;
+    int stage;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    Stage(Prof &p_, int stage_, cudaStream_t s_) : p(p_), stage(stage_), s(s_)
+    {
+        if (p.on && (a = p.take())) cudaEventRecord(a, s);
+    }
+    ~Stage()
+    {
+        if (!a) return;
+        cudaEvent_t b = p.take();
+        if (!b) {
+            p.spare.push_back(a);
+            return;
+        }
+        cudaEventRecord(b, s);
+        p.pending.push_back({stage, a, b});
+    }
+};
+}  // namespace
+
+namespace splash {
+void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+}  // namespace splash
+
+struct splash_ctx {
+    splash_options opt;
+    uint32_t *d_status = nullptr;  // kernel-reported error bits
+    Prof prof;
+};
+
+struct splash_state {
+    splash_ctx *ctx = nullptr;
+    // per Gaussian
+    Buf rec, depth_key, tt, rect, dk0, dv0, dk1, dv1, offsets, scan_sums;
+    // per (tile, Gaussian) pair
+    Buf tk0, tv0, tk1, tv1;
+    Buf ranges, sort_scratch;
+    // per pixel
+    Buf fT, aA, zh, nlast, nwalk;
+    // backward
+    Buf gacc, tile_med, block_med;
+    // loss / standalone sort
+    Buf loss_scratch, tmp_k, tmp_v;
+    Buf small;  // [0] = pair count K, [1..] spare
+    uint32_t *h_small = nullptr;  // pinned: K, status
+    // what the last forward produced
+    bool has_forward = false;
+    int64_t n = 0;
+    int W = 0, H = 0;
+    TileGeom tg{};
+    int64_t K = 0;
+    const uint32_t *order = nullptr;    // depth-sorted Gaussian indices
+    const uint32_t *tile_ids = nullptr; // sorted pairs
+    const uint32_t *gauss_ids = nullptr;
+};
+
+namespace {
+
+splash_status fail(splash_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+#define ENSURE(buf, bytes)                                                                       \
+    do {                                                                                         \
+        if (!(buf).ensure(bytes)) return fail(SPLASH_ERR_OOM, "cudaMalloc failed for " #buf);    \
+    } while (0)
+
+bool valid_tile(int tw, int th) { return (tw == 16 && th == 16) || (tw == 8 && th == 32) || (tw == 32 && th == 8); }
+
+CamK make_cam(const splash_camera &c)
+{
+    CamK k{};
+    for (int r = 0; r < 3; r++) {
+        for (int j = 0; j < 3; j++) k.R[3 * r + j] = c.world_to_cam[4 * r + j];
+        k.t[r] = c.world_to_cam[4 * r + 3];
+    }
+    for (int j = 0; j < 3; j++)
+        k.cpos[j] = (float)-((double)k.R[j] * k.t[0] + (double)k.R[3 + j] * k.t[1] + (double)k.R[6 + j] * k.t[2]);
+    k.fx = c.fx;
+    k.fy = c.fy;
+    k.cx = c.cx;
+    k.cy = c.cy;
+    k.limx = (float)(1.3 * 0.5 * c.width / c.fx);
+    k.limy = (float)(1.3 * 0.5 * c.height / c.fy);
+    k.znear = c.z_near;
+    k.zfar = c.z_far;
+    k.W = c.width;
+    k.H = c.height;
+    return k;
+}
+
+splash_status check_camera(const splash_camera *cam)
+{
+    if (!cam) return fail(SPLASH_ERR_INVALID_ARG, "null camera");
+    if (cam->width <= 0 || cam->height <= 0 || cam->width > 32768 || cam->height > 32768)
+        return fail(SPLASH_ERR_INVALID_ARG, "image size must be in 1..32768");
+    if (!(cam->fx > 0.f) || !(cam->fy > 0.f)) return fail(SPLASH_ERR_INVALID_ARG, "focal lengths must be positive");
+    if (!(cam->z_near > 0.f) || !(cam->z_far > cam->z_near))
+        return fail(SPLASH_ERR_INVALID_ARG, "need 0 < z_near < z_far");
+    return SPLASH_OK;
+}
+
+splash_status check_gaussians(const splash_gaussians *g)
+{
+    if (!g) return fail(SPLASH_ERR_INVALID_ARG, "null gaussians");
+    if (g->n < 0 || g->n >= (int64_t)1 << 31) return fail(SPLASH_ERR_INVALID_ARG, "n must be in [0, 2^31)");
+    if (g->sh_degree < 0 || g->sh_degree > 3) return fail(SPLASH_ERR_INVALID_ARG, "sh_degree must be 0..3");
+    if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
+        return fail(SPLASH_ERR_INVALID_ARG, "null gaussian buffer");
+    if (g->n > 0 && (reinterpret_cast<uintptr_t>(g->quats) & 15))
+        return fail(SPLASH_ERR_INVALID_ARG, "quats must be 16-byte aligned");
+    return SPLASH_OK;
+}
+
+int bits_for(int64_t count)
+{
+    int b = 0;
+    while (((int64_t)1 << b) < count) b++;
+    return b;
+}
+
+splash_status read_status(splash_ctx *ctx, splash_state *st, cudaStream_t s, bool with_k)
+{
+    // K (when asked) and the status word in one round trip
+    if (with_k) SPLASH_CUDA_TRY(cudaMemcpyAsync(st->h_small, st->small.as<uint32_t>(), sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    SPLASH_CUDA_TRY(cudaMemcpyAsync(st->h_small + 1, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    SPLASH_CUDA_TRY(cudaStreamSynchronize(s));
+    const uint32_t status = st->h_small[1];
+    if (status) {
+        SPLASH_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), s));
+        if (status & kStatusTimeout) return fail(SPLASH_ERR_TIMEOUT, "a device-side wait gave up (spin limit reached)");
+        if (status & kStatusCapacity) return fail(SPLASH_ERR_CAPACITY, "tile/Gaussian pairs exceeded the workspace");
+    }
+    return SPLASH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *splash_last_error(void) { return g_last_error.c_str(); }
+
+splash_status splash_create(const splash_options *opt, splash_ctx **out)
+{
+    if (!out) return fail(SPLASH_ERR_INVALID_ARG, "null output pointer");
+    *out = nullptr;
+    splash_options o{16, 16, 0, 0};
+    if (opt) o = *opt;
+    if (o.tile_w == 0 && o.tile_h == 0) o.tile_w = o.tile_h = 16;
+    if (!valid_tile(o.tile_w, o.tile_h)) return fail(SPLASH_ERR_INVALID_ARG, "tile shape must be 16x16, 8x32 or 32x8");
+    if (o.spin_limit < 0 || o.test_stall_partition < 0)
+        return fail(SPLASH_ERR_INVALID_ARG, "spin_limit and test_stall_partition must be >= 0");
+    if (o.spin_limit == 0) o.spin_limit = 1 << 22;
+    splash_ctx *c = new splash_ctx();
+    c->opt = o;
+    if (cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess || cudaMemset(c->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
+        const std::string e = cudaGetErrorString(cudaGetLastError());
+        delete c;
+        return fail(SPLASH_ERR_CUDA, "splash_create: " + e);
+    }
+    *out = c;
+    return SPLASH_OK;
+}
+
+splash_status splash_destroy(splash_ctx *ctx)
+{
+    if (!ctx) return SPLASH_OK;
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    delete ctx;
+    return SPLASH_OK;
+}
+
+splash_status splash_state_create(splash_ctx *ctx, splash_state **out)
+{
+    if (!ctx || !out) return fail(SPLASH_ERR_INVALID_ARG, "null argument");
+    splash_state *s = new splash_state();
+    s->ctx = ctx;
+    if (cudaMallocHost(&s->h_small, 16 * sizeof(uint32_t)) != cudaSuccess || !s->small.ensure(64)) {
+        cudaGetLastError();
+        delete s;
+        return fail(SPLASH_ERR_OOM, "splash_state_create: allocation failed");
+    }
+    *out = s;
+    return SPLASH_OK;
+}
+
+splash_status splash_state_destroy(splash_state *st)
+{
+    if (!st) return SPLASH_OK;
+    if (st->h_small) cudaFreeHost(st->h_small);
+    delete st;
+    return SPLASH_OK;
+}
+
+splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const splash_gaussians *g,
+                                    const float *medium, const splash_camera *cam, float *image, float *depth,
+                                    float *depth01, void *stream)
+{
+    if (!ctx || !st || st->ctx != ctx) return fail(SPLASH_ERR_INVALID_ARG, "bad context or state");
+    splash_status rc;
+    if ((rc = check_gaussians(g)) != SPLASH_OK) return rc;
+    if ((rc = check_camera(cam)) != SPLASH_OK) return rc;
+    if (!medium || !image) return fail(SPLASH_ERR_INVALID_ARG, "null medium or image");
+    cudaStream_t s = (cudaStream_t)stream;
+    st->has_forward = false;
+
+    const int64_t n = g->n;
+    TileGeom tg{ctx->opt.tile_w, ctx->opt.tile_h, 0, 0};
+    tg.tx = (cam->width + tg.tw - 1) / tg.tw;
+    tg.ty = (cam->height + tg.th - 1) / tg.th;
+    const int ntiles = tg.tx * tg.ty;
+    const int64_t npix = (int64_t)cam->width * cam->height;
+    const int64_t nn = std::max<int64_t>(n, 1);
+    ENSURE(st->rec, sizeof(Rec) * nn);
+    ENSURE(st->depth_key, 4 * nn);
+    ENSURE(st->tt, 4 * nn);
+    ENSURE(st->rect, 8 * nn);
+    ENSURE(st->dk0, 4 * nn);
+    ENSURE(st->dv0, 4 * nn);
+    ENSURE(st->dk1, 4 * nn);
+    ENSURE(st->dv1, 4 * nn);
+    ENSURE(st->offsets, 4 * nn);
+    ENSURE(st->scan_sums, 4 * (nn / 4096 + 2));
+    ENSURE(st->ranges, 8 * (size_t)ntiles);
+    ENSURE(st->fT, 4 * npix);
+    ENSURE(st->aA, 4 * npix);
+    ENSURE(st->zh, 4 * npix);
+    ENSURE(st->nlast, 4 * npix);
+    ENSURE(st->nwalk, 4 * npix);
+    ENSURE(st->sort_scratch, sort_scratch_bytes(nn));
+    SortScratch ss;
+    sort_scratch_carve(st->sort_scratch.p, nn, &ss);
+
+    const CamK ck = make_cam(*cam);
+    uint32_t *dK = st->small.as<uint32_t>();
+    {
+        Stage t(ctx->prof, SPLASH_STAGE_PREPROCESS, s);
+        launch_preprocess_fwd(n, *g, medium, ck, tg, st->rec.as<Rec>(), st->depth_key.as<uint32_t>(),
+                              st->tt.as<uint32_t>(), st->rect.as<uint2>(), s);
+    }
+    const uint32_t *order = nullptr;
+    if (n > 0) {
+        Stage t(ctx->prof, SPLASH_STAGE_DEPTH_SORT, s);
+        const int which = sort_pairs(st->depth_key.as<uint32_t>(), nullptr, st->dk0.as<uint32_t>(), st->dv0.as<uint32_t>(),
+                                     st->dk1.as<uint32_t>(), st->dv1.as<uint32_t>(), n, nullptr, 32, ss, ctx->d_status,
+                                     ctx->opt.spin_limit, ctx->opt.test_stall_partition, s);
+        order = which ? st->dv1.as<uint32_t>() : st->dv0.as<uint32_t>();
+    }
+    {
+        Stage t(ctx->prof, SPLASH_STAGE_SCAN, s);
+        launch_count_scan(n, order, st->tt.as<uint32_t>(), st->offsets.as<uint32_t>(), st->scan_sums.as<uint32_t>(), dK, s);
+    }
+    SPLASH_CUDA_TRY(cudaGetLastError());
+    if ((rc = read_status(ctx, st, s, true)) != SPLASH_OK) return rc;
+    const int64_t K = st->h_small[0];
+    if (K >= ((int64_t)1 << 30)) return fail(SPLASH_ERR_CAPACITY, "more than 2^30 tile/Gaussian pairs");
+
+    const int64_t kk = std::max<int64_t>(K, 1);
+    ENSURE(st->tk0, 4 * kk);
+    ENSURE(st->tv0, 4 * kk);
+    ENSURE(st->tk1, 4 * kk);
+    ENSURE(st->tv1, 4 * kk);
+    if (kk > nn) {
+        ENSURE(st->sort_scratch, sort_scratch_bytes(kk));
+    }
+    sort_scratch_carve(st->sort_scratch.p, std::max(nn, kk), &ss);
+    // emit into buffer pair 1; the tile sort reads it once, then ping-pongs 0 <-> 1
+    {
+        Stage t(ctx->prof, SPLASH_STAGE_EMIT, s);
+        launch_emit(n, order, st->offsets.as<uint32_t>(), st->tt.as<uint32_t>(), st->rect.as<uint2>(), tg,
+                    st->tk1.as<uint32_t>(), st->tv1.as<uint32_t>(), (uint64_t)K, ctx->d_status, s);
+    }
+    const uint32_t *tids = st->tk1.as<uint32_t>(), *gids = st->tv1.as<uint32_t>();
+    if (K > 0) {
+        Stage t(ctx->prof, SPLASH_STAGE_TILE_SORT, s);
+        const int which = sort_pairs(st->tk1.as<uint32_t>(), st->tv1.as<uint32_t>(), st->tk0.as<uint32_t>(), st->tv0.as<uint32_t>(),
+                                     st->tk1.as<uint32_t>(), st->tv1.as<uint32_t>(), K, nullptr, bits_for(ntiles), ss,
+                                     ctx->d_status, ctx->opt.spin_limit, ctx->opt.test_stall_partition, s);
+        tids = which ? st->tk1.as<uint32_t>() : st->tk0.as<uint32_t>();
+        gids = which ? st->tv1.as<uint32_t>() : st->tv0.as<uint32_t>();
+    }
+    {
+        Stage t(ctx->prof, SPLASH_STAGE_RANGES, s);
+        launch_ranges(K, nullptr, tids, st->ranges.as<uint2>(), ntiles, s);
+    }
+    {
+        Stage t(ctx->prof, SPLASH_STAGE_BLEND_FWD, s);
+        launch_blend_fwd(tg, ck, st->ranges.as<uint2>(), gids, st->rec.as<Rec>(), medium, image, depth, depth01,
+                         st->fT.as<float>(), st->aA.as<float>(), st->zh.as<float>(), st->nlast.as<uint32_t>(),
+                         st->nwalk.as<uint32_t>(), s);
+    }
+    SPLASH_CUDA_TRY(cudaGetLastError());
+
+    st->has_forward = true;
+    st->n = n;
+    st->W = cam->width;
+    st->H = cam->height;
+    st->tg = tg;
+    st->K = K;
+    st->order = order;
+    st->tile_ids = tids;
+    st->gauss_ids = gids;
+    return SPLASH_OK;
+}
+
+splash_status splash_render_backward(splash_ctx *ctx, splash_state *st, const splash_gaussians *g,
+                                     const float *medium, const splash_camera *cam, const float *dL_dimage,
+                                     const float *dL_ddepth, const float *dL_ddepth01, const splash_grads *grads,
+                                     void *stream)
+{
+    if (!ctx || !st || st->ctx != ctx) return fail(SPLASH_ERR_INVALID_ARG, "bad context or state");
+    splash_status rc;
+    if ((rc = check_gaussians(g)) != SPLASH_OK) return rc;
+    if ((rc = check_camera(cam)) != SPLASH_OK) return rc;
+    if (!medium || !dL_dimage || !grads) return fail(SPLASH_ERR_INVALID_ARG, "null medium, dL_dimage or grads");
+    if (!st->has_forward || st->n != g->n || st->W != cam->width || st->H != cam->height)
+        return fail(SPLASH_ERR_STATE, "backward does not match the last forward on this state");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = g->n;
+    const int ntiles = st->tg.tx * st->tg.ty;
+    const int nblocks = preprocess_bwd_blocks(std::max<int64_t>(n, 1));
+    ENSURE(st->gacc, sizeof(GAcc) * std::max<int64_t>(n, 1));
+    ENSURE(st->tile_med, 4 * 6 * (size_t)ntiles);
+    ENSURE(st->block_med, 4 * 9 * (size_t)nblocks);
+    SPLASH_CUDA_TRY(cudaMemsetAsync(st->gacc.p, 0, sizeof(GAcc) * (size_t)n, s));
+    SPLASH_CUDA_TRY(cudaMemsetAsync(st->block_med.p, 0, 4 * 9 * (size_t)nblocks, s));
+    const CamK ck = make_cam(*cam);
+    {
+        Stage t(ctx->prof, SPLASH_STAGE_BLEND_BWD, s);
+        launch_blend_bwd(st->tg, ck, st->ranges.as<uint2>(), st->gauss_ids, st->rec.as<Rec>(), medium, st->fT.as<float>(),
+                         st->aA.as<float>(), st->zh.as<float>(), st->nlast.as<uint32_t>(), dL_dimage, dL_ddepth,
+                         dL_ddepth01, st->gacc.as<GAcc>(), st->tile_med.as<float>(), s);
+    }
+    int nb = 0;
+    {
+        Stage t(ctx->prof, SPLASH_STAGE_PREPROCESS_BWD, s);
+        launch_preprocess_bwd(n, *g, medium, ck, st->gacc.as<GAcc>(), st->depth_key.as<uint32_t>(), *grads,
+                              st->block_med.as<float>(), &nb, s);
+    }
+    if (grads->medium) {
+        Stage t(ctx->prof, SPLASH_STAGE_MEDIUM_REDUCE, s);
+        launch_medium_reduce(st->tile_med.as<float>(), ntiles, st->block_med.as<float>(), nb, grads->medium, s);
+    }
+    SPLASH_CUDA_TRY(cudaGetLastError());
+    return SPLASH_OK;
+}
+
+splash_status splash_state_get_info(const splash_state *st, splash_state_info *out)
+{
+    if (!st || !out) return fail(SPLASH_ERR_INVALID_ARG, "null argument");
+    if (!st->has_forward) return fail(SPLASH_ERR_STATE, "no forward on this state");
+    out->n_keys = st->K;
+    out->tiles_x = st->tg.tx;
+    out->tiles_y = st->tg.ty;
+    out->tile_w = st->tg.tw;
+    out->tile_h = st->tg.th;
+    out->n_gaussians = st->n;
+    out->tile_ids = st->tile_ids;
+    out->gauss_ids = st->gauss_ids;
+    out->ranges = st->ranges.as<uint32_t>();
+    out->depth_keys = st->depth_key.as<uint32_t>();
+    out->tiles_touched = st->tt.as<uint32_t>();
+    out->records = st->rec.as<float>();
+    out->final_T = st->fT.as<float>();
+    out->acc_alpha = st->aA.as<float>();
+    out->n_last = st->nlast.as<uint32_t>();
+    out->n_walk = st->nwalk.as<uint32_t>();
+    return SPLASH_OK;
+}
+
+splash_status splash_state_copy(const splash_state *st, int32_t field, void *dst, int64_t bytes, void *stream)
+{
+    if (!st || !dst) return fail(SPLASH_ERR_INVALID_ARG, "null argument");
+    if (!st->has_forward) return fail(SPLASH_ERR_STATE, "no forward on this state");
+    const int64_t npix = (int64_t)st->W * st->H, ntiles = (int64_t)st->tg.tx * st->tg.ty;
+    const void *src = nullptr;
+    int64_t size = 0;
+    switch (field) {
+    case SPLASH_FIELD_TILE_IDS: src = st->tile_ids; size = 4 * st->K; break;
+    case SPLASH_FIELD_GAUSS_IDS: src = st->gauss_ids; size = 4 * st->K; break;
+    case SPLASH_FIELD_RANGES: src = st->ranges.p; size = 8 * ntiles; break;
+    case SPLASH_FIELD_DEPTH_KEYS: src = st->depth_key.p; size = 4 * st->n; break;
+    case SPLASH_FIELD_TILES_TOUCHED: src = st->tt.p; size = 4 * st->n; break;
+    case SPLASH_FIELD_RECORDS: src = st->rec.p; size = (int64_t)sizeof(Rec) * st->n; break;
+    case SPLASH_FIELD_FINAL_T: src = st->fT.p; size = 4 * npix; break;
+    case SPLASH_FIELD_ACC_ALPHA: src = st->aA.p; size = 4 * npix; break;
+    case SPLASH_FIELD_N_LAST: src = st->nlast.p; size = 4 * npix; break;
+    case SPLASH_FIELD_N_WALK: src = st->nwalk.p; size = 4 * npix; break;
+    case SPLASH_FIELD_RECTS: src = st->rect.p; size = 8 * st->n; break;
+    default: return fail(SPLASH_ERR_INVALID_ARG, "unknown field");
+    }
+    if (bytes != size) return fail(SPLASH_ERR_INVALID_ARG, "byte count does not match the field's size");
+    if (size > 0) SPLASH_CUDA_TRY(cudaMemcpyAsync(dst, src, (size_t)size, cudaMemcpyDefault, (cudaStream_t)stream));
+    return SPLASH_OK;
+}
+
+splash_status splash_loss_l1_ssim(splash_ctx *ctx, splash_state *st, const float *image, const float *target,
+                                  int32_t channels, int32_t height, int32_t width, float lam, float *loss_dev,
+                                  float *dL_dimage, void *stream)
+{
+    if (!ctx || !st || st->ctx != ctx) return fail(SPLASH_ERR_INVALID_ARG, "bad context or state");
+    if (!image || !target || !loss_dev) return fail(SPLASH_ERR_INVALID_ARG, "null image, target or loss");
+    if (channels <= 0 || height <= 0 || width <= 0) return fail(SPLASH_ERR_INVALID_ARG, "bad image shape");
+    ENSURE(st->loss_scratch, 4 * ssim_scratch_floats(channels, height, width));
+    {
+        Stage t(ctx->prof, SPLASH_STAGE_LOSS, (cudaStream_t)stream);
+        launch_ssim_loss(image, target, channels, height, width, lam, loss_dev, dL_dimage,
+                         st->loss_scratch.as<float>(), (cudaStream_t)stream);
+    }
+    SPLASH_CUDA_TRY(cudaGetLastError());
+    return SPLASH_OK;
+}
+
+splash_status splash_sort_pairs_u32(splash_ctx *ctx, splash_state *st, const uint32_t *keys_in, const uint32_t *vals_in,
+                                    uint32_t *keys_out, uint32_t *vals_out, int64_t n, int32_t key_bits, void *stream)
+{
+    if (!ctx || !st || st->ctx != ctx) return fail(SPLASH_ERR_INVALID_ARG, "bad context or state");
+    if (n < 0 || n >= ((int64_t)1 << 30)) return fail(SPLASH_ERR_INVALID_ARG, "n must be in [0, 2^30)");
+    if (key_bits < 0 || key_bits > 32) return fail(SPLASH_ERR_INVALID_ARG, "key_bits must be in 0..32");
+    if (n == 0) return SPLASH_OK;
+    if (!keys_in || !keys_out || !vals_out) return fail(SPLASH_ERR_INVALID_ARG, "null buffer");
+    if (reinterpret_cast<uintptr_t>(keys_in) & 15) return fail(SPLASH_ERR_INVALID_ARG, "keys_in must be 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    ENSURE(st->tmp_k, 4 * (size_t)n);
+    ENSURE(st->tmp_v, 4 * (size_t)n);
+    ENSURE(st->sort_scratch, sort_scratch_bytes(n));
+    SortScratch ss;
+    sort_scratch_carve(st->sort_scratch.p, n, &ss);
+    const int which = sort_pairs(keys_in, vals_in, keys_out, vals_out, st->tmp_k.as<uint32_t>(), st->tmp_v.as<uint32_t>(),
+                                 n, nullptr, key_bits, ss, ctx->d_status, ctx->opt.spin_limit, ctx->opt.test_stall_partition, s);
+    if (which) {
+        SPLASH_CUDA_TRY(cudaMemcpyAsync(keys_out, st->tmp_k.p, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s));
+        SPLASH_CUDA_TRY(cudaMemcpyAsync(vals_out, st->tmp_v.p, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    }
+    SPLASH_CUDA_TRY(cudaGetLastError());
+    // the forward state's pair buffers are untouched, but the scratch is shared
+    return SPLASH_OK;
+}
+
+splash_status splash_profile_enable(splash_ctx *ctx, int32_t on)
+{
+    if (!ctx) return fail(SPLASH_ERR_INVALID_ARG, "null context");
+    double ms[SPLASH_STAGE_COUNT];
+    int64_t cnt[SPLASH_STAGE_COUNT];
+    splash_status rc = splash_profile_read(ctx, ms, cnt);  // drain and clear
+    ctx->prof.on = on != 0;
+    return rc;
+}
+
+splash_status splash_profile_read(splash_ctx *ctx, double *ms, int64_t *counts)
+{
+    if (!ctx || !ms || !counts) return fail(SPLASH_ERR_INVALID_ARG, "null argument");
+    Prof &p = ctx->prof;
+    splash_status rc = SPLASH_OK;
+    for (auto &r : p.pending) {
+        float t = 0.f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) {
+            rc = fail(SPLASH_ERR_CUDA, std::string("profile: ") + cudaGetErrorString(cudaGetLastError()));
+        } else {
+            p.ms[r.stage] += t;
+            p.cnt[r.stage] += 1;
+        }
+        p.spare.push_back(r.a);
+        p.spare.push_back(r.b);
+    }
+    p.pending.clear();
+    for (int i = 0; i < SPLASH_STAGE_COUNT; i++) {
+        ms[i] = p.ms[i];
+        counts[i] = p.cnt[i];
+        p.ms[i] = 0.0;
+        p.cnt[i] = 0;
+    }
+    return rc;
+}
+
+uint64_t splash_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+splash_status splash_sync_status(splash_ctx *ctx, void *stream)
+{
+    if (!ctx) return fail(SPLASH_ERR_INVALID_ARG, "null context");
+    cudaStream_t s = (cudaStream_t)stream;
+    SPLASH_CUDA_TRY(cudaStreamSynchronize(s));
+    uint32_t status = 0;
+    SPLASH_CUDA_TRY(cudaMemcpy(&status, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    if (status) {
+        SPLASH_CUDA_TRY(cudaMemset(ctx->d_status, 0, sizeof(uint32_t)));
+        if (status & kStatusTimeout) return fail(SPLASH_ERR_TIMEOUT, "a device-side wait gave up (spin limit reached)");
+        if (status & kStatusCapacity) return fail(SPLASH_ERR_CAPACITY, "tile/Gaussian pairs exceeded the workspace");
+    }
+    return SPLASH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,483 @@
+// Per-tile front-to-back blending with the water model (forward) and its
+// back-to-front adjoint (backward).
+//
+// Passages: Eq. 1 (alpha compositing over depth-sorted Gaussians), Eq. 2
+// (alpha = sigmoid(o) e^{-q/2}), Sec. III-A (tiles, tile-parallel rendering),
+// Eq. 3-5 (water), Eq. 6 (expected depth), Sec. IV-D (logistic depth map).
+//
+// Water model per pixel, Gaussians i = 1..m front to back with transmittance
+// T_i in front of each, d_0 = 0 and the last segment ending at z_far:
+//   C = sum_i c_i e^{-bD d_i} a_i T_i + B sum_{i=1}^{m+1} T_i (e^{-bB d_{i-1}} - e^{-bB d_i})
+// Summation by parts turns the water sum into per-Gaussian terms:
+//   C = sum_i a_i T_i ct_i + B (1 - T_final e^{-bB z_far}),  ct_i = c_i e^{-bD d_i} - B e^{-bB d_i}
+// so the inner loop is plain compositing of the effective colour ct (made
+// once per Gaussian in the preprocess) and the water costs one epilogue.
+//
+// Work decomposition: one CTA per tile, two pixels of one row per thread
+// (they share the dy terms). Gaussians are staged in shared memory in
+// batches of one per thread; the tile-local centre is formed once per
+// (tile, Gaussian) from the doubled-precision record. A warp skips a batch
+// once all its pixels are done; the CTA stops when all are.
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+
+namespace splash {
+namespace {
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// qs = A dx^2 + B dx dy + C dy^2 with the dy terms precomputed; used by both
+// passes so that they take identical decisions
+__device__ __forceinline__ float quad(float dx, float A, float Bdy, float Cdy2) { return fmaf(dx, fmaf(A, dx, Bdy), Cdy2); }
+
+template <int TW, int TH>
+struct Tile {
+    static constexpr int NT = TW * TH / 2;  // threads per CTA
+    static constexpr int HW = TW / 2;       // second pixel of a thread is HW columns right
+};
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW *TH / 2) k_blend_fwd(TileGeom tg, CamK cam, const uint2 *__restrict__ ranges,
+                                                         const uint32_t *__restrict__ gauss_ids, const Rec *__restrict__ rec,
+                                                         const float *__restrict__ medium, float *__restrict__ image,
+                                                         float *__restrict__ depth, float *__restrict__ depth01,
+                                                         float *__restrict__ final_T, float *__restrict__ acc_alpha,
+                                                         float *__restrict__ zhat, uint32_t *__restrict__ n_last,
+                                                         uint32_t *__restrict__ n_walk)
+{
+    constexpr int NT = Tile<TW, TH>::NT, HW = Tile<TW, TH>::HW;
+    __shared__ float4 s0[NT];  // {x_loc, y_loc, A, B}
+    __shared__ float4 s1[NT];  // {C, lo, ct_r, ct_g}
+    __shared__ float2 s2[NT];  // {ct_b, d}
+    const int tile = blockIdx.x;
+    const int tyi = tile / tg.tx, txi = tile - tyi * tg.tx;
+    const int x0 = txi * TW, y0 = tyi * TH;
+    const int tid = threadIdx.x;
+    const int row = tid / HW, col = tid - row * HW;
+    const float pyl = (float)row + 0.5f;
+    const float pxl0 = (float)col + 0.5f, pxl1 = (float)(col + HW) + 0.5f;
+    const int gy = y0 + row, gx0 = x0 + col, gx1 = x0 + col + HW;
+    const bool in0 = gy < cam.H && gx0 < cam.W, in1 = gy < cam.H && gx1 < cam.W;
+    const uint2 rg = ranges[tile];
+    const int n = (int)(rg.y - rg.x);
+
+    float T0 = 1.f, T1 = 1.f;
+    float c00 = 0.f, c01 = 0.f, c02 = 0.f, c10 = 0.f, c11 = 0.f, c12 = 0.f;
+    float D0 = 0.f, D1 = 0.f, A0 = 0.f, A1 = 0.f;
+    int last0 = 0, last1 = 0, walk0 = n, walk1 = n;
+    bool done0 = !in0, done1 = !in1;
+    if (done0) walk0 = 0;
+    if (done1) walk1 = 0;
+
+    for (int b0 = 0; b0 < n; b0 += NT) {
+        if (__syncthreads_count(!(done0 && done1)) == 0) break;
+        const int j = b0 + tid;
+        if (j < n) {
+            const uint32_t gid = gauss_ids[rg.x + j];
+            const Rec r = rec[gid];
+            const float xl = (r.r0.x - (float)x0) + r.r0.z;
+            const float yl = (r.r0.y - (float)y0) + r.r0.w;
+            s0[tid] = make_float4(xl, yl, r.r1.x, r.r1.y);
+            s1[tid] = make_float4(r.r1.z, r.r1.w, r.r2.y, r.r2.z);
+            s2[tid] = make_float2(r.r2.w, r.r2.x);
+        }
+        __syncthreads();
+        const int nb = min(NT, n - b0);
+        if (!__any_sync(0xffffffffu, !(done0 && done1))) continue;
+        for (int k = 0; k < nb; k++) {
+            const float4 a = s0[k];
+            const float4 c = s1[k];
+            const float dy = pyl - a.y;
+            const float Bdy = a.w * dy;
+            const float Cdy2 = c.x * dy * dy;
+            if (!done0) {
+                const float dx = pxl0 - a.x;
+                const float qs = quad(dx, a.z, Bdy, Cdy2);
+                if (qs >= kQsMin) {
+                    const float alpha = fminf(kAlphaMax, ex2_approx(qs + c.y));
+                    if (alpha >= kAlphaMin) {
+                        const float tn = fmaf(-alpha, T0, T0);
+                        if (tn < kTStop) {
+                            done0 = true;
+                            walk0 = b0 + k + 1;
+                        } else {
+                            const float w = alpha * T0;
+                            const float2 e = s2[k];
+                            c00 = fmaf(w, c.z, c00);
+                            c01 = fmaf(w, c.w, c01);
+                            c02 = fmaf(w, e.x, c02);
+                            D0 = fmaf(w, e.y, D0);
+                            A0 += w;
+                            T0 = tn;
+                            last0 = b0 + k + 1;
+                        }
+                    }
+                }
+            }
+            if (!done1) {
+                const float dx = pxl1 - a.x;
+                const float qs = quad(dx, a.z, Bdy, Cdy2);
+                if (qs >= kQsMin) {
+                    const float alpha = fminf(kAlphaMax, ex2_approx(qs + c.y));
+                    if (alpha >= kAlphaMin) {
+                        const float tn = fmaf(-alpha, T1, T1);
+                        if (tn < kTStop) {
+                            done1 = true;
+                            walk1 = b0 + k + 1;
+                        } else {
+                            const float w = alpha * T1;
+                            const float2 e = s2[k];
+                            c10 = fmaf(w, c.z, c10);
+                            c11 = fmaf(w, c.w, c11);
+                            c12 = fmaf(w, e.x, c12);
+                            D1 = fmaf(w, e.y, D1);
+                            A1 += w;
+                            T1 = tn;
+                            last1 = b0 + k + 1;
+                        }
+                    }
+                }
+            }
+        }
+    }
+
+    // epilogue: water behind the last Gaussian, depth, forward state
+    const float zfar = cam.zfar;
+    float binf[3], bfar[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        binf[ch] = __ldg(medium + 6 + ch);
+        bfar[ch] = expf(-__ldg(medium + 3 + ch) * zfar);
+    }
+    const int HWimg = cam.W * cam.H;
+    if (in0) {
+        const int p = gy * cam.W + gx0;
+        image[p] = c00 + binf[0] * (1.f - T0 * bfar[0]);
+        image[HWimg + p] = c01 + binf[1] * (1.f - T0 * bfar[1]);
+        image[2 * HWimg + p] = c02 + binf[2] * (1.f - T0 * bfar[2]);
+        const float z = A0 > 0.f ? D0 / A0 : zfar;
+        if (depth) depth[p] = z;
+        if (depth01) depth01[p] = 2.f / (1.f + expf(-0.1f * z)) - 1.f;
+        final_T[p] = T0;
+        acc_alpha[p] = A0;
+        zhat[p] = z;
+        n_last[p] = (uint32_t)last0;
+        n_walk[p] = (uint32_t)walk0;
+    }
+    if (in1) {
+        const int p = gy * cam.W + gx1;
+        image[p] = c10 + binf[0] * (1.f - T1 * bfar[0]);
+        image[HWimg + p] = c11 + binf[1] * (1.f - T1 * bfar[1]);
+        image[2 * HWimg + p] = c12 + binf[2] * (1.f - T1 * bfar[2]);
+        const float z = A1 > 0.f ? D1 / A1 : zfar;
+        if (depth) depth[p] = z;
+        if (depth01) depth01[p] = 2.f / (1.f + expf(-0.1f * z)) - 1.f;
+        final_T[p] = T1;
+        acc_alpha[p] = A1;
+        zhat[p] = z;
+        n_last[p] = (uint32_t)last1;
+        n_walk[p] = (uint32_t)walk1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Backward.
+
+// Per-pixel state of the back-to-front walk.
+struct PixB {
+    float T;      // transmittance behind the current Gaussian (starts at T_final)
+    float S;      // sum over Gaussians behind: w * (G.ct + gD d + gA), plus the water term
+    float G0, G1, G2, gD, gA;
+    int last;
+};
+
+// One warp-wide sum of 10 values by recursive halving: after five exchange
+// steps lane L holds the warp total of field kLaneField[L] (12 shuffles
+// instead of 50 for ten separate butterflies).
+template <int C>
+__device__ __forceinline__ void rs_step(float *v, int m, bool hi)
+{
+    constexpr int H = (C + 1) / 2;
+    float out[H];
+#pragma unroll
+    for (int i = 0; i < H; i++) {
+        const float upper = (H + i < C) ? v[H + i] : 0.f;
+        const float keep = hi ? upper : v[i];
+        const float send = hi ? v[i] : upper;
+        out[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+    }
+#pragma unroll
+    for (int i = 0; i < H; i++) v[i] = out[i];
+}
+
+__device__ __forceinline__ float warp_reduce10(float *v, int lane)
+{
+    rs_step<10>(v, 16, lane & 16);
+    rs_step<5>(v, 8, lane & 8);
+    rs_step<3>(v, 4, lane & 4);
+    rs_step<2>(v, 2, lane & 2);
+    rs_step<1>(v, 1, lane & 1);
+    return v[0];
+}
+
+// which of the ten fields lane `lane` holds after warp_reduce10 (-1: none)
+__device__ __forceinline__ int reduce10_field(int lane)
+{
+    int base = 0, nreal = 10, c = 10;
+    const int masks[5] = {16, 8, 4, 2, 1};
+#pragma unroll
+    for (int s = 0; s < 5; s++) {
+        const int h = (c + 1) / 2;
+        if (lane & masks[s]) {
+            base += h;
+            nreal = max(0, nreal - h);
+        } else {
+            nreal = min(nreal, h);
+        }
+        c = h;
+    }
+    return nreal > 0 ? base : -1;
+}
+
+// adjoint of one pixel at one Gaussian; returns false if it does not contribute
+__device__ __forceinline__ bool pix_grad(PixB &p, int j, float dx, float dy, float A, float B, float C, float Bdy,
+                                         float Cdy2, float lo, float ctr, float ctg, float ctb, float d, float *acc)
+{
+    if (j >= p.last) return false;
+    const float qs = quad(dx, A, Bdy, Cdy2);
+    if (qs < kQsMin) return false;
+    const float araw = ex2_approx(qs + lo);
+    const float alpha = fminf(kAlphaMax, araw);
+    if (alpha < kAlphaMin) return false;
+    const float inv = __frcp_rn(1.f - alpha);
+    const float Tj = p.T * inv;  // transmittance in front of this Gaussian
+    const float w = alpha * Tj;
+    const float u = fmaf(p.G0, ctr, fmaf(p.G1, ctg, fmaf(p.G2, ctb, fmaf(p.gD, d, p.gA))));
+    // dL/dalpha = T_j u - S / (1 - alpha)
+    const float galpha = fmaf(Tj, u, -p.S * inv);
+    const float gqs = araw < kAlphaMax ? galpha * alpha * kLn2 : 0.f;
+    acc[0] += gqs * -fmaf(2.f * A, dx, B * dy);
+    acc[1] += gqs * -fmaf(B, dx, 2.f * C * dy);
+    acc[2] += gqs * dx * dx;
+    acc[3] += gqs * dx * dy;
+    acc[4] += gqs * dy * dy;
+    acc[5] += gqs;
+    acc[6] += p.gD * w;
+    acc[7] += p.G0 * w;
+    acc[8] += p.G1 * w;
+    acc[9] += p.G2 * w;
+    p.S = fmaf(w, u, p.S);
+    p.T = Tj;
+    return true;
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW *TH / 2) k_blend_bwd(TileGeom tg, CamK cam, const uint2 *__restrict__ ranges,
+                                                         const uint32_t *__restrict__ gauss_ids, const Rec *__restrict__ rec,
+                                                         const float *__restrict__ medium, const float *__restrict__ final_T,
+                                                         const float *__restrict__ acc_alpha, const float *__restrict__ zhat,
+                                                         const uint32_t *__restrict__ n_last,
+                                                         const float *__restrict__ dL_dimage,
+                                                         const float *__restrict__ dL_ddepth,
+                                                         const float *__restrict__ dL_ddepth01, GAcc *__restrict__ gacc,
+                                                         float *__restrict__ tile_medium)
+{
+    constexpr int NT = Tile<TW, TH>::NT, HW = Tile<TW, TH>::HW;
+    constexpr int NW = NT / 32;
+    __shared__ float4 s0[NT];
+    __shared__ float4 s1[NT];
+    __shared__ float2 s2[NT];
+    __shared__ uint32_t s_id[NT];
+    __shared__ float s_g[10][NT];
+    __shared__ float s_med[NW][6];
+    __shared__ int s_maxlast;
+
+    const int tile = blockIdx.x;
+    const int tyi = tile / tg.tx, txi = tile - tyi * tg.tx;
+    const int x0 = txi * TW, y0 = tyi * TH;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int row = tid / HW, col = tid - row * HW;
+    const float pyl = (float)row + 0.5f;
+    const float pxl0 = (float)col + 0.5f, pxl1 = (float)(col + HW) + 0.5f;
+    const int gy = y0 + row, gx0 = x0 + col, gx1 = x0 + col + HW;
+    const bool in0 = gy < cam.H && gx0 < cam.W, in1 = gy < cam.H && gx1 < cam.W;
+    const uint2 rg = ranges[tile];
+    const int HWimg = cam.W * cam.H;
+    const float zfar = cam.zfar;
+    float binf[3], bfar[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        binf[ch] = __ldg(medium + 6 + ch);
+        bfar[ch] = expf(-__ldg(medium + 3 + ch) * zfar);
+    }
+    if (tid == 0) s_maxlast = 0;
+
+    // per-pixel set-up; medium terms that do not go through any Gaussian:
+    //   dC/dB_inf = 1 - T_f b_far, dC/dbeta_B = B_inf T_f z_far b_far
+    float mB[3] = {0.f, 0.f, 0.f}, mBB[3] = {0.f, 0.f, 0.f};
+    PixB P[2];
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+        const bool in = q ? in1 : in0;
+        PixB &p = P[q];
+        p.T = 1.f; p.S = 0.f; p.G0 = p.G1 = p.G2 = p.gD = p.gA = 0.f; p.last = 0;
+        if (!in) continue;
+        const int pix = gy * cam.W + (q ? gx1 : gx0);
+        p.T = final_T[pix];
+        p.last = (int)n_last[pix];
+        p.G0 = dL_dimage[pix];
+        p.G1 = dL_dimage[HWimg + pix];
+        p.G2 = dL_dimage[2 * HWimg + pix];
+        const float A = acc_alpha[pix], z = zhat[pix];
+        float gz = dL_ddepth ? dL_ddepth[pix] : 0.f;
+        if (dL_ddepth01) {
+            const float e = expf(-0.1f * z);
+            gz += dL_ddepth01[pix] * 0.2f * e / ((1.f + e) * (1.f + e));
+        }
+        if (A > 0.f) {
+            p.gD = gz / A;       // z = D / A
+            p.gA = -gz * z / A;
+        }
+        const float Gc[3] = {p.G0, p.G1, p.G2};
+        float S = 0.f;
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) {
+            mB[ch] += Gc[ch] * (1.f - p.T * bfar[ch]);
+            mBB[ch] += Gc[ch] * binf[ch] * p.T * zfar * bfar[ch];
+            S -= Gc[ch] * binf[ch] * bfar[ch] * p.T;  // the water behind the last Gaussian
+        }
+        p.S = S;
+    }
+    __syncthreads();
+    atomicMax(&s_maxlast, max(P[0].last, P[1].last));
+    const int my_field = reduce10_field(lane);
+    __syncthreads();
+    const int maxlast = s_maxlast;
+
+    for (int bend = maxlast; bend > 0; bend -= NT) {
+        const int b0 = max(0, bend - NT);
+        const int nb = bend - b0;
+        __syncthreads();  // the previous batch's flush has read s_g / s_id
+        if (tid < nb) {
+            const uint32_t gid = gauss_ids[rg.x + b0 + tid];
+            const Rec r = rec[gid];
+            const float xl = (r.r0.x - (float)x0) + r.r0.z;
+            const float yl = (r.r0.y - (float)y0) + r.r0.w;
+            s0[tid] = make_float4(xl, yl, r.r1.x, r.r1.y);
+            s1[tid] = make_float4(r.r1.z, r.r1.w, r.r2.y, r.r2.z);
+            s2[tid] = make_float2(r.r2.w, r.r2.x);
+            s_id[tid] = gid;
+        }
+#pragma unroll
+        for (int f = 0; f < 10; f++) s_g[f][tid] = 0.f;
+        __syncthreads();
+        if (__any_sync(0xffffffffu, P[0].last > b0 || P[1].last > b0)) {
+            for (int k = nb - 1; k >= 0; k--) {
+                const int j = b0 + k;
+                const float4 a = s0[k];
+                const float4 c = s1[k];
+                const float2 e = s2[k];
+                const float dy = pyl - a.y;
+                const float Bdy = a.w * dy;
+                const float Cdy2 = c.x * dy * dy;
+                float acc[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                bool any = pix_grad(P[0], j, pxl0 - a.x, dy, a.z, a.w, c.x, Bdy, Cdy2, c.y, c.z, c.w, e.x, e.y, acc);
+                any |= pix_grad(P[1], j, pxl1 - a.x, dy, a.z, a.w, c.x, Bdy, Cdy2, c.y, c.z, c.w, e.x, e.y, acc);
+                if (__any_sync(0xffffffffu, any)) {
+                    const float v = warp_reduce10(acc, lane);
+                    if (my_field >= 0) atomicAdd(&s_g[my_field][k], v);
+                }
+            }
+        }
+        __syncthreads();
+        if (tid < nb) {
+            const float g[10] = {s_g[0][tid], s_g[1][tid], s_g[2][tid], s_g[3][tid], s_g[4][tid],
+                                 s_g[5][tid], s_g[6][tid], s_g[7][tid], s_g[8][tid], s_g[9][tid]};
+            bool nz = false;
+#pragma unroll
+            for (int f = 0; f < 10; f++) nz |= g[f] != 0.f;
+            if (nz) {
+                GAcc *dst = gacc + s_id[tid];
+                atomicAdd(&dst->a0, make_float4(g[0], g[1], g[2], g[3]));
+                atomicAdd(&dst->a1, make_float4(g[4], g[5], g[6], 0.f));
+                atomicAdd(&dst->a2, make_float4(g[7], g[8], g[9], 0.f));
+            }
+        }
+    }
+
+    // per-tile medium partials: {beta_B[3], B_inf[3]}
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        float a = mBB[ch], b = mB[ch];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if (lane == 0) {
+            s_med[warp][ch] = a;
+            s_med[warp][3 + ch] = b;
+        }
+    }
+    __syncthreads();
+    if (tid < 6) {
+        float v = 0.f;
+#pragma unroll
+        for (int w = 0; w < NW; w++) v += s_med[w][tid];
+        tile_medium[6 * tile + tid] = v;
+    }
+}
+
+template <int TW, int TH>
+void fwd_launch(const TileGeom &tg, const CamK &cam, const uint2 *ranges, const uint32_t *ids, const Rec *rec,
+                const float *medium, float *image, float *depth, float *depth01, float *fT, float *aA, float *zh,
+                uint32_t *nl, uint32_t *nw, cudaStream_t s)
+{
+    k_blend_fwd<TW, TH><<<tg.tx * tg.ty, TW * TH / 2, 0, s>>>(tg, cam, ranges, ids, rec, medium, image, depth, depth01,
+                                                              fT, aA, zh, nl, nw);
+    count_launch();
+}
+
+template <int TW, int TH>
+void bwd_launch(const TileGeom &tg, const CamK &cam, const uint2 *ranges, const uint32_t *ids, const Rec *rec,
+                const float *medium, const float *fT, const float *aA, const float *zh, const uint32_t *nl,
+                const float *gi, const float *gd, const float *g01, GAcc *acc, float *tm, cudaStream_t s)
+{
+    k_blend_bwd<TW, TH><<<tg.tx * tg.ty, TW * TH / 2, 0, s>>>(tg, cam, ranges, ids, rec, medium, fT, aA, zh, nl, gi, gd,
+                                                              g01, acc, tm);
+    count_launch();
+}
+
+}  // namespace
+
+void launch_blend_fwd(const TileGeom &tg, const CamK &cam, const uint2 *ranges, const uint32_t *ids, const Rec *rec,
+                      const float *medium, float *image, float *depth, float *depth01, float *fT, float *aA, float *zh,
+                      uint32_t *nl, uint32_t *nw, cudaStream_t s)
+{
+    if (tg.tw == 8)
+        fwd_launch<8, 32>(tg, cam, ranges, ids, rec, medium, image, depth, depth01, fT, aA, zh, nl, nw, s);
+    else if (tg.tw == 32)
+        fwd_launch<32, 8>(tg, cam, ranges, ids, rec, medium, image, depth, depth01, fT, aA, zh, nl, nw, s);
+    else
+        fwd_launch<16, 16>(tg, cam, ranges, ids, rec, medium, image, depth, depth01, fT, aA, zh, nl, nw, s);
+}
+
+void launch_blend_bwd(const TileGeom &tg, const CamK &cam, const uint2 *ranges, const uint32_t *ids, const Rec *rec,
+                      const float *medium, const float *fT, const float *aA, const float *zh, const uint32_t *nl,
+                      const float *gi, const float *gd, const float *g01, GAcc *acc, float *tm, cudaStream_t s)
+{
+    if (tg.tw == 8)
+        bwd_launch<8, 32>(tg, cam, ranges, ids, rec, medium, fT, aA, zh, nl, gi, gd, g01, acc, tm, s);
+    else if (tg.tw == 32)
+        bwd_launch<32, 8>(tg, cam, ranges, ids, rec, medium, fT, aA, zh, nl, gi, gd, g01, acc, tm, s);
+    else
+        bwd_launch<16, 16>(tg, cam, ranges, ids, rec, medium, fT, aA, zh, nl, gi, gd, g01, acc, tm, s);
+}
+
+}  // namespace splash

@@ -1,0 +1,132 @@
+// Internal declarations of libsplash: constants of the rasterizer, the
+// kernel-side camera, the projected-Gaussian record, the workspace state
+// and the launch wrappers each .cu file provides.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "splash.h"
+
+namespace splash {
+
+// ---- rasterizer constants (3DGS conventions the paper inherits, Sec. III-A)
+constexpr float kAlphaMax = 0.99f;           // alpha clamp
+constexpr float kAlphaMin = 1.0f / 255.0f;   // a Gaussian below this at a pixel is skipped
+constexpr float kTStop = 1e-4f;              // stop before T would fall below this
+constexpr float kDilate = 0.3f;              // 2D covariance dilation (px^2)
+constexpr float kJClamp = 1.3f;              // projection Jacobian clamp, x half-FOV tangent
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+// q <= 9 (3 sigma) expressed on the scaled form qs = -log2(e)/2 * q
+constexpr float kQsMin = -4.5f * kLog2e;
+
+// ---- camera as the kernels see it
+struct CamK {
+    float R[9];      // world -> camera rotation, row-major
+    float t[3];      // world -> camera translation
+    float cpos[3];   // camera centre in world coordinates
+    float fx, fy, cx, cy;
+    float limx, limy;  // clamp of t_x/t_z, t_y/t_z inside the Jacobian
+    float znear, zfar;
+    int W, H;
+};
+
+struct TileGeom {
+    int tw, th;      // tile size in pixels
+    int tx, ty;      // tiles across, down
+};
+
+// ---- projected Gaussian (48 B, three float4):
+// r0 = {x_hi, y_hi, x_lo, y_lo}, r1 = {A, B, C, lo}, r2 = {d, ct_r, ct_g, ct_b}
+//  centre x = x_hi + x_lo (doubled precision; the blend forms tile-local
+//  coordinates (x_hi - tile_x0) + x_lo once per tile)
+//  qs(dx, dy) = A dx^2 + B dx dy + C dy^2 = -log2(e)/2 * (d^T Sigma2^-1 d)
+//  alpha = min(0.99, 2^(qs + lo)), lo = log2(sigmoid(o))
+//  ct = c e^{-beta_D d} - B_inf e^{-beta_B d} (per-Gaussian effective colour)
+struct __align__(16) Rec {
+    float4 r0, r1, r2;
+};
+
+// per-Gaussian accumulators of the blend backward (three float4):
+// a0 = {g_x, g_y, g_A, g_B}, a1 = {g_C, g_lo, g_d, 0}, a2 = {g_ct_r, g_ct_g, g_ct_b, 0}
+struct __align__(16) GAcc {
+    float4 a0, a1, a2;
+};
+
+// device status word bits
+enum : uint32_t { kStatusTimeout = 1u, kStatusCapacity = 2u };
+
+// ---- onesweep radix sort (sort.cu)
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;   // keys per partition
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+
+struct SortScratch {
+    uint32_t *hist;      // [4][256] per-pass digit offsets
+    uint32_t *lookback;  // [4][max_parts][256]
+    uint32_t *counters;  // [4] partition tickets
+    int64_t max_parts;
+};
+size_t sort_scratch_bytes(int64_t n_max);
+void sort_scratch_carve(void *base, int64_t n_max, SortScratch *s);
+// Sorts n pairs (n read from n_dev when non-null, else n_host) on bits
+// [0, bits). Ping-pongs between (k0,v0) and (k1,v1); returns which buffer
+// pair holds the result (0 or 1). grid is sized from n_host, which must be
+// >= the device count.
+int sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *k0, uint32_t *v0, uint32_t *k1,
+               uint32_t *v1, int64_t n_host, const uint32_t *n_dev, int bits, const SortScratch &s,
+               uint32_t *status, int spin_limit, int stall_part, cudaStream_t stream);
+
+// ---- kernels by stage (launch wrappers)
+void launch_preprocess_fwd(int64_t n, const splash_gaussians &g, const float *medium, const CamK &cam,
+                           const TileGeom &tg, Rec *rec, uint32_t *depth_key, uint32_t *tiles_touched,
+                           uint2 *rect, cudaStream_t s);
+void launch_count_scan(int64_t n, const uint32_t *order, const uint32_t *tiles_touched, uint32_t *offsets,
+                       uint32_t *block_sums, uint32_t *total, cudaStream_t s);
+void launch_emit(int64_t n, const uint32_t *order, const uint32_t *offsets, const uint32_t *tt, const uint2 *rect,
+                 const TileGeom &tg, uint32_t *tile_ids, uint32_t *gauss_ids, uint64_t capacity, uint32_t *status,
+                 cudaStream_t s);
+void launch_ranges(int64_t k_host, const uint32_t *k_dev, const uint32_t *tile_ids, uint2 *ranges, int ntiles,
+                   cudaStream_t s);
+void launch_blend_fwd(const TileGeom &tg, const CamK &cam, const uint2 *ranges, const uint32_t *gauss_ids,
+                      const Rec *rec, const float *medium, float *image, float *depth, float *depth01,
+                      float *final_T, float *acc_alpha, float *zhat, uint32_t *n_last, uint32_t *n_walk,
+                      cudaStream_t s);
+void launch_blend_bwd(const TileGeom &tg, const CamK &cam, const uint2 *ranges, const uint32_t *gauss_ids,
+                      const Rec *rec, const float *medium, const float *final_T, const float *acc_alpha,
+                      const float *zhat, const uint32_t *n_last, const float *dL_dimage, const float *dL_ddepth,
+                      const float *dL_ddepth01, GAcc *acc, float *tile_medium, cudaStream_t s);
+void launch_preprocess_bwd(int64_t n, const splash_gaussians &g, const float *medium, const CamK &cam,
+                           const GAcc *acc, const uint32_t *depth_key, const splash_grads &out,
+                           float *block_medium, int *n_blocks_out, cudaStream_t s);
+void launch_medium_reduce(const float *tile_medium, int ntiles, const float *block_medium, int nblocks,
+                          float *d_medium, cudaStream_t s);
+int preprocess_bwd_blocks(int64_t n);
+
+void launch_ssim_loss(const float *img, const float *tgt, int C, int H, int W, float lam, float *loss,
+                      float *grad, float *scratch, cudaStream_t s);
+size_t ssim_scratch_floats(int C, int H, int W);
+
+}  // namespace splash
+
+namespace splash {
+// every kernel launch site bumps this (reported by splash_kernel_launches)
+void count_launch(int n = 1);
+}  // namespace splash
+
+// ---- error plumbing shared by the host code
+void splash_set_error(const std::string &msg);
+
+#define SPLASH_CUDA_TRY(expr)                                                                  \
+    do {                                                                                       \
+        cudaError_t e__ = (expr);                                                              \
+        if (e__ != cudaSuccess) {                                                              \
+            splash_set_error(std::string(#expr) + ": " + cudaGetErrorString(e__));             \
+            return SPLASH_ERR_CUDA;                                                            \
+        }                                                                                      \
+    } while (0)

@@ -1,0 +1,595 @@
+// Per-Gaussian stages of the rasterizer:
+//   k_preprocess_fwd  -- view transform, cull, EWA projection of the 3D
+//                        covariance to a 2D conic, tile rectangle, SH colour,
+//                        water attenuation folded into an effective colour.
+//   k_preprocess_bwd  -- the adjoint of the above, from the per-Gaussian
+//                        accumulators of the blend backward to the parameters.
+//   k_medium_reduce   -- deterministic sum of the medium-gradient partials.
+//
+// Passages: Gaussian parameters and the affine (EWA) projection, Sec. III-A
+// (the sentence after Eq. 2); opacity sigmoid, Eq. 2; colour via spherical
+// harmonics, Sec. III-A; water model, Eq. 3-5 (Sec. III-B, IV-A).
+//
+// HBM-bound: one pass over the parameters (236 B per Gaussian at SH degree 3)
+// writing a 48 B record, a depth key, a tile count and a tile rectangle.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace splash {
+namespace {
+
+// ---- real spherical harmonics (orthonormal, no Condon-Shortley phase).
+// Constants: 1/(2 sqrt(pi)), sqrt(3/(4 pi)), sqrt(15/pi)/2, sqrt(5/pi)/4,
+// sqrt(15/pi)/4, sqrt(35/(2 pi))/4, sqrt(105/pi)/2, sqrt(21/(2 pi))/4,
+// sqrt(7/pi)/4, sqrt(105/pi)/4.
+constexpr float kY0 = 0.28209479177387814f;
+constexpr float kY1 = 0.4886025119029199f;
+constexpr float kY2a = 1.0925484305920792f;
+constexpr float kY2b = 0.31539156525252005f;
+constexpr float kY2c = 0.5462742152960396f;
+constexpr float kY3a = 0.5900435899266435f;
+constexpr float kY3b = 2.890611442640554f;
+constexpr float kY3c = 0.4570457994644658f;
+constexpr float kY3d = 0.3731763325901154f;
+constexpr float kY3e = 1.445305721320277f;
+
+// Basis at the unit vector (x, y, z). Degree-2/3 terms use the forms valid on
+// the unit sphere (3z^2 - 1 and the like); their gradients differ from the
+// harmonic polynomials only along the radius, which the direction
+// normalisation projects out.
+template <int DEG>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float *Y)
+{
+    Y[0] = kY0;
+    if constexpr (DEG >= 1) {
+        Y[1] = kY1 * y;
+        Y[2] = kY1 * z;
+        Y[3] = kY1 * x;
+    }
+    if constexpr (DEG >= 2) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = kY2a * x * y;
+        Y[5] = kY2a * y * z;
+        Y[6] = kY2b * (3.f * zz - 1.f);
+        Y[7] = kY2a * x * z;
+        Y[8] = kY2c * (xx - yy);
+        if constexpr (DEG >= 3) {
+            Y[9] = kY3a * y * (3.f * xx - yy);
+            Y[10] = kY3b * x * y * z;
+            Y[11] = kY3c * y * (5.f * zz - 1.f);
+            Y[12] = kY3d * z * (5.f * zz - 3.f);
+            Y[13] = kY3c * x * (5.f * zz - 1.f);
+            Y[14] = kY3e * z * (xx - yy);
+            Y[15] = kY3a * x * (xx - 3.f * yy);
+        }
+    }
+}
+
+// sum_k w_k grad Y_k for the forms above
+template <int DEG>
+__device__ __forceinline__ float3 sh_basis_vjp(float x, float y, float z, const float *w)
+{
+    float3 g = make_float3(0.f, 0.f, 0.f);
+    if constexpr (DEG >= 1) {
+        g.y += kY1 * w[1];
+        g.z += kY1 * w[2];
+        g.x += kY1 * w[3];
+    }
+    if constexpr (DEG >= 2) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        g.x += kY2a * (y * w[4] + z * w[7]) + 2.f * kY2c * x * w[8];
+        g.y += kY2a * (x * w[4] + z * w[5]) - 2.f * kY2c * y * w[8];
+        g.z += kY2a * (y * w[5] + x * w[7]) + 6.f * kY2b * z * w[6];
+        if constexpr (DEG >= 3) {
+            g.x += kY3a * 6.f * x * y * w[9] + kY3b * y * z * w[10] + kY3c * (5.f * zz - 1.f) * w[13] +
+                   kY3e * 2.f * x * z * w[14] + kY3a * (3.f * xx - 3.f * yy) * w[15];
+            g.y += kY3a * (3.f * xx - 3.f * yy) * w[9] + kY3b * x * z * w[10] + kY3c * (5.f * zz - 1.f) * w[11] -
+                   kY3e * 2.f * y * z * w[14] - kY3a * 6.f * x * y * w[15];
+            g.z += kY3b * x * y * w[10] + kY3c * 10.f * y * z * w[11] + kY3d * (15.f * zz - 3.f) * w[12] +
+                   kY3c * 10.f * x * z * w[13] + kY3e * (xx - yy) * w[14];
+        }
+    }
+    return g;
+}
+
+// ---- doubled-precision helpers (error-free transforms, Knuth TwoSum and an
+// FMA-based TwoProduct). The _rn intrinsics keep the compiler from fusing.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ DF two_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ DF renorm(float hi, float lo)
+{
+    const float s = __fadd_rn(hi, lo);
+    return {s, __fsub_rn(lo, __fsub_rn(s, hi))};
+}
+// r . m + t with about twice FP32 precision (compensated dot product)
+__device__ __forceinline__ DF dot3_plus(const float *r, float m0, float m1, float m2, float t)
+{
+    DF p = two_prod(r[0], m0);
+    DF s = two_sum(t, p.hi);
+    float err = __fadd_rn(p.lo, s.lo);
+    p = two_prod(r[1], m1);
+    s = two_sum(s.hi, p.hi);
+    err = __fadd_rn(err, __fadd_rn(p.lo, s.lo));
+    p = two_prod(r[2], m2);
+    s = two_sum(s.hi, p.hi);
+    err = __fadd_rn(err, __fadd_rn(p.lo, s.lo));
+    return renorm(s.hi, err);
+}
+// f * (a / b) + c for doubled-precision a, b
+__device__ __forceinline__ DF pinhole(float f, DF a, DF b, float c)
+{
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const float r = __fadd_rn(__fmaf_rn(-q1, b.hi, a.hi), __fmaf_rn(-q1, b.lo, a.lo));
+    const float q2 = __fdiv_rn(r, b.hi);
+    DF p = two_prod(f, q1);
+    const float pe = __fmaf_rn(f, q2, p.lo);
+    DF s = two_sum(p.hi, c);
+    return renorm(s.hi, __fadd_rn(s.lo, pe));
+}
+
+__device__ __forceinline__ float clampf(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
+
+constexpr int kPreThreads = 128;
+
+// Stage one warp's SH rows (32 Gaussians x K*3 floats, contiguous in HBM)
+// into shared memory with coalesced 16-byte loads; rows get an odd stride
+// so that per-lane reads are bank-conflict free.
+template <int KC>
+__device__ __forceinline__ void stage_sh(const float *__restrict__ sh, int64_t wbase, int cnt, int lane, float *dst)
+{
+    constexpr int ROW = KC + 1;
+    const float *src = sh + wbase * KC;
+    const int total = cnt * KC;
+    int done = 0;
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        const int n4 = total >> 2;
+        const float4 *s4 = reinterpret_cast<const float4 *>(src);
+        for (int e = lane; e < n4; e += 32) {
+            const float4 v = __ldg(s4 + e);
+            const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int f = 4 * e + k;
+                dst[(f / KC) * ROW + (f % KC)] = vv[k];
+            }
+        }
+        done = n4 * 4;
+    }
+    for (int f = done + lane; f < total; f += 32) dst[(f / KC) * ROW + (f % KC)] = __ldg(src + f);
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(kPreThreads) k_preprocess_fwd(
+    int n, const float *__restrict__ means, const float *__restrict__ log_scales, const float *__restrict__ quats,
+    const float *__restrict__ ologits, const float *__restrict__ sh, const float *__restrict__ medium, CamK cam,
+    TileGeom tg, Rec *__restrict__ rec, uint32_t *__restrict__ depth_key, uint32_t *__restrict__ tiles_touched,
+    uint2 *__restrict__ rect)
+{
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int KC = 3 * K;
+    constexpr int ROW = KC + 1;
+    __shared__ float s_sh[kPreThreads / 32][32 * ROW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t wbase = (int64_t)blockIdx.x * kPreThreads + warp * 32;
+    const int cnt = (int)max((int64_t)0, min((int64_t)32, (int64_t)n - wbase));
+    stage_sh<KC>(sh, wbase, cnt, lane, s_sh[warp]);
+    __syncwarp();
+    const int i = (int)(wbase + lane);
+    if (i >= n) return;
+
+    const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
+    const DF tzd = dot3_plus(cam.R + 6, mx, my, mz, cam.t[2]);
+    const float tz = tzd.hi;
+    const float opac = 1.f / (1.f + expf(-ologits[i]));
+    // culled: outside (z_near, z_far], or too transparent ever to reach alpha >= 1/255
+    if (!(tz > cam.znear && tz <= cam.zfar && opac >= kAlphaMin)) {
+        depth_key[i] = 0xffffffffu;
+        tiles_touched[i] = 0u;
+        rect[i] = make_uint2(0u, 0u);
+        return;
+    }
+    const DF txd = dot3_plus(cam.R, mx, my, mz, cam.t[0]);
+    const DF tyd = dot3_plus(cam.R + 3, mx, my, mz, cam.t[1]);
+    const float tx = txd.hi, ty = tyd.hi;
+
+    // Gaussian rotation from the normalised quaternion (w, x, y, z)
+    const float4 q4 = reinterpret_cast<const float4 *>(quats)[i];
+    const float qinv = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
+    const float qw = q4.x * qinv, qx = q4.y * qinv, qy = q4.z * qinv, qz = q4.w * qinv;
+    const float Rq[9] = {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
+                         2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
+                         2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
+    const float s0 = expf(log_scales[3 * i]), s1 = expf(log_scales[3 * i + 1]), s2 = expf(log_scales[3 * i + 2]);
+    // V = W Rq S: the scaled Gaussian axes in camera coordinates
+    float V[9];
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+        V[3 * r + 0] = (cam.R[3 * r] * Rq[0] + cam.R[3 * r + 1] * Rq[3] + cam.R[3 * r + 2] * Rq[6]) * s0;
+        V[3 * r + 1] = (cam.R[3 * r] * Rq[1] + cam.R[3 * r + 1] * Rq[4] + cam.R[3 * r + 2] * Rq[7]) * s1;
+        V[3 * r + 2] = (cam.R[3 * r] * Rq[2] + cam.R[3 * r + 1] * Rq[5] + cam.R[3 * r + 2] * Rq[8]) * s2;
+    }
+    // EWA: M = J V with the local Jacobian of the pinhole map; Sigma2 = M M^T + 0.3 I
+    const float rz = 1.f / tz;
+    const float rxc = clampf(tx * rz, -cam.limx, cam.limx), ryc = clampf(ty * rz, -cam.limy, cam.limy);
+    const float jx = cam.fx * rz, jy = cam.fy * rz;
+    float m1[3], m2[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        m1[c] = jx * (V[c] - rxc * V[6 + c]);
+        m2[c] = jy * (V[3 + c] - ryc * V[6 + c]);
+    }
+    const float n1 = m1[0] * m1[0] + m1[1] * m1[1] + m1[2] * m1[2];
+    const float n2 = m2[0] * m2[0] + m2[1] * m2[1] + m2[2] * m2[2];
+    const float b = m1[0] * m2[0] + m1[1] * m2[1] + m1[2] * m2[2];
+    const float cx_ = m1[1] * m2[2] - m1[2] * m2[1], cy_ = m1[2] * m2[0] - m1[0] * m2[2],
+                cz_ = m1[0] * m2[1] - m1[1] * m2[0];
+    const float a = n1 + kDilate, c = n2 + kDilate;
+    // det(M M^T + 0.3 I) = |m1 x m2|^2 + 0.3 (|m1|^2 + |m2|^2) + 0.09: a sum of
+    // non-negative terms, so no cancellation for thin, edge-on Gaussians
+    const float det = (cx_ * cx_ + cy_ * cy_ + cz_ * cz_) + kDilate * (n1 + n2) + kDilate * kDilate;
+    const float idet = 1.f / det;
+    const float A = -0.5f * kLog2e * c * idet, B = kLog2e * b * idet, C = -0.5f * kLog2e * a * idet;
+
+    // projected centre in doubled precision (hi + lo)
+    const DF px = pinhole(cam.fx, txd, tzd, cam.cx);
+    const DF py = pinhole(cam.fy, tyd, tzd, cam.cy);
+
+    // tile rectangle: every pixel centre inside the 3-sigma ellipse lies within
+    // +-3 sqrt(Sigma2_xx), +-3 sqrt(Sigma2_yy) of the centre (small safety margin)
+    const float hx = 3.f * sqrtf(a) * 1.0001f + 1e-3f, hy = 3.f * sqrtf(c) * 1.0001f + 1e-3f;
+    const float fx0 = ceilf(px.hi - hx - 0.5f), fx1 = floorf(px.hi + hx - 0.5f);
+    const float fy0 = ceilf(py.hi - hy - 0.5f), fy1 = floorf(py.hi + hy - 0.5f);
+    const int ix0 = (int)clampf(fx0, 0.f, (float)cam.W), ix1 = (int)clampf(fx1, -1.f, (float)(cam.W - 1));
+    const int iy0 = (int)clampf(fy0, 0.f, (float)cam.H), iy1 = (int)clampf(fy1, -1.f, (float)(cam.H - 1));
+    uint32_t ntiles = 0;
+    uint2 rc = make_uint2(0u, 0u);
+    if (ix0 <= ix1 && iy0 <= iy1) {
+        const uint32_t tx0 = ix0 / tg.tw, tx1 = ix1 / tg.tw, ty0 = iy0 / tg.th, ty1 = iy1 / tg.th;
+        ntiles = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
+        rc = make_uint2(tx0 | (tx1 << 16), ty0 | (ty1 << 16));
+    }
+
+    // view-dependent colour: direction from the camera centre to the mean
+    const float vx = mx - cam.cpos[0], vy = my - cam.cpos[1], vz = mz - cam.cpos[2];
+    const float vinv = rsqrtf(vx * vx + vy * vy + vz * vz);
+    float Y[K];
+    sh_basis<DEG>(vx * vinv, vy * vinv, vz * vinv, Y);
+    const float *coef = s_sh[warp] + lane * ROW;
+    float col[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        float acc = 0.5f;
+#pragma unroll
+        for (int k = 0; k < K; k++) acc = fmaf(coef[3 * k + ch], Y[k], acc);
+        col[ch] = fmaxf(acc, 0.f);
+    }
+    // water: ct = c e^{-beta_D d} - B_inf e^{-beta_B d}
+    float ct[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++)
+        ct[ch] = col[ch] * expf(-__ldg(medium + ch) * tz) - __ldg(medium + 6 + ch) * expf(-__ldg(medium + 3 + ch) * tz);
+    // log2(sigmoid(o)) = -log2(1 + e^{-o})
+    const float lo = -log1pf(expf(-ologits[i])) * kLog2e;
+
+    Rec r;
+    r.r0 = make_float4(px.hi, py.hi, px.lo, py.lo);
+    r.r1 = make_float4(A, B, C, lo);
+    r.r2 = make_float4(tz, ct[0], ct[1], ct[2]);
+    rec[i] = r;
+    depth_key[i] = __float_as_uint(tz);
+    tiles_touched[i] = ntiles;
+    rect[i] = rc;
+}
+
+constexpr int kBwdThreads = 128;
+
+template <int DEG>
+__global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd(
+    int n, const float *__restrict__ means, const float *__restrict__ log_scales, const float *__restrict__ quats,
+    const float *__restrict__ ologits, const float *__restrict__ sh, const float *__restrict__ medium, CamK cam,
+    const GAcc *__restrict__ acc, const uint32_t *__restrict__ depth_key, float *__restrict__ g_means,
+    float *__restrict__ g_ls, float *__restrict__ g_quats, float *__restrict__ g_ologits, float *__restrict__ g_sh,
+    float *__restrict__ block_medium)
+{
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int KC = 3 * K;
+    constexpr int ROW = KC + 1;
+    __shared__ float s_sh[kBwdThreads / 32][32 * ROW];
+    __shared__ float s_med[kBwdThreads / 32][9];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t wbase = (int64_t)blockIdx.x * kBwdThreads + warp * 32;
+    const int cnt = (int)max((int64_t)0, min((int64_t)32, (int64_t)n - wbase));
+    stage_sh<KC>(sh, wbase, cnt, lane, s_sh[warp]);
+    __syncwarp();
+    const int i = (int)(wbase + lane);
+    float gmed[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+
+    bool live = i < n && depth_key[i] != 0xffffffffu;
+    GAcc ga;
+    if (live) {
+        ga = acc[i];
+        live = (ga.a0.x != 0.f) | (ga.a0.y != 0.f) | (ga.a0.z != 0.f) | (ga.a0.w != 0.f) | (ga.a1.x != 0.f) |
+               (ga.a1.y != 0.f) | (ga.a1.z != 0.f) | (ga.a2.x != 0.f) | (ga.a2.y != 0.f) | (ga.a2.z != 0.f);
+    }
+    float *gsh_out = g_sh ? g_sh + (int64_t)i * KC : nullptr;
+    if (i < n && !live) {
+        if (g_means) g_means[3 * i] = g_means[3 * i + 1] = g_means[3 * i + 2] = 0.f;
+        if (g_ls) g_ls[3 * i] = g_ls[3 * i + 1] = g_ls[3 * i + 2] = 0.f;
+        if (g_quats) reinterpret_cast<float4 *>(g_quats)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (g_ologits) g_ologits[i] = 0.f;
+        if (gsh_out)
+            for (int k = 0; k < KC; k++) gsh_out[k] = 0.f;
+    }
+    if (live) {
+        const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
+        // same rounding as the forward pass, so clamp decisions agree
+        const float tx = dot3_plus(cam.R, mx, my, mz, cam.t[0]).hi;
+        const float ty = dot3_plus(cam.R + 3, mx, my, mz, cam.t[1]).hi;
+        const float tz = dot3_plus(cam.R + 6, mx, my, mz, cam.t[2]).hi;
+        const float4 q4 = reinterpret_cast<const float4 *>(quats)[i];
+        const float qn2 = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
+        const float qinv = rsqrtf(qn2);
+        const float qw = q4.x * qinv, qx = q4.y * qinv, qy = q4.z * qinv, qz = q4.w * qinv;
+        const float Rq[9] = {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
+                             2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
+                             2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
+        const float s[3] = {expf(log_scales[3 * i]), expf(log_scales[3 * i + 1]), expf(log_scales[3 * i + 2])};
+        float WR[9];  // W Rq
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                WR[3 * r + c] = cam.R[3 * r] * Rq[c] + cam.R[3 * r + 1] * Rq[3 + c] + cam.R[3 * r + 2] * Rq[6 + c];
+        float V[9];
+#pragma unroll
+        for (int e = 0; e < 9; e++) V[e] = WR[e] * s[e % 3];
+        const float rz = 1.f / tz;
+        const float rx = tx * rz, ry = ty * rz;
+        const bool clx = rx < -cam.limx || rx > cam.limx, cly = ry < -cam.limy || ry > cam.limy;
+        const float rxc = clampf(rx, -cam.limx, cam.limx), ryc = clampf(ry, -cam.limy, cam.limy);
+        const float jx = cam.fx * rz, jy = cam.fy * rz;
+        float u1[3], u2[3], m1[3], m2[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            u1[c] = V[c] - rxc * V[6 + c];
+            u2[c] = V[3 + c] - ryc * V[6 + c];
+            m1[c] = jx * u1[c];
+            m2[c] = jy * u2[c];
+        }
+        const float n1 = m1[0] * m1[0] + m1[1] * m1[1] + m1[2] * m1[2];
+        const float n2 = m2[0] * m2[0] + m2[1] * m2[1] + m2[2] * m2[2];
+        const float b = m1[0] * m2[0] + m1[1] * m2[1] + m1[2] * m2[2];
+        const float cx_ = m1[1] * m2[2] - m1[2] * m2[1], cy_ = m1[2] * m2[0] - m1[0] * m2[2],
+                    cz_ = m1[0] * m2[1] - m1[1] * m2[0];
+        const float a = n1 + kDilate, c = n2 + kDilate;
+        const float det = (cx_ * cx_ + cy_ * cy_ + cz_ * cz_) + kDilate * (n1 + n2) + kDilate * kDilate;
+        const float idet2 = 1.f / (det * det);
+
+        // scaled conic -> conic: A = -log2e/2 Ka, B = -log2e Kb, C = -log2e/2 Kc
+        const float gKa = -0.5f * kLog2e * ga.a0.z, gKb = -kLog2e * ga.a0.w, gKc = -0.5f * kLog2e * ga.a1.x;
+        // conic (Ka, Kb, Kc) = (c, -b, a) / det with det = a c - b^2: explicit partials
+        const float g_a = (-c * c * gKa + b * c * gKb - b * b * gKc) * idet2;
+        const float g_b = (2.f * b * c * gKa - (a * c + b * b) * gKb + 2.f * a * b * gKc) * idet2;
+        const float g_c = (-b * b * gKa + a * b * gKb - a * a * gKc) * idet2;
+        // a = |m1|^2 + 0.3, b = m1.m2, c = |m2|^2 + 0.3
+        float gm1[3], gm2[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            gm1[k] = 2.f * g_a * m1[k] + g_b * m2[k];
+            gm2[k] = 2.f * g_c * m2[k] + g_b * m1[k];
+        }
+        // m1 = (fx/tz)(V0 - rxc V2), m2 = (fy/tz)(V1 - ryc V2)
+        float gV[9];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            gV[k] = jx * gm1[k];
+            gV[3 + k] = jy * gm2[k];
+            gV[6 + k] = -jx * rxc * gm1[k] - jy * ryc * gm2[k];
+        }
+        float gtx = 0.f, gty = 0.f, gtz = 0.f;
+        gtz -= ((gm1[0] * m1[0] + gm1[1] * m1[1] + gm1[2] * m1[2]) + (gm2[0] * m2[0] + gm2[1] * m2[1] + gm2[2] * m2[2])) * rz;
+        if (!clx) {
+            const float grxc = -jx * (gm1[0] * V[6] + gm1[1] * V[7] + gm1[2] * V[8]);
+            gtx += grxc * rz;
+            gtz -= grxc * rx * rz;
+        }
+        if (!cly) {
+            const float gryc = -jy * (gm2[0] * V[6] + gm2[1] * V[7] + gm2[2] * V[8]);
+            gty += gryc * rz;
+            gtz -= gryc * ry * rz;
+        }
+        // V = (W Rq) diag(s): gradients for the scales and for Rq = W^T (gV diag(s))
+        float gls[3], GR[9];
+#pragma unroll
+        for (int c2 = 0; c2 < 3; c2++) gls[c2] = (gV[c2] * WR[c2] + gV[3 + c2] * WR[3 + c2] + gV[6 + c2] * WR[6 + c2]) * s[c2];
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+#pragma unroll
+            for (int c2 = 0; c2 < 3; c2++)
+                GR[3 * k + c2] = (cam.R[k] * gV[c2] + cam.R[3 + k] * gV[3 + c2] + cam.R[6 + k] * gV[6 + c2]) * s[c2];
+        // Rq(w, x, y, z) -> unit-quaternion gradient, then through the normalisation
+        const float guw = 2.f * (qz * (GR[3] - GR[1]) + qy * (GR[2] - GR[6]) + qx * (GR[7] - GR[5]));
+        const float gux = 2.f * (qy * (GR[1] + GR[3]) + qz * (GR[2] + GR[6]) + qw * (GR[7] - GR[5])) - 4.f * qx * (GR[4] + GR[8]);
+        const float guy = 2.f * (qx * (GR[1] + GR[3]) + qw * (GR[2] - GR[6]) + qz * (GR[5] + GR[7])) - 4.f * qy * (GR[0] + GR[8]);
+        const float guz = 2.f * (qw * (GR[3] - GR[1]) + qx * (GR[2] + GR[6]) + qy * (GR[5] + GR[7])) - 4.f * qz * (GR[0] + GR[4]);
+        const float ud = qw * guw + qx * gux + qy * guy + qz * guz;
+
+        // colour and water: ct = c a - B b, a = e^{-beta_D d}, b = e^{-beta_B d}
+        const float vx = mx - cam.cpos[0], vy = my - cam.cpos[1], vz = mz - cam.cpos[2];
+        const float vinv = rsqrtf(vx * vx + vy * vy + vz * vz);
+        const float dx = vx * vinv, dy = vy * vinv, dz = vz * vinv;
+        float Y[K];
+        sh_basis<DEG>(dx, dy, dz, Y);
+        const float *coef = s_sh[warp] + lane * ROW;
+        const float gct[3] = {ga.a2.x, ga.a2.y, ga.a2.z};
+        float graw[3];
+        float gd = ga.a1.z;
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) {
+            float raw = 0.5f;
+#pragma unroll
+            for (int k = 0; k < K; k++) raw = fmaf(coef[3 * k + ch], Y[k], raw);
+            const float col = fmaxf(raw, 0.f);
+            const float bd = __ldg(medium + ch), bb = __ldg(medium + 3 + ch), binf = __ldg(medium + 6 + ch);
+            const float ea = expf(-bd * tz), eb = expf(-bb * tz);
+            graw[ch] = raw > 0.f ? gct[ch] * ea : 0.f;
+            const float gea = gct[ch] * col, geb = -gct[ch] * binf;
+            gmed[ch] += gea * (-tz * ea);
+            gmed[3 + ch] += geb * (-tz * eb);
+            gmed[6 + ch] += -gct[ch] * eb;
+            gd += gea * (-bd * ea) + geb * (-bb * eb);
+        }
+        float w[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            w[k] = graw[0] * coef[3 * k] + graw[1] * coef[3 * k + 1] + graw[2] * coef[3 * k + 2];
+            if (gsh_out) {
+                gsh_out[3 * k] = graw[0] * Y[k];
+                gsh_out[3 * k + 1] = graw[1] * Y[k];
+                gsh_out[3 * k + 2] = graw[2] * Y[k];
+            }
+        }
+        const float3 gdir = sh_basis_vjp<DEG>(dx, dy, dz, w);
+        const float gdd = gdir.x * dx + gdir.y * dy + gdir.z * dz;
+
+        // projected centre x = fx tx/tz + cx, y = fy ty/tz + cy; depth d = tz
+        const float gx = ga.a0.x, gy = ga.a0.y;
+        gtx += gx * jx;
+        gty += gy * jy;
+        gtz += -(gx * jx * tx + gy * jy * ty) * rz + gd;
+
+        if (g_means) {
+            g_means[3 * i + 0] = cam.R[0] * gtx + cam.R[3] * gty + cam.R[6] * gtz + (gdir.x - dx * gdd) * vinv;
+            g_means[3 * i + 1] = cam.R[1] * gtx + cam.R[4] * gty + cam.R[7] * gtz + (gdir.y - dy * gdd) * vinv;
+            g_means[3 * i + 2] = cam.R[2] * gtx + cam.R[5] * gty + cam.R[8] * gtz + (gdir.z - dz * gdd) * vinv;
+        }
+        if (g_ls) {
+            g_ls[3 * i] = gls[0];
+            g_ls[3 * i + 1] = gls[1];
+            g_ls[3 * i + 2] = gls[2];
+        }
+        if (g_quats)
+            reinterpret_cast<float4 *>(g_quats)[i] = make_float4((guw - qw * ud) * qinv, (gux - qx * ud) * qinv,
+                                                                 (guy - qy * ud) * qinv, (guz - qz * ud) * qinv);
+        if (g_ologits) {
+            // lo = log2(sigmoid(o)): dlo/do = (1 - sigmoid(o)) / ln 2
+            const float opac = 1.f / (1.f + expf(-ologits[i]));
+            g_ologits[i] = ga.a1.y * (1.f - opac) * (1.f / kLn2);
+        }
+    }
+    // medium partials: warp shuffle, then one row per block
+#pragma unroll
+    for (int j = 0; j < 9; j++) {
+        float v = gmed[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_med[warp][j] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) {
+        float v = 0.f;
+#pragma unroll
+        for (int w2 = 0; w2 < kBwdThreads / 32; w2++) v += s_med[w2][threadIdx.x];
+        block_medium[blockIdx.x * 9 + threadIdx.x] = v;
+    }
+}
+
+// One block: d_medium[j] = sum of per-tile (pixel terms: B_inf, beta_B) and
+// per-block (Gaussian terms) partials, in a fixed order.
+__global__ void k_medium_reduce(const float *__restrict__ tile_medium, int ntiles, const float *__restrict__ block_medium,
+                                int nblocks, float *__restrict__ d_medium)
+{
+    __shared__ float s_part[256][9];
+    float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
+#pragma unroll
+        for (int j = 0; j < 6; j++) acc[3 + j] += tile_medium[6 * t + j];  // B-beta[3], B_inf[3]
+    for (int t = threadIdx.x; t < nblocks; t += blockDim.x)
+#pragma unroll
+        for (int j = 0; j < 9; j++) acc[j] += block_medium[9 * t + j];
+#pragma unroll
+    for (int j = 0; j < 9; j++) s_part[threadIdx.x][j] = acc[j];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+#pragma unroll
+            for (int j = 0; j < 9; j++) s_part[threadIdx.x][j] += s_part[threadIdx.x + s][j];
+        __syncthreads();
+    }
+    if (threadIdx.x < 9) d_medium[threadIdx.x] = s_part[0][threadIdx.x];
+}
+
+template <int DEG>
+void pre_fwd(int64_t n, const splash_gaussians &g, const float *medium, const CamK &cam, const TileGeom &tg, Rec *rec,
+             uint32_t *dk, uint32_t *tt, uint2 *rect, cudaStream_t s)
+{
+    const int blocks = (int)((n + kPreThreads - 1) / kPreThreads);
+    k_preprocess_fwd<DEG><<<blocks, kPreThreads, 0, s>>>((int)n, g.means, g.log_scales, g.quats, g.opacity_logits, g.sh,
+                                                        medium, cam, tg, rec, dk, tt, rect);
+    count_launch();
+}
+
+template <int DEG>
+void pre_bwd(int64_t n, const splash_gaussians &g, const float *medium, const CamK &cam, const GAcc *acc,
+             const uint32_t *dk, const splash_grads &o, float *bm, cudaStream_t s)
+{
+    const int blocks = (int)((n + kBwdThreads - 1) / kBwdThreads);
+    k_preprocess_bwd<DEG><<<blocks, kBwdThreads, 0, s>>>((int)n, g.means, g.log_scales, g.quats, g.opacity_logits, g.sh,
+                                                        medium, cam, acc, dk, o.means, o.log_scales, o.quats,
+                                                        o.opacity_logits, o.sh, bm);
+    count_launch();
+}
+
+}  // namespace
+
+void launch_preprocess_fwd(int64_t n, const splash_gaussians &g, const float *medium, const CamK &cam,
+                           const TileGeom &tg, Rec *rec, uint32_t *dk, uint32_t *tt, uint2 *rect, cudaStream_t s)
+{
+    if (n <= 0) return;
+    switch (g.sh_degree) {
+    case 0: pre_fwd<0>(n, g, medium, cam, tg, rec, dk, tt, rect, s); break;
+    case 1: pre_fwd<1>(n, g, medium, cam, tg, rec, dk, tt, rect, s); break;
+    case 2: pre_fwd<2>(n, g, medium, cam, tg, rec, dk, tt, rect, s); break;
+    default: pre_fwd<3>(n, g, medium, cam, tg, rec, dk, tt, rect, s); break;
+    }
+}
+
+int preprocess_bwd_blocks(int64_t n) { return (int)((n + kBwdThreads - 1) / kBwdThreads); }
+
+void launch_preprocess_bwd(int64_t n, const splash_gaussians &g, const float *medium, const CamK &cam,
+                           const GAcc *acc, const uint32_t *dk, const splash_grads &o, float *bm, int *nb,
+                           cudaStream_t s)
+{
+    *nb = n > 0 ? preprocess_bwd_blocks(n) : 0;
+    if (n <= 0) return;
+    switch (g.sh_degree) {
+    case 0: pre_bwd<0>(n, g, medium, cam, acc, dk, o, bm, s); break;
+    case 1: pre_bwd<1>(n, g, medium, cam, acc, dk, o, bm, s); break;
+    case 2: pre_bwd<2>(n, g, medium, cam, acc, dk, o, bm, s); break;
+    default: pre_bwd<3>(n, g, medium, cam, acc, dk, o, bm, s); break;
+    }
+}
+
+void launch_medium_reduce(const float *tile_medium, int ntiles, const float *block_medium, int nblocks,
+                          float *d_medium, cudaStream_t s)
+{
+    k_medium_reduce<<<1, 256, 0, s>>>(tile_medium, ntiles, block_medium, nblocks, d_medium);
+    count_launch();
+}
+
+}  // namespace splash

@@ -1,0 +1,270 @@
+// Stable LSD radix sort of (uint32 key, uint32 value) pairs, onesweep form:
+// one kernel reads all keys once to build the digit histograms of every
+// pass; then one kernel per 8-bit digit ranks a 4096-key partition in
+// shared memory, learns its global offset by decoupled look-back over the
+// partitions before it, and scatters. Each pass reads and writes every pair
+// once (16 B per pair per pass), which makes it HBM-bound.
+//
+// The rasterizer needs the per-tile lists ordered by depth (Sec. III-A: the
+// Gaussians of a pixel are composited in increasing depth). It sorts the
+// Gaussians by FP32 depth bits once (N pairs, 4 passes) and then the
+// (tile, Gaussian) pairs emitted in that order by tile index only
+// (ceil(log2 tiles) bits); stability makes the result identical to one
+// sort of 64-bit (tile << 32 | depth bits) keys emitted in index order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace splash {
+namespace {
+
+constexpr uint32_t kFlagAgg = 1u << 30;  // partition aggregate published
+constexpr uint32_t kFlagInc = 2u << 30;  // inclusive prefix published
+constexpr uint32_t kValMask = (1u << 30) - 1u;
+constexpr int kWarps = kSortThreads / 32;
+
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) { return *reinterpret_cast<const volatile uint32_t *>(p); }
+__device__ __forceinline__ void st_volatile(uint32_t *p, uint32_t v) { *reinterpret_cast<volatile uint32_t *>(p) = v; }
+
+__global__ void __launch_bounds__(256) k_hist(const uint32_t *__restrict__ keys, int64_t n_host,
+                                              const uint32_t *__restrict__ n_dev, int bits, uint32_t *__restrict__ hist)
+{
+    __shared__ uint32_t s[4][kRadix];
+    const int passes = (bits + kRadixBits - 1) / kRadixBits;
+    for (int e = threadIdx.x; e < 4 * kRadix; e += blockDim.x) (&s[0][0])[e] = 0u;
+    __syncthreads();
+    uint32_t pmask[4];
+    for (int p = 0; p < 4; p++) pmask[p] = (1u << min(kRadixBits, max(0, bits - kRadixBits * p))) - 1u;
+    const int64_t n = n_dev ? (int64_t)*n_dev : n_host;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n4 = n >> 2;
+    const uint4 *k4 = reinterpret_cast<const uint4 *>(keys);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        const uint4 v = k4[i];
+        const uint32_t kk[4] = {v.x, v.y, v.z, v.w};
+        for (int p = 0; p < passes; p++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) atomicAdd(&s[p][(kk[q] >> (kRadixBits * p)) & pmask[p]], 1u);
+    }
+    for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t k = keys[i];
+        for (int p = 0; p < passes; p++) atomicAdd(&s[p][(k >> (kRadixBits * p)) & pmask[p]], 1u);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < passes * kRadix; e += blockDim.x) {
+        const uint32_t c = (&s[0][0])[e];
+        if (c) atomicAdd(&hist[e], c);
+    }
+}
+
+// exclusive scan of each pass's 256 digit counts (one block per pass)
+__global__ void __launch_bounds__(kRadix) k_hist_scan(uint32_t *__restrict__ hist)
+{
+    __shared__ uint32_t s_w[kRadix / 32];
+    uint32_t *h = hist + blockIdx.x * kRadix;
+    const uint32_t v = h[threadIdx.x];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[w] = x;
+    __syncthreads();
+    uint32_t base = 0;
+    for (int i = 0; i < w; i++) base += s_w[i];
+    h[threadIdx.x] = base + x - v;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_onesweep(
+    const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
+    uint32_t *__restrict__ vout, int64_t n_host, const uint32_t *__restrict__ n_dev, int shift, uint32_t mask,
+    const uint32_t *__restrict__ goff, uint32_t *__restrict__ lookback, uint32_t *__restrict__ counter,
+    uint32_t *__restrict__ status, int spin_limit, uint32_t stall_part)
+{
+    __shared__ uint32_t s_whist[kWarps][kRadix];  // per-warp digit counts, then warp offsets
+    __shared__ uint32_t s_doff[kRadix];           // block-local exclusive digit offsets
+    __shared__ uint32_t s_gbase[kRadix];          // global position of each digit's first key
+    __shared__ uint32_t s_wsum[kWarps];
+    __shared__ uint32_t s_keys[kSortTile];
+    __shared__ uint32_t s_vals[kSortTile];
+    __shared__ uint32_t s_part;
+
+    if (threadIdx.x == 0) s_part = atomicAdd(counter, 1u);  // partitions start in ticket order
+    for (int e = threadIdx.x; e < kWarps * kRadix; e += kSortThreads) (&s_whist[0][0])[e] = 0u;
+    __syncthreads();
+    const uint32_t part = s_part;
+    const int64_t n = n_dev ? (int64_t)*n_dev : n_host;
+    const int64_t base = (int64_t)part * kSortTile;
+    if (base >= n) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t wbase = base + (int64_t)warp * 32 * kSortItems;
+    const uint32_t lt = (1u << lane) - 1u;
+
+    // warp-striped loads: item j of lane l is key wbase + 32 j + l (input order)
+    uint32_t k[kSortItems], v[kSortItems], rank[kSortItems];
+#pragma unroll
+    for (int j = 0; j < kSortItems; j++) {
+        const int64_t idx = wbase + 32 * j + lane;
+        const bool ok = idx < n;
+        k[j] = ok ? kin[idx] : 0xffffffffu;  // past the end: largest digit, ranked last
+        v[j] = ok ? (vin ? vin[idx] : (uint32_t)idx) : 0u;
+    }
+    // stable rank within the warp: lanes with equal digits via match.any
+    uint32_t *wh = s_whist[warp];
+#pragma unroll
+    for (int j = 0; j < kSortItems; j++) {
+        const uint32_t d = (k[j] >> shift) & mask;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const int leader = 31 - __clz(peers);
+        uint32_t old = 0;
+        if (lane == leader) {
+            old = wh[d];
+            wh[d] = old + __popc(peers);
+        }
+        old = __shfl_sync(0xffffffffu, old, leader);
+        rank[j] = old + __popc(peers & lt);
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // per digit (one thread each): warp offsets and the block total
+    const uint32_t d0 = threadIdx.x;  // kSortThreads == kRadix
+    uint32_t total = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; w++) {
+        const uint32_t c = s_whist[w][d0];
+        s_whist[w][d0] = total;
+        total += c;
+    }
+    // block-wide exclusive scan of the digit totals
+    uint32_t x = total;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wsum[warp] = x;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < warp; w++) wpre += s_wsum[w];
+    s_doff[d0] = wpre + x - total;
+
+    // decoupled look-back for this digit
+    uint32_t *lb = lookback + (int64_t)part * kRadix + d0;
+    uint32_t excl = 0;
+    const bool publish = stall_part == 0u || part != stall_part;  // test hook: a partition that never reports
+    if (part == 0) {
+        st_volatile(lb, kFlagInc | total);
+    } else {
+        if (publish) st_volatile(lb, kFlagAgg | total);
+        int64_t p = (int64_t)part - 1;
+        int spins = 0;
+        while (true) {
+            const uint32_t w = ld_volatile(lookback + p * kRadix + d0);
+            const uint32_t flag = w & ~kValMask;
+            if (flag == 0u) {
+                if (++spins > spin_limit) {  // give up: report, keep offsets in range
+                    atomicOr(status, kStatusTimeout);
+                    break;
+                }
+                continue;
+            }
+            excl += w & kValMask;
+            if (flag == kFlagInc || p == 0) break;
+            --p;
+        }
+        if (publish) st_volatile(lb, kFlagInc | (excl + total));
+    }
+    s_gbase[d0] = goff[d0] + excl;
+    __syncthreads();
+
+    // scatter into shared memory in block-sorted order
+#pragma unroll
+    for (int j = 0; j < kSortItems; j++) {
+        const uint32_t d = (k[j] >> shift) & mask;
+        const uint32_t slot = s_doff[d] + s_whist[warp][d] + rank[j];
+        s_keys[slot] = k[j];
+        s_vals[slot] = v[j];
+    }
+    __syncthreads();
+    // runs of equal digits go to consecutive global addresses
+    const int nvalid = (int)min((int64_t)kSortTile, n - base);
+    for (int s = threadIdx.x; s < nvalid; s += kSortThreads) {
+        const uint32_t kk = s_keys[s];
+        const uint32_t d = (kk >> shift) & mask;
+        const uint32_t dst = s_gbase[d] + (uint32_t)s - s_doff[d];
+        kout[dst] = kk;
+        vout[dst] = s_vals[s];
+    }
+}
+
+__global__ void k_iota_copy(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
+                            uint32_t *__restrict__ vout, int64_t n_host, const uint32_t *__restrict__ n_dev)
+{
+    const int64_t n = n_dev ? (int64_t)*n_dev : n_host;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        kout[i] = kin[i];
+        vout[i] = vin ? vin[i] : (uint32_t)i;
+    }
+}
+
+}  // namespace
+
+size_t sort_scratch_bytes(int64_t n_max)
+{
+    const int64_t parts = (n_max + kSortTile - 1) / kSortTile + 1;
+    return sizeof(uint32_t) * (size_t)(4 * kRadix + 4 * parts * kRadix + 64);
+}
+
+void sort_scratch_carve(void *base, int64_t n_max, SortScratch *s)
+{
+    const int64_t parts = (n_max + kSortTile - 1) / kSortTile + 1;
+    uint32_t *p = static_cast<uint32_t *>(base);
+    s->hist = p;
+    s->counters = p + 4 * kRadix;
+    s->lookback = p + 4 * kRadix + 64;
+    s->max_parts = parts;
+}
+
+int sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
+               int64_t n_host, const uint32_t *n_dev, int bits, const SortScratch &s, uint32_t *status, int spin_limit,
+               int stall_part, cudaStream_t stream)
+{
+    if (n_host <= 0) return 0;
+    const int passes = (bits + kRadixBits - 1) / kRadixBits;
+    if (passes == 0) {
+        const int blocks = (int)std::min<int64_t>((n_host + 255) / 256, 148 * 16);
+        k_iota_copy<<<blocks, 256, 0, stream>>>(keys_in, vals_in, k0, v0, n_host, n_dev);
+        count_launch();
+        return 0;
+    }
+    const int64_t parts = (n_host + kSortTile - 1) / kSortTile;
+    cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * (4 * kRadix + 64), stream);
+    // look-back flags of every pass; pass p uses rows [p * parts, (p + 1) * parts)
+    cudaMemsetAsync(s.lookback, 0, sizeof(uint32_t) * (size_t)passes * (size_t)parts * kRadix, stream);
+    const int hblocks = (int)std::min<int64_t>((n_host / 4 + 255) / 256 + 1, 148 * 8);
+    k_hist<<<hblocks, 256, 0, stream>>>(keys_in, n_host, n_dev, bits, s.hist);
+    count_launch();
+    k_hist_scan<<<passes, kRadix, 0, stream>>>(s.hist);
+    count_launch();
+    const uint32_t *ki = keys_in, *vi = vals_in;
+    for (int p = 0; p < passes; p++) {
+        uint32_t *ko = (p & 1) ? k1 : k0, *vo = (p & 1) ? v1 : v0;
+        const int pbits = std::min(kRadixBits, bits - kRadixBits * p);
+        const uint32_t mask = (1u << pbits) - 1u;
+        k_onesweep<<<(unsigned)parts, kSortThreads, 0, stream>>>(ki, vi, ko, vo, n_host, n_dev, kRadixBits * p, mask,
+                                                                 s.hist + kRadix * p, s.lookback + (size_t)p * parts * kRadix,
+                                                                 s.counters + p, status, spin_limit,
+                                                                 (uint32_t)stall_part);
+        count_launch();
+        ki = ko;
+        vi = vo;
+    }
+    return (passes - 1) & 1;
+}
+
+}  // namespace splash

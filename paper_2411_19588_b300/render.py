@@ -1,0 +1,270 @@
+"""Torch-facing API of the rasterizer: tensors in, tensors out, all work in
+libsplash's kernels (argument marshalling only here).
+
+    r = Renderer()                                   # tile 16x16
+    img, depth, depth01 = r.render(params, medium, camera)
+    img, depth, depth01 = render(params, medium, camera, renderer=r)  # autograd
+
+``params`` holds CUDA float32 contiguous tensors ``means`` [n,3],
+``log_scales`` [n,3], ``quats`` [n,4] (w,x,y,z), ``opacity_logits`` [n],
+``sh`` [n,(deg+1)^2,3]; ``medium`` is a CUDA float32 [9] tensor
+(beta_D[3], beta_B[3], B_inf[3]); ``camera`` is a ``scenes.Camera``.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _abi
+from . import scenes
+
+PARAM_NAMES = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def camera_struct(cam: scenes.Camera) -> _abi.Camera:
+    c = _abi.Camera()
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    w2c = np.asarray(cam.world_to_cam, np.float32).reshape(12)
+    for i in range(12):
+        c.world_to_cam[i] = float(w2c[i])
+    c.z_near, c.z_far = float(cam.z_near), float(cam.z_far)
+    return c
+
+
+def _check_tensor(t: torch.Tensor, name: str, shape=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA float32 tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+def params_to_device(g: scenes.Gaussians, device="cuda") -> dict:
+    out = {k: torch.from_numpy(np.ascontiguousarray(getattr(g, k), np.float32)).to(device) for k in PARAM_NAMES}
+    out["sh_degree"] = int(g.sh_degree)
+    return out
+
+
+def gaussians_struct(p: dict) -> _abi.Gaussians:
+    n = p["means"].shape[0]
+    deg = int(p["sh_degree"])
+    K = (deg + 1) ** 2
+    shapes = {"means": (n, 3), "log_scales": (n, 3), "quats": (n, 4), "opacity_logits": (n,), "sh": (n, K, 3)}
+    for k in PARAM_NAMES:
+        _check_tensor(p[k], k, shapes[k])
+    g = _abi.Gaussians()
+    g.means, g.log_scales, g.quats = p["means"].data_ptr(), p["log_scales"].data_ptr(), p["quats"].data_ptr()
+    g.opacity_logits, g.sh = p["opacity_logits"].data_ptr(), p["sh"].data_ptr()
+    g.n, g.sh_degree = n, deg
+    return g
+
+
+class State:
+    """A render workspace (device buffers grow on demand). Returned to its
+    renderer's pool when garbage collected."""
+
+    def __init__(self, renderer: "Renderer", handle: ctypes.c_void_p):
+        self._renderer = renderer
+        self.handle = handle
+        self.shape = None
+
+    def __del__(self):
+        r = getattr(self, "_renderer", None)
+        if r is not None and self.handle:
+            r._release(self.handle)
+            self.handle = None
+
+
+class Renderer:
+    def __init__(self, tile=(16, 16), spin_limit: int = 0, test_stall_partition: int = 0):
+        L = _abi.lib()
+        opt = _abi.Options(int(tile[0]), int(tile[1]), int(spin_limit), int(test_stall_partition))
+        h = ctypes.c_void_p()
+        _abi.check(L.splash_create(ctypes.byref(opt), ctypes.byref(h)), "splash_create")
+        self._ctx = h
+        self._pool = []
+        self.tile = tuple(tile)
+
+    def close(self):
+        L = _abi.lib()
+        for h in self._pool:
+            L.splash_state_destroy(h)
+        self._pool = []
+        if self._ctx:
+            L.splash_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- states
+    def state(self) -> State:
+        if self._pool:
+            return State(self, self._pool.pop())
+        h = ctypes.c_void_p()
+        _abi.check(_abi.lib().splash_state_create(self._ctx, ctypes.byref(h)), "splash_state_create")
+        return State(self, h)
+
+    def _release(self, h):
+        if self._ctx:
+            self._pool.append(h)
+        else:
+            _abi.lib().splash_state_destroy(h)
+
+    # -- render
+    def forward(self, st: State, params: dict, medium: torch.Tensor, cam: scenes.Camera, image=None, depth=None,
+                depth01=None):
+        _check_tensor(medium, "medium", (9,))
+        H, W = cam.height, cam.width
+        dev = medium.device
+        image = torch.empty((3, H, W), device=dev, dtype=torch.float32) if image is None else image
+        depth = torch.empty((H, W), device=dev, dtype=torch.float32) if depth is None else depth
+        depth01 = torch.empty((H, W), device=dev, dtype=torch.float32) if depth01 is None else depth01
+        g = gaussians_struct(params)
+        c = camera_struct(cam)
+        rc = _abi.lib().splash_render_forward(self._ctx, st.handle, ctypes.byref(g), medium.data_ptr(), ctypes.byref(c),
+                                              image.data_ptr(), _abi.ptr(depth), _abi.ptr(depth01), _stream())
+        _abi.check(rc, "splash_render_forward")
+        st.shape = (params["means"].shape[0], H, W)
+        return image, depth, depth01
+
+    def render(self, params: dict, medium: torch.Tensor, cam: scenes.Camera):
+        st = self.state()
+        return self.forward(st, params, medium, cam)
+
+    def backward(self, st: State, params: dict, medium: torch.Tensor, cam: scenes.Camera, dL_dimage,
+                 dL_ddepth=None, dL_ddepth01=None, grads: dict | None = None) -> dict:
+        H, W = cam.height, cam.width
+        _check_tensor(dL_dimage, "dL_dimage", (3, H, W))
+        if dL_ddepth is not None:
+            _check_tensor(dL_ddepth, "dL_ddepth", (H, W))
+        if dL_ddepth01 is not None:
+            _check_tensor(dL_ddepth01, "dL_ddepth01", (H, W))
+        if grads is None:
+            grads = {k: torch.empty_like(params[k]) for k in PARAM_NAMES}
+            grads["medium"] = torch.empty_like(medium)
+        gs = _abi.Grads(*(grads[k].data_ptr() if grads.get(k) is not None else None
+                          for k in PARAM_NAMES + ("medium",)))
+        g = gaussians_struct(params)
+        c = camera_struct(cam)
+        rc = _abi.lib().splash_render_backward(self._ctx, st.handle, ctypes.byref(g), medium.data_ptr(),
+                                               ctypes.byref(c), dL_dimage.data_ptr(), _abi.ptr(dL_ddepth),
+                                               _abi.ptr(dL_ddepth01), ctypes.byref(gs), _stream())
+        _abi.check(rc, "splash_render_backward")
+        return grads
+
+    def state_array(self, st: State, field: str, dtype=torch.int32, shape=None) -> torch.Tensor:
+        """Copy of one forward-state buffer (see splash_state_copy)."""
+        info = _abi.StateInfo()
+        _abi.check(_abi.lib().splash_state_get_info(st.handle, ctypes.byref(info)), "splash_state_get_info")
+        n, K = info.n_gaussians, info.n_keys
+        tiles = info.tiles_x * info.tiles_y
+        _, H, W = st.shape
+        sizes = {"tile_ids": (K,), "gauss_ids": (K,), "ranges": (tiles, 2), "depth_keys": (n,), "tiles_touched": (n,),
+                 "records": (n, 12), "final_T": (H, W), "acc_alpha": (H, W), "n_last": (H, W), "n_walk": (H, W),
+                 "rects": (n, 2)}
+        floaty = field in ("records", "final_T", "acc_alpha")
+        out = torch.empty(sizes[field], dtype=torch.float32 if floaty else torch.int32, device="cuda")
+        rc = _abi.lib().splash_state_copy(st.handle, _abi.FIELDS[field], out.data_ptr(), out.numel() * 4, _stream())
+        _abi.check(rc, "splash_state_copy")
+        return out if floaty else out.view(dtype)
+
+    def info(self, st: State) -> dict:
+        info = _abi.StateInfo()
+        _abi.check(_abi.lib().splash_state_get_info(st.handle, ctypes.byref(info)), "splash_state_get_info")
+        return {"n_keys": info.n_keys, "tiles_x": info.tiles_x, "tiles_y": info.tiles_y, "tile_w": info.tile_w,
+                "tile_h": info.tile_h, "n_gaussians": info.n_gaussians}
+
+    # -- training-step pieces
+    def loss(self, st: State, image: torch.Tensor, target: torch.Tensor, lam: float = 0.2, need_grad: bool = True):
+        _check_tensor(image, "image")
+        _check_tensor(target, "target", tuple(image.shape))
+        C, H, W = image.shape
+        loss = torch.empty(1, device=image.device, dtype=torch.float32)
+        grad = torch.empty_like(image) if need_grad else None
+        rc = _abi.lib().splash_loss_l1_ssim(self._ctx, st.handle, image.data_ptr(), target.data_ptr(), C, H, W,
+                                            float(lam), loss.data_ptr(), _abi.ptr(grad), _stream())
+        _abi.check(rc, "splash_loss_l1_ssim")
+        return loss, grad
+
+    def sort_pairs(self, st: State, keys: torch.Tensor, vals: torch.Tensor | None = None, bits: int = 32):
+        n = keys.numel()
+        ko = torch.empty_like(keys)
+        vo = torch.empty(n, dtype=torch.int32, device=keys.device)
+        rc = _abi.lib().splash_sort_pairs_u32(self._ctx, st.handle, keys.data_ptr(), _abi.ptr(vals), ko.data_ptr(),
+                                              vo.data_ptr(), n, int(bits), _stream())
+        _abi.check(rc, "splash_sort_pairs_u32")
+        return ko, vo
+
+    def profile(self, on: bool = True):
+        _abi.check(_abi.lib().splash_profile_enable(self._ctx, int(on)), "splash_profile_enable")
+
+    def profile_read(self) -> dict:
+        ms = (ctypes.c_double * len(_abi.STAGES))()
+        cnt = (ctypes.c_int64 * len(_abi.STAGES))()
+        _abi.check(_abi.lib().splash_profile_read(self._ctx, ms, cnt), "splash_profile_read")
+        return {s: (ms[i], cnt[i]) for i, s in enumerate(_abi.STAGES)}
+
+    def sync_status(self):
+        _abi.check(_abi.lib().splash_sync_status(self._ctx, _stream()), "splash_sync_status")
+
+
+def kernel_launches() -> int:
+    return int(_abi.lib().splash_kernel_launches())
+
+
+def adam_step(groups, step: int, betas=(0.9, 0.999), eps: float = 1e-15):
+    """groups: list of dicts {param, grad, m, v, lr, clamp_min (optional)}."""
+    if len(groups) > _abi.ADAM_MAX_GROUPS:
+        raise ValueError("too many Adam groups")
+    arr = (_abi.AdamGroup * len(groups))()
+    for i, g in enumerate(groups):
+        for k in ("param", "grad", "m", "v"):
+            _check_tensor(g[k], f"adam {k}")
+        cm = g.get("clamp_min")
+        arr[i] = _abi.AdamGroup(g["param"].data_ptr(), g["grad"].data_ptr(), g["m"].data_ptr(), g["v"].data_ptr(),
+                                g["param"].numel(), float(g["lr"]), float(cm if cm is not None else 0.0),
+                                1 if cm is not None else 0)
+    rc = _abi.lib().splash_adam_step(arr, len(groups), int(step), float(betas[0]), float(betas[1]), float(eps), _stream())
+    _abi.check(rc, "splash_adam_step")
+
+
+class _RenderFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, renderer, cam, sh_degree, means, log_scales, quats, opacity_logits, sh, medium):
+        params = {"means": means, "log_scales": log_scales, "quats": quats, "opacity_logits": opacity_logits, "sh": sh,
+                  "sh_degree": sh_degree}
+        st = renderer.state()
+        img, depth, depth01 = renderer.forward(st, params, medium, cam)
+        ctx.renderer, ctx.cam, ctx.st, ctx.sh_degree = renderer, cam, st, sh_degree
+        ctx.save_for_backward(means, log_scales, quats, opacity_logits, sh, medium)
+        return img, depth, depth01
+
+    @staticmethod
+    def backward(ctx, g_img, g_depth, g_depth01):
+        means, log_scales, quats, opacity_logits, sh, medium = ctx.saved_tensors
+        params = {"means": means, "log_scales": log_scales, "quats": quats, "opacity_logits": opacity_logits, "sh": sh,
+                  "sh_degree": ctx.sh_degree}
+        dev = medium.device
+        g_img = torch.zeros((3, ctx.cam.height, ctx.cam.width), device=dev) if g_img is None else g_img.contiguous()
+        g_depth = None if g_depth is None else g_depth.contiguous()
+        g_depth01 = None if g_depth01 is None else g_depth01.contiguous()
+        grads = ctx.renderer.backward(ctx.st, params, medium, ctx.cam, g_img, g_depth, g_depth01)
+        ctx.st = None
+        return (None, None, None, grads["means"], grads["log_scales"], grads["quats"], grads["opacity_logits"],
+                grads["sh"], grads["medium"])
+
+
+def render(params: dict, medium: torch.Tensor, cam: scenes.Camera, renderer: Renderer):
+    """Differentiable render: returns (image [3,H,W], depth [H,W], depth01 [H,W])."""
+    return _RenderFn.apply(renderer, cam, int(params["sh_degree"]), params["means"], params["log_scales"],
+                           params["quats"], params["opacity_logits"], params["sh"], medium)

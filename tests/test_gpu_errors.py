@@ -1,0 +1,86 @@
+"""Error paths on the GPU: every failure is made on the host (bad arguments,
+a partition that never reports) and must come back as a status code with
+the context still usable. Nothing here faults, traps or hangs the GPU: the
+device-side wait that is made to run out is bounded by spin_limit."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2411_19588_b300 import _abi
+from paper_2411_19588_b300 import render as R
+from paper_2411_19588_b300 import scenes
+
+from parity import gpu_forward
+
+pytestmark = pytest.mark.gpu
+
+
+def test_invalid_arguments_are_rejected(cuda_lib):
+    L = _abi.lib()
+    h = ctypes.c_void_p()
+    assert L.splash_create(ctypes.byref(_abi.Options(12, 12, 0, 0)), ctypes.byref(h)) == _abi.ERR_INVALID_ARG
+    r = R.Renderer()
+    st = r.state()
+    g, m, cam = scenes.tiny_scene(0)
+    params = R.params_to_device(g)
+    med = torch.tensor(m.as_array(), device="cuda")
+    gs = R.gaussians_struct(params)
+    c = R.camera_struct(cam)
+    img = torch.empty((3, cam.height, cam.width), device="cuda")
+    s = R._stream()
+    # sh degree out of range
+    gs.sh_degree = 4
+    assert L.splash_render_forward(r._ctx, st.handle, ctypes.byref(gs), med.data_ptr(), ctypes.byref(c), img.data_ptr(),
+                                   None, None, s) == _abi.ERR_INVALID_ARG
+    gs.sh_degree = 0
+    # zero-size image, null image, null medium
+    c.width = 0
+    assert L.splash_render_forward(r._ctx, st.handle, ctypes.byref(gs), med.data_ptr(), ctypes.byref(c), img.data_ptr(),
+                                   None, None, s) == _abi.ERR_INVALID_ARG
+    c.width = cam.width
+    assert L.splash_render_forward(r._ctx, st.handle, ctypes.byref(gs), med.data_ptr(), ctypes.byref(c), None, None, None,
+                                   s) == _abi.ERR_INVALID_ARG
+    assert L.splash_render_forward(r._ctx, st.handle, ctypes.byref(gs), None, ctypes.byref(c), img.data_ptr(), None, None,
+                                   s) == _abi.ERR_INVALID_ARG
+    # backward before any forward on a fresh state
+    st2 = r.state()
+    gr = _abi.Grads()
+    assert L.splash_render_backward(r._ctx, st2.handle, ctypes.byref(gs), med.data_ptr(), ctypes.byref(c),
+                                    img.data_ptr(), None, None, ctypes.byref(gr), s) == _abi.ERR_STATE
+    assert b"forward" in L.splash_last_error()
+    # the context still renders correctly afterwards
+    out = gpu_forward(r, g, m, cam)
+    assert np.isfinite(out["image"]).all()
+
+
+def test_nan_parameters_do_not_break_the_render(cuda_lib):
+    r = R.Renderer()
+    g, m, cam = scenes.tiny_scene(0)
+    g = g.copy()
+    g.means[::7] = np.nan
+    g.log_scales[1::11] = np.nan
+    out = gpu_forward(r, g, m, cam)
+    r.sync_status()
+    assert out["image"].shape == (3, cam.height, cam.width)
+
+
+def test_stalled_lookback_reports_timeout_and_context_survives(cuda_lib):
+    """Partition 2 of every sort pass never publishes; partition 3's bounded
+    wait runs out, the kernel sets the status word and returns, and the call
+    reports SPLASH_ERR_TIMEOUT. The same process then renders correctly."""
+    bad = R.Renderer(spin_limit=20000, test_stall_partition=2)
+    st = bad.state()
+    n = 5 * 4096 + 17
+    keys = torch.randint(0, 1 << 20, (n,), dtype=torch.int32, device="cuda")
+    with pytest.raises(_abi.SplashError) as ei:
+        bad.sort_pairs(st, keys, None, 20)
+        bad.sync_status()
+    assert ei.value.status == _abi.ERR_TIMEOUT
+    bad.sync_status()  # the status word was cleared
+    good = R.Renderer()
+    ko, vo = good.sort_pairs(good.state(), keys, None, 20)
+    good.sync_status()
+    ref = np.argsort(keys.cpu().numpy().astype(np.int64), kind="stable")
+    np.testing.assert_array_equal(vo.cpu().numpy(), ref)
