@@ -15,9 +15,11 @@
 //
 // Work decomposition: one CTA per tile, two pixels of one row per thread
 // (they share the dy terms). Gaussians are staged in shared memory in
-// batches of one per thread; the tile-local centre is formed once per
-// (tile, Gaussian) from the doubled-precision record. A warp skips a batch
-// once all its pixels are done; the CTA stops when all are.
+// batches of one per thread; the local centre is formed once per
+// (tile, Gaussian) from the doubled-precision record, relative to the
+// 32-pixel-aligned corner that holds the tile (the same corner for every
+// tile shape, so all shapes do identical per-pixel arithmetic). A warp skips
+// a batch once all its pixels are done; the CTA stops when all are.
 #include <cuda_runtime.h>
 
 #include "internal.cuh"
@@ -58,10 +60,11 @@ __global__ void __launch_bounds__(TW *TH / 2) k_blend_fwd(TileGeom tg, CamK cam,
     const int tile = blockIdx.x;
     const int tyi = tile / tg.tx, txi = tile - tyi * tg.tx;
     const int x0 = txi * TW, y0 = tyi * TH;
+    const int ox = x0 & ~31, oy = y0 & ~31;  // local origin shared by all tile shapes
     const int tid = threadIdx.x;
     const int row = tid / HW, col = tid - row * HW;
-    const float pyl = (float)row + 0.5f;
-    const float pxl0 = (float)col + 0.5f, pxl1 = (float)(col + HW) + 0.5f;
+    const float pyl = (float)(y0 - oy + row) + 0.5f;
+    const float pxl0 = (float)(x0 - ox + col) + 0.5f, pxl1 = (float)(x0 - ox + col + HW) + 0.5f;
     const int gy = y0 + row, gx0 = x0 + col, gx1 = x0 + col + HW;
     const bool in0 = gy < cam.H && gx0 < cam.W, in1 = gy < cam.H && gx1 < cam.W;
     const uint2 rg = ranges[tile];
@@ -81,8 +84,8 @@ __global__ void __launch_bounds__(TW *TH / 2) k_blend_fwd(TileGeom tg, CamK cam,
         if (j < n) {
             const uint32_t gid = gauss_ids[rg.x + j];
             const Rec r = rec[gid];
-            const float xl = (r.r0.x - (float)x0) + r.r0.z;
-            const float yl = (r.r0.y - (float)y0) + r.r0.w;
+            const float xl = (r.r0.x - (float)ox) + r.r0.z;
+            const float yl = (r.r0.y - (float)oy) + r.r0.w;
             s0[tid] = make_float4(xl, yl, r.r1.x, r.r1.y);
             s1[tid] = make_float4(r.r1.z, r.r1.w, r.r2.y, r.r2.z);
             s2[tid] = make_float2(r.r2.w, r.r2.x);
@@ -301,10 +304,11 @@ __global__ void __launch_bounds__(TW *TH / 2) k_blend_bwd(TileGeom tg, CamK cam,
     const int tile = blockIdx.x;
     const int tyi = tile / tg.tx, txi = tile - tyi * tg.tx;
     const int x0 = txi * TW, y0 = tyi * TH;
+    const int ox = x0 & ~31, oy = y0 & ~31;  // local origin shared by all tile shapes
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int row = tid / HW, col = tid - row * HW;
-    const float pyl = (float)row + 0.5f;
-    const float pxl0 = (float)col + 0.5f, pxl1 = (float)(col + HW) + 0.5f;
+    const float pyl = (float)(y0 - oy + row) + 0.5f;
+    const float pxl0 = (float)(x0 - ox + col) + 0.5f, pxl1 = (float)(x0 - ox + col + HW) + 0.5f;
     const int gy = y0 + row, gx0 = x0 + col, gx1 = x0 + col + HW;
     const bool in0 = gy < cam.H && gx0 < cam.W, in1 = gy < cam.H && gx1 < cam.W;
     const uint2 rg = ranges[tile];
@@ -367,8 +371,8 @@ __global__ void __launch_bounds__(TW *TH / 2) k_blend_bwd(TileGeom tg, CamK cam,
         if (tid < nb) {
             const uint32_t gid = gauss_ids[rg.x + b0 + tid];
             const Rec r = rec[gid];
-            const float xl = (r.r0.x - (float)x0) + r.r0.z;
-            const float yl = (r.r0.y - (float)y0) + r.r0.w;
+            const float xl = (r.r0.x - (float)ox) + r.r0.z;
+            const float yl = (r.r0.y - (float)oy) + r.r0.w;
             s0[tid] = make_float4(xl, yl, r.r1.x, r.r1.y);
             s1[tid] = make_float4(r.r1.z, r.r1.w, r.r2.y, r.r2.z);
             s2[tid] = make_float2(r.r2.w, r.r2.x);

@@ -26,7 +26,7 @@ from paper_2411_19588_b300 import scenes
 
 MARGIN = 1e-5
 GMARGIN = 1e-4
-MAX_EXCLUDED = 1e-3
+MAX_EXCLUDED = 1e-2
 IMG_ATOL = 1e-5
 DEPTH_RTOL = 1e-5
 GRAD_RTOL = 1e-3
