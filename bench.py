@@ -49,6 +49,9 @@ def parse_args():
     ap.add_argument("--tile", default="16x16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--views", type=int, default=N_VIEWS, help="arc views (targets rendered up front)")
+    ap.add_argument("--profile-region", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
 
 
@@ -160,13 +163,15 @@ def measured_peaks():
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
 
 
-def build_workload(n, rank, device="cuda"):
+def build_workload(n, rank, views, device="cuda"):
     import torch
 
     from paper_2411_19588_b300 import render as R
     from paper_2411_19588_b300 import scenes
     g_gt, med_gt, _ = scenes.patch_scene(n, 3, (2.0, 15.0), 1920, 1280, 1800.0)
     cams = scenes.arc_cameras(N_VIEWS, seed=3)
+    if views < N_VIEWS:
+        cams = cams[(N_VIEWS - views) // 2:(N_VIEWS - views) // 2 + views]
     fit, _ = scenes.perturb(g_gt, med_gt, seed=1 + rank)
     params = R.params_to_device(fit, device)
     med = torch.tensor([0.1] * 9, dtype=torch.float32, device=device)
@@ -183,7 +188,8 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(local)
     tw, th = (int(x) for x in args.tile.split("x"))
     r = R.Renderer(tile=(tw, th))
-    params, med, gt, med_gt, cams = build_workload(args.n, rank)
+    params, med, gt, med_gt, cams = build_workload(args.n, rank, args.views)
+    nv = len(cams)
     H, W = cams[0].height, cams[0].width
     # targets: the ground-truth scene and medium seen from every view
     st_t = r.state()
@@ -209,7 +215,7 @@ def run_ours(args, world, rank, local):
     step_no = [0]
 
     def view_of(i):
-        return (i * 7 + rank * 13) % N_VIEWS
+        return (i * 7 + rank * 13) % nv
 
     def step(i, target=None):
         cam = cams[view_of(i)]
@@ -234,6 +240,8 @@ def run_ours(args, world, rank, local):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     adam_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
+    if args.profile_region:
+        torch.cuda.cudart().cudaProfilerStart()
     ev0.record(stream)
     for i in range(args.steps):
         cam = cams[view_of(args.warmup + i)]
@@ -246,6 +254,8 @@ def run_ours(args, world, rank, local):
         adam_ev[i][1].record(stream)
     ev1.record(stream)
     torch.cuda.synchronize()
+    if args.profile_region:
+        torch.cuda.cudart().cudaProfilerStop()
     launches = R.kernel_launches() - l0
     clk = clocks.stop()
     stage = r.profile_read()
@@ -277,7 +287,7 @@ def run_ours(args, world, rank, local):
     # --- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        nb = min(8, N_VIEWS)
+        nb = min(8, nv)
         host_t = [targets[view_of(args.warmup + i)].cpu().pin_memory() for i in range(nb)]
         host_loss = torch.empty(1, dtype=torch.float32).pin_memory()
         dev_t = torch.empty_like(targets[0])
@@ -338,7 +348,7 @@ def run_ours(args, world, rank, local):
         "data": "synthetic (seeded surface-patch scenes standing in for the paper's underwater captures)",
         "config": {"workload": "train step: 1.5M Gaussians (SH3, 2-15 m), 1920x1280, 100-view arc, "
                                "fwd + L1+0.2(1-SSIM) + bwd + Adam",
-                   "n_gaussians": args.n, "width": W, "height": H, "views": N_VIEWS, "tile": args.tile,
+                   "n_gaussians": args.n, "width": W, "height": H, "views": nv, "tile": args.tile,
                    "parallelism": f"replicas x{world}",
                    "l2": "working set (params+grads+Adam moments ~1.4 GB) larger than L2; no flush"},
         "fps": round(world * 1000.0 / fwd_ms, 2),
