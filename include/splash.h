@@ -226,6 +226,30 @@ splash_status splash_profile_read(splash_ctx *ctx, double *ms, int64_t *counts);
 /* Number of kernels this library has launched in this process so far. */
 uint64_t splash_kernel_launches(void);
 
+/* The pair sort above for callers that cannot allocate device memory
+ * (no counterpart in the paper; it exists for library users). Some callers
+ * may not call cudaMalloc at all: code embedded in a host application whose
+ * device memory is owned and budgeted by that application, or latency-bound
+ * code that cannot take the synchronisation an allocation may imply. This
+ * entry point allocates nothing: its scratch (ping-pong pair buffers, digit
+ * histograms, look-back flags, a status word) is one static device array of
+ * about 9.1 MB that every GPU loading this library holds until the process
+ * exits. Same arguments and result as splash_sort_pairs_u32, without the
+ * context and state: keys_in/vals_in (device, n; vals_in NULL = 0..n-1) are
+ * left unchanged, keys_out/vals_out (device, n) receive the pairs sorted
+ * stably on key bits [0, key_bits). n must be at most 1,048,576 (2^20);
+ * larger n returns SPLASH_ERR_INVALID_ARG. keys_in must be 16-byte aligned.
+ * status_out (device uint32, may be NULL) receives 0, or SPLASH_ERR_TIMEOUT's
+ * kernel bit (1) if a bounded device-side wait gave up. All calls share the
+ * one array (each call clears what must start at zero), so calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller. The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress with that device current);
+ * make that first call before any stream capture. */
+splash_status splash_sort_pairs_u32_noalloc(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_out,
+                                            uint32_t *vals_out, int64_t n, int32_t key_bits, uint32_t *status_out,
+                                            void *stream);
+
 /* Synchronise `stream` and report any error a kernel recorded since the last check. */
 splash_status splash_sync_status(splash_ctx *ctx, void *stream);
 

@@ -87,7 +87,11 @@ _SIGS = {
     "splash_state_copy": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p],
     "splash_profile_enable": [ctypes.c_void_p, ctypes.c_int32],
     "splash_profile_read": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
+    "splash_sort_pairs_u32_noalloc": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p],
 }
+
+NOALLOC_MAX_PAIRS = 1 << 20
 
 STAGES = ["preprocess", "depth_sort", "scan", "emit", "tile_sort", "ranges", "blend_fwd", "blend_bwd",
           "preprocess_bwd", "medium_reduce", "loss"]
