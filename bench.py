@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--views", type=int, default=N_VIEWS, help="arc views (targets rendered up front)")
+    ap.add_argument("--step", choices=["fused", "unfused"], default="fused",
+                    help="fused: backward and Adam in one kernel; unfused: backward, then the multi-group Adam")
     ap.add_argument("--profile-region", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -87,6 +89,66 @@ def barrier(world: int):
         dist.barrier()
 
 
+class _Nvml:
+    """Just enough NVML for clock sampling: pynvml when installed, else the
+    driver's libnvidia-ml through ctypes."""
+    SM = 1  # NVML_CLOCK_SM
+
+    def __init__(self, cuda_index: int):
+        import ctypes
+        self.ct = ctypes
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            self.py = pynvml
+        except ImportError:
+            self.py = None
+            self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+            rc = self.lib.nvmlInit_v2()
+            if rc != 0:
+                raise RuntimeError(f"nvmlInit_v2 returned {rc}")
+        self.handle = self._handle(cuda_index)
+
+    def _handle(self, cuda_index):
+        import torch
+        p = torch.cuda.get_device_properties(cuda_index)
+        bus = f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+        if self.py:
+            try:
+                return self.py.nvmlDeviceGetHandleByPciBusId(bus)
+            except Exception:
+                return self.py.nvmlDeviceGetHandleByIndex(cuda_index)
+        h = self.ct.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), self.ct.byref(h)) != 0:
+            if self.lib.nvmlDeviceGetHandleByIndex_v2(self.ct.c_uint(cuda_index), self.ct.byref(h)) != 0:
+                raise RuntimeError("no NVML handle for the device")
+        return h
+
+    def sm_clock(self, maximum=False):
+        if self.py:
+            f = self.py.nvmlDeviceGetMaxClockInfo if maximum else self.py.nvmlDeviceGetClockInfo
+            return f(self.handle, self.SM)
+        v = self.ct.c_uint()
+        f = self.lib.nvmlDeviceGetMaxClockInfo if maximum else self.lib.nvmlDeviceGetClockInfo
+        rc = f(self.handle, self.ct.c_int(self.SM), self.ct.byref(v))
+        if rc != 0:
+            raise RuntimeError(f"NVML clock query returned {rc}")
+        return v.value
+
+    def reasons(self):
+        if self.py:
+            f = getattr(self.py, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                self.py.nvmlDeviceGetCurrentClocksThrottleReasons
+            return f(self.handle)
+        v = self.ct.c_ulonglong()
+        f = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        rc = f(self.handle, self.ct.byref(v))
+        if rc != 0:
+            raise RuntimeError(f"NVML reasons query returned {rc}")
+        return v.value
+
+
 class ClockSampler:
     """SM clock and clock-event (throttle) reasons sampled through NVML every
     few milliseconds in a background thread during the timed region."""
@@ -98,41 +160,24 @@ class ClockSampler:
         self.interval = interval_s
         self.samples = []
         self.thread = None
-        self.handle = None
-
-    def _open(self):
-        import pynvml
-        import torch
-        pynvml.nvmlInit()
-        try:
-            p = torch.cuda.get_device_properties(self.cuda_index)
-            bus = f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
-            return pynvml.nvmlDeviceGetHandleByPciBusId(bus)
-        except Exception:
-            return pynvml.nvmlDeviceGetHandleByIndex(self.cuda_index)
+        self.error = None
 
     def start(self):
         import threading
         try:
-            import pynvml
-            self.handle = self._open()
-            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.handle, pynvml.NVML_CLOCK_SM)
-        except Exception:
-            self.handle = None
+            self.nvml = _Nvml(self.cuda_index)
+            self.max_mhz = self.nvml.sm_clock(maximum=True)
+        except Exception as e:  # no NVML: report why instead of a clock record
+            self.error = f"nvml: {type(e).__name__}: {e}"
             return
         self.stop_flag = False
 
         def run():
-            import pynvml
-            get_reasons = getattr(pynvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
-                pynvml.nvmlDeviceGetCurrentClocksThrottleReasons
             while not self.stop_flag:
                 try:
-                    sm = pynvml.nvmlDeviceGetClockInfo(self.handle, pynvml.NVML_CLOCK_SM)
-                    rs = get_reasons(self.handle)
-                    self.samples.append((sm, rs))
-                except Exception:
-                    pass
+                    self.samples.append((self.nvml.sm_clock(), self.nvml.reasons()))
+                except Exception as e:
+                    self.error = f"nvml sample: {type(e).__name__}: {e}"
                 time.sleep(self.interval)
 
         self.thread = threading.Thread(target=run, daemon=True)
@@ -140,11 +185,11 @@ class ClockSampler:
 
     def stop(self):
         if self.thread is None:
-            return None
+            return {"error": self.error} if self.error else None
         self.stop_flag = True
         self.thread.join(timeout=2)
         if not self.samples:
-            return None
+            return {"error": self.error or "no samples"}
         sm = [a for a, _ in self.samples]
         reasons = set()
         for _, rs in self.samples:
@@ -200,14 +245,13 @@ def run_ours(args, world, rank, local):
     del gt
     torch.cuda.synchronize()
 
-    names = list(R.PARAM_NAMES) + ["medium"]
     tensors = {k: params[k] for k in R.PARAM_NAMES}
     tensors["medium"] = med
-    grads = {k: torch.zeros_like(v) for k, v in tensors.items()}
     mom = {k: torch.zeros_like(v) for k, v in tensors.items()}
     vel = {k: torch.zeros_like(v) for k, v in tensors.items()}
+    grads = {k: torch.zeros_like(v) for k, v in tensors.items()} if args.step == "unfused" else None
     groups = [{"param": tensors[k], "grad": grads[k], "m": mom[k], "v": vel[k], "lr": LR[k],
-               "clamp_min": 0.0 if k == "medium" else None} for k in names]
+               "clamp_min": 0.0 if k == "medium" else None} for k in tensors] if grads else None
     st = r.state()
     image = torch.empty((3, H, W), device="cuda")
     depth = torch.empty((H, W), device="cuda")
@@ -218,12 +262,16 @@ def run_ours(args, world, rank, local):
         return (i * 7 + rank * 13) % nv
 
     def step(i, target=None):
+        """forward, loss, then the fused backward + Adam (parameters updated in place)"""
         cam = cams[view_of(i)]
         r.forward(st, params, med, cam, image, depth, depth01)
         loss, gimg = r.loss(st, image, targets[view_of(i)] if target is None else target, LAMBDA_SSIM)
-        r.backward(st, params, med, cam, gimg, None, None, grads)
         step_no[0] += 1
-        R.adam_step(groups, step_no[0])
+        if grads is None:
+            r.backward_adam(st, params, med, cam, gimg, mom, vel, LR, step_no[0])
+        else:
+            r.backward(st, params, med, cam, gimg, None, None, grads)
+            R.adam_step(groups, step_no[0])
         return loss
 
     stream = torch.cuda.current_stream()
@@ -238,20 +286,12 @@ def run_ours(args, world, rank, local):
     r.profile(True)
     l0 = R.kernel_launches()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    adam_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
     if args.profile_region:
         torch.cuda.cudart().cudaProfilerStart()
     ev0.record(stream)
     for i in range(args.steps):
-        cam = cams[view_of(args.warmup + i)]
-        r.forward(st, params, med, cam, image, depth, depth01)
-        loss, gimg = r.loss(st, image, targets[view_of(args.warmup + i)], LAMBDA_SSIM)
-        r.backward(st, params, med, cam, gimg, None, None, grads)
-        step_no[0] += 1
-        adam_ev[i][0].record(stream)
-        R.adam_step(groups, step_no[0])
-        adam_ev[i][1].record(stream)
+        step(args.warmup + i)
     ev1.record(stream)
     torch.cuda.synchronize()
     if args.profile_region:
@@ -261,7 +301,6 @@ def run_ours(args, world, rank, local):
     stage = r.profile_read()
     r.profile(False)
     ms_step = ev0.elapsed_time(ev1) / args.steps
-    adam_ms = sum(a.elapsed_time(b) for a, b in adam_ev) / args.steps
     ms_step_max = max_over_ranks(ms_step, world)
 
     # --- forward-only frames per second
@@ -295,12 +334,7 @@ def run_ours(args, world, rank, local):
         t0 = time.perf_counter()
         for i in range(args.steps):
             dev_t.copy_(host_t[i % nb], non_blocking=True)
-            cam = cams[view_of(args.warmup + i)]
-            r.forward(st, params, med, cam, image, depth, depth01)
-            loss, gimg = r.loss(st, image, dev_t, LAMBDA_SSIM)
-            r.backward(st, params, med, cam, gimg, None, None, grads)
-            step_no[0] += 1
-            R.adam_step(groups, step_no[0])
+            loss = step(args.warmup + i, target=dev_t)
             host_loss.copy_(loss, non_blocking=True)
             torch.cuda.current_stream().synchronize()
         e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
@@ -314,13 +348,13 @@ def run_ours(args, world, rank, local):
     fp32_peak_tflops = sm_count * 128 * 2 * f_mhz * 1e6 / 1e12
     n_total = sum(t.numel() for t in tensors.values())
     per_launch = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in stage.items()}
-    per_launch["adam"] = adam_ms
     work = {
         "blend_fwd": ("alu", FLOP_PER_PAIR_FWD * walk, "TFLOP/s"),
         "blend_bwd": ("alu", FLOP_PER_PAIR_BWD * last, "TFLOP/s"),
-        "adam": ("hbm", 28.0 * n_total, "GB/s"),
         "preprocess": ("hbm", (236 + 68) * args.n, "GB/s"),
-        "preprocess_bwd": ("hbm", (236 + 48 + 236) * args.n, "GB/s"),
+        # fused adjoint + Adam: parameters, both moments and the blend accumulators
+        # read; parameters and moments written
+        "preprocess_bwd": ("hbm", ((3 * 236 + 48 + 3 * 236) if grads is None else (236 + 48 + 236)) * args.n, "GB/s"),
         "tile_sort": ("hbm", 2 * 16.0 * n_keys + 4.0 * n_keys, "GB/s"),
         "loss": ("hbm", 4.0 * 3 * H * W * 9, "GB/s"),
     }
@@ -348,7 +382,7 @@ def run_ours(args, world, rank, local):
         "data": "synthetic (seeded surface-patch scenes standing in for the paper's underwater captures)",
         "config": {"workload": "train step: 1.5M Gaussians (SH3, 2-15 m), 1920x1280, 100-view arc, "
                                "fwd + L1+0.2(1-SSIM) + bwd + Adam",
-                   "n_gaussians": args.n, "width": W, "height": H, "views": nv, "tile": args.tile,
+                   "n_gaussians": args.n, "width": W, "height": H, "views": nv, "tile": args.tile, "step": args.step,
                    "parallelism": f"replicas x{world}",
                    "l2": "working set (params+grads+Adam moments ~1.4 GB) larger than L2; no flush"},
         "fps": round(world * 1000.0 / fwd_ms, 2),
@@ -357,7 +391,7 @@ def run_ours(args, world, rank, local):
                      "unit": unit, "frac": round(achieved / peak, 4), "traffic": None, "peak_source": note},
         "stages_ms": stages_ms,
         "pairs": {"walked_fwd": int(walk), "walked_bwd": int(last), "keys": int(n_keys)},
-        "gpu_launches": int(launches + args.steps),
+        "gpu_launches": int(launches),
         "clocks": clk,
         "e2e": e2e,
     }

@@ -124,6 +124,40 @@ splash_status splash_render_backward(splash_ctx *ctx, splash_state *st, const sp
                                      const float *dL_dimage, const float *dL_ddepth,
                                      const float *dL_ddepth01, const splash_grads *grads, void *stream);
 
+/* Training step, fused: the backward of the last forward on `st` followed
+ * by one Adam step (Sec. IV-C: Adam over all Gaussian and medium
+ * parameters) applied in place, without writing the parameter gradients to
+ * memory. params: the device buffers the forward read (same layouts as
+ * splash_gaussians; medium [9]); they are updated in place. adam->m and
+ * adam->v: first and second moments, same layouts, updated in place.
+ * lr_*: per-group learning rates; beta1, beta2, eps: Adam constants; step:
+ * 1-based step count for the bias corrections; if clamp_medium is non-zero
+ * the medium parameters are clamped at >= medium_min after the step.
+ * Every Gaussian steps (a zero gradient still moves its moments), as in
+ * dense Adam. grad_medium (device float[9], may be NULL) receives the medium
+ * gradient. Upstream gradients as in splash_render_backward. */
+typedef struct {
+    float *means;
+    float *log_scales;
+    float *quats;
+    float *opacity_logits;
+    float *sh;
+    float *medium;
+} splash_param_buffers;
+typedef struct {
+    splash_param_buffers m;
+    splash_param_buffers v;
+    float lr_means, lr_log_scales, lr_quats, lr_opacity_logits, lr_sh, lr_medium;
+    float beta1, beta2, eps;
+    int32_t step;
+    int32_t clamp_medium;
+    float medium_min;
+} splash_adam_config;
+splash_status splash_render_backward_adam(splash_ctx *ctx, splash_state *st, const splash_param_buffers *params,
+                                          int64_t n, int32_t sh_degree, const splash_camera *cam,
+                                          const float *dL_dimage, const float *dL_ddepth, const float *dL_ddepth01,
+                                          const splash_adam_config *adam, float *grad_medium, void *stream);
+
 /* Read-only views of the forward state, for tests and diagnostics. Device
  * pointers stay valid until the next forward on the state. */
 typedef struct {

@@ -63,6 +63,19 @@ class AdamGroup(ctypes.Structure):
                 ("has_clamp", ctypes.c_int32)]
 
 
+class ParamBuffers(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("opacity_logits", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("medium", ctypes.c_void_p)]
+
+
+class AdamConfig(ctypes.Structure):
+    _fields_ = [("m", ParamBuffers), ("v", ParamBuffers), ("lr_means", ctypes.c_float),
+                ("lr_log_scales", ctypes.c_float), ("lr_quats", ctypes.c_float), ("lr_opacity_logits", ctypes.c_float),
+                ("lr_sh", ctypes.c_float), ("lr_medium", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("step", ctypes.c_int32),
+                ("clamp_medium", ctypes.c_int32), ("medium_min", ctypes.c_float)]
+
+
 ADAM_MAX_GROUPS = 8
 
 _SIGS = {
@@ -76,6 +89,9 @@ _SIGS = {
                                ctypes.POINTER(Camera), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                ctypes.POINTER(Grads), ctypes.c_void_p],
     "splash_state_get_info": [ctypes.c_void_p, ctypes.POINTER(StateInfo)],
+    "splash_render_backward_adam": [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ParamBuffers), ctypes.c_int64,
+                                    ctypes.c_int32, ctypes.POINTER(Camera), ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.POINTER(AdamConfig), ctypes.c_void_p, ctypes.c_void_p],
     "splash_loss_l1_ssim": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                             ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p,
                             ctypes.c_void_p],

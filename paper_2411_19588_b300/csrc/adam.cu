@@ -21,17 +21,13 @@ struct AdamTable {
     splash_adam_group g[SPLASH_ADAM_MAX_GROUPS];
     int64_t block_start[SPLASH_ADAM_MAX_GROUPS + 1];
     int n;
-    float b1, b2, eps, bc1, bc2;
+    AdamHyper h;
 };
 
 __device__ __forceinline__ void adam1(float &p, float g, float &m, float &v, float lr, const AdamTable &t,
                                       const splash_adam_group &G)
 {
-    m = fmaf(t.b1, m, (1.f - t.b1) * g);
-    v = fmaf(t.b2, v, (1.f - t.b2) * g * g);
-    const float mh = m / t.bc1;
-    const float vh = v / t.bc2;
-    p -= lr * mh / (sqrtf(vh) + t.eps);
+    adam_update(p, g, m, v, lr, t.h);
     if (G.has_clamp) p = fmaxf(p, G.clamp_min);
 }
 
@@ -83,11 +79,7 @@ extern "C" splash_status splash_adam_step(const splash_adam_group *groups, int32
     }
     AdamTable t{};
     t.n = n_groups;
-    t.b1 = beta1;
-    t.b2 = beta2;
-    t.eps = eps;
-    t.bc1 = (float)(1.0 - pow((double)beta1, step));
-    t.bc2 = (float)(1.0 - pow((double)beta2, step));
+    t.h = make_adam_hyper(beta1, beta2, eps, step);
     int64_t blocks = 0;
     for (int i = 0; i < n_groups; i++) {
         const splash_adam_group &G = groups[i];

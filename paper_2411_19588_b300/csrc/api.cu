@@ -134,7 +134,7 @@ struct splash_state {
     // per pixel
     Buf fT, aA, zh, nlast, nwalk;
     // backward
-    Buf gacc, tile_med, block_med;
+    Buf gacc, tile_med, block_med, gmed, red_scratch;
     // loss / standalone sort
     Buf loss_scratch, tmp_k, tmp_v;
     Buf small;  // [0] = pair count K, [1..] spare
@@ -420,6 +420,7 @@ splash_status splash_render_backward(splash_ctx *ctx, splash_state *st, const sp
     ENSURE(st->gacc, sizeof(GAcc) * std::max<int64_t>(n, 1));
     ENSURE(st->tile_med, 4 * 6 * (size_t)ntiles);
     ENSURE(st->block_med, 4 * 9 * (size_t)nblocks);
+    ENSURE(st->red_scratch, 4 * 16 * (size_t)kColsumParts);
     SPLASH_CUDA_TRY(cudaMemsetAsync(st->gacc.p, 0, sizeof(GAcc) * (size_t)n, s));
     SPLASH_CUDA_TRY(cudaMemsetAsync(st->block_med.p, 0, 4 * 9 * (size_t)nblocks, s));
     const CamK ck = make_cam(*cam);
@@ -437,8 +438,67 @@ splash_status splash_render_backward(splash_ctx *ctx, splash_state *st, const sp
     }
     if (grads->medium) {
         Stage t(ctx->prof, SPLASH_STAGE_MEDIUM_REDUCE, s);
-        launch_medium_reduce(st->tile_med.as<float>(), ntiles, st->block_med.as<float>(), nb, grads->medium, s);
+        launch_medium_reduce(st->tile_med.as<float>(), ntiles, st->block_med.as<float>(), nb, grads->medium,
+                             st->red_scratch.as<float>(), s);
     }
+    SPLASH_CUDA_TRY(cudaGetLastError());
+    return SPLASH_OK;
+}
+
+splash_status splash_render_backward_adam(splash_ctx *ctx, splash_state *st, const splash_param_buffers *params,
+                                          int64_t n, int32_t sh_degree, const splash_camera *cam,
+                                          const float *dL_dimage, const float *dL_ddepth, const float *dL_ddepth01,
+                                          const splash_adam_config *adam, float *grad_medium, void *stream)
+{
+    if (!ctx || !st || st->ctx != ctx) return fail(SPLASH_ERR_INVALID_ARG, "bad context or state");
+    if (!params || !adam || !dL_dimage) return fail(SPLASH_ERR_INVALID_ARG, "null params, adam config or dL_dimage");
+    splash_gaussians g{params->means, params->log_scales, params->quats, params->opacity_logits, params->sh, n, sh_degree};
+    splash_status rc;
+    if ((rc = check_gaussians(&g)) != SPLASH_OK) return rc;
+    if ((rc = check_camera(cam)) != SPLASH_OK) return rc;
+    if (!params->medium) return fail(SPLASH_ERR_INVALID_ARG, "null medium");
+    if (adam->step < 1) return fail(SPLASH_ERR_INVALID_ARG, "Adam step must be >= 1");
+    const splash_param_buffers *mv[2] = {&adam->m, &adam->v};
+    for (int w = 0; w < 2; w++) {
+        const splash_param_buffers &b = *mv[w];
+        if (!b.medium || (n > 0 && (!b.means || !b.log_scales || !b.quats || !b.opacity_logits || !b.sh)))
+            return fail(SPLASH_ERR_INVALID_ARG, "null Adam moment buffer");
+        if (n > 0 && (reinterpret_cast<uintptr_t>(b.quats) & 15))
+            return fail(SPLASH_ERR_INVALID_ARG, "quaternion moments must be 16-byte aligned");
+    }
+    if (!st->has_forward || st->n != n || st->W != cam->width || st->H != cam->height)
+        return fail(SPLASH_ERR_STATE, "backward does not match the last forward on this state");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int ntiles = st->tg.tx * st->tg.ty;
+    const int nblocks = preprocess_bwd_blocks(std::max<int64_t>(n, 1));
+    ENSURE(st->gacc, sizeof(GAcc) * std::max<int64_t>(n, 1));
+    ENSURE(st->tile_med, 4 * 6 * (size_t)ntiles);
+    ENSURE(st->block_med, 4 * 9 * (size_t)nblocks);
+    ENSURE(st->gmed, 4 * 16);
+    ENSURE(st->red_scratch, 4 * 16 * (size_t)kColsumParts);
+    SPLASH_CUDA_TRY(cudaMemsetAsync(st->gacc.p, 0, sizeof(GAcc) * (size_t)n, s));
+    SPLASH_CUDA_TRY(cudaMemsetAsync(st->block_med.p, 0, 4 * 9 * (size_t)nblocks, s));
+    const CamK ck = make_cam(*cam);
+    {
+        Stage t(ctx->prof, SPLASH_STAGE_BLEND_BWD, s);
+        launch_blend_bwd(st->tg, ck, st->ranges.as<uint2>(), st->gauss_ids, st->rec.as<Rec>(), params->medium,
+                         st->fT.as<float>(), st->aA.as<float>(), st->zh.as<float>(), st->nlast.as<uint32_t>(), dL_dimage,
+                         dL_ddepth, dL_ddepth01, st->gacc.as<GAcc>(), st->tile_med.as<float>(), s);
+    }
+    int nb = 0;
+    {
+        Stage t(ctx->prof, SPLASH_STAGE_PREPROCESS_BWD, s);
+        launch_preprocess_bwd_adam(n, sh_degree, *params, params->medium, ck, st->gacc.as<GAcc>(),
+                                   st->depth_key.as<uint32_t>(), *adam, st->block_med.as<float>(), &nb, s);
+    }
+    {
+        Stage t(ctx->prof, SPLASH_STAGE_MEDIUM_REDUCE, s);
+        launch_medium_reduce(st->tile_med.as<float>(), ntiles, st->block_med.as<float>(), nb, st->gmed.as<float>(),
+                             st->red_scratch.as<float>(), s);
+        launch_medium_adam(params->medium, st->gmed.as<float>(), *adam, s);
+    }
+    if (grad_medium)
+        SPLASH_CUDA_TRY(cudaMemcpyAsync(grad_medium, st->gmed.p, 9 * sizeof(float), cudaMemcpyDeviceToDevice, s));
     SPLASH_CUDA_TRY(cudaGetLastError());
     return SPLASH_OK;
 }

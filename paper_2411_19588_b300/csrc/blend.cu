@@ -45,7 +45,7 @@ struct Tile {
 };
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH / 2) k_blend_fwd(TileGeom tg, CamK cam, const uint2 *__restrict__ ranges,
+__global__ void __launch_bounds__(TW *TH / 2, 10) k_blend_fwd(TileGeom tg, CamK cam, const uint2 *__restrict__ ranges,
                                                          const uint32_t *__restrict__ gauss_ids, const Rec *__restrict__ rec,
                                                          const float *__restrict__ medium, float *__restrict__ image,
                                                          float *__restrict__ depth, float *__restrict__ depth01,
@@ -281,7 +281,7 @@ __device__ __forceinline__ bool pix_grad(PixB &p, int j, float dx, float dy, flo
 }
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH / 2) k_blend_bwd(TileGeom tg, CamK cam, const uint2 *__restrict__ ranges,
+__global__ void __launch_bounds__(TW *TH / 2, 8) k_blend_bwd(TileGeom tg, CamK cam, const uint2 *__restrict__ ranges,
                                                          const uint32_t *__restrict__ gauss_ids, const Rec *__restrict__ rec,
                                                          const float *__restrict__ medium, const float *__restrict__ final_T,
                                                          const float *__restrict__ acc_alpha, const float *__restrict__ zhat,
@@ -358,8 +358,29 @@ __global__ void __launch_bounds__(TW *TH / 2) k_blend_bwd(TileGeom tg, CamK cam,
         }
         p.S = S;
     }
+    // per-tile medium partials {beta_B[3], B_inf[3]}, reduced now so that the
+    // accumulators do not stay live through the main loop
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        float a = mBB[ch], b = mB[ch];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if (lane == 0) {
+            s_med[warp][ch] = a;
+            s_med[warp][3 + ch] = b;
+        }
+    }
     __syncthreads();
     atomicMax(&s_maxlast, max(P[0].last, P[1].last));
+    if (tid < 6) {
+        float v = 0.f;
+#pragma unroll
+        for (int w = 0; w < NW; w++) v += s_med[w][tid];
+        tile_medium[6 * tile + tid] = v;
+    }
     const int my_field = reduce10_field(lane);
     __syncthreads();
     const int maxlast = s_maxlast;
@@ -415,27 +436,6 @@ __global__ void __launch_bounds__(TW *TH / 2) k_blend_bwd(TileGeom tg, CamK cam,
         }
     }
 
-    // per-tile medium partials: {beta_B[3], B_inf[3]}
-#pragma unroll
-    for (int ch = 0; ch < 3; ch++) {
-        float a = mBB[ch], b = mB[ch];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            b += __shfl_xor_sync(0xffffffffu, b, o);
-        }
-        if (lane == 0) {
-            s_med[warp][ch] = a;
-            s_med[warp][3 + ch] = b;
-        }
-    }
-    __syncthreads();
-    if (tid < 6) {
-        float v = 0.f;
-#pragma unroll
-        for (int w = 0; w < NW; w++) v += s_med[w][tid];
-        tile_medium[6 * tile + tid] = v;
-    }
 }
 
 template <int TW, int TH>

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <string>
@@ -56,6 +57,34 @@ struct __align__(16) GAcc {
     float4 a0, a1, a2;
 };
 
+// ---- one Adam step (Kingma & Ba), shared by the standalone and the fused kernels
+struct AdamHyper {
+    float b1, b2, eps;
+    float rbc1, rsbc2;  // 1 / (1 - b1^step), 1 / sqrt(1 - b2^step): the bias corrections
+};
+inline AdamHyper make_adam_hyper(float b1, float b2, float eps, int step)
+{
+    AdamHyper h;
+    h.b1 = b1;
+    h.b2 = b2;
+    h.eps = eps;
+    double p1 = 1.0, p2 = 1.0;
+    for (int k = 0; k < step; k++) {
+        p1 *= b1;
+        p2 *= b2;
+    }
+    h.rbc1 = (float)(1.0 / (1.0 - p1));
+    h.rsbc2 = (float)(1.0 / sqrt(1.0 - p2));
+    return h;
+}
+// p -= lr * m_hat / (sqrt(v_hat) + eps) with m_hat = m / bc1, sqrt(v_hat) = sqrt(v) / sqrt(bc2)
+__device__ __forceinline__ void adam_update(float &p, float g, float &m, float &v, float lr, const AdamHyper &h)
+{
+    m = fmaf(h.b1, m, (1.f - h.b1) * g);
+    v = fmaf(h.b2, v, (1.f - h.b2) * g * g);
+    p -= __fdividef(lr * h.rbc1 * m, fmaf(sqrtf(v), h.rsbc2, h.eps));
+}
+
 // device status word bits
 enum : uint32_t { kStatusTimeout = 1u, kStatusCapacity = 2u };
 
@@ -104,9 +133,20 @@ void launch_blend_bwd(const TileGeom &tg, const CamK &cam, const uint2 *ranges, 
 void launch_preprocess_bwd(int64_t n, const splash_gaussians &g, const float *medium, const CamK &cam,
                            const GAcc *acc, const uint32_t *depth_key, const splash_grads &out,
                            float *block_medium, int *n_blocks_out, cudaStream_t s);
+// scratch: kColsumParts * 15 floats
 void launch_medium_reduce(const float *tile_medium, int ntiles, const float *block_medium, int nblocks,
-                          float *d_medium, cudaStream_t s);
+                          float *d_medium, float *scratch, cudaStream_t s);
+void launch_preprocess_bwd_adam(int64_t n, int sh_degree, const splash_param_buffers &p, const float *medium,
+                                const CamK &cam, const GAcc *acc, const uint32_t *dk, const splash_adam_config &cfg,
+                                float *block_medium, int *n_blocks_out, cudaStream_t s);
+void launch_medium_adam(float *medium, const float *grad, const splash_adam_config &cfg, cudaStream_t s);
 int preprocess_bwd_blocks(int64_t n);
+
+// Deterministic column sums of a row-major [rows][cols] float table (cols <=
+// 16), first stage: kColsumParts CTAs each write one row of partial sums to
+// part[kColsumParts][cols].
+constexpr int kColsumParts = 64;
+void launch_colsum_partial(const float *data, int rows, int cols, float *part, cudaStream_t s);
 
 void launch_ssim_loss(const float *img, const float *tgt, int C, int H, int W, float lam, float *loss,
                       float *grad, float *scratch, cudaStream_t s);

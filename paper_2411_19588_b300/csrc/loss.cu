@@ -166,25 +166,17 @@ __global__ void __launch_bounds__(256) k_ssim_pass2(const float *__restrict__ X,
     }
 }
 
-__global__ void k_loss_final(const float *__restrict__ partial, int nblocks, double inv_count, float lam, float *__restrict__ loss)
+// Final stage: the kColsumParts partial rows of (sum |x-y|, sum SSIM) in a
+// fixed order, then the loss.
+__global__ void k_loss_final(const float *__restrict__ part, double inv_count, float lam, float *__restrict__ loss)
 {
-    __shared__ double s[2][256];
+    if (threadIdx.x != 0) return;
     double l1 = 0.0, ss = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += 256) {
-        l1 += partial[2 * b];
-        ss += partial[2 * b + 1];
+    for (int p = 0; p < kColsumParts; p++) {
+        l1 += part[2 * p];
+        ss += part[2 * p + 1];
     }
-    s[0][threadIdx.x] = l1;
-    s[1][threadIdx.x] = ss;
-    __syncthreads();
-    for (int st = 128; st > 0; st >>= 1) {
-        if (threadIdx.x < st) {
-            s[0][threadIdx.x] += s[0][threadIdx.x + st];
-            s[1][threadIdx.x] += s[1][threadIdx.x + st];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *loss = (float)(s[0][0] * inv_count + (double)lam * (1.0 - s[1][0] * inv_count));
+    *loss = (float)(l1 * inv_count + (double)lam * (1.0 - ss * inv_count));
 }
 
 Win make_window()
@@ -205,7 +197,7 @@ Win make_window()
 size_t ssim_scratch_floats(int C, int H, int W)
 {
     const size_t nb = (size_t)((W + kTX - 1) / kTX) * ((H + kTY - 1) / kTY) * C;
-    return 3 * (size_t)C * H * W + 2 * nb + 64;
+    return 3 * (size_t)C * H * W + 2 * nb + 2 * kColsumParts + 64;
 }
 
 void launch_ssim_loss(const float *img, const float *tgt, int C, int H, int W, float lam, float *loss, float *grad,
@@ -219,7 +211,9 @@ void launch_ssim_loss(const float *img, const float *tgt, int C, int H, int W, f
     k_ssim_pass1<<<grid, 256, 0, s>>>(img, tgt, W, H, win, (float)(-lam * inv), d_mu, d_xx, d_xy, partial);
     count_launch();
     const int nb = grid.x * grid.y * grid.z;
-    k_loss_final<<<1, 256, 0, s>>>(partial, nb, inv, lam, loss);
+    float *part2 = partial + 2 * nb;
+    launch_colsum_partial(partial, nb, 2, part2, s);
+    k_loss_final<<<1, 32, 0, s>>>(part2, inv, lam, loss);
     count_launch();
     if (grad) k_ssim_pass2<<<grid, 256, 0, s>>>(img, tgt, W, H, win, (float)inv, d_mu, d_xx, d_xy, grad);
     if (grad) count_launch();

@@ -4,7 +4,8 @@
 //                        water attenuation folded into an effective colour.
 //   k_preprocess_bwd  -- the adjoint of the above, from the per-Gaussian
 //                        accumulators of the blend backward to the parameters.
-//   k_medium_reduce   -- deterministic sum of the medium-gradient partials.
+//   k_preprocess_bwd_adam -- the same adjoint followed by Adam in place.
+//   k_medium_final    -- deterministic sum of the medium-gradient partials.
 //
 // Passages: Gaussian parameters and the affine (EWA) projection, Sec. III-A
 // (the sentence after Eq. 2); opacity sigmoid, Eq. 2; colour via spherical
@@ -173,6 +174,32 @@ __device__ __forceinline__ void stage_sh(const float *__restrict__ sh, int64_t w
     for (int f = done + lane; f < total; f += 32) dst[(f / KC) * ROW + (f % KC)] = __ldg(src + f);
 }
 
+// Inverse of stage_sh: write one warp's rows back to HBM with coalesced
+// 16-byte stores.
+template <int KC>
+__device__ __forceinline__ void unstage_rows(float *__restrict__ dst_base, int64_t wbase, int cnt, int lane, const float *src)
+{
+    constexpr int ROW = KC + 1;
+    float *dst = dst_base + wbase * KC;
+    const int total = cnt * KC;
+    int done = 0;
+    if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+        const int n4 = total >> 2;
+        float4 *d4 = reinterpret_cast<float4 *>(dst);
+        for (int e = lane; e < n4; e += 32) {
+            float vv[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int f = 4 * e + k;
+                vv[k] = src[(f / KC) * ROW + (f % KC)];
+            }
+            d4[e] = make_float4(vv[0], vv[1], vv[2], vv[3]);
+        }
+        done = n4 * 4;
+    }
+    for (int f = done + lane; f < total; f += 32) dst[f] = src[(f / KC) * ROW + (f % KC)];
+}
+
 template <int DEG>
 __global__ void __launch_bounds__(kPreThreads) k_preprocess_fwd(
     int n, const float *__restrict__ means, const float *__restrict__ log_scales, const float *__restrict__ quats,
@@ -298,201 +325,177 @@ __global__ void __launch_bounds__(kPreThreads) k_preprocess_fwd(
 
 constexpr int kBwdThreads = 128;
 
+// Adjoint of the preprocess for one Gaussian: from its blend accumulators
+// `ga` to the gradients of its parameters. `row` holds the Gaussian's SH
+// coefficients on entry and their gradients on exit; gmed accumulates the
+// Gaussian's share of the medium gradient (through ct = c a - B b).
 template <int DEG>
-__global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd(
-    int n, const float *__restrict__ means, const float *__restrict__ log_scales, const float *__restrict__ quats,
-    const float *__restrict__ ologits, const float *__restrict__ sh, const float *__restrict__ medium, CamK cam,
-    const GAcc *__restrict__ acc, const uint32_t *__restrict__ depth_key, float *__restrict__ g_means,
-    float *__restrict__ g_ls, float *__restrict__ g_quats, float *__restrict__ g_ologits, float *__restrict__ g_sh,
-    float *__restrict__ block_medium)
+__device__ __forceinline__ void gaussian_chain(int i, const float *__restrict__ means, const float *__restrict__ log_scales,
+                                               const float *__restrict__ quats, const float *__restrict__ ologits,
+                                               const float *__restrict__ medium, const CamK &cam, const GAcc &ga,
+                                               float *row, float gmean[3], float gls[3], float gq[4], float &glogit,
+                                               float gmed[9])
 {
     constexpr int K = (DEG + 1) * (DEG + 1);
-    constexpr int KC = 3 * K;
-    constexpr int ROW = KC + 1;
-    __shared__ float s_sh[kBwdThreads / 32][32 * ROW];
-    __shared__ float s_med[kBwdThreads / 32][9];
+    const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
+    // same rounding as the forward pass, so clamp decisions agree
+    const float tx = dot3_plus(cam.R, mx, my, mz, cam.t[0]).hi;
+    const float ty = dot3_plus(cam.R + 3, mx, my, mz, cam.t[1]).hi;
+    const float tz = dot3_plus(cam.R + 6, mx, my, mz, cam.t[2]).hi;
+    const float4 q4 = reinterpret_cast<const float4 *>(quats)[i];
+    const float qn2 = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
+    const float qinv = rsqrtf(qn2);
+    const float qw = q4.x * qinv, qx = q4.y * qinv, qy = q4.z * qinv, qz = q4.w * qinv;
+    const float Rq[9] = {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
+                         2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
+                         2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
+    const float s[3] = {expf(log_scales[3 * i]), expf(log_scales[3 * i + 1]), expf(log_scales[3 * i + 2])};
+    float WR[9];  // W Rq
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            WR[3 * r + c] = cam.R[3 * r] * Rq[c] + cam.R[3 * r + 1] * Rq[3 + c] + cam.R[3 * r + 2] * Rq[6 + c];
+    float V[9];
+#pragma unroll
+    for (int e = 0; e < 9; e++) V[e] = WR[e] * s[e % 3];
+    const float rz = 1.f / tz;
+    const float rx = tx * rz, ry = ty * rz;
+    const bool clx = rx < -cam.limx || rx > cam.limx, cly = ry < -cam.limy || ry > cam.limy;
+    const float rxc = clampf(rx, -cam.limx, cam.limx), ryc = clampf(ry, -cam.limy, cam.limy);
+    const float jx = cam.fx * rz, jy = cam.fy * rz;
+    float m1[3], m2[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        m1[c] = jx * (V[c] - rxc * V[6 + c]);
+        m2[c] = jy * (V[3 + c] - ryc * V[6 + c]);
+    }
+    const float n1 = m1[0] * m1[0] + m1[1] * m1[1] + m1[2] * m1[2];
+    const float n2 = m2[0] * m2[0] + m2[1] * m2[1] + m2[2] * m2[2];
+    const float b = m1[0] * m2[0] + m1[1] * m2[1] + m1[2] * m2[2];
+    const float cx_ = m1[1] * m2[2] - m1[2] * m2[1], cy_ = m1[2] * m2[0] - m1[0] * m2[2],
+                cz_ = m1[0] * m2[1] - m1[1] * m2[0];
+    const float a = n1 + kDilate, c = n2 + kDilate;
+    const float det = (cx_ * cx_ + cy_ * cy_ + cz_ * cz_) + kDilate * (n1 + n2) + kDilate * kDilate;
+    const float idet2 = 1.f / (det * det);
+
+    // scaled conic -> conic: A = -log2e/2 Ka, B = -log2e Kb, C = -log2e/2 Kc
+    const float gKa = -0.5f * kLog2e * ga.a0.z, gKb = -kLog2e * ga.a0.w, gKc = -0.5f * kLog2e * ga.a1.x;
+    // conic (Ka, Kb, Kc) = (c, -b, a) / det with det = a c - b^2: explicit partials
+    const float g_a = (-c * c * gKa + b * c * gKb - b * b * gKc) * idet2;
+    const float g_b = (2.f * b * c * gKa - (a * c + b * b) * gKb + 2.f * a * b * gKc) * idet2;
+    const float g_c = (-b * b * gKa + a * b * gKb - a * a * gKc) * idet2;
+    // a = |m1|^2 + 0.3, b = m1.m2, c = |m2|^2 + 0.3
+    float gm1[3], gm2[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        gm1[k] = 2.f * g_a * m1[k] + g_b * m2[k];
+        gm2[k] = 2.f * g_c * m2[k] + g_b * m1[k];
+    }
+    // m1 = (fx/tz)(V0 - rxc V2), m2 = (fy/tz)(V1 - ryc V2)
+    float gV[9];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        gV[k] = jx * gm1[k];
+        gV[3 + k] = jy * gm2[k];
+        gV[6 + k] = -jx * rxc * gm1[k] - jy * ryc * gm2[k];
+    }
+    float gtx = 0.f, gty = 0.f, gtz = 0.f;
+    gtz -= ((gm1[0] * m1[0] + gm1[1] * m1[1] + gm1[2] * m1[2]) + (gm2[0] * m2[0] + gm2[1] * m2[1] + gm2[2] * m2[2])) * rz;
+    if (!clx) {
+        const float grxc = -jx * (gm1[0] * V[6] + gm1[1] * V[7] + gm1[2] * V[8]);
+        gtx += grxc * rz;
+        gtz -= grxc * rx * rz;
+    }
+    if (!cly) {
+        const float gryc = -jy * (gm2[0] * V[6] + gm2[1] * V[7] + gm2[2] * V[8]);
+        gty += gryc * rz;
+        gtz -= gryc * ry * rz;
+    }
+    // V = (W Rq) diag(s): gradients for the scales and for Rq = W^T (gV diag(s))
+    float GR[9];
+#pragma unroll
+    for (int c2 = 0; c2 < 3; c2++) gls[c2] = (gV[c2] * WR[c2] + gV[3 + c2] * WR[3 + c2] + gV[6 + c2] * WR[6 + c2]) * s[c2];
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int c2 = 0; c2 < 3; c2++)
+            GR[3 * k + c2] = (cam.R[k] * gV[c2] + cam.R[3 + k] * gV[3 + c2] + cam.R[6 + k] * gV[6 + c2]) * s[c2];
+    // Rq(w, x, y, z) -> unit-quaternion gradient, then through the normalisation
+    const float guw = 2.f * (qz * (GR[3] - GR[1]) + qy * (GR[2] - GR[6]) + qx * (GR[7] - GR[5]));
+    const float gux = 2.f * (qy * (GR[1] + GR[3]) + qz * (GR[2] + GR[6]) + qw * (GR[7] - GR[5])) - 4.f * qx * (GR[4] + GR[8]);
+    const float guy = 2.f * (qx * (GR[1] + GR[3]) + qw * (GR[2] - GR[6]) + qz * (GR[5] + GR[7])) - 4.f * qy * (GR[0] + GR[8]);
+    const float guz = 2.f * (qw * (GR[3] - GR[1]) + qx * (GR[2] + GR[6]) + qy * (GR[5] + GR[7])) - 4.f * qz * (GR[0] + GR[4]);
+    const float ud = qw * guw + qx * gux + qy * guy + qz * guz;
+    gq[0] = (guw - qw * ud) * qinv;
+    gq[1] = (gux - qx * ud) * qinv;
+    gq[2] = (guy - qy * ud) * qinv;
+    gq[3] = (guz - qz * ud) * qinv;
+
+    // colour and water: ct = c a - B b, a = e^{-beta_D d}, b = e^{-beta_B d}
+    const float vx = mx - cam.cpos[0], vy = my - cam.cpos[1], vz = mz - cam.cpos[2];
+    const float vinv = rsqrtf(vx * vx + vy * vy + vz * vz);
+    const float dx = vx * vinv, dy = vy * vinv, dz = vz * vinv;
+    float Y[K];
+    sh_basis<DEG>(dx, dy, dz, Y);
+    const float gct[3] = {ga.a2.x, ga.a2.y, ga.a2.z};
+    float graw[3];
+    float gd = ga.a1.z;
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        float raw = 0.5f;
+#pragma unroll
+        for (int k = 0; k < K; k++) raw = fmaf(row[3 * k + ch], Y[k], raw);
+        const float col = fmaxf(raw, 0.f);
+        const float bd = __ldg(medium + ch), bb = __ldg(medium + 3 + ch), binf = __ldg(medium + 6 + ch);
+        const float ea = expf(-bd * tz), eb = expf(-bb * tz);
+        graw[ch] = raw > 0.f ? gct[ch] * ea : 0.f;
+        const float gea = gct[ch] * col, geb = -gct[ch] * binf;
+        gmed[ch] += gea * (-tz * ea);
+        gmed[3 + ch] += geb * (-tz * eb);
+        gmed[6 + ch] += -gct[ch] * eb;
+        gd += gea * (-bd * ea) + geb * (-bb * eb);
+    }
+    float w[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) w[k] = graw[0] * row[3 * k] + graw[1] * row[3 * k + 1] + graw[2] * row[3 * k + 2];
+    // the coefficients are no longer needed: overwrite them with their gradients
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        row[3 * k] = graw[0] * Y[k];
+        row[3 * k + 1] = graw[1] * Y[k];
+        row[3 * k + 2] = graw[2] * Y[k];
+    }
+    const float3 gdir = sh_basis_vjp<DEG>(dx, dy, dz, w);
+    const float gdd = gdir.x * dx + gdir.y * dy + gdir.z * dz;
+
+    // projected centre x = fx tx/tz + cx, y = fy ty/tz + cy; depth d = tz
+    const float gx = ga.a0.x, gy = ga.a0.y;
+    gtx += gx * jx;
+    gty += gy * jy;
+    gtz += -(gx * jx * tx + gy * jy * ty) * rz + gd;
+    gmean[0] = cam.R[0] * gtx + cam.R[3] * gty + cam.R[6] * gtz + (gdir.x - dx * gdd) * vinv;
+    gmean[1] = cam.R[1] * gtx + cam.R[4] * gty + cam.R[7] * gtz + (gdir.y - dy * gdd) * vinv;
+    gmean[2] = cam.R[2] * gtx + cam.R[5] * gty + cam.R[8] * gtz + (gdir.z - dz * gdd) * vinv;
+    // lo = log2(sigmoid(o)): dlo/do = (1 - sigmoid(o)) / ln 2
+    const float opac = 1.f / (1.f + expf(-ologits[i]));
+    glogit = ga.a1.y * (1.f - opac) * (1.f / kLn2);
+}
+
+// Whether a Gaussian got any blend gradient (culled ones never do).
+__device__ __forceinline__ bool has_grad(int i, int n, const GAcc *__restrict__ acc, const uint32_t *__restrict__ depth_key,
+                                         GAcc &ga)
+{
+    if (i >= n || depth_key[i] == 0xffffffffu) return false;
+    ga = acc[i];
+    return (ga.a0.x != 0.f) | (ga.a0.y != 0.f) | (ga.a0.z != 0.f) | (ga.a0.w != 0.f) | (ga.a1.x != 0.f) |
+           (ga.a1.y != 0.f) | (ga.a1.z != 0.f) | (ga.a2.x != 0.f) | (ga.a2.y != 0.f) | (ga.a2.z != 0.f);
+}
+
+// block partial of the 9 medium-gradient terms: warp shuffle, then one row per block
+__device__ __forceinline__ void medium_partial(float gmed[9], float (*s_med)[9], float *__restrict__ block_medium)
+{
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t wbase = (int64_t)blockIdx.x * kBwdThreads + warp * 32;
-    const int cnt = (int)max((int64_t)0, min((int64_t)32, (int64_t)n - wbase));
-    stage_sh<KC>(sh, wbase, cnt, lane, s_sh[warp]);
-    __syncwarp();
-    const int i = (int)(wbase + lane);
-    float gmed[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-
-    bool live = i < n && depth_key[i] != 0xffffffffu;
-    GAcc ga;
-    if (live) {
-        ga = acc[i];
-        live = (ga.a0.x != 0.f) | (ga.a0.y != 0.f) | (ga.a0.z != 0.f) | (ga.a0.w != 0.f) | (ga.a1.x != 0.f) |
-               (ga.a1.y != 0.f) | (ga.a1.z != 0.f) | (ga.a2.x != 0.f) | (ga.a2.y != 0.f) | (ga.a2.z != 0.f);
-    }
-    float *gsh_out = g_sh ? g_sh + (int64_t)i * KC : nullptr;
-    if (i < n && !live) {
-        if (g_means) g_means[3 * i] = g_means[3 * i + 1] = g_means[3 * i + 2] = 0.f;
-        if (g_ls) g_ls[3 * i] = g_ls[3 * i + 1] = g_ls[3 * i + 2] = 0.f;
-        if (g_quats) reinterpret_cast<float4 *>(g_quats)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (g_ologits) g_ologits[i] = 0.f;
-        if (gsh_out)
-            for (int k = 0; k < KC; k++) gsh_out[k] = 0.f;
-    }
-    if (live) {
-        const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
-        // same rounding as the forward pass, so clamp decisions agree
-        const float tx = dot3_plus(cam.R, mx, my, mz, cam.t[0]).hi;
-        const float ty = dot3_plus(cam.R + 3, mx, my, mz, cam.t[1]).hi;
-        const float tz = dot3_plus(cam.R + 6, mx, my, mz, cam.t[2]).hi;
-        const float4 q4 = reinterpret_cast<const float4 *>(quats)[i];
-        const float qn2 = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
-        const float qinv = rsqrtf(qn2);
-        const float qw = q4.x * qinv, qx = q4.y * qinv, qy = q4.z * qinv, qz = q4.w * qinv;
-        const float Rq[9] = {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
-                             2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
-                             2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
-        const float s[3] = {expf(log_scales[3 * i]), expf(log_scales[3 * i + 1]), expf(log_scales[3 * i + 2])};
-        float WR[9];  // W Rq
-#pragma unroll
-        for (int r = 0; r < 3; r++)
-#pragma unroll
-            for (int c = 0; c < 3; c++)
-                WR[3 * r + c] = cam.R[3 * r] * Rq[c] + cam.R[3 * r + 1] * Rq[3 + c] + cam.R[3 * r + 2] * Rq[6 + c];
-        float V[9];
-#pragma unroll
-        for (int e = 0; e < 9; e++) V[e] = WR[e] * s[e % 3];
-        const float rz = 1.f / tz;
-        const float rx = tx * rz, ry = ty * rz;
-        const bool clx = rx < -cam.limx || rx > cam.limx, cly = ry < -cam.limy || ry > cam.limy;
-        const float rxc = clampf(rx, -cam.limx, cam.limx), ryc = clampf(ry, -cam.limy, cam.limy);
-        const float jx = cam.fx * rz, jy = cam.fy * rz;
-        float u1[3], u2[3], m1[3], m2[3];
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            u1[c] = V[c] - rxc * V[6 + c];
-            u2[c] = V[3 + c] - ryc * V[6 + c];
-            m1[c] = jx * u1[c];
-            m2[c] = jy * u2[c];
-        }
-        const float n1 = m1[0] * m1[0] + m1[1] * m1[1] + m1[2] * m1[2];
-        const float n2 = m2[0] * m2[0] + m2[1] * m2[1] + m2[2] * m2[2];
-        const float b = m1[0] * m2[0] + m1[1] * m2[1] + m1[2] * m2[2];
-        const float cx_ = m1[1] * m2[2] - m1[2] * m2[1], cy_ = m1[2] * m2[0] - m1[0] * m2[2],
-                    cz_ = m1[0] * m2[1] - m1[1] * m2[0];
-        const float a = n1 + kDilate, c = n2 + kDilate;
-        const float det = (cx_ * cx_ + cy_ * cy_ + cz_ * cz_) + kDilate * (n1 + n2) + kDilate * kDilate;
-        const float idet2 = 1.f / (det * det);
-
-        // scaled conic -> conic: A = -log2e/2 Ka, B = -log2e Kb, C = -log2e/2 Kc
-        const float gKa = -0.5f * kLog2e * ga.a0.z, gKb = -kLog2e * ga.a0.w, gKc = -0.5f * kLog2e * ga.a1.x;
-        // conic (Ka, Kb, Kc) = (c, -b, a) / det with det = a c - b^2: explicit partials
-        const float g_a = (-c * c * gKa + b * c * gKb - b * b * gKc) * idet2;
-        const float g_b = (2.f * b * c * gKa - (a * c + b * b) * gKb + 2.f * a * b * gKc) * idet2;
-        const float g_c = (-b * b * gKa + a * b * gKb - a * a * gKc) * idet2;
-        // a = |m1|^2 + 0.3, b = m1.m2, c = |m2|^2 + 0.3
-        float gm1[3], gm2[3];
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            gm1[k] = 2.f * g_a * m1[k] + g_b * m2[k];
-            gm2[k] = 2.f * g_c * m2[k] + g_b * m1[k];
-        }
-        // m1 = (fx/tz)(V0 - rxc V2), m2 = (fy/tz)(V1 - ryc V2)
-        float gV[9];
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            gV[k] = jx * gm1[k];
-            gV[3 + k] = jy * gm2[k];
-            gV[6 + k] = -jx * rxc * gm1[k] - jy * ryc * gm2[k];
-        }
-        float gtx = 0.f, gty = 0.f, gtz = 0.f;
-        gtz -= ((gm1[0] * m1[0] + gm1[1] * m1[1] + gm1[2] * m1[2]) + (gm2[0] * m2[0] + gm2[1] * m2[1] + gm2[2] * m2[2])) * rz;
-        if (!clx) {
-            const float grxc = -jx * (gm1[0] * V[6] + gm1[1] * V[7] + gm1[2] * V[8]);
-            gtx += grxc * rz;
-            gtz -= grxc * rx * rz;
-        }
-        if (!cly) {
-            const float gryc = -jy * (gm2[0] * V[6] + gm2[1] * V[7] + gm2[2] * V[8]);
-            gty += gryc * rz;
-            gtz -= gryc * ry * rz;
-        }
-        // V = (W Rq) diag(s): gradients for the scales and for Rq = W^T (gV diag(s))
-        float gls[3], GR[9];
-#pragma unroll
-        for (int c2 = 0; c2 < 3; c2++) gls[c2] = (gV[c2] * WR[c2] + gV[3 + c2] * WR[3 + c2] + gV[6 + c2] * WR[6 + c2]) * s[c2];
-#pragma unroll
-        for (int k = 0; k < 3; k++)
-#pragma unroll
-            for (int c2 = 0; c2 < 3; c2++)
-                GR[3 * k + c2] = (cam.R[k] * gV[c2] + cam.R[3 + k] * gV[3 + c2] + cam.R[6 + k] * gV[6 + c2]) * s[c2];
-        // Rq(w, x, y, z) -> unit-quaternion gradient, then through the normalisation
-        const float guw = 2.f * (qz * (GR[3] - GR[1]) + qy * (GR[2] - GR[6]) + qx * (GR[7] - GR[5]));
-        const float gux = 2.f * (qy * (GR[1] + GR[3]) + qz * (GR[2] + GR[6]) + qw * (GR[7] - GR[5])) - 4.f * qx * (GR[4] + GR[8]);
-        const float guy = 2.f * (qx * (GR[1] + GR[3]) + qw * (GR[2] - GR[6]) + qz * (GR[5] + GR[7])) - 4.f * qy * (GR[0] + GR[8]);
-        const float guz = 2.f * (qw * (GR[3] - GR[1]) + qx * (GR[2] + GR[6]) + qy * (GR[5] + GR[7])) - 4.f * qz * (GR[0] + GR[4]);
-        const float ud = qw * guw + qx * gux + qy * guy + qz * guz;
-
-        // colour and water: ct = c a - B b, a = e^{-beta_D d}, b = e^{-beta_B d}
-        const float vx = mx - cam.cpos[0], vy = my - cam.cpos[1], vz = mz - cam.cpos[2];
-        const float vinv = rsqrtf(vx * vx + vy * vy + vz * vz);
-        const float dx = vx * vinv, dy = vy * vinv, dz = vz * vinv;
-        float Y[K];
-        sh_basis<DEG>(dx, dy, dz, Y);
-        const float *coef = s_sh[warp] + lane * ROW;
-        const float gct[3] = {ga.a2.x, ga.a2.y, ga.a2.z};
-        float graw[3];
-        float gd = ga.a1.z;
-#pragma unroll
-        for (int ch = 0; ch < 3; ch++) {
-            float raw = 0.5f;
-#pragma unroll
-            for (int k = 0; k < K; k++) raw = fmaf(coef[3 * k + ch], Y[k], raw);
-            const float col = fmaxf(raw, 0.f);
-            const float bd = __ldg(medium + ch), bb = __ldg(medium + 3 + ch), binf = __ldg(medium + 6 + ch);
-            const float ea = expf(-bd * tz), eb = expf(-bb * tz);
-            graw[ch] = raw > 0.f ? gct[ch] * ea : 0.f;
-            const float gea = gct[ch] * col, geb = -gct[ch] * binf;
-            gmed[ch] += gea * (-tz * ea);
-            gmed[3 + ch] += geb * (-tz * eb);
-            gmed[6 + ch] += -gct[ch] * eb;
-            gd += gea * (-bd * ea) + geb * (-bb * eb);
-        }
-        float w[K];
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            w[k] = graw[0] * coef[3 * k] + graw[1] * coef[3 * k + 1] + graw[2] * coef[3 * k + 2];
-            if (gsh_out) {
-                gsh_out[3 * k] = graw[0] * Y[k];
-                gsh_out[3 * k + 1] = graw[1] * Y[k];
-                gsh_out[3 * k + 2] = graw[2] * Y[k];
-            }
-        }
-        const float3 gdir = sh_basis_vjp<DEG>(dx, dy, dz, w);
-        const float gdd = gdir.x * dx + gdir.y * dy + gdir.z * dz;
-
-        // projected centre x = fx tx/tz + cx, y = fy ty/tz + cy; depth d = tz
-        const float gx = ga.a0.x, gy = ga.a0.y;
-        gtx += gx * jx;
-        gty += gy * jy;
-        gtz += -(gx * jx * tx + gy * jy * ty) * rz + gd;
-
-        if (g_means) {
-            g_means[3 * i + 0] = cam.R[0] * gtx + cam.R[3] * gty + cam.R[6] * gtz + (gdir.x - dx * gdd) * vinv;
-            g_means[3 * i + 1] = cam.R[1] * gtx + cam.R[4] * gty + cam.R[7] * gtz + (gdir.y - dy * gdd) * vinv;
-            g_means[3 * i + 2] = cam.R[2] * gtx + cam.R[5] * gty + cam.R[8] * gtz + (gdir.z - dz * gdd) * vinv;
-        }
-        if (g_ls) {
-            g_ls[3 * i] = gls[0];
-            g_ls[3 * i + 1] = gls[1];
-            g_ls[3 * i + 2] = gls[2];
-        }
-        if (g_quats)
-            reinterpret_cast<float4 *>(g_quats)[i] = make_float4((guw - qw * ud) * qinv, (gux - qx * ud) * qinv,
-                                                                 (guy - qy * ud) * qinv, (guz - qz * ud) * qinv);
-        if (g_ologits) {
-            // lo = log2(sigmoid(o)): dlo/do = (1 - sigmoid(o)) / ln 2
-            const float opac = 1.f / (1.f + expf(-ologits[i]));
-            g_ologits[i] = ga.a1.y * (1.f - opac) * (1.f / kLn2);
-        }
-    }
-    // medium partials: warp shuffle, then one row per block
 #pragma unroll
     for (int j = 0; j < 9; j++) {
         float v = gmed[j];
@@ -509,29 +512,173 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd(
     }
 }
 
-// One block: d_medium[j] = sum of per-tile (pixel terms: B_inf, beta_B) and
-// per-block (Gaussian terms) partials, in a fixed order.
-__global__ void k_medium_reduce(const float *__restrict__ tile_medium, int ntiles, const float *__restrict__ block_medium,
-                                int nblocks, float *__restrict__ d_medium)
+template <int DEG>
+__global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd(
+    int n, const float *__restrict__ means, const float *__restrict__ log_scales, const float *__restrict__ quats,
+    const float *__restrict__ ologits, const float *__restrict__ sh, const float *__restrict__ medium, CamK cam,
+    const GAcc *__restrict__ acc, const uint32_t *__restrict__ depth_key, float *__restrict__ g_means,
+    float *__restrict__ g_ls, float *__restrict__ g_quats, float *__restrict__ g_ologits, float *__restrict__ g_sh,
+    float *__restrict__ block_medium)
 {
-    __shared__ float s_part[256][9];
-    float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
+    constexpr int KC = 3 * (DEG + 1) * (DEG + 1);
+    constexpr int ROW = KC + 1;
+    __shared__ float s_sh[kBwdThreads / 32][32 * ROW];
+    __shared__ float s_med[kBwdThreads / 32][9];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t wbase = (int64_t)blockIdx.x * kBwdThreads + warp * 32;
+    const int cnt = (int)max((int64_t)0, min((int64_t)32, (int64_t)n - wbase));
+    stage_sh<KC>(sh, wbase, cnt, lane, s_sh[warp]);
+    __syncwarp();
+    const int i = (int)(wbase + lane);
+    float gmed[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float gmean[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, glogit = 0.f;
+    float *row = s_sh[warp] + lane * ROW;  // SH coefficients in, their gradients out
+    GAcc ga;
+    if (has_grad(i, n, acc, depth_key, ga)) {
+        gaussian_chain<DEG>(i, means, log_scales, quats, ologits, medium, cam, ga, row, gmean, gls, gq, glogit, gmed);
+    } else if (i < n) {
 #pragma unroll
-        for (int j = 0; j < 6; j++) acc[3 + j] += tile_medium[6 * t + j];  // B-beta[3], B_inf[3]
-    for (int t = threadIdx.x; t < nblocks; t += blockDim.x)
-#pragma unroll
-        for (int j = 0; j < 9; j++) acc[j] += block_medium[9 * t + j];
-#pragma unroll
-    for (int j = 0; j < 9; j++) s_part[threadIdx.x][j] = acc[j];
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-#pragma unroll
-            for (int j = 0; j < 9; j++) s_part[threadIdx.x][j] += s_part[threadIdx.x + s][j];
-        __syncthreads();
+        for (int k = 0; k < KC; k++) row[k] = 0.f;
     }
-    if (threadIdx.x < 9) d_medium[threadIdx.x] = s_part[0][threadIdx.x];
+    if (i < n) {
+        if (g_means) {
+            g_means[3 * i] = gmean[0];
+            g_means[3 * i + 1] = gmean[1];
+            g_means[3 * i + 2] = gmean[2];
+        }
+        if (g_ls) {
+            g_ls[3 * i] = gls[0];
+            g_ls[3 * i + 1] = gls[1];
+            g_ls[3 * i + 2] = gls[2];
+        }
+        if (g_quats) reinterpret_cast<float4 *>(g_quats)[i] = make_float4(gq[0], gq[1], gq[2], gq[3]);
+        if (g_ologits) g_ologits[i] = glogit;
+    }
+    __syncwarp();
+    if (g_sh) unstage_rows<KC>(g_sh, wbase, cnt, lane, s_sh[warp]);
+    medium_partial(gmed, s_med, block_medium);
+}
+
+// Moments and learning rates of the fused update: groups 0..4 = means,
+// log-scales, quaternions, opacity logits, SH coefficients.
+struct AdamK {
+    float *m[5];
+    float *v[5];
+    float lr[5];
+    AdamHyper h;
+};
+
+// The same adjoint, followed by one Adam step on the Gaussian's parameters
+// in place: the gradients never go to HBM. The 11 geometric/opacity values
+// are updated per lane; the SH block (the bulk of the bytes) by the whole
+// warp with coalesced 16-byte accesses, its gradients read from shared memory.
+template <int DEG>
+__global__ void __launch_bounds__(kBwdThreads, 6) k_preprocess_bwd_adam(
+    int n, float *__restrict__ means, float *__restrict__ log_scales, float *__restrict__ quats,
+    float *__restrict__ ologits, float *__restrict__ sh, const float *__restrict__ medium, CamK cam,
+    const GAcc *__restrict__ acc, const uint32_t *__restrict__ depth_key, AdamK ad, float *__restrict__ block_medium)
+{
+    constexpr int KC = 3 * (DEG + 1) * (DEG + 1);
+    constexpr int ROW = KC + 1;
+    __shared__ float s_sh[kBwdThreads / 32][32 * ROW];
+    __shared__ float s_med[kBwdThreads / 32][9];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t wbase = (int64_t)blockIdx.x * kBwdThreads + warp * 32;
+    const int cnt = (int)max((int64_t)0, min((int64_t)32, (int64_t)n - wbase));
+    stage_sh<KC>(sh, wbase, cnt, lane, s_sh[warp]);
+    __syncwarp();
+    const int i = (int)(wbase + lane);
+    float gmed[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float gmean[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, glogit = 0.f;
+    float *row = s_sh[warp] + lane * ROW;
+    GAcc ga;
+    if (has_grad(i, n, acc, depth_key, ga)) {
+        gaussian_chain<DEG>(i, means, log_scales, quats, ologits, medium, cam, ga, row, gmean, gls, gq, glogit, gmed);
+    } else if (i < n) {
+#pragma unroll
+        for (int k = 0; k < KC; k++) row[k] = 0.f;
+    }
+    if (i < n) {  // every Gaussian steps (zero gradient still moves its moments), as in plain Adam
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            adam_update(means[3 * i + k], gmean[k], ad.m[0][3 * i + k], ad.v[0][3 * i + k], ad.lr[0], ad.h);
+            adam_update(log_scales[3 * i + k], gls[k], ad.m[1][3 * i + k], ad.v[1][3 * i + k], ad.lr[1], ad.h);
+        }
+        float4 p = reinterpret_cast<float4 *>(quats)[i];
+        float4 m = reinterpret_cast<float4 *>(ad.m[2])[i];
+        float4 v = reinterpret_cast<float4 *>(ad.v[2])[i];
+        adam_update(p.x, gq[0], m.x, v.x, ad.lr[2], ad.h);
+        adam_update(p.y, gq[1], m.y, v.y, ad.lr[2], ad.h);
+        adam_update(p.z, gq[2], m.z, v.z, ad.lr[2], ad.h);
+        adam_update(p.w, gq[3], m.w, v.w, ad.lr[2], ad.h);
+        reinterpret_cast<float4 *>(quats)[i] = p;
+        reinterpret_cast<float4 *>(ad.m[2])[i] = m;
+        reinterpret_cast<float4 *>(ad.v[2])[i] = v;
+        adam_update(ologits[i], glogit, ad.m[3][i], ad.v[3][i], ad.lr[3], ad.h);
+    }
+    __syncwarp();
+    {  // warp-cooperative step of this warp's SH block
+        const float *gsrc = s_sh[warp];
+        float *P = sh + wbase * KC, *M = ad.m[4] + wbase * KC, *Vv = ad.v[4] + wbase * KC;
+        const int total = cnt * KC;
+        int done = 0;
+        const float lr = ad.lr[4];
+        if (((reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(M) | reinterpret_cast<uintptr_t>(Vv)) & 15) == 0) {
+            const int n4 = total >> 2;
+            for (int e = lane; e < n4; e += 32) {
+                float4 p = reinterpret_cast<float4 *>(P)[e];
+                float4 m = reinterpret_cast<float4 *>(M)[e];
+                float4 v = reinterpret_cast<float4 *>(Vv)[e];
+                float g[4];
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const int f = 4 * e + k;
+                    g[k] = gsrc[(f / KC) * ROW + (f % KC)];
+                }
+                adam_update(p.x, g[0], m.x, v.x, lr, ad.h);
+                adam_update(p.y, g[1], m.y, v.y, lr, ad.h);
+                adam_update(p.z, g[2], m.z, v.z, lr, ad.h);
+                adam_update(p.w, g[3], m.w, v.w, lr, ad.h);
+                reinterpret_cast<float4 *>(P)[e] = p;
+                reinterpret_cast<float4 *>(M)[e] = m;
+                reinterpret_cast<float4 *>(Vv)[e] = v;
+            }
+            done = n4 * 4;
+        }
+        for (int f = done + lane; f < total; f += 32)
+            adam_update(P[f], gsrc[(f / KC) * ROW + (f % KC)], M[f], Vv[f], lr, ad.h);
+    }
+    medium_partial(gmed, s_med, block_medium);
+}
+
+// Final stage of the medium-gradient reduction: d_medium[j] = column sums of
+// the stage-1 partial rows of the per-tile table (pixel terms: beta_B[3],
+// B_inf[3]) and of the per-block table (Gaussian terms, 9), in a fixed order.
+__global__ void k_medium_final(const float *__restrict__ part_tile, const float *__restrict__ part_block,
+                               float *__restrict__ d_medium)
+{
+    const int j = threadIdx.x;
+    if (j >= 9) return;
+    float v = 0.f;
+    for (int p = 0; p < kColsumParts; p++) v += part_block[9 * p + j];
+    if (j >= 3)
+        for (int p = 0; p < kColsumParts; p++) v += part_tile[6 * p + (j - 3)];
+    d_medium[j] = v;
+}
+
+// Adam step on the 9 medium parameters from their reduced gradient.
+__global__ void k_medium_adam(float *__restrict__ medium, const float *__restrict__ grad, float *__restrict__ m,
+                              float *__restrict__ v, float lr, AdamHyper h, int clamp, float lo)
+{
+    const int j = threadIdx.x;
+    if (j < 9) {
+        float p = medium[j], mm = m[j], vv = v[j];
+        adam_update(p, grad[j], mm, vv, lr, h);
+        if (clamp) p = fmaxf(p, lo);
+        medium[j] = p;
+        m[j] = mm;
+        v[j] = vv;
+    }
 }
 
 template <int DEG>
@@ -541,6 +688,16 @@ void pre_fwd(int64_t n, const splash_gaussians &g, const float *medium, const Ca
     const int blocks = (int)((n + kPreThreads - 1) / kPreThreads);
     k_preprocess_fwd<DEG><<<blocks, kPreThreads, 0, s>>>((int)n, g.means, g.log_scales, g.quats, g.opacity_logits, g.sh,
                                                         medium, cam, tg, rec, dk, tt, rect);
+    count_launch();
+}
+
+template <int DEG>
+void pre_bwd_adam(int64_t n, const splash_param_buffers &p, const float *medium, const CamK &cam, const GAcc *acc,
+                  const uint32_t *dk, const AdamK &ad, float *bm, cudaStream_t s)
+{
+    const int blocks = (int)((n + kBwdThreads - 1) / kBwdThreads);
+    k_preprocess_bwd_adam<DEG><<<blocks, kBwdThreads, 0, s>>>((int)n, p.means, p.log_scales, p.quats, p.opacity_logits,
+                                                             p.sh, medium, cam, acc, dk, ad, bm);
     count_launch();
 }
 
@@ -586,9 +743,51 @@ void launch_preprocess_bwd(int64_t n, const splash_gaussians &g, const float *me
 }
 
 void launch_medium_reduce(const float *tile_medium, int ntiles, const float *block_medium, int nblocks,
-                          float *d_medium, cudaStream_t s)
+                          float *d_medium, float *scratch, cudaStream_t s)
 {
-    k_medium_reduce<<<1, 256, 0, s>>>(tile_medium, ntiles, block_medium, nblocks, d_medium);
+    // scratch: kColsumParts * (6 + 9) floats
+    float *part_tile = scratch, *part_block = scratch + 6 * kColsumParts;
+    launch_colsum_partial(tile_medium, ntiles, 6, part_tile, s);
+    launch_colsum_partial(block_medium, nblocks, 9, part_block, s);
+    k_medium_final<<<1, 32, 0, s>>>(part_tile, part_block, d_medium);
+    count_launch();
+}
+
+void launch_preprocess_bwd_adam(int64_t n, int sh_degree, const splash_param_buffers &p, const float *medium,
+                                const CamK &cam, const GAcc *acc, const uint32_t *dk, const splash_adam_config &cfg,
+                                float *bm, int *nb, cudaStream_t s)
+{
+    *nb = n > 0 ? preprocess_bwd_blocks(n) : 0;
+    if (n <= 0) return;
+    AdamK ad;
+    const splash_param_buffers *mv[2] = {&cfg.m, &cfg.v};
+    for (int w = 0; w < 2; w++) {
+        float **dst = w ? ad.v : ad.m;
+        dst[0] = mv[w]->means;
+        dst[1] = mv[w]->log_scales;
+        dst[2] = mv[w]->quats;
+        dst[3] = mv[w]->opacity_logits;
+        dst[4] = mv[w]->sh;
+    }
+    ad.lr[0] = cfg.lr_means;
+    ad.lr[1] = cfg.lr_log_scales;
+    ad.lr[2] = cfg.lr_quats;
+    ad.lr[3] = cfg.lr_opacity_logits;
+    ad.lr[4] = cfg.lr_sh;
+    ad.h = make_adam_hyper(cfg.beta1, cfg.beta2, cfg.eps, cfg.step);
+    switch (sh_degree) {
+    case 0: pre_bwd_adam<0>(n, p, medium, cam, acc, dk, ad, bm, s); break;
+    case 1: pre_bwd_adam<1>(n, p, medium, cam, acc, dk, ad, bm, s); break;
+    case 2: pre_bwd_adam<2>(n, p, medium, cam, acc, dk, ad, bm, s); break;
+    default: pre_bwd_adam<3>(n, p, medium, cam, acc, dk, ad, bm, s); break;
+    }
+}
+
+void launch_medium_adam(float *medium, const float *grad, const splash_adam_config &cfg, cudaStream_t s)
+{
+    k_medium_adam<<<1, 32, 0, s>>>(medium, grad, cfg.m.medium, cfg.v.medium, cfg.lr_medium,
+                                   make_adam_hyper(cfg.beta1, cfg.beta2, cfg.eps, cfg.step), cfg.clamp_medium,
+                                   cfg.medium_min);
     count_launch();
 }
 

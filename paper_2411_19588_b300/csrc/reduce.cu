@@ -1,0 +1,55 @@
+// Deterministic column sums of small row-major tables (per-tile and
+// per-block partials of the medium gradient, per-block loss partials).
+// Stage 1 spreads the rows over kColsumParts CTAs (one row per thread per
+// step, coalesced) and reduces each column inside the CTA in a fixed order;
+// the caller's final stage adds the kColsumParts partial rows.
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+
+namespace splash {
+namespace {
+
+constexpr int kColsumThreads = 256;
+
+template <int COLS>
+__global__ void __launch_bounds__(kColsumThreads) k_colsum_partial(const float *__restrict__ data, int rows,
+                                                                   float *__restrict__ part)
+{
+    __shared__ float s_w[kColsumThreads / 32][COLS];
+    float acc[COLS];
+#pragma unroll
+    for (int c = 0; c < COLS; c++) acc[c] = 0.f;
+    for (int r = blockIdx.x * kColsumThreads + threadIdx.x; r < rows; r += kColsumParts * kColsumThreads)
+#pragma unroll
+        for (int c = 0; c < COLS; c++) acc[c] += data[(size_t)r * COLS + c];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < COLS; c++) {
+        float v = acc[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_w[warp][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < COLS) {
+        float v = 0.f;
+#pragma unroll
+        for (int w = 0; w < kColsumThreads / 32; w++) v += s_w[w][threadIdx.x];
+        part[blockIdx.x * COLS + threadIdx.x] = v;
+    }
+}
+
+}  // namespace
+
+void launch_colsum_partial(const float *data, int rows, int cols, float *part, cudaStream_t s)
+{
+    switch (cols) {
+    case 2: k_colsum_partial<2><<<kColsumParts, kColsumThreads, 0, s>>>(data, rows, part); break;
+    case 6: k_colsum_partial<6><<<kColsumParts, kColsumThreads, 0, s>>>(data, rows, part); break;
+    default: k_colsum_partial<9><<<kColsumParts, kColsumThreads, 0, s>>>(data, rows, part); break;
+    }
+    count_launch();
+}
+
+}  // namespace splash

@@ -162,6 +162,35 @@ class Renderer:
         _abi.check(rc, "splash_render_backward")
         return grads
 
+    def backward_adam(self, st: State, params: dict, medium: torch.Tensor, cam: scenes.Camera, dL_dimage,
+                      m: dict, v: dict, lr: dict, step: int, betas=(0.9, 0.999), eps: float = 1e-15,
+                      medium_min: float | None = 0.0, dL_ddepth=None, dL_ddepth01=None, grad_medium=None):
+        """Fused training-step backward: gradients of the last forward on `st`
+        followed by one Adam step applied in place to params/medium and the
+        moment dicts m, v (keys PARAM_NAMES + 'medium')."""
+        H, W = cam.height, cam.width
+        _check_tensor(dL_dimage, "dL_dimage", (3, H, W))
+        names = PARAM_NAMES + ("medium",)
+        tens = dict(params)
+        tens["medium"] = medium
+        for k in names:
+            _check_tensor(tens[k], k)
+            _check_tensor(m[k], f"m[{k}]", tuple(tens[k].shape))
+            _check_tensor(v[k], f"v[{k}]", tuple(tens[k].shape))
+        pb = _abi.ParamBuffers(*(tens[k].data_ptr() for k in names))
+        cfg = _abi.AdamConfig(_abi.ParamBuffers(*(m[k].data_ptr() for k in names)),
+                              _abi.ParamBuffers(*(v[k].data_ptr() for k in names)),
+                              float(lr["means"]), float(lr["log_scales"]), float(lr["quats"]),
+                              float(lr["opacity_logits"]), float(lr["sh"]), float(lr["medium"]),
+                              float(betas[0]), float(betas[1]), float(eps), int(step),
+                              0 if medium_min is None else 1, float(medium_min or 0.0))
+        c = camera_struct(cam)
+        rc = _abi.lib().splash_render_backward_adam(self._ctx, st.handle, ctypes.byref(pb), params["means"].shape[0],
+                                                    int(params["sh_degree"]), ctypes.byref(c), dL_dimage.data_ptr(),
+                                                    _abi.ptr(dL_ddepth), _abi.ptr(dL_ddepth01), ctypes.byref(cfg),
+                                                    _abi.ptr(grad_medium), _stream())
+        _abi.check(rc, "splash_render_backward_adam")
+
     def state_array(self, st: State, field: str, dtype=torch.int32, shape=None) -> torch.Tensor:
         """Copy of one forward-state buffer (see splash_state_copy)."""
         info = _abi.StateInfo()
