@@ -50,6 +50,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--views", type=int, default=N_VIEWS, help="arc views (targets rendered up front)")
+    ap.add_argument("--workload", choices=["train", "batch"], default="train",
+                    help="train: the training step (the headline metric); batch: 64 uneven views forward+backward, "
+                         "sequential plain launches vs one persistent launch each way under a CUDA graph")
+    ap.add_argument("--batch-views", type=int, default=64)
     ap.add_argument("--step", choices=["fused", "unfused"], default="fused",
                     help="fused: backward and Adam in one kernel; unfused: backward, then the multi-group Adam")
     ap.add_argument("--profile-region", action="store_true",
@@ -401,6 +405,102 @@ def run_ours(args, world, rank, local):
         print(json.dumps(out), flush=True)
 
 
+def run_batch(args, world, rank, local):
+    """Batched form: args.batch_views cameras of uneven resolution (640x480
+    .. 1920x1280) over the 1.5M-Gaussian scene; per view forward, the
+    L1 + 0.2 (1 - SSIM) loss against its target and backward, gradients
+    summed over the views. Three ways: the plain per-view path in sequence,
+    the batched path (one persistent blend launch each way), and the batched
+    path replayed from a CUDA graph. Tile shape and staging batch of the
+    batched path come from the autotuner."""
+    import torch
+
+    from paper_2411_19588_b300 import autotune
+    from paper_2411_19588_b300 import render as R
+    from paper_2411_19588_b300 import scenes
+
+    torch.cuda.set_device(local)
+    g_gt, med_gt, _ = scenes.patch_scene(args.n, 3, (2.0, 15.0), 1920, 1280, 1800.0)
+    cams = scenes.uneven_cameras(args.batch_views, seed=4)
+    fit, _ = scenes.perturb(g_gt, med_gt, seed=1 + rank)
+    params = R.params_to_device(fit)
+    med = torch.tensor([0.1] * 9, dtype=torch.float32, device="cuda")
+    gt = R.params_to_device(g_gt)
+    med_gt_t = torch.tensor(med_gt.as_array(), device="cuda")
+    r0 = R.Renderer()
+    targets = [r0.render(gt, med_gt_t, c)[0].clone() for c in cams]
+    del gt
+    V = len(cams)
+    upstream = [torch.full_like(t, 1e-3) for t in targets]
+    tune = autotune.autotune(params, med, cams, upstream)
+    r = R.Renderer(tile=tune["tile"], batch=tune["batch"])
+    b = R.Batch(r, cams)
+    b.calibrate(params, med)
+    st = r.state()
+    lossbuf = [torch.empty(1, device="cuda") for _ in range(V)]
+    gbuf = [torch.empty_like(t) for t in targets]
+    grads = {k: torch.empty_like(params[k]) for k in R.PARAM_NAMES}
+    grads["medium"] = torch.empty_like(med)
+
+    def batched():
+        imgs = b.forward(params, med)
+        for v in range(V):
+            r.loss(st, imgs[v], targets[v], LAMBDA_SSIM, loss_out=lossbuf[v], grad_out=gbuf[v])
+        b.backward(params, med, gbuf, grads)
+
+    rp = R.Renderer()
+    stp = rp.state()
+    imgp = [torch.empty_like(t) for t in targets]
+    dp = [torch.empty((c.height, c.width), device="cuda") for c in cams]
+    dp01 = [torch.empty((c.height, c.width), device="cuda") for c in cams]
+
+    def plain():
+        for v in range(V):
+            rp.forward(stp, params, med, cams[v], imgp[v], dp[v], dp01[v])
+            rp.loss(stp, imgp[v], targets[v], LAMBDA_SSIM, loss_out=lossbuf[v], grad_out=gbuf[v])
+            rp.backward(stp, params, med, cams[v], gbuf[v], grads=grads)
+
+    def timed(fn, reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    steps = max(1, min(args.steps, 10))
+    for _ in range(max(1, args.warmup // 3)):
+        plain()
+        batched()
+    ms_plain = timed(plain, steps)
+    ms_batched = timed(batched, steps)
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            batched()
+    torch.cuda.current_stream().wait_stream(side)
+    graph.replay()
+    ms_graph = timed(graph.replay, steps)
+    r.sync_status()
+    ms = max_over_ranks(ms_graph, world)
+    out = {"metric": f"batched {V}-view forward+backward (uneven 640x480..1920x1280, 1.5M Gaussians)",
+           "value": round(world * V * 1000.0 / ms, 2), "unit": "views/s", "n_gpus": world, "steps": steps,
+           "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "batch", "views": V, "n_gaussians": args.n,
+                      "pixels": int(sum(c.width * c.height for c in cams)), "tile": list(tune["tile"]),
+                      "gaussian_batch": tune["batch"]},
+           "ms_plain_sequential": round(ms_plain, 3), "ms_batched_eager": round(ms_batched, 3),
+           "ms_batched_graph": round(ms_graph, 3), "speedup_graph_vs_plain": round(ms_plain / ms_graph, 3),
+           "autotune": {"cached": tune["cached"], "table_ms": {k: round(v, 3) for k, v in tune["table"].items()}}}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def cpu_baseline(budget_s: float = 20.0, n: int = N_GAUSS) -> dict:
     """The FP64 oracle (as it stands) on a bounded sample of the training
     step: projection of all Gaussians, forward and adjoint at a random
@@ -471,6 +571,8 @@ def main():
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "batch":
+        run_batch(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

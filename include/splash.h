@@ -83,6 +83,8 @@ typedef struct {
                                      sort pass never publishes its look-back entry, so the
                                      wait of partition p + 1 runs out and the call reports
                                      SPLASH_ERR_TIMEOUT (results are then invalid) */
+    int32_t gaussian_batch;       /* Gaussians staged in shared memory per blend step:
+                                     64, 128 (default, also for 0) or 256 */
 } splash_options;
 
 /* Context: options and a device status word. Allocates only the status
@@ -157,6 +159,34 @@ splash_status splash_render_backward_adam(splash_ctx *ctx, splash_state *st, con
                                           int64_t n, int32_t sh_degree, const splash_camera *cam,
                                           const float *dL_dimage, const float *dL_ddepth, const float *dL_ddepth01,
                                           const splash_adam_config *adam, float *grad_medium, void *stream);
+
+/* Batched form: n_views fixed cameras (uneven resolutions allowed) of one
+ * scene, rendered and differentiated as one unit. After one
+ * splash_batch_calibrate (which renders each view once to size the per-view
+ * pair buffers and synchronises), splash_batch_forward / _backward neither
+ * allocate nor synchronise, so a caller may capture them in a CUDA graph.
+ * Each view keeps its own preprocess, depth sort, binning and tile sort;
+ * every (view, tile) of the batch then goes through ONE persistent blend
+ * launch forward and ONE backward, taken longest tile list first. A view
+ * whose pair count outgrows its calibrated capacity is truncated and
+ * SPLASH_ERR_CAPACITY is reported by splash_sync_status (recalibrate).
+ * Tile shape and staging batch come from the context's options. */
+typedef struct splash_batch splash_batch;
+splash_status splash_batch_create(splash_ctx *ctx, int32_t n_views, const splash_camera *cams, splash_batch **out);
+splash_status splash_batch_destroy(splash_batch *b);
+/* headroom: capacity = measured pairs * headroom + 1024 per view (>= 0.01; 1.25 is a good default). */
+splash_status splash_batch_calibrate(splash_batch *b, const splash_gaussians *g, const float *medium_dev,
+                                     float headroom, void *stream);
+/* images: host array of n_views device pointers [3,H_v,W_v]; depths, depth01s: host arrays or NULL
+ * (entries may be NULL). The Gaussians must match the calibration in n and SH degree. */
+splash_status splash_batch_forward(splash_batch *b, const splash_gaussians *g, const float *medium_dev,
+                                   float *const *images, float *const *depths, float *const *depth01s, void *stream);
+/* dL_dimages: host array of n_views device pointers [3,H_v,W_v]. grads: the gradient of the sum of
+ * the views' losses, OVERWRITTEN. */
+splash_status splash_batch_backward(splash_batch *b, const splash_gaussians *g, const float *medium_dev,
+                                    const float *const *dL_dimages, const splash_grads *grads, void *stream);
+/* Per view: pairs emitted by the last forward and the calibrated capacity (synchronises). */
+splash_status splash_batch_pair_counts(const splash_batch *b, int64_t *emitted, int64_t *capacity, void *stream);
 
 /* Read-only views of the forward state, for tests and diagnostics. Device
  * pointers stay valid until the next forward on the state. */

@@ -45,7 +45,7 @@ class Grads(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("spin_limit", ctypes.c_int32),
-                ("test_stall_partition", ctypes.c_int32)]
+                ("test_stall_partition", ctypes.c_int32), ("gaussian_batch", ctypes.c_int32)]
 
 
 class StateInfo(ctypes.Structure):
@@ -103,6 +103,16 @@ _SIGS = {
     "splash_state_copy": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p],
     "splash_profile_enable": [ctypes.c_void_p, ctypes.c_int32],
     "splash_profile_read": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
+    "splash_batch_create": [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(Camera), ctypes.POINTER(ctypes.c_void_p)],
+    "splash_batch_destroy": [ctypes.c_void_p],
+    "splash_batch_calibrate": [ctypes.c_void_p, ctypes.POINTER(Gaussians), ctypes.c_void_p, ctypes.c_float,
+                               ctypes.c_void_p],
+    "splash_batch_forward": [ctypes.c_void_p, ctypes.POINTER(Gaussians), ctypes.c_void_p, ctypes.c_void_p,
+                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "splash_batch_backward": [ctypes.c_void_p, ctypes.POINTER(Gaussians), ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.POINTER(Grads), ctypes.c_void_p],
+    "splash_batch_pair_counts": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                 ctypes.c_void_p],
     "splash_sort_pairs_u32_noalloc": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p],
 }

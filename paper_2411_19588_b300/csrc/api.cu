@@ -14,207 +14,43 @@
 #include <string>
 #include <vector>
 
-#include "internal.cuh"
+#include "host.h"
 
 using namespace splash;
+using namespace splash_host;
 
 namespace {
 thread_local std::string g_last_error;
-
-struct Buf {
-    void *p = nullptr;
-    size_t cap = 0;
-    ~Buf() { release(); }
-    void release()
-    {
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
-    }
-    // grow-only; contents are not preserved
-    bool ensure(size_t bytes)
-    {
-        if (bytes <= cap) return true;
-        release();
-        const size_t want = std::max<size_t>(bytes + bytes / 4, 256);
-        if (cudaMalloc(&p, want) != cudaSuccess) {
-            cudaGetLastError();
-            p = nullptr;
-            return false;
-        }
-        cap = want;
-        return true;
-    }
-    template <class T>
-    T *as() const { return static_cast<T *>(p); }
-};
+std::atomic<uint64_t> g_launches{0};
 }  // namespace
 
 void splash_set_error(const std::string &msg) { g_last_error = msg; }
-
-namespace {
-std::atomic<uint64_t> g_launches{0};
-
-// Per-stage CUDA-event timing (tracing aid)
-struct Prof {
-    bool on = false;
-    struct Rec {
-        int stage;
-        cudaEvent_t a, b;
-    };
-    std::vector<cudaEvent_t> spare;
-    std::vector<Rec> pending;
-    double ms[SPLASH_STAGE_COUNT] = {};
-    int64_t cnt[SPLASH_STAGE_COUNT] = {};
-    cudaEvent_t take()
-    {
-        if (!spare.empty()) {
-            cudaEvent_t e = spare.back();
-            spare.pop_back();
-            return e;
-        }
-        cudaEvent_t e = nullptr;
-        if (cudaEventCreate(&e) != cudaSuccess) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        return e;
-    }
-    ~Prof()
-    {
-        for (auto &r : pending) {
-            cudaEventDestroy(r.a);
-            cudaEventDestroy(r.b);
-        }
-        for (auto e : spare) cudaEventDestroy(e);
-    }
-};
-
-// Records a start event on construction and the stop event on destruction.
-struct Stage {
-    Prof &p;
-    int stage;
-    cudaStream_t s;
-    cudaEvent_t a = nullptr;
-    Stage(Prof &p_, int stage_, cudaStream_t s_) : p(p_), stage(stage_), s(s_)
-    {
-        if (p.on && (a = p.take())) cudaEventRecord(a, s);
-    }
-    ~Stage()
-    {
-        if (!a) return;
-        cudaEvent_t b = p.take();
-        if (!b) {
-            p.spare.push_back(a);
-            return;
-        }
-        cudaEventRecord(b, s);
-        p.pending.push_back({stage, a, b});
-    }
-};
-}  // namespace
 
 namespace splash {
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 }  // namespace splash
 
-struct splash_ctx {
-    splash_options opt;
-    uint32_t *d_status = nullptr;  // kernel-reported error bits
-    Prof prof;
-};
-
-struct splash_state {
-    splash_ctx *ctx = nullptr;
-    // per Gaussian
-    Buf rec, depth_key, tt, rect, dk0, dv0, dk1, dv1, offsets, scan_sums;
-    // per (tile, Gaussian) pair
-    Buf tk0, tv0, tk1, tv1;
-    Buf ranges, sort_scratch;
-    // per pixel
-    Buf fT, aA, zh, nlast, nwalk;
-    // backward
-    Buf gacc, tile_med, block_med, gmed, red_scratch;
-    // loss / standalone sort
-    Buf loss_scratch, tmp_k, tmp_v;
-    Buf small;  // [0] = pair count K, [1..] spare
-    uint32_t *h_small = nullptr;  // pinned: K, status
-    // what the last forward produced
-    bool has_forward = false;
-    int64_t n = 0;
-    int W = 0, H = 0;
-    TileGeom tg{};
-    int64_t K = 0;
-    const uint32_t *order = nullptr;    // depth-sorted Gaussian indices
-    const uint32_t *tile_ids = nullptr; // sorted pairs
-    const uint32_t *gauss_ids = nullptr;
-};
-
 namespace {
 
-splash_status fail(splash_status s, const std::string &msg)
+BlendView backward_view(splash_state *st, const CamK &ck, const float *gi, const float *gd, const float *g01)
 {
-    g_last_error = msg;
-    return s;
-}
-
-#define ENSURE(buf, bytes)                                                                       \
-    do {                                                                                         \
-        if (!(buf).ensure(bytes)) return fail(SPLASH_ERR_OOM, "cudaMalloc failed for " #buf);    \
-    } while (0)
-
-bool valid_tile(int tw, int th) { return (tw == 16 && th == 16) || (tw == 8 && th == 32) || (tw == 32 && th == 8); }
-
-CamK make_cam(const splash_camera &c)
-{
-    CamK k{};
-    for (int r = 0; r < 3; r++) {
-        for (int j = 0; j < 3; j++) k.R[3 * r + j] = c.world_to_cam[4 * r + j];
-        k.t[r] = c.world_to_cam[4 * r + 3];
-    }
-    for (int j = 0; j < 3; j++)
-        k.cpos[j] = (float)-((double)k.R[j] * k.t[0] + (double)k.R[3 + j] * k.t[1] + (double)k.R[6 + j] * k.t[2]);
-    k.fx = c.fx;
-    k.fy = c.fy;
-    k.cx = c.cx;
-    k.cy = c.cy;
-    k.limx = (float)(1.3 * 0.5 * c.width / c.fx);
-    k.limy = (float)(1.3 * 0.5 * c.height / c.fy);
-    k.znear = c.z_near;
-    k.zfar = c.z_far;
-    k.W = c.width;
-    k.H = c.height;
-    return k;
-}
-
-splash_status check_camera(const splash_camera *cam)
-{
-    if (!cam) return fail(SPLASH_ERR_INVALID_ARG, "null camera");
-    if (cam->width <= 0 || cam->height <= 0 || cam->width > 32768 || cam->height > 32768)
-        return fail(SPLASH_ERR_INVALID_ARG, "image size must be in 1..32768");
-    if (!(cam->fx > 0.f) || !(cam->fy > 0.f)) return fail(SPLASH_ERR_INVALID_ARG, "focal lengths must be positive");
-    if (!(cam->z_near > 0.f) || !(cam->z_far > cam->z_near))
-        return fail(SPLASH_ERR_INVALID_ARG, "need 0 < z_near < z_far");
-    return SPLASH_OK;
-}
-
-splash_status check_gaussians(const splash_gaussians *g)
-{
-    if (!g) return fail(SPLASH_ERR_INVALID_ARG, "null gaussians");
-    if (g->n < 0 || g->n >= (int64_t)1 << 31) return fail(SPLASH_ERR_INVALID_ARG, "n must be in [0, 2^31)");
-    if (g->sh_degree < 0 || g->sh_degree > 3) return fail(SPLASH_ERR_INVALID_ARG, "sh_degree must be 0..3");
-    if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
-        return fail(SPLASH_ERR_INVALID_ARG, "null gaussian buffer");
-    if (g->n > 0 && (reinterpret_cast<uintptr_t>(g->quats) & 15))
-        return fail(SPLASH_ERR_INVALID_ARG, "quats must be 16-byte aligned");
-    return SPLASH_OK;
-}
-
-int bits_for(int64_t count)
-{
-    int b = 0;
-    while (((int64_t)1 << b) < count) b++;
-    return b;
+    BlendView v{};
+    v.cam = ck;
+    v.tg = st->tg;
+    v.ranges = st->ranges.as<uint2>();
+    v.gauss_ids = st->gauss_ids;
+    v.rec = st->rec.as<Rec>();
+    v.final_T = st->fT.as<float>();
+    v.acc_alpha = st->aA.as<float>();
+    v.zhat = st->zh.as<float>();
+    v.n_last = st->nlast.as<uint32_t>();
+    v.n_walk = st->nwalk.as<uint32_t>();
+    v.dL_dimage = gi;
+    v.dL_ddepth = gd;
+    v.dL_ddepth01 = g01;
+    v.gacc = st->gacc.as<GAcc>();
+    v.tile_medium = st->tile_med.as<float>();
+    return v;
 }
 
 splash_status read_status(splash_ctx *ctx, splash_state *st, cudaStream_t s, bool with_k)
@@ -242,13 +78,16 @@ splash_status splash_create(const splash_options *opt, splash_ctx **out)
 {
     if (!out) return fail(SPLASH_ERR_INVALID_ARG, "null output pointer");
     *out = nullptr;
-    splash_options o{16, 16, 0, 0};
+    splash_options o{16, 16, 0, 0, 128};
     if (opt) o = *opt;
     if (o.tile_w == 0 && o.tile_h == 0) o.tile_w = o.tile_h = 16;
     if (!valid_tile(o.tile_w, o.tile_h)) return fail(SPLASH_ERR_INVALID_ARG, "tile shape must be 16x16, 8x32 or 32x8");
     if (o.spin_limit < 0 || o.test_stall_partition < 0)
         return fail(SPLASH_ERR_INVALID_ARG, "spin_limit and test_stall_partition must be >= 0");
     if (o.spin_limit == 0) o.spin_limit = 1 << 22;
+    if (o.gaussian_batch == 0) o.gaussian_batch = 128;
+    if (o.gaussian_batch != 64 && o.gaussian_batch != 128 && o.gaussian_batch != 256)
+        return fail(SPLASH_ERR_INVALID_ARG, "gaussian_batch must be 64, 128 or 256");
     splash_ctx *c = new splash_ctx();
     c->opt = o;
     if (cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess || cudaMemset(c->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
@@ -383,9 +222,21 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
     }
     {
         Stage t(ctx->prof, SPLASH_STAGE_BLEND_FWD, s);
-        launch_blend_fwd(tg, ck, st->ranges.as<uint2>(), gids, st->rec.as<Rec>(), medium, image, depth, depth01,
-                         st->fT.as<float>(), st->aA.as<float>(), st->zh.as<float>(), st->nlast.as<uint32_t>(),
-                         st->nwalk.as<uint32_t>(), s);
+        BlendView v{};
+        v.cam = ck;
+        v.tg = tg;
+        v.ranges = st->ranges.as<uint2>();
+        v.gauss_ids = gids;
+        v.rec = st->rec.as<Rec>();
+        v.image = image;
+        v.depth = depth;
+        v.depth01 = depth01;
+        v.final_T = st->fT.as<float>();
+        v.acc_alpha = st->aA.as<float>();
+        v.zhat = st->zh.as<float>();
+        v.n_last = st->nlast.as<uint32_t>();
+        v.n_walk = st->nwalk.as<uint32_t>();
+        launch_blend_fwd(v, medium, ctx->opt.gaussian_batch, s);
     }
     SPLASH_CUDA_TRY(cudaGetLastError());
 
@@ -411,6 +262,8 @@ splash_status splash_render_backward(splash_ctx *ctx, splash_state *st, const sp
     if ((rc = check_gaussians(g)) != SPLASH_OK) return rc;
     if ((rc = check_camera(cam)) != SPLASH_OK) return rc;
     if (!medium || !dL_dimage || !grads) return fail(SPLASH_ERR_INVALID_ARG, "null medium, dL_dimage or grads");
+    if (grads->quats && (reinterpret_cast<uintptr_t>(grads->quats) & 15))
+        return fail(SPLASH_ERR_INVALID_ARG, "grads.quats must be 16-byte aligned");
     if (!st->has_forward || st->n != g->n || st->W != cam->width || st->H != cam->height)
         return fail(SPLASH_ERR_STATE, "backward does not match the last forward on this state");
     cudaStream_t s = (cudaStream_t)stream;
@@ -426,9 +279,7 @@ splash_status splash_render_backward(splash_ctx *ctx, splash_state *st, const sp
     const CamK ck = make_cam(*cam);
     {
         Stage t(ctx->prof, SPLASH_STAGE_BLEND_BWD, s);
-        launch_blend_bwd(st->tg, ck, st->ranges.as<uint2>(), st->gauss_ids, st->rec.as<Rec>(), medium, st->fT.as<float>(),
-                         st->aA.as<float>(), st->zh.as<float>(), st->nlast.as<uint32_t>(), dL_dimage, dL_ddepth,
-                         dL_ddepth01, st->gacc.as<GAcc>(), st->tile_med.as<float>(), s);
+        launch_blend_bwd(backward_view(st, ck, dL_dimage, dL_ddepth, dL_ddepth01), medium, ctx->opt.gaussian_batch, s);
     }
     int nb = 0;
     {
@@ -481,9 +332,8 @@ splash_status splash_render_backward_adam(splash_ctx *ctx, splash_state *st, con
     const CamK ck = make_cam(*cam);
     {
         Stage t(ctx->prof, SPLASH_STAGE_BLEND_BWD, s);
-        launch_blend_bwd(st->tg, ck, st->ranges.as<uint2>(), st->gauss_ids, st->rec.as<Rec>(), params->medium,
-                         st->fT.as<float>(), st->aA.as<float>(), st->zh.as<float>(), st->nlast.as<uint32_t>(), dL_dimage,
-                         dL_ddepth, dL_ddepth01, st->gacc.as<GAcc>(), st->tile_med.as<float>(), s);
+        launch_blend_bwd(backward_view(st, ck, dL_dimage, dL_ddepth, dL_ddepth01), params->medium,
+                         ctx->opt.gaussian_batch, s);
     }
     int nb = 0;
     {

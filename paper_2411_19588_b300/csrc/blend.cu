@@ -13,13 +13,15 @@
 // so the inner loop is plain compositing of the effective colour ct (made
 // once per Gaussian in the preprocess) and the water costs one epilogue.
 //
-// Work decomposition: one CTA per tile, two pixels of one row per thread
-// (they share the dy terms). Gaussians are staged in shared memory in
-// batches of one per thread; the local centre is formed once per
-// (tile, Gaussian) from the doubled-precision record, relative to the
+// Work decomposition: one CTA of 128 threads per tile, two pixels of one row
+// per thread (they share the dy terms). Gaussians are staged in shared
+// memory in batches of NB (64, 128 or 256); the local centre is formed once
+// per (tile, Gaussian) from the doubled-precision record, relative to the
 // 32-pixel-aligned corner that holds the tile (the same corner for every
 // tile shape, so all shapes do identical per-pixel arithmetic). A warp skips
 // a batch once all its pixels are done; the CTA stops when all are.
+// Plain launches run one CTA per tile of one view; the persistent launches
+// keep one wave of CTAs that pull (view, tile) items from a queue.
 #include <cuda_runtime.h>
 
 #include "internal.cuh"
@@ -42,32 +44,40 @@ template <int TW, int TH>
 struct Tile {
     static constexpr int NT = TW * TH / 2;  // threads per CTA
     static constexpr int HW = TW / 2;       // second pixel of a thread is HW columns right
+    static_assert(NT == 128, "128 threads per tile");
 };
 
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH / 2, 10) k_blend_fwd(TileGeom tg, CamK cam, const uint2 *__restrict__ ranges,
-                                                         const uint32_t *__restrict__ gauss_ids, const Rec *__restrict__ rec,
-                                                         const float *__restrict__ medium, float *__restrict__ image,
-                                                         float *__restrict__ depth, float *__restrict__ depth01,
-                                                         float *__restrict__ final_T, float *__restrict__ acc_alpha,
-                                                         float *__restrict__ zhat, uint32_t *__restrict__ n_last,
-                                                         uint32_t *__restrict__ n_walk)
+// stage list entry `slot` of the batch: local centre, conic, log-opacity, colour, depth
+__device__ __forceinline__ void stage_rec(const Rec *__restrict__ rec, uint32_t gid, int ox, int oy, float4 *s0, float4 *s1,
+                                          float2 *s2, int slot)
+{
+    const Rec r = rec[gid];
+    const float xl = (r.r0.x - (float)ox) + r.r0.z;
+    const float yl = (r.r0.y - (float)oy) + r.r0.w;
+    s0[slot] = make_float4(xl, yl, r.r1.x, r.r1.y);
+    s1[slot] = make_float4(r.r1.z, r.r1.w, r.r2.y, r.r2.z);
+    s2[slot] = make_float2(r.r2.w, r.r2.x);
+}
+
+template <int TW, int TH, int NB>
+__device__ __forceinline__ void blend_tile_fwd(const BlendView &v, int tile, const float *__restrict__ medium)
 {
     constexpr int NT = Tile<TW, TH>::NT, HW = Tile<TW, TH>::HW;
-    __shared__ float4 s0[NT];  // {x_loc, y_loc, A, B}
-    __shared__ float4 s1[NT];  // {C, lo, ct_r, ct_g}
-    __shared__ float2 s2[NT];  // {ct_b, d}
-    const int tile = blockIdx.x;
-    const int tyi = tile / tg.tx, txi = tile - tyi * tg.tx;
+    __shared__ float4 s0[NB];  // {x_loc, y_loc, A, B}
+    __shared__ float4 s1[NB];  // {C, lo, ct_r, ct_g}
+    __shared__ float2 s2[NB];  // {ct_b, d}
+    const CamK &cam = v.cam;
+    const int tyi = tile / v.tg.tx, txi = tile - tyi * v.tg.tx;
     const int x0 = txi * TW, y0 = tyi * TH;
     const int ox = x0 & ~31, oy = y0 & ~31;  // local origin shared by all tile shapes
     const int tid = threadIdx.x;
     const int row = tid / HW, col = tid - row * HW;
     const float pyl = (float)(y0 - oy + row) + 0.5f;
     const float pxl0 = (float)(x0 - ox + col) + 0.5f, pxl1 = (float)(x0 - ox + col + HW) + 0.5f;
+    const int W = cam.W, H = cam.H;
     const int gy = y0 + row, gx0 = x0 + col, gx1 = x0 + col + HW;
-    const bool in0 = gy < cam.H && gx0 < cam.W, in1 = gy < cam.H && gx1 < cam.W;
-    const uint2 rg = ranges[tile];
+    const bool in0 = gy < H && gx0 < W, in1 = gy < H && gx1 < W;
+    const uint2 rg = v.ranges[tile];
     const int n = (int)(rg.y - rg.x);
 
     float T0 = 1.f, T1 = 1.f;
@@ -78,20 +88,11 @@ __global__ void __launch_bounds__(TW *TH / 2, 10) k_blend_fwd(TileGeom tg, CamK 
     if (done0) walk0 = 0;
     if (done1) walk1 = 0;
 
-    for (int b0 = 0; b0 < n; b0 += NT) {
+    for (int b0 = 0; b0 < n; b0 += NB) {
         if (__syncthreads_count(!(done0 && done1)) == 0) break;
-        const int j = b0 + tid;
-        if (j < n) {
-            const uint32_t gid = gauss_ids[rg.x + j];
-            const Rec r = rec[gid];
-            const float xl = (r.r0.x - (float)ox) + r.r0.z;
-            const float yl = (r.r0.y - (float)oy) + r.r0.w;
-            s0[tid] = make_float4(xl, yl, r.r1.x, r.r1.y);
-            s1[tid] = make_float4(r.r1.z, r.r1.w, r.r2.y, r.r2.z);
-            s2[tid] = make_float2(r.r2.w, r.r2.x);
-        }
+        for (int sl = tid; sl < NB && b0 + sl < n; sl += NT) stage_rec(v.rec, v.gauss_ids[rg.x + b0 + sl], ox, oy, s0, s1, s2, sl);
         __syncthreads();
-        const int nb = min(NT, n - b0);
+        const int nb = min(NB, n - b0);
         if (!__any_sync(0xffffffffu, !(done0 && done1))) continue;
         for (int k = 0; k < nb; k++) {
             const float4 a = s0[k];
@@ -158,34 +159,23 @@ __global__ void __launch_bounds__(TW *TH / 2, 10) k_blend_fwd(TileGeom tg, CamK 
         binf[ch] = __ldg(medium + 6 + ch);
         bfar[ch] = expf(-__ldg(medium + 3 + ch) * zfar);
     }
-    const int HWimg = cam.W * cam.H;
-    if (in0) {
-        const int p = gy * cam.W + gx0;
-        image[p] = c00 + binf[0] * (1.f - T0 * bfar[0]);
-        image[HWimg + p] = c01 + binf[1] * (1.f - T0 * bfar[1]);
-        image[2 * HWimg + p] = c02 + binf[2] * (1.f - T0 * bfar[2]);
-        const float z = A0 > 0.f ? D0 / A0 : zfar;
-        if (depth) depth[p] = z;
-        if (depth01) depth01[p] = 2.f / (1.f + expf(-0.1f * z)) - 1.f;
-        final_T[p] = T0;
-        acc_alpha[p] = A0;
-        zhat[p] = z;
-        n_last[p] = (uint32_t)last0;
-        n_walk[p] = (uint32_t)walk0;
-    }
-    if (in1) {
-        const int p = gy * cam.W + gx1;
-        image[p] = c10 + binf[0] * (1.f - T1 * bfar[0]);
-        image[HWimg + p] = c11 + binf[1] * (1.f - T1 * bfar[1]);
-        image[2 * HWimg + p] = c12 + binf[2] * (1.f - T1 * bfar[2]);
-        const float z = A1 > 0.f ? D1 / A1 : zfar;
-        if (depth) depth[p] = z;
-        if (depth01) depth01[p] = 2.f / (1.f + expf(-0.1f * z)) - 1.f;
-        final_T[p] = T1;
-        acc_alpha[p] = A1;
-        zhat[p] = z;
-        n_last[p] = (uint32_t)last1;
-        n_walk[p] = (uint32_t)walk1;
+    const int HWimg = W * H;
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+        if (!(q ? in1 : in0)) continue;
+        const int p = gy * W + (q ? gx1 : gx0);
+        const float T = q ? T1 : T0, Dd = q ? D1 : D0, Aa = q ? A1 : A0;
+        v.image[p] = (q ? c10 : c00) + binf[0] * (1.f - T * bfar[0]);
+        v.image[HWimg + p] = (q ? c11 : c01) + binf[1] * (1.f - T * bfar[1]);
+        v.image[2 * HWimg + p] = (q ? c12 : c02) + binf[2] * (1.f - T * bfar[2]);
+        const float z = Aa > 0.f ? Dd / Aa : zfar;
+        if (v.depth) v.depth[p] = z;
+        if (v.depth01) v.depth01[p] = 2.f / (1.f + expf(-0.1f * z)) - 1.f;
+        v.final_T[p] = T;
+        v.acc_alpha[p] = Aa;
+        v.zhat[p] = z;
+        v.n_last[p] = (uint32_t)(q ? last1 : last0);
+        v.n_walk[p] = (uint32_t)(q ? walk1 : walk0);
     }
 }
 
@@ -201,7 +191,7 @@ struct PixB {
 };
 
 // One warp-wide sum of 10 values by recursive halving: after five exchange
-// steps lane L holds the warp total of field kLaneField[L] (12 shuffles
+// steps lane L holds the warp total of field reduce10_field(L) (12 shuffles
 // instead of 50 for ten separate butterflies).
 template <int C>
 __device__ __forceinline__ void rs_step(float *v, int m, bool hi)
@@ -280,39 +270,32 @@ __device__ __forceinline__ bool pix_grad(PixB &p, int j, float dx, float dy, flo
     return true;
 }
 
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH / 2, 8) k_blend_bwd(TileGeom tg, CamK cam, const uint2 *__restrict__ ranges,
-                                                         const uint32_t *__restrict__ gauss_ids, const Rec *__restrict__ rec,
-                                                         const float *__restrict__ medium, const float *__restrict__ final_T,
-                                                         const float *__restrict__ acc_alpha, const float *__restrict__ zhat,
-                                                         const uint32_t *__restrict__ n_last,
-                                                         const float *__restrict__ dL_dimage,
-                                                         const float *__restrict__ dL_ddepth,
-                                                         const float *__restrict__ dL_ddepth01, GAcc *__restrict__ gacc,
-                                                         float *__restrict__ tile_medium)
+template <int TW, int TH, int NB>
+__device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, const float *__restrict__ medium)
 {
     constexpr int NT = Tile<TW, TH>::NT, HW = Tile<TW, TH>::HW;
     constexpr int NW = NT / 32;
-    __shared__ float4 s0[NT];
-    __shared__ float4 s1[NT];
-    __shared__ float2 s2[NT];
-    __shared__ uint32_t s_id[NT];
-    __shared__ float s_g[10][NT];
+    __shared__ float4 s0[NB];
+    __shared__ float4 s1[NB];
+    __shared__ float2 s2[NB];
+    __shared__ uint32_t s_id[NB];
+    __shared__ float s_g[10][NB];
     __shared__ float s_med[NW][6];
     __shared__ int s_maxlast;
 
-    const int tile = blockIdx.x;
-    const int tyi = tile / tg.tx, txi = tile - tyi * tg.tx;
+    const CamK &cam = v.cam;
+    const int tyi = tile / v.tg.tx, txi = tile - tyi * v.tg.tx;
     const int x0 = txi * TW, y0 = tyi * TH;
     const int ox = x0 & ~31, oy = y0 & ~31;  // local origin shared by all tile shapes
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int row = tid / HW, col = tid - row * HW;
     const float pyl = (float)(y0 - oy + row) + 0.5f;
     const float pxl0 = (float)(x0 - ox + col) + 0.5f, pxl1 = (float)(x0 - ox + col + HW) + 0.5f;
+    const int W = cam.W, H = cam.H;
     const int gy = y0 + row, gx0 = x0 + col, gx1 = x0 + col + HW;
-    const bool in0 = gy < cam.H && gx0 < cam.W, in1 = gy < cam.H && gx1 < cam.W;
-    const uint2 rg = ranges[tile];
-    const int HWimg = cam.W * cam.H;
+    const bool in0 = gy < H && gx0 < W, in1 = gy < H && gx1 < W;
+    const uint2 rg = v.ranges[tile];
+    const int HWimg = W * H;
     const float zfar = cam.zfar;
     float binf[3], bfar[3];
 #pragma unroll
@@ -332,20 +315,20 @@ __global__ void __launch_bounds__(TW *TH / 2, 8) k_blend_bwd(TileGeom tg, CamK c
         PixB &p = P[q];
         p.T = 1.f; p.S = 0.f; p.G0 = p.G1 = p.G2 = p.gD = p.gA = 0.f; p.last = 0;
         if (!in) continue;
-        const int pix = gy * cam.W + (q ? gx1 : gx0);
-        p.T = final_T[pix];
-        p.last = (int)n_last[pix];
-        p.G0 = dL_dimage[pix];
-        p.G1 = dL_dimage[HWimg + pix];
-        p.G2 = dL_dimage[2 * HWimg + pix];
-        const float A = acc_alpha[pix], z = zhat[pix];
-        float gz = dL_ddepth ? dL_ddepth[pix] : 0.f;
-        if (dL_ddepth01) {
+        const int pix = gy * W + (q ? gx1 : gx0);
+        p.T = v.final_T[pix];
+        p.last = (int)v.n_last[pix];
+        p.G0 = v.dL_dimage[pix];
+        p.G1 = v.dL_dimage[HWimg + pix];
+        p.G2 = v.dL_dimage[2 * HWimg + pix];
+        const float A = v.acc_alpha[pix], z = v.zhat[pix];
+        float gz = v.dL_ddepth ? v.dL_ddepth[pix] : 0.f;
+        if (v.dL_ddepth01) {
             const float e = expf(-0.1f * z);
-            gz += dL_ddepth01[pix] * 0.2f * e / ((1.f + e) * (1.f + e));
+            gz += v.dL_ddepth01[pix] * 0.2f * e / ((1.f + e) * (1.f + e));
         }
         if (A > 0.f) {
-            p.gD = gz / A;       // z = D / A
+            p.gD = gz / A;  // z = D / A
             p.gA = -gz * z / A;
         }
         const float Gc[3] = {p.G0, p.G1, p.G2};
@@ -376,31 +359,27 @@ __global__ void __launch_bounds__(TW *TH / 2, 8) k_blend_bwd(TileGeom tg, CamK c
     __syncthreads();
     atomicMax(&s_maxlast, max(P[0].last, P[1].last));
     if (tid < 6) {
-        float v = 0.f;
+        float acc = 0.f;
 #pragma unroll
-        for (int w = 0; w < NW; w++) v += s_med[w][tid];
-        tile_medium[6 * tile + tid] = v;
+        for (int w = 0; w < NW; w++) acc += s_med[w][tid];
+        v.tile_medium[6 * tile + tid] = acc;
     }
     const int my_field = reduce10_field(lane);
     __syncthreads();
     const int maxlast = s_maxlast;
 
-    for (int bend = maxlast; bend > 0; bend -= NT) {
-        const int b0 = max(0, bend - NT);
+    for (int bend = maxlast; bend > 0; bend -= NB) {
+        const int b0 = max(0, bend - NB);
         const int nb = bend - b0;
         __syncthreads();  // the previous batch's flush has read s_g / s_id
-        if (tid < nb) {
-            const uint32_t gid = gauss_ids[rg.x + b0 + tid];
-            const Rec r = rec[gid];
-            const float xl = (r.r0.x - (float)ox) + r.r0.z;
-            const float yl = (r.r0.y - (float)oy) + r.r0.w;
-            s0[tid] = make_float4(xl, yl, r.r1.x, r.r1.y);
-            s1[tid] = make_float4(r.r1.z, r.r1.w, r.r2.y, r.r2.z);
-            s2[tid] = make_float2(r.r2.w, r.r2.x);
-            s_id[tid] = gid;
+        for (int sl = tid; sl < nb; sl += NT) {
+            const uint32_t gid = v.gauss_ids[rg.x + b0 + sl];
+            stage_rec(v.rec, gid, ox, oy, s0, s1, s2, sl);
+            s_id[sl] = gid;
         }
+        for (int sl = tid; sl < NB; sl += NT)
 #pragma unroll
-        for (int f = 0; f < 10; f++) s_g[f][tid] = 0.f;
+            for (int f = 0; f < 10; f++) s_g[f][sl] = 0.f;
         __syncthreads();
         if (__any_sync(0xffffffffu, P[0].last > b0 || P[1].last > b0)) {
             for (int k = nb - 1; k >= 0; k--) {
@@ -415,73 +394,183 @@ __global__ void __launch_bounds__(TW *TH / 2, 8) k_blend_bwd(TileGeom tg, CamK c
                 bool any = pix_grad(P[0], j, pxl0 - a.x, dy, a.z, a.w, c.x, Bdy, Cdy2, c.y, c.z, c.w, e.x, e.y, acc);
                 any |= pix_grad(P[1], j, pxl1 - a.x, dy, a.z, a.w, c.x, Bdy, Cdy2, c.y, c.z, c.w, e.x, e.y, acc);
                 if (__any_sync(0xffffffffu, any)) {
-                    const float v = warp_reduce10(acc, lane);
-                    if (my_field >= 0) atomicAdd(&s_g[my_field][k], v);
+                    const float r = warp_reduce10(acc, lane);
+                    if (my_field >= 0) atomicAdd(&s_g[my_field][k], r);
                 }
             }
         }
         __syncthreads();
-        if (tid < nb) {
-            const float g[10] = {s_g[0][tid], s_g[1][tid], s_g[2][tid], s_g[3][tid], s_g[4][tid],
-                                 s_g[5][tid], s_g[6][tid], s_g[7][tid], s_g[8][tid], s_g[9][tid]};
+        for (int sl = tid; sl < nb; sl += NT) {
+            const float g[10] = {s_g[0][sl], s_g[1][sl], s_g[2][sl], s_g[3][sl], s_g[4][sl],
+                                 s_g[5][sl], s_g[6][sl], s_g[7][sl], s_g[8][sl], s_g[9][sl]};
             bool nz = false;
 #pragma unroll
             for (int f = 0; f < 10; f++) nz |= g[f] != 0.f;
             if (nz) {
-                GAcc *dst = gacc + s_id[tid];
+                GAcc *dst = v.gacc + s_id[sl];
                 atomicAdd(&dst->a0, make_float4(g[0], g[1], g[2], g[3]));
                 atomicAdd(&dst->a1, make_float4(g[4], g[5], g[6], 0.f));
                 atomicAdd(&dst->a2, make_float4(g[7], g[8], g[9], 0.f));
             }
         }
     }
-
 }
 
-template <int TW, int TH>
-void fwd_launch(const TileGeom &tg, const CamK &cam, const uint2 *ranges, const uint32_t *ids, const Rec *rec,
-                const float *medium, float *image, float *depth, float *depth01, float *fT, float *aA, float *zh,
-                uint32_t *nl, uint32_t *nw, cudaStream_t s)
+// ---------------------------------------------------------------------------
+// Kernels.
+
+template <int TW, int TH, int NB>
+__global__ void __launch_bounds__(128, 10) k_blend_fwd(BlendView v, const float *__restrict__ medium)
 {
-    k_blend_fwd<TW, TH><<<tg.tx * tg.ty, TW * TH / 2, 0, s>>>(tg, cam, ranges, ids, rec, medium, image, depth, depth01,
-                                                              fT, aA, zh, nl, nw);
-    count_launch();
+    blend_tile_fwd<TW, TH, NB>(v, blockIdx.x, medium);
 }
 
-template <int TW, int TH>
-void bwd_launch(const TileGeom &tg, const CamK &cam, const uint2 *ranges, const uint32_t *ids, const Rec *rec,
-                const float *medium, const float *fT, const float *aA, const float *zh, const uint32_t *nl,
-                const float *gi, const float *gd, const float *g01, GAcc *acc, float *tm, cudaStream_t s)
+template <int TW, int TH, int NB>
+__global__ void __launch_bounds__(128, 8) k_blend_bwd(BlendView v, const float *__restrict__ medium)
 {
-    k_blend_bwd<TW, TH><<<tg.tx * tg.ty, TW * TH / 2, 0, s>>>(tg, cam, ranges, ids, rec, medium, fT, aA, zh, nl, gi, gd,
-                                                              g01, acc, tm);
-    count_launch();
+    blend_tile_bwd<TW, TH, NB>(v, blockIdx.x, medium);
 }
+
+// Persistent: one wave of CTAs; each takes the next (view, tile) item from the
+// queue (items are ordered longest list first) until none is left. The only
+// shared state is an atomic ticket counter: nothing waits on another CTA.
+__device__ __forceinline__ bool next_item(int *counter, const uint32_t *n_items, int &it)
+{
+    __shared__ int s_item;
+    __syncthreads();  // everyone is done with the previous item
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    it = s_item;
+    return it < (int)*n_items;
+}
+
+template <int TW, int TH, int NB>
+__global__ void __launch_bounds__(128, 9) k_blend_fwd_persistent(const BlendView *__restrict__ views,
+                                                                  const uint32_t *__restrict__ items,
+                                                                  const uint32_t *__restrict__ n_items, int *counter,
+                                                                  const float *__restrict__ medium)
+{
+    int it;
+    while (next_item(counter, n_items, it)) {
+        const uint32_t code = items[it];
+        blend_tile_fwd<TW, TH, NB>(views[code >> 24], (int)(code & 0xffffffu), medium);
+    }
+}
+
+template <int TW, int TH, int NB>
+__global__ void __launch_bounds__(128, 8) k_blend_bwd_persistent(const BlendView *__restrict__ views,
+                                                                 const uint32_t *__restrict__ items,
+                                                                 const uint32_t *__restrict__ n_items, int *counter,
+                                                                 const float *__restrict__ medium)
+{
+    int it;
+    while (next_item(counter, n_items, it)) {
+        const uint32_t code = items[it];
+        blend_tile_bwd<TW, TH, NB>(views[code >> 24], (int)(code & 0xffffffu), medium);
+    }
+}
+
+// dispatch over tile shape x staging batch
+template <template <int, int, int> class F, class... Args>
+void dispatch(int tw, int nb, Args... args)
+{
+    const int bi = nb <= 64 ? 0 : (nb <= 128 ? 1 : 2);
+    if (tw == 8) {
+        if (bi == 0) F<8, 32, 64>::run(args...);
+        else if (bi == 1) F<8, 32, 128>::run(args...);
+        else F<8, 32, 256>::run(args...);
+    } else if (tw == 32) {
+        if (bi == 0) F<32, 8, 64>::run(args...);
+        else if (bi == 1) F<32, 8, 128>::run(args...);
+        else F<32, 8, 256>::run(args...);
+    } else {
+        if (bi == 0) F<16, 16, 64>::run(args...);
+        else if (bi == 1) F<16, 16, 128>::run(args...);
+        else F<16, 16, 256>::run(args...);
+    }
+}
+
+template <int TW, int TH, int NB>
+struct FwdPlain {
+    static void run(const BlendView &v, const float *medium, cudaStream_t s)
+    {
+        k_blend_fwd<TW, TH, NB><<<v.tg.tx * v.tg.ty, 128, 0, s>>>(v, medium);
+        count_launch();
+    }
+};
+template <int TW, int TH, int NB>
+struct BwdPlain {
+    static void run(const BlendView &v, const float *medium, cudaStream_t s)
+    {
+        k_blend_bwd<TW, TH, NB><<<v.tg.tx * v.tg.ty, 128, 0, s>>>(v, medium);
+        count_launch();
+    }
+};
+template <int TW, int TH, int NB>
+struct FwdPersistent {
+    static void run(const BlendView *v, const uint32_t *items, const uint32_t *n, int *counter, const float *medium,
+                    int ctas, cudaStream_t s)
+    {
+        k_blend_fwd_persistent<TW, TH, NB><<<ctas, 128, 0, s>>>(v, items, n, counter, medium);
+        count_launch();
+    }
+};
+template <int TW, int TH, int NB>
+struct BwdPersistent {
+    static void run(const BlendView *v, const uint32_t *items, const uint32_t *n, int *counter, const float *medium,
+                    int ctas, cudaStream_t s)
+    {
+        k_blend_bwd_persistent<TW, TH, NB><<<ctas, 128, 0, s>>>(v, items, n, counter, medium);
+        count_launch();
+    }
+};
+template <int TW, int TH, int NB>
+struct Occupancy {
+    static void run(bool backward, int *out)
+    {
+        int dev = 0, sms = 148, per = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (backward)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_blend_bwd_persistent<TW, TH, NB>, 128, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_blend_fwd_persistent<TW, TH, NB>, 128, 0);
+        *out = sms * (per > 0 ? per : 1);
+    }
+};
 
 }  // namespace
 
-void launch_blend_fwd(const TileGeom &tg, const CamK &cam, const uint2 *ranges, const uint32_t *ids, const Rec *rec,
-                      const float *medium, float *image, float *depth, float *depth01, float *fT, float *aA, float *zh,
-                      uint32_t *nl, uint32_t *nw, cudaStream_t s)
+void launch_blend_fwd(const BlendView &v, const float *medium, int batch, cudaStream_t s)
 {
-    if (tg.tw == 8)
-        fwd_launch<8, 32>(tg, cam, ranges, ids, rec, medium, image, depth, depth01, fT, aA, zh, nl, nw, s);
-    else if (tg.tw == 32)
-        fwd_launch<32, 8>(tg, cam, ranges, ids, rec, medium, image, depth, depth01, fT, aA, zh, nl, nw, s);
-    else
-        fwd_launch<16, 16>(tg, cam, ranges, ids, rec, medium, image, depth, depth01, fT, aA, zh, nl, nw, s);
+    dispatch<FwdPlain>(v.tg.tw, batch, v, medium, s);
 }
 
-void launch_blend_bwd(const TileGeom &tg, const CamK &cam, const uint2 *ranges, const uint32_t *ids, const Rec *rec,
-                      const float *medium, const float *fT, const float *aA, const float *zh, const uint32_t *nl,
-                      const float *gi, const float *gd, const float *g01, GAcc *acc, float *tm, cudaStream_t s)
+void launch_blend_bwd(const BlendView &v, const float *medium, int batch, cudaStream_t s)
 {
-    if (tg.tw == 8)
-        bwd_launch<8, 32>(tg, cam, ranges, ids, rec, medium, fT, aA, zh, nl, gi, gd, g01, acc, tm, s);
-    else if (tg.tw == 32)
-        bwd_launch<32, 8>(tg, cam, ranges, ids, rec, medium, fT, aA, zh, nl, gi, gd, g01, acc, tm, s);
-    else
-        bwd_launch<16, 16>(tg, cam, ranges, ids, rec, medium, fT, aA, zh, nl, gi, gd, g01, acc, tm, s);
+    dispatch<BwdPlain>(v.tg.tw, batch, v, medium, s);
+}
+
+void launch_blend_fwd_persistent(int tw, int th, int batch, const BlendView *views, const uint32_t *items,
+                                 const uint32_t *n_items, int *counter, const float *medium, int ctas, cudaStream_t s)
+{
+    (void)th;
+    dispatch<FwdPersistent>(tw, batch, views, items, n_items, counter, medium, ctas, s);
+}
+
+void launch_blend_bwd_persistent(int tw, int th, int batch, const BlendView *views, const uint32_t *items,
+                                 const uint32_t *n_items, int *counter, const float *medium, int ctas, cudaStream_t s)
+{
+    (void)th;
+    dispatch<BwdPersistent>(tw, batch, views, items, n_items, counter, medium, ctas, s);
+}
+
+int blend_persistent_ctas(int tw, int th, int batch, bool backward)
+{
+    (void)th;
+    int out = 148;
+    dispatch<Occupancy>(tw, batch, backward, &out);
+    return out;
 }
 
 }  // namespace splash

@@ -1,0 +1,201 @@
+// Host-side pieces shared by the C ABI translation units: grow-only device
+// buffers, stage timing, argument checks, and the context/state objects.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace splash_host {
+
+struct Buf {
+    void *p = nullptr;
+    size_t cap = 0;
+    Buf() = default;
+    Buf(const Buf &) = delete;
+    Buf &operator=(const Buf &) = delete;
+    ~Buf() { release(); }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    // grow-only; contents are not preserved
+    bool ensure(size_t bytes)
+    {
+        if (bytes <= cap) return true;
+        release();
+        const size_t want = std::max<size_t>(bytes + bytes / 4, 256);
+        if (cudaMalloc(&p, want) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return false;
+        }
+        cap = want;
+        return true;
+    }
+    template <class T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+// Per-stage CUDA-event timing (tracing aid)
+struct Prof {
+    bool on = false;
+    struct Rec {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<cudaEvent_t> spare;
+    std::vector<Rec> pending;
+    double ms[SPLASH_STAGE_COUNT] = {};
+    int64_t cnt[SPLASH_STAGE_COUNT] = {};
+    cudaEvent_t take()
+    {
+        if (!spare.empty()) {
+            cudaEvent_t e = spare.back();
+            spare.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return e;
+    }
+    ~Prof()
+    {
+        for (auto &r : pending) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        for (auto e : spare) cudaEventDestroy(e);
+    }
+};
+
+// Records a start event on construction and the stop event on destruction.
+struct Stage {
+    Prof &p;
+    int stage;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    Stage(Prof &p_, int stage_, cudaStream_t s_) : p(p_), stage(stage_), s(s_)
+    {
+        if (p.on && (a = p.take())) cudaEventRecord(a, s);
+    }
+    ~Stage()
+    {
+        if (!a) return;
+        cudaEvent_t b = p.take();
+        if (!b) {
+            p.spare.push_back(a);
+            return;
+        }
+        cudaEventRecord(b, s);
+        p.pending.push_back({stage, a, b});
+    }
+};
+
+inline splash_status fail(splash_status s, const std::string &msg)
+{
+    splash_set_error(msg);
+    return s;
+}
+
+inline bool valid_tile(int tw, int th) { return (tw == 16 && th == 16) || (tw == 8 && th == 32) || (tw == 32 && th == 8); }
+
+inline splash::CamK make_cam(const splash_camera &c)
+{
+    splash::CamK k{};
+    for (int r = 0; r < 3; r++) {
+        for (int j = 0; j < 3; j++) k.R[3 * r + j] = c.world_to_cam[4 * r + j];
+        k.t[r] = c.world_to_cam[4 * r + 3];
+    }
+    for (int j = 0; j < 3; j++)
+        k.cpos[j] = (float)-((double)k.R[j] * k.t[0] + (double)k.R[3 + j] * k.t[1] + (double)k.R[6 + j] * k.t[2]);
+    k.fx = c.fx;
+    k.fy = c.fy;
+    k.cx = c.cx;
+    k.cy = c.cy;
+    k.limx = (float)(1.3 * 0.5 * c.width / c.fx);
+    k.limy = (float)(1.3 * 0.5 * c.height / c.fy);
+    k.znear = c.z_near;
+    k.zfar = c.z_far;
+    k.W = c.width;
+    k.H = c.height;
+    return k;
+}
+
+inline splash_status check_camera(const splash_camera *cam)
+{
+    if (!cam) return fail(SPLASH_ERR_INVALID_ARG, "null camera");
+    if (cam->width <= 0 || cam->height <= 0 || cam->width > 32768 || cam->height > 32768)
+        return fail(SPLASH_ERR_INVALID_ARG, "image size must be in 1..32768");
+    if (!(cam->fx > 0.f) || !(cam->fy > 0.f)) return fail(SPLASH_ERR_INVALID_ARG, "focal lengths must be positive");
+    if (!(cam->z_near > 0.f) || !(cam->z_far > cam->z_near))
+        return fail(SPLASH_ERR_INVALID_ARG, "need 0 < z_near < z_far");
+    return SPLASH_OK;
+}
+
+inline splash_status check_gaussians(const splash_gaussians *g)
+{
+    if (!g) return fail(SPLASH_ERR_INVALID_ARG, "null gaussians");
+    if (g->n < 0 || g->n >= (int64_t)1 << 31) return fail(SPLASH_ERR_INVALID_ARG, "n must be in [0, 2^31)");
+    if (g->sh_degree < 0 || g->sh_degree > 3) return fail(SPLASH_ERR_INVALID_ARG, "sh_degree must be 0..3");
+    if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
+        return fail(SPLASH_ERR_INVALID_ARG, "null gaussian buffer");
+    if (g->n > 0 && (reinterpret_cast<uintptr_t>(g->quats) & 15))
+        return fail(SPLASH_ERR_INVALID_ARG, "quats must be 16-byte aligned");
+    return SPLASH_OK;
+}
+
+inline int bits_for(int64_t count)
+{
+    int b = 0;
+    while (((int64_t)1 << b) < count) b++;
+    return b;
+}
+
+}  // namespace splash_host
+
+#define ENSURE(buf, bytes)                                                                                \
+    do {                                                                                                  \
+        if (!(buf).ensure(bytes)) return splash_host::fail(SPLASH_ERR_OOM, "cudaMalloc failed for " #buf); \
+    } while (0)
+
+struct splash_ctx {
+    splash_options opt;
+    uint32_t *d_status = nullptr;  // kernel-reported error bits
+    splash_host::Prof prof;
+};
+
+struct splash_state {
+    splash_ctx *ctx = nullptr;
+    // per Gaussian
+    splash_host::Buf rec, depth_key, tt, rect, dk0, dv0, dk1, dv1, offsets, scan_sums;
+    // per (tile, Gaussian) pair
+    splash_host::Buf tk0, tv0, tk1, tv1;
+    splash_host::Buf ranges, sort_scratch;
+    // per pixel
+    splash_host::Buf fT, aA, zh, nlast, nwalk;
+    // backward
+    splash_host::Buf gacc, tile_med, block_med, gmed, red_scratch;
+    // loss / standalone sort
+    splash_host::Buf loss_scratch, tmp_k, tmp_v;
+    splash_host::Buf small;       // [0] = pair count K, [1..] spare
+    uint32_t *h_small = nullptr;  // pinned: K, status
+    // what the last forward produced
+    bool has_forward = false;
+    int64_t n = 0;
+    int W = 0, H = 0;
+    splash::TileGeom tg{};
+    int64_t K = 0;
+    const uint32_t *order = nullptr;     // depth-sorted Gaussian indices
+    const uint32_t *tile_ids = nullptr;  // sorted pairs
+    const uint32_t *gauss_ids = nullptr;
+};

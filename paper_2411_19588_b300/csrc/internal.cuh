@@ -85,6 +85,23 @@ __device__ __forceinline__ void adam_update(float &p, float g, float &m, float &
     p -= __fdividef(lr * h.rbc1 * m, fmaf(sqrtf(v), h.rsbc2, h.eps));
 }
 
+// Everything the blend of one view needs (forward state, outputs, and for the
+// backward the upstream gradients and accumulators). Plain launches take one
+// by value; the persistent launches read an array of them.
+struct BlendView {
+    CamK cam;
+    TileGeom tg;
+    const uint2 *ranges;
+    const uint32_t *gauss_ids;
+    const Rec *rec;
+    float *image, *depth, *depth01;       // outputs (depth, depth01 may be null)
+    float *final_T, *acc_alpha, *zhat;    // per-pixel forward state
+    uint32_t *n_last, *n_walk;
+    const float *dL_dimage, *dL_ddepth, *dL_ddepth01;  // backward inputs (last two may be null)
+    GAcc *gacc;                           // backward: per-Gaussian accumulators
+    float *tile_medium;                   // backward: per-tile medium partials [tiles][6]
+};
+
 // device status word bits
 enum : uint32_t { kStatusTimeout = 1u, kStatusCapacity = 2u };
 
@@ -122,14 +139,18 @@ void launch_emit(int64_t n, const uint32_t *order, const uint32_t *offsets, cons
                  cudaStream_t s);
 void launch_ranges(int64_t k_host, const uint32_t *k_dev, const uint32_t *tile_ids, uint2 *ranges, int ntiles,
                    cudaStream_t s);
-void launch_blend_fwd(const TileGeom &tg, const CamK &cam, const uint2 *ranges, const uint32_t *gauss_ids,
-                      const Rec *rec, const float *medium, float *image, float *depth, float *depth01,
-                      float *final_T, float *acc_alpha, float *zhat, uint32_t *n_last, uint32_t *n_walk,
-                      cudaStream_t s);
-void launch_blend_bwd(const TileGeom &tg, const CamK &cam, const uint2 *ranges, const uint32_t *gauss_ids,
-                      const Rec *rec, const float *medium, const float *final_T, const float *acc_alpha,
-                      const float *zhat, const uint32_t *n_last, const float *dL_dimage, const float *dL_ddepth,
-                      const float *dL_ddepth01, GAcc *acc, float *tile_medium, cudaStream_t s);
+// staging batch sizes the blend kernels are built for
+constexpr int kBlendBatches[3] = {64, 128, 256};
+void launch_blend_fwd(const BlendView &v, const float *medium, int batch, cudaStream_t s);
+void launch_blend_bwd(const BlendView &v, const float *medium, int batch, cudaStream_t s);
+// Persistent forms: `ctas` CTAs pull work items from a queue (items[k] =
+// view << 24 | tile, taken in order; *counter must be zero on entry) until
+// n_items (read from the device) are done. All views share one tile shape.
+void launch_blend_fwd_persistent(int tw, int th, int batch, const BlendView *views, const uint32_t *items,
+                                 const uint32_t *n_items, int *counter, const float *medium, int ctas, cudaStream_t s);
+void launch_blend_bwd_persistent(int tw, int th, int batch, const BlendView *views, const uint32_t *items,
+                                 const uint32_t *n_items, int *counter, const float *medium, int ctas, cudaStream_t s);
+int blend_persistent_ctas(int tw, int th, int batch, bool backward);
 void launch_preprocess_bwd(int64_t n, const splash_gaussians &g, const float *medium, const CamK &cam,
                            const GAcc *acc, const uint32_t *depth_key, const splash_grads &out,
                            float *block_medium, int *n_blocks_out, cudaStream_t s);
@@ -141,6 +162,10 @@ void launch_preprocess_bwd_adam(int64_t n, int sh_degree, const splash_param_buf
                                 float *block_medium, int *n_blocks_out, cudaStream_t s);
 void launch_medium_adam(float *medium, const float *grad, const splash_adam_config &cfg, cudaStream_t s);
 int preprocess_bwd_blocks(int64_t n);
+int preprocess_bwd_multi_blocks(int64_t n);
+void launch_preprocess_bwd_multi(int64_t n, int V, const splash_gaussians &g, const float *medium, const BlendView *views,
+                                 const GAcc *gacc, const uint32_t *depth_keys, int64_t key_stride,
+                                 const splash_grads &out, float *block_medium, cudaStream_t s);
 
 // Deterministic column sums of a row-major [rows][cols] float table (cols <=
 // 16), first stage: kColsumParts CTAs each write one row of partial sums to

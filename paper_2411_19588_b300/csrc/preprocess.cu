@@ -327,14 +327,16 @@ constexpr int kBwdThreads = 128;
 
 // Adjoint of the preprocess for one Gaussian: from its blend accumulators
 // `ga` to the gradients of its parameters. `row` holds the Gaussian's SH
-// coefficients on entry and their gradients on exit; gmed accumulates the
-// Gaussian's share of the medium gradient (through ct = c a - B b).
-template <int DEG>
+// coefficients; their gradients go to `grow` (which may be `row` itself:
+// every coefficient is read before any gradient is written), added to it
+// when ACC. gmed accumulates the Gaussian's share of the medium gradient
+// (through ct = c a - B b).
+template <int DEG, bool ACC = false>
 __device__ __forceinline__ void gaussian_chain(int i, const float *__restrict__ means, const float *__restrict__ log_scales,
                                                const float *__restrict__ quats, const float *__restrict__ ologits,
                                                const float *__restrict__ medium, const CamK &cam, const GAcc &ga,
-                                               float *row, float gmean[3], float gls[3], float gq[4], float &glogit,
-                                               float gmed[9])
+                                               const float *row, float *grow, float gmean[3], float gls[3], float gq[4],
+                                               float &glogit, float gmed[9])
 {
     constexpr int K = (DEG + 1) * (DEG + 1);
     const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
@@ -459,13 +461,14 @@ __device__ __forceinline__ void gaussian_chain(int i, const float *__restrict__ 
     float w[K];
 #pragma unroll
     for (int k = 0; k < K; k++) w[k] = graw[0] * row[3 * k] + graw[1] * row[3 * k + 1] + graw[2] * row[3 * k + 2];
-    // the coefficients are no longer needed: overwrite them with their gradients
+    // the coefficients have all been read: write (or add) their gradients
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-        row[3 * k] = graw[0] * Y[k];
-        row[3 * k + 1] = graw[1] * Y[k];
-        row[3 * k + 2] = graw[2] * Y[k];
-    }
+    for (int k = 0; k < K; k++)
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) {
+            if constexpr (ACC) grow[3 * k + ch] += graw[ch] * Y[k];
+            else grow[3 * k + ch] = graw[ch] * Y[k];
+        }
     const float3 gdir = sh_basis_vjp<DEG>(dx, dy, dz, w);
     const float gdd = gdir.x * dx + gdir.y * dy + gdir.z * dz;
 
@@ -493,6 +496,7 @@ __device__ __forceinline__ bool has_grad(int i, int n, const GAcc *__restrict__ 
 }
 
 // block partial of the 9 medium-gradient terms: warp shuffle, then one row per block
+template <int NWARPS = kBwdThreads / 32>
 __device__ __forceinline__ void medium_partial(float gmed[9], float (*s_med)[9], float *__restrict__ block_medium)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -507,7 +511,7 @@ __device__ __forceinline__ void medium_partial(float gmed[9], float (*s_med)[9],
     if (threadIdx.x < 9) {
         float v = 0.f;
 #pragma unroll
-        for (int w2 = 0; w2 < kBwdThreads / 32; w2++) v += s_med[w2][threadIdx.x];
+        for (int w2 = 0; w2 < NWARPS; w2++) v += s_med[w2][threadIdx.x];
         block_medium[blockIdx.x * 9 + threadIdx.x] = v;
     }
 }
@@ -535,7 +539,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd(
     float *row = s_sh[warp] + lane * ROW;  // SH coefficients in, their gradients out
     GAcc ga;
     if (has_grad(i, n, acc, depth_key, ga)) {
-        gaussian_chain<DEG>(i, means, log_scales, quats, ologits, medium, cam, ga, row, gmean, gls, gq, glogit, gmed);
+        gaussian_chain<DEG>(i, means, log_scales, quats, ologits, medium, cam, ga, row, row, gmean, gls, gq, glogit, gmed);
     } else if (i < n) {
 #pragma unroll
         for (int k = 0; k < KC; k++) row[k] = 0.f;
@@ -557,6 +561,70 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd(
     __syncwarp();
     if (g_sh) unstage_rows<KC>(g_sh, wbase, cnt, lane, s_sh[warp]);
     medium_partial(gmed, s_med, block_medium);
+}
+
+// Adjoint over a batch of views: each Gaussian's parameters and SH block are
+// read once, its gradient from every view (accumulators gacc[v][i]) is added
+// in registers and in a shared-memory row, and written once.
+constexpr int kMultiThreads = 64;
+template <int DEG>
+__global__ void __launch_bounds__(kMultiThreads) k_preprocess_bwd_multi(
+    int n, int V, const float *__restrict__ means, const float *__restrict__ log_scales, const float *__restrict__ quats,
+    const float *__restrict__ ologits, const float *__restrict__ sh, const float *__restrict__ medium,
+    const BlendView *__restrict__ views, const GAcc *__restrict__ gacc, const uint32_t *__restrict__ depth_keys,
+    int64_t key_stride, float *__restrict__ g_means, float *__restrict__ g_ls, float *__restrict__ g_quats, float *__restrict__ g_ologits,
+    float *__restrict__ g_sh, float *__restrict__ block_medium)
+{
+    constexpr int KC = 3 * (DEG + 1) * (DEG + 1);
+    constexpr int ROW = KC + 1;
+    constexpr int NW = kMultiThreads / 32;
+    __shared__ float s_sh[NW][32 * ROW];  // coefficients
+    __shared__ float s_gr[NW][32 * ROW];  // their gradients, summed over views
+    __shared__ float s_med[NW][9];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t wbase = (int64_t)blockIdx.x * kMultiThreads + warp * 32;
+    const int cnt = (int)max((int64_t)0, min((int64_t)32, (int64_t)n - wbase));
+    stage_sh<KC>(sh, wbase, cnt, lane, s_sh[warp]);
+    const int i = (int)(wbase + lane);
+    const float *row = s_sh[warp] + lane * ROW;
+    float *grow = s_gr[warp] + lane * ROW;
+#pragma unroll
+    for (int k = 0; k < KC; k++) grow[k] = 0.f;
+    __syncwarp();
+    float gmed[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float gmean[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, glogit = 0.f;
+    for (int v = 0; v < V; v++) {
+        GAcc ga;
+        if (!has_grad(i, n, gacc + (int64_t)v * n, depth_keys + (int64_t)v * key_stride, ga)) continue;
+        float m3[3], l3[3], q4[4], lg;
+        gaussian_chain<DEG, true>(i, means, log_scales, quats, ologits, medium, views[v].cam, ga, row, grow, m3, l3, q4,
+                                  lg, gmed);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            gmean[k] += m3[k];
+            gls[k] += l3[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) gq[k] += q4[k];
+        glogit += lg;
+    }
+    if (i < n) {
+        if (g_means) {
+            g_means[3 * i] = gmean[0];
+            g_means[3 * i + 1] = gmean[1];
+            g_means[3 * i + 2] = gmean[2];
+        }
+        if (g_ls) {
+            g_ls[3 * i] = gls[0];
+            g_ls[3 * i + 1] = gls[1];
+            g_ls[3 * i + 2] = gls[2];
+        }
+        if (g_quats) reinterpret_cast<float4 *>(g_quats)[i] = make_float4(gq[0], gq[1], gq[2], gq[3]);
+        if (g_ologits) g_ologits[i] = glogit;
+    }
+    __syncwarp();
+    if (g_sh) unstage_rows<KC>(g_sh, wbase, cnt, lane, s_gr[warp]);
+    medium_partial<NW>(gmed, s_med, block_medium);
 }
 
 // Moments and learning rates of the fused update: groups 0..4 = means,
@@ -593,7 +661,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_preprocess_bwd_adam(
     float *row = s_sh[warp] + lane * ROW;
     GAcc ga;
     if (has_grad(i, n, acc, depth_key, ga)) {
-        gaussian_chain<DEG>(i, means, log_scales, quats, ologits, medium, cam, ga, row, gmean, gls, gq, glogit, gmed);
+        gaussian_chain<DEG>(i, means, log_scales, quats, ologits, medium, cam, ga, row, row, gmean, gls, gq, glogit, gmed);
     } else if (i < n) {
 #pragma unroll
         for (int k = 0; k < KC; k++) row[k] = 0.f;
@@ -727,6 +795,29 @@ void launch_preprocess_fwd(int64_t n, const splash_gaussians &g, const float *me
 }
 
 int preprocess_bwd_blocks(int64_t n) { return (int)((n + kBwdThreads - 1) / kBwdThreads); }
+int preprocess_bwd_multi_blocks(int64_t n) { return (int)((n + kMultiThreads - 1) / kMultiThreads); }
+
+void launch_preprocess_bwd_multi(int64_t n, int V, const splash_gaussians &g, const float *medium, const BlendView *views,
+                                 const GAcc *gacc, const uint32_t *depth_keys, int64_t key_stride, const splash_grads &o,
+                                 float *bm, cudaStream_t s)
+{
+    if (n <= 0) return;
+    const int blocks = preprocess_bwd_multi_blocks(n);
+#define SPLASH_MULTI(D)                                                                                               \
+    k_preprocess_bwd_multi<D><<<blocks, kMultiThreads, 0, s>>>((int)n, V, g.means, g.log_scales, g.quats,             \
+                                                               g.opacity_logits, g.sh, medium, views, gacc, depth_keys, \
+                                                               key_stride,                                              \
+                                                               o.means, o.log_scales, o.quats, o.opacity_logits, o.sh,  \
+                                                               bm)
+    switch (g.sh_degree) {
+    case 0: SPLASH_MULTI(0); break;
+    case 1: SPLASH_MULTI(1); break;
+    case 2: SPLASH_MULTI(2); break;
+    default: SPLASH_MULTI(3); break;
+    }
+#undef SPLASH_MULTI
+    count_launch();
+}
 
 void launch_preprocess_bwd(int64_t n, const splash_gaussians &g, const float *medium, const CamK &cam,
                            const GAcc *acc, const uint32_t *dk, const splash_grads &o, float *bm, int *nb,

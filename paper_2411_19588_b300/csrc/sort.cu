@@ -39,7 +39,8 @@ __global__ void __launch_bounds__(256) k_hist(const uint32_t *__restrict__ keys,
     for (int p = 0; p < 4; p++) pmask[p] = (1u << min(kRadixBits, max(0, bits - kRadixBits * p))) - 1u;
     const int64_t n = n_dev ? (int64_t)*n_dev : n_host;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t n4 = n >> 2;
+    // 16-byte loads only from a 16-byte-aligned base; otherwise all scalar
+    const int64_t n4 = (reinterpret_cast<uintptr_t>(keys) & 15) ? 0 : (n >> 2);
     const uint4 *k4 = reinterpret_cast<const uint4 *>(keys);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
         const uint4 v = k4[i];

@@ -124,11 +124,13 @@ __global__ void __launch_bounds__(256) k_emit(int64_t n, const uint32_t *__restr
 }
 
 __global__ void __launch_bounds__(256) k_ranges(int64_t k_host, const uint32_t *__restrict__ k_dev,
-                                                const uint32_t *__restrict__ tile_ids, uint2 *__restrict__ ranges)
+                                                const uint32_t *__restrict__ tile_ids, uint2 *__restrict__ ranges,
+                                                uint32_t ntiles)
 {
     const int64_t k = k_dev ? (int64_t)*k_dev : k_host;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t t = tile_ids[i];
+        if (t >= ntiles) continue;  // only after a capacity overflow (reported through the status word)
         if (i == 0 || tile_ids[i - 1] != t) ranges[t].x = (uint32_t)i;
         if (i == k - 1 || tile_ids[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
     }
@@ -167,7 +169,7 @@ void launch_ranges(int64_t k_host, const uint32_t *k_dev, const uint32_t *tile_i
     cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)ntiles, s);
     if (k_host <= 0) return;
     const int blocks = (int)std::min<int64_t>((k_host + 255) / 256, 148 * 32);
-    k_ranges<<<blocks, 256, 0, s>>>(k_host, k_dev, tile_ids, ranges);
+    k_ranges<<<blocks, 256, 0, s>>>(k_host, k_dev, tile_ids, ranges, (uint32_t)ntiles);
     count_launch();
 }
 

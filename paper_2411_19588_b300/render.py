@@ -82,9 +82,9 @@ class State:
 
 
 class Renderer:
-    def __init__(self, tile=(16, 16), spin_limit: int = 0, test_stall_partition: int = 0):
+    def __init__(self, tile=(16, 16), spin_limit: int = 0, test_stall_partition: int = 0, batch: int = 128):
         L = _abi.lib()
-        opt = _abi.Options(int(tile[0]), int(tile[1]), int(spin_limit), int(test_stall_partition))
+        opt = _abi.Options(int(tile[0]), int(tile[1]), int(spin_limit), int(test_stall_partition), int(batch))
         h = ctypes.c_void_p()
         _abi.check(L.splash_create(ctypes.byref(opt), ctypes.byref(h)), "splash_create")
         self._ctx = h
@@ -214,12 +214,13 @@ class Renderer:
                 "tile_h": info.tile_h, "n_gaussians": info.n_gaussians}
 
     # -- training-step pieces
-    def loss(self, st: State, image: torch.Tensor, target: torch.Tensor, lam: float = 0.2, need_grad: bool = True):
+    def loss(self, st: State, image: torch.Tensor, target: torch.Tensor, lam: float = 0.2, need_grad: bool = True,
+             loss_out: torch.Tensor | None = None, grad_out: torch.Tensor | None = None):
         _check_tensor(image, "image")
         _check_tensor(target, "target", tuple(image.shape))
         C, H, W = image.shape
-        loss = torch.empty(1, device=image.device, dtype=torch.float32)
-        grad = torch.empty_like(image) if need_grad else None
+        loss = torch.empty(1, device=image.device, dtype=torch.float32) if loss_out is None else loss_out
+        grad = (torch.empty_like(image) if grad_out is None else grad_out) if need_grad else None
         rc = _abi.lib().splash_loss_l1_ssim(self._ctx, st.handle, image.data_ptr(), target.data_ptr(), C, H, W,
                                             float(lam), loss.data_ptr(), _abi.ptr(grad), _stream())
         _abi.check(rc, "splash_loss_l1_ssim")
@@ -245,6 +246,64 @@ class Renderer:
 
     def sync_status(self):
         _abi.check(_abi.lib().splash_sync_status(self._ctx, _stream()), "splash_sync_status")
+
+
+class Batch:
+    """Many views of one scene rendered and differentiated as one unit (one
+    persistent blend launch each way, no host synchronisation after
+    calibrate(): forward/backward can be captured in a CUDA graph)."""
+
+    def __init__(self, renderer: Renderer, cams: list):
+        self.r = renderer
+        self.cams = list(cams)
+        arr = (_abi.Camera * len(cams))(*[camera_struct(c) for c in cams])
+        h = ctypes.c_void_p()
+        _abi.check(_abi.lib().splash_batch_create(renderer._ctx, len(cams), arr, ctypes.byref(h)), "splash_batch_create")
+        self._h = h
+        self.images = None
+
+    def close(self):
+        if self._h:
+            _abi.lib().splash_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def calibrate(self, params: dict, medium: torch.Tensor, headroom: float = 1.25):
+        g = gaussians_struct(params)
+        _abi.check(_abi.lib().splash_batch_calibrate(self._h, ctypes.byref(g), medium.data_ptr(), float(headroom),
+                                                     _stream()), "splash_batch_calibrate")
+        dev = medium.device
+        self.images = [torch.empty((3, c.height, c.width), device=dev) for c in self.cams]
+
+    def forward(self, params: dict, medium: torch.Tensor, images=None):
+        images = images if images is not None else self.images
+        ptrs = (ctypes.c_void_p * len(images))(*[t.data_ptr() for t in images])
+        g = gaussians_struct(params)
+        _abi.check(_abi.lib().splash_batch_forward(self._h, ctypes.byref(g), medium.data_ptr(), ptrs, None, None,
+                                                   _stream()), "splash_batch_forward")
+        return images
+
+    def backward(self, params: dict, medium: torch.Tensor, dL_dimages: list, grads: dict | None = None) -> dict:
+        if grads is None:
+            grads = {k: torch.empty_like(params[k]) for k in PARAM_NAMES}
+            grads["medium"] = torch.empty_like(medium)
+        ptrs = (ctypes.c_void_p * len(dL_dimages))(*[t.data_ptr() for t in dL_dimages])
+        gs = _abi.Grads(*(grads[k].data_ptr() if grads.get(k) is not None else None for k in PARAM_NAMES + ("medium",)))
+        g = gaussians_struct(params)
+        _abi.check(_abi.lib().splash_batch_backward(self._h, ctypes.byref(g), medium.data_ptr(), ptrs, ctypes.byref(gs),
+                                                    _stream()), "splash_batch_backward")
+        return grads
+
+    def pair_counts(self):
+        V = len(self.cams)
+        em, cap = (ctypes.c_int64 * V)(), (ctypes.c_int64 * V)()
+        _abi.check(_abi.lib().splash_batch_pair_counts(self._h, em, cap, _stream()), "splash_batch_pair_counts")
+        return list(em), list(cap)
 
 
 def kernel_launches() -> int:

@@ -22,7 +22,7 @@ def test_binding_struct_sizes_match_header_layout():
     # int32 x2 + float x4 + float[12] + float x2
     assert ctypes.sizeof(_abi.Camera) == 4 * (2 + 4 + 12 + 2)
     assert ctypes.sizeof(_abi.Gaussians) == 8 * 5 + 8 + 8
-    assert ctypes.sizeof(_abi.Options) == 16
+    assert ctypes.sizeof(_abi.Options) == 20
     assert ctypes.sizeof(_abi.AdamGroup) == 8 * 4 + 8 + 4 + 4 + 4 + 4
 
 

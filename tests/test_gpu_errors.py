@@ -20,7 +20,8 @@ pytestmark = pytest.mark.gpu
 def test_invalid_arguments_are_rejected(cuda_lib):
     L = _abi.lib()
     h = ctypes.c_void_p()
-    assert L.splash_create(ctypes.byref(_abi.Options(12, 12, 0, 0)), ctypes.byref(h)) == _abi.ERR_INVALID_ARG
+    assert L.splash_create(ctypes.byref(_abi.Options(12, 12, 0, 0, 0)), ctypes.byref(h)) == _abi.ERR_INVALID_ARG
+    assert L.splash_create(ctypes.byref(_abi.Options(16, 16, 0, 0, 96)), ctypes.byref(h)) == _abi.ERR_INVALID_ARG
     r = R.Renderer()
     st = r.state()
     g, m, cam = scenes.tiny_scene(0)
