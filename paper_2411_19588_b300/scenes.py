@@ -317,3 +317,30 @@ def perturb(g: Gaussians, medium: Medium, seed: int = 1):
     p.sh[:, 0, :] += (rng.normal(0, 0.05, (p.n, 3)) / _SH_DC).astype(np.float32)
     m = Medium(*(np.asarray(a * (1 + rng.normal(0, 0.1, 3)), np.float32) for a in (medium.beta_d, medium.beta_b, medium.b_inf)))
     return p, m
+
+
+def mlp_init(seed: int):
+    """Initial weights of the 3080 -> 128 -> 128 -> 9 warm-start MLP: He-normal
+    hidden layers, output layer N(0, 0.01), zero hidden biases and output
+    biases -0.957 (softplus -> 0.325, the centre of the beta range) and
+    -1.237 (sigmoid -> 0.225, the centre of the B_inf range). FP32."""
+    rng = np.random.default_rng(seed)
+    f = lambda a: np.asarray(a, np.float32)
+    return {"W1": f(rng.normal(0, math.sqrt(2.0 / 3080), (128, 3080))), "b1": f(np.zeros(128)),
+            "W2": f(rng.normal(0, math.sqrt(2.0 / 128), (128, 128))), "b2": f(np.zeros(128)),
+            "W3": f(rng.normal(0, 0.01, (9, 128))), "b3": f([-0.957] * 6 + [-1.237] * 3)}
+
+
+def view_maps(seed: int, width: int, height: int, z_far: float = 20.0):
+    """A synthetic rendered view for feature tests: image [3,H,W] with smooth
+    gradients plus noise in [0, 1.2], depth [H,W] in (0, z_far] with a
+    background region at exactly z_far and a few pixels on bin edges."""
+    rng = np.random.default_rng(seed)
+    yy, xx = np.mgrid[0:height, 0:width]
+    img = np.stack([0.5 + 0.4 * np.sin(xx / (7.0 + c) + yy / (11.0 - c)) for c in range(3)])
+    img = np.clip(img + rng.normal(0, 0.1, img.shape), 0, 1.2).astype(np.float32)
+    depth = rng.uniform(0.3, z_far, (height, width)).astype(np.float32)
+    depth[: height // 4, : width // 3] = z_far
+    edges = (np.arange(1, 8) * (z_far / 8.0)).astype(np.float32)
+    depth.ravel()[rng.choice(depth.size, 7, replace=False)] = edges
+    return img, depth
