@@ -314,6 +314,71 @@ splash_status splash_sort_pairs_u32_noalloc(const uint32_t *keys_in, const uint3
                                             uint32_t *vals_out, int64_t n, int32_t key_bits, uint32_t *status_out,
                                             void *stream);
 
+/* ---- Learned warm-start (Sec. IV-C fit initialisation) --------------------
+ * The paper has no learned part. These calls predict the nine per-channel
+ * medium parameters of Eq. 4-5 (beta_D[3], beta_B[3], B_inf[3]) from one
+ * rendered view, so that the fit can start from them; the plain fit stays the
+ * fallback and the judge of the prediction.
+ *
+ * Feature row of a view (splash_featurise): SPLASH_MLP_ROW BF16 values =
+ * the 32x32 adaptive-average downsample of image [3,H,W] (channel-major,
+ * cell (i,j) averages rows floor(iH/32)..ceil((i+1)H/32)-1 and the same in
+ * x), then an 8-bin histogram of the Eq. 6 depth over [0, z_far] (bin =
+ * floor(fl32(8 z) / z_far) clamped to 0..7, NaN in bin 7, divided by H W),
+ * then 1 (the bias input), then zeros. All pointers are device pointers; the
+ * row must be 16-byte aligned. The call uses an 8-counter scratch owned by
+ * the context, so featurise calls sharing a context must be stream-ordered. */
+#define SPLASH_MLP_IN 3080
+#define SPLASH_MLP_ROW 3136
+#define SPLASH_MLP_HIDDEN 128
+#define SPLASH_MLP_OUT 9
+splash_status splash_featurise(splash_ctx *ctx, const float *image, const float *depth, int32_t width, int32_t height,
+                               float z_far, uint16_t *row, void *stream);
+
+/* D[M,N] = A[M,K] . B[N,K]^T with BF16 A and B (row-major, leading dimensions
+ * lda, ldb in elements) and FP32 D (ldd): the tensor-core GEMM the MLP runs
+ * on (TMA-staged operands, tcgen05.mma with the accumulator in tensor
+ * memory). Needs M % 128 == 0, N % 16 == 0, K % 64 == 0; lda, ldb >= K and
+ * multiples of 8; ldd >= N and a multiple of 4; A, B, D 16-byte aligned.
+ * Otherwise SPLASH_ERR_INVALID_ARG and nothing is launched. */
+splash_status splash_gemm_bf16(splash_ctx *ctx, const uint16_t *A, int64_t lda, const uint16_t *B, int64_t ldb,
+                               float *D, int64_t ldd, int32_t M, int32_t N, int32_t K, void *stream);
+
+/* The MLP 3080 -> 128 -> 128 -> 9: ReLU hidden layers; heads softplus
+ * (beta_D, beta_B) and sigmoid (B_inf); BF16 weights and activations, FP32
+ * accumulation; loss = mean over batch and outputs of |log p - log target|.
+ * The handle owns FP32 master weights, Adam moments, BF16 copies and every
+ * activation buffer for batches up to max_batch (rounded up to 128). */
+typedef struct splash_mlp splash_mlp;
+typedef struct { /* device pointers, FP32, row-major */
+    float *W1; /* [128, 3080] */
+    float *b1; /* [128] */
+    float *W2; /* [128, 128] */
+    float *b2; /* [128] */
+    float *W3; /* [9, 128] */
+    float *b3; /* [9] */
+} splash_mlp_params;
+typedef struct {
+    float lr, beta1, beta2, eps;
+} splash_mlp_adam;
+splash_status splash_mlp_create(splash_ctx *ctx, int32_t max_batch, splash_mlp **out);
+splash_status splash_mlp_destroy(splash_mlp *mlp);
+/* Load weights (and reset the Adam moments and step count). */
+splash_status splash_mlp_set_params(splash_mlp *mlp, const splash_mlp_params *params, void *stream);
+splash_status splash_mlp_get_params(splash_mlp *mlp, splash_mlp_params *params, void *stream);
+/* pred[batch, 9] for `batch` consecutive feature rows. */
+splash_status splash_mlp_predict(splash_mlp *mlp, const uint16_t *rows, int32_t batch, float *pred, void *stream);
+/* One training step on rows bank[idx[b]] of a bank of n_rows feature rows
+ * (idx null: the first `batch` rows) with targets[idx[b]] ([n_rows, 9]
+ * FP32): forward, loss (written to *loss if non-null, device), backward, and
+ * with `adam` non-null one Adam step on the masters followed by the BF16
+ * refresh. `grads` (nullable) receives the gradients in the natural layout.
+ * An index outside [0, n_rows) is clamped and reported by splash_sync_status
+ * as SPLASH_ERR_INVALID_ARG. */
+splash_status splash_mlp_step(splash_mlp *mlp, const uint16_t *bank, int64_t n_rows, const int32_t *idx,
+                              const float *targets, int32_t batch, const splash_mlp_adam *adam, float *loss, splash_mlp_params *grads,
+                              void *stream);
+
 /* Synchronise `stream` and report any error a kernel recorded since the last check. */
 splash_status splash_sync_status(splash_ctx *ctx, void *stream);
 

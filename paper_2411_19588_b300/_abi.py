@@ -78,6 +78,17 @@ class AdamConfig(ctypes.Structure):
 
 ADAM_MAX_GROUPS = 8
 
+
+class MlpParams(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("W1", "b1", "W2", "b2", "W3", "b3")]
+
+
+class MlpAdam(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float)]
+
+
+MLP_IN, MLP_ROW, MLP_HIDDEN, MLP_OUT = 3080, 3136, 128, 9
+
 _SIGS = {
     "splash_create": [ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_void_p)],
     "splash_destroy": [ctypes.c_void_p],
@@ -113,6 +124,18 @@ _SIGS = {
                               ctypes.POINTER(Grads), ctypes.c_void_p],
     "splash_batch_pair_counts": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                  ctypes.c_void_p],
+    "splash_featurise": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                         ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p],
+    "splash_gemm_bf16": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                         ctypes.c_void_p],
+    "splash_mlp_create": [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)],
+    "splash_mlp_destroy": [ctypes.c_void_p],
+    "splash_mlp_set_params": [ctypes.c_void_p, ctypes.POINTER(MlpParams), ctypes.c_void_p],
+    "splash_mlp_get_params": [ctypes.c_void_p, ctypes.POINTER(MlpParams), ctypes.c_void_p],
+    "splash_mlp_predict": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p],
+    "splash_mlp_step": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                        ctypes.POINTER(MlpAdam), ctypes.c_void_p, ctypes.POINTER(MlpParams), ctypes.c_void_p],
     "splash_sort_pairs_u32_noalloc": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p],
 }

@@ -64,6 +64,7 @@ splash_status read_status(splash_ctx *ctx, splash_state *st, cudaStream_t s, boo
         SPLASH_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), s));
         if (status & kStatusTimeout) return fail(SPLASH_ERR_TIMEOUT, "a device-side wait gave up (spin limit reached)");
         if (status & kStatusCapacity) return fail(SPLASH_ERR_CAPACITY, "tile/Gaussian pairs exceeded the workspace");
+        if (status & kStatusIndex) return fail(SPLASH_ERR_INVALID_ARG, "a row index was outside the feature bank");
     }
     return SPLASH_OK;
 }
@@ -494,6 +495,7 @@ splash_status splash_sync_status(splash_ctx *ctx, void *stream)
         SPLASH_CUDA_TRY(cudaMemset(ctx->d_status, 0, sizeof(uint32_t)));
         if (status & kStatusTimeout) return fail(SPLASH_ERR_TIMEOUT, "a device-side wait gave up (spin limit reached)");
         if (status & kStatusCapacity) return fail(SPLASH_ERR_CAPACITY, "tile/Gaussian pairs exceeded the workspace");
+        if (status & kStatusIndex) return fail(SPLASH_ERR_INVALID_ARG, "a row index was outside the feature bank");
     }
     return SPLASH_OK;
 }

@@ -172,6 +172,7 @@ struct splash_ctx {
     splash_options opt;
     uint32_t *d_status = nullptr;  // kernel-reported error bits
     splash_host::Prof prof;
+    splash_host::Buf feat_counts;  // featuriser histogram counters (kept zero between calls)
 };
 
 struct splash_state {

@@ -103,7 +103,7 @@ struct BlendView {
 };
 
 // device status word bits
-enum : uint32_t { kStatusTimeout = 1u, kStatusCapacity = 2u };
+enum : uint32_t { kStatusTimeout = 1u, kStatusCapacity = 2u, kStatusIndex = 4u };
 
 // ---- onesweep radix sort (sort.cu)
 constexpr int kSortThreads = 256;

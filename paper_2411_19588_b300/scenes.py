@@ -344,3 +344,99 @@ def view_maps(seed: int, width: int, height: int, z_far: float = 20.0):
     edges = (np.arange(1, 8) * (z_far / 8.0)).astype(np.float32)
     depth.ravel()[rng.choice(depth.size, 7, replace=False)] = edges
     return img, depth
+
+
+def _rotmat_to_quat_t(R):
+    """Torch version of _rotmat_to_quat (Shepperd), for device-side generation."""
+    import torch
+    tr = R[:, 0, 0] + R[:, 1, 1] + R[:, 2, 2]
+    diag = torch.stack([R[:, 0, 0], R[:, 1, 1], R[:, 2, 2]], 1)
+    dmax, darg = diag.max(1)
+    case = torch.where(tr > dmax, torch.full_like(darg, 3), darg)
+    q = torch.empty((R.shape[0], 4), dtype=R.dtype, device=R.device)
+    m = case == 3
+    s = torch.sqrt(torch.clamp(1.0 + tr[m], min=1e-30)) * 2
+    q[m, 0] = 0.25 * s
+    q[m, 1] = (R[m, 2, 1] - R[m, 1, 2]) / s
+    q[m, 2] = (R[m, 0, 2] - R[m, 2, 0]) / s
+    q[m, 3] = (R[m, 1, 0] - R[m, 0, 1]) / s
+    for i in range(3):
+        m = case == i
+        j, k = (i + 1) % 3, (i + 2) % 3
+        s = torch.sqrt(torch.clamp(1.0 + R[m, i, i] - R[m, j, j] - R[m, k, k], min=1e-30)) * 2
+        q[m, 1 + i] = 0.25 * s
+        q[m, 0] = (R[m, k, j] - R[m, j, k]) / s
+        q[m, 1 + j] = (R[m, j, i] + R[m, i, j]) / s
+        q[m, 1 + k] = (R[m, k, i] + R[m, i, k]) / s
+    return q / q.norm(dim=1, keepdim=True)
+
+
+def patch_scene_device(n: int, seed: int, z_range=(1.0, 8.0), width=1280, height=854, fx=1200.0, n_patches=40,
+                       floater_frac=0.10, sh_degree=3, device="cuda"):
+    """The patch_scene recipe drawn with torch's generator on the device (same
+    distributions, different random stream), for generating many training
+    scenes quickly. Returns the parameter dict of render.params_to_device."""
+    import torch
+    g = torch.Generator(device=device).manual_seed(int(seed))
+    f64 = dict(device=device, dtype=torch.float64)
+
+    def U(lo, hi, *shape):
+        return lo + (hi - lo) * torch.rand(*shape, generator=g, **f64)
+
+    def N(mu, sd, *shape):
+        return mu + sd * torch.randn(*shape, generator=g, **f64)
+
+    tanx, tany = 0.5 * width / fx, 0.5 * height / fx
+    n_float = int(round(n * floater_frac))
+    n_surf = n - n_float
+    z0, z1 = z_range
+    pz = U(z0, z1, n_patches)
+    centers = torch.stack([pz * U(-0.8, 0.8, n_patches) * tanx, pz * U(-0.8, 0.8, n_patches) * tany, pz], 1)
+    views = centers / centers.norm(dim=1, keepdim=True)
+    # normals with |n . view| >= 0.3, facing the camera: first acceptable of 64 draws
+    cand = N(0, 1, n_patches, 64, 3)
+    cand = cand / cand.norm(dim=2, keepdim=True)
+    dots = (cand * views[:, None, :]).sum(2)
+    first = (dots.abs() >= 0.3).to(torch.int8).argmax(1)
+    normals = cand[torch.arange(n_patches, device=device), first]
+    normals = torch.where((normals * views).sum(1, keepdim=True) < 0, normals, -normals)
+    sides = U(0.5, 3.0, n_patches)
+    areas = sides ** 2
+    owner = torch.multinomial(areas / areas.sum(), n_surf, replacement=True, generator=g)
+    counts = torch.bincount(owner, minlength=n_patches).to(torch.float64)
+    ex = torch.tensor([1.0, 0.0, 0.0], **f64).expand(n_patches, 3)
+    ey = torch.tensor([0.0, 1.0, 0.0], **f64).expand(n_patches, 3)
+    helper = torch.where(normals[:, :1].abs() < 0.9, ex, ey)
+    t1 = torch.linalg.cross(normals, helper)
+    t1 = t1 / t1.norm(dim=1, keepdim=True)
+    t2 = torch.linalg.cross(normals, t1)
+    u = U(-0.5, 0.5, n_surf) * sides[owner]
+    v = U(-0.5, 0.5, n_surf) * sides[owner]
+    s_means = centers[owner] + u[:, None] * t1[owner] + v[:, None] * t2[owner]
+    spacing = torch.sqrt(areas / torch.clamp(counts, min=1))
+    s_log = torch.empty((n_surf, 3), **f64)
+    s_log[:, 0] = torch.log(0.8 * spacing[owner]) + N(0, 0.2, n_surf)
+    s_log[:, 1] = torch.log(0.8 * spacing[owner]) + N(0, 0.2, n_surf)
+    s_log[:, 2] = -5.0
+    twist = U(0, 2 * math.pi, n_surf)
+    c, s = torch.cos(twist)[:, None], torch.sin(twist)[:, None]
+    e1 = c * t1[owner] + s * t2[owner]
+    e2 = -s * t1[owner] + c * t2[owner]
+    s_quats = _rotmat_to_quat_t(torch.stack([e1, e2, normals[owner]], 2))
+    s_logits = N(2.0, 1.0, n_surf)
+    zf = torch.pow(U(z0 ** 3, z1 ** 3, n_float), 1.0 / 3.0)
+    f_means = torch.stack([zf * U(-tanx, tanx, n_float), zf * U(-tany, tany, n_float), zf], 1)
+    f_log = N(-3.0, 0.5, n_float, 1).expand(n_float, 3)
+    f_quats = N(0, 1, n_float, 4)
+    f_quats = f_quats / f_quats.norm(dim=1, keepdim=True)
+    f_logits = N(0.0, 1.0, n_float)
+    perm = torch.randperm(n, generator=g, device=device)
+    k = (sh_degree + 1) ** 2
+    sh = torch.zeros((n, k, 3), **f64)
+    sh[:, 0, :] = (U(0, 1, n, 3) - 0.5) / _SH_DC
+    if k > 1:
+        sh[:, 1:, :] = N(0, 0.1, n, k - 1, 3)
+    f32 = lambda a: a.to(torch.float32).contiguous()
+    return {"means": f32(torch.cat([s_means, f_means])[perm]), "log_scales": f32(torch.cat([s_log, f_log])[perm]),
+            "quats": f32(torch.cat([s_quats, f_quats])[perm]),
+            "opacity_logits": f32(torch.cat([s_logits, f_logits])[perm]), "sh": f32(sh), "sh_degree": sh_degree}
