@@ -50,11 +50,13 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--views", type=int, default=N_VIEWS, help="arc views (targets rendered up front)")
-    ap.add_argument("--workload", choices=["train", "batch", "warmstart"], default="train",
+    ap.add_argument("--gemm-size", type=int, default=8192, help="gemm: M = N = K")
+    ap.add_argument("--workload", choices=["train", "batch", "warmstart", "gemm"], default="train",
                     help="train: the training step (the headline metric); batch: 64 uneven views forward+backward, "
                          "sequential plain launches vs one persistent launch each way under a CUDA graph; "
                          "warmstart: MLP trained on generated renders, then the 1.5M fit from its predicted medium "
-                         "vs from the default medium")
+                         "vs from the default medium; gemm: the tensor-core BF16 GEMM the MLP runs on, "
+                         "at M = N = K = --gemm-size")
     ap.add_argument("--ws-scenes", type=int, default=200, help="warmstart: generated 300k-Gaussian scenes")
     ap.add_argument("--ws-views", type=int, default=100, help="warmstart: (medium, view) draws per scene")
     ap.add_argument("--ws-epochs", type=int, default=30)
@@ -365,7 +367,13 @@ def run_ours(args, world, rank, local):
         # fused adjoint + Adam: parameters, both moments and the blend accumulators
         # read; parameters and moments written
         "preprocess_bwd": ("hbm", ((3 * 236 + 48 + 3 * 236) if grads is None else (236 + 48 + 236)) * args.n, "GB/s"),
+        # two-phase sort: 4 passes over the N depth keys, 2 over the K pairs (keys + values read
+        # and written per pass, plus one key read for the histograms)
+        "depth_sort": ("hbm", 4 * 16.0 * args.n + 4.0 * args.n, "GB/s"),
+        "scan": ("hbm", 8.0 * args.n, "GB/s"),
+        "emit": ("hbm", 16.0 * args.n + 8.0 * n_keys, "GB/s"),
         "tile_sort": ("hbm", 2 * 16.0 * n_keys + 4.0 * n_keys, "GB/s"),
+        "ranges": ("hbm", 4.0 * n_keys, "GB/s"),
         "loss": ("hbm", 4.0 * 3 * H * W * 9, "GB/s"),
     }
     dom = max((k for k in work if per_launch.get(k, 0) > 0), key=lambda k: per_launch[k])
@@ -376,6 +384,12 @@ def run_ours(args, world, rank, local):
     else:
         achieved, peak, note = units / t_s / 1e9, float(peaks["hbm_gbs"]), f"{peak_src} HBM copy bandwidth"
     stages_ms = {k: round(v, 4) for k, v in per_launch.items() if v > 0}
+    stage_roofline = {}
+    for k, (b_, u_, un_) in work.items():
+        if per_launch.get(k, 0) > 0:
+            a_ = u_ / (per_launch[k] * 1e-3) / (1e12 if un_ == "TFLOP/s" else 1e9)
+            p_ = fp32_peak_tflops if un_ == "TFLOP/s" else float(peaks["hbm_gbs"])
+            stage_roofline[k] = {"bound": b_, "achieved": round(a_, 2), "unit": un_, "frac": round(a_ / p_, 4)}
 
     out = {
         "metric": METRIC,
@@ -400,6 +414,7 @@ def run_ours(args, world, rank, local):
         "roofline": {"kernel": dom, "bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 2),
                      "unit": unit, "frac": round(achieved / peak, 4), "traffic": None, "peak_source": note},
         "stages_ms": stages_ms,
+        "stage_roofline": stage_roofline,
         "pairs": {"walked_fwd": int(walk), "walked_bwd": int(last), "keys": int(n_keys)},
         "gpu_launches": int(launches),
         "clocks": clk,
@@ -600,6 +615,56 @@ def run_warmstart(args, world, rank, local):
         print(json.dumps(out), flush=True)
 
 
+def run_gemm(args, world, rank, local):
+    """The tensor-core GEMM of the warm-start MLP (TMA + tcgen05.mma + tensor
+    memory) at a size large enough to measure its throughput against the
+    measured cuBLAS BF16 peak; inputs larger than L2."""
+    import torch
+
+    from paper_2411_19588_b300 import mlp as M
+    from paper_2411_19588_b300 import render as R
+
+    torch.cuda.set_device(local)
+    r = R.Renderer()
+    n = args.gemm_size
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    A = torch.randn((n, n), generator=gen, device="cuda").to(torch.bfloat16)
+    B = torch.randn((n, n), generator=gen, device="cuda").to(torch.bfloat16)
+    D = torch.empty((n, n), device="cuda")
+    for _ in range(max(3, args.warmup)):
+        M.gemm(r, A, B, D)
+    steps = max(1, min(args.steps, 20))
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = R.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        M.gemm(r, A, B, D)
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = R.kernel_launches() - l0
+    r.sync_status()
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, world)
+    tflops = 2.0 * n ** 3 / (ms * 1e-3) / 1e12
+    peaks, src = measured_peaks()
+    peak = float(peaks.get("bf16_tflops", 1800.0))
+    # spot check against torch's own matmul on a few rows
+    ref = (A[:64].float() @ B.float().T)
+    err = float((D[:64] - ref).abs().max() / ref.abs().max())
+    out = {"metric": f"BF16 GEMM D = A B^T, M = N = K = {n} (FP32 accumulate)", "value": round(world * tflops, 2),
+           "unit": "TFLOP/s", "n_gpus": world, "steps": steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms, 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+           "config": {"workload": "gemm", "m": n, "n": n, "k": n, "l2": "inputs 2 x 128 MB > L2"},
+           "roofline": {"kernel": "k_gemm_bf16", "bound": "tensor", "achieved": round(tflops, 2), "peak": round(peak, 1),
+                        "unit": "TFLOP/s", "frac": round(tflops / peak, 4), "traffic": None,
+                        "peak_source": f"{src} cuBLAS BF16 burst"},
+           "max_rel_err_vs_fp32_rows": err, "gpu_launches": int(launches), "clocks": clk}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def cpu_baseline(budget_s: float = 20.0, n: int = N_GAUSS) -> dict:
     """The FP64 oracle (as it stands) on a bounded sample of the training
     step: projection of all Gaussians, forward and adjoint at a random
@@ -674,6 +739,8 @@ def main():
         run_batch(args, world, rank, local)
     elif args.workload == "warmstart":
         run_warmstart(args, world, rank, local)
+    elif args.workload == "gemm":
+        run_gemm(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -13,8 +13,9 @@
 // so the inner loop is plain compositing of the effective colour ct (made
 // once per Gaussian in the preprocess) and the water costs one epilogue.
 //
-// Work decomposition: one CTA of 128 threads per tile, two pixels of one row
-// per thread (they share the dy terms). Gaussians are staged in shared
+// Work decomposition: one CTA per tile, kPxFwd / kPxBwd pixels of one row per
+// thread (they share the dy terms and, backward, one warp reduction of the
+// gradient fields per Gaussian). Gaussians are staged in shared
 // memory in batches of NB (64, 128 or 256); the local centre is formed once
 // per (tile, Gaussian) from the doubled-precision record, relative to the
 // 32-pixel-aligned corner that holds the tile (the same corner for every
@@ -40,12 +41,20 @@ __device__ __forceinline__ float ex2_approx(float x)
 // passes so that they take identical decisions
 __device__ __forceinline__ float quad(float dx, float A, float Bdy, float Cdy2) { return fmaf(dx, fmaf(A, dx, Bdy), Cdy2); }
 
-template <int TW, int TH>
+// pixels per thread, forward and backward
+constexpr int kPxFwd = 2;
+constexpr int kPxBwd = 4;
+
+template <int TW, int TH, int PX>
 struct Tile {
-    static constexpr int NT = TW * TH / 2;  // threads per CTA
-    static constexpr int HW = TW / 2;       // second pixel of a thread is HW columns right
-    static_assert(NT == 128, "128 threads per tile");
+    static constexpr int NT = TW * TH / PX;  // threads per CTA
+    static constexpr int HW = TW / PX;       // a thread's pixels are HW columns apart in one row
+    static_assert(TW % PX == 0 && NT % 32 == 0, "tile width must split into PX pixels per thread");
 };
+template <int TW, int TH>
+constexpr int fwd_threads() { return Tile<TW, TH, kPxFwd>::NT; }
+template <int TW, int TH>
+constexpr int bwd_threads() { return Tile<TW, TH, kPxBwd>::NT; }
 
 // stage list entry `slot` of the batch: local centre, conic, log-opacity, colour, depth
 __device__ __forceinline__ void stage_rec(const Rec *__restrict__ rec, uint32_t gid, int ox, int oy, float4 *s0, float4 *s1,
@@ -62,7 +71,8 @@ __device__ __forceinline__ void stage_rec(const Rec *__restrict__ rec, uint32_t 
 template <int TW, int TH, int NB>
 __device__ __forceinline__ void blend_tile_fwd(const BlendView &v, int tile, const float *__restrict__ medium)
 {
-    constexpr int NT = Tile<TW, TH>::NT, HW = Tile<TW, TH>::HW;
+    constexpr int PX = kPxFwd;
+    constexpr int NT = Tile<TW, TH, PX>::NT, HW = Tile<TW, TH, PX>::HW;
     __shared__ float4 s0[NB];  // {x_loc, y_loc, A, B}
     __shared__ float4 s1[NB];  // {C, lo, ct_r, ct_g}
     __shared__ float2 s2[NB];  // {ct_b, d}
@@ -73,79 +83,61 @@ __device__ __forceinline__ void blend_tile_fwd(const BlendView &v, int tile, con
     const int tid = threadIdx.x;
     const int row = tid / HW, col = tid - row * HW;
     const float pyl = (float)(y0 - oy + row) + 0.5f;
-    const float pxl0 = (float)(x0 - ox + col) + 0.5f, pxl1 = (float)(x0 - ox + col + HW) + 0.5f;
     const int W = cam.W, H = cam.H;
-    const int gy = y0 + row, gx0 = x0 + col, gx1 = x0 + col + HW;
-    const bool in0 = gy < H && gx0 < W, in1 = gy < H && gx1 < W;
+    const int gy = y0 + row;
     const uint2 rg = v.ranges[tile];
     const int n = (int)(rg.y - rg.x);
 
-    float T0 = 1.f, T1 = 1.f;
-    float c00 = 0.f, c01 = 0.f, c02 = 0.f, c10 = 0.f, c11 = 0.f, c12 = 0.f;
-    float D0 = 0.f, D1 = 0.f, A0 = 0.f, A1 = 0.f;
-    int last0 = 0, last1 = 0, walk0 = n, walk1 = n;
-    bool done0 = !in0, done1 = !in1;
-    if (done0) walk0 = 0;
-    if (done1) walk1 = 0;
+    float pxl[PX], T[PX], cr[PX], cg[PX], cb[PX], D[PX], A[PX];
+    int last[PX], walk[PX];
+    bool done[PX];
+#pragma unroll
+    for (int q = 0; q < PX; q++) {
+        pxl[q] = (float)(x0 - ox + col + q * HW) + 0.5f;
+        T[q] = 1.f;
+        cr[q] = cg[q] = cb[q] = D[q] = A[q] = 0.f;
+        last[q] = 0;
+        done[q] = !(gy < H && x0 + col + q * HW < W);
+        walk[q] = done[q] ? 0 : n;
+    }
 
     for (int b0 = 0; b0 < n; b0 += NB) {
-        if (__syncthreads_count(!(done0 && done1)) == 0) break;
+        bool all = true;
+#pragma unroll
+        for (int q = 0; q < PX; q++) all &= done[q];
+        if (__syncthreads_count(!all) == 0) break;
         for (int sl = tid; sl < NB && b0 + sl < n; sl += NT) stage_rec(v.rec, v.gauss_ids[rg.x + b0 + sl], ox, oy, s0, s1, s2, sl);
         __syncthreads();
         const int nb = min(NB, n - b0);
-        if (!__any_sync(0xffffffffu, !(done0 && done1))) continue;
+        if (!__any_sync(0xffffffffu, !all)) continue;
         for (int k = 0; k < nb; k++) {
             const float4 a = s0[k];
             const float4 c = s1[k];
             const float dy = pyl - a.y;
             const float Bdy = a.w * dy;
             const float Cdy2 = c.x * dy * dy;
-            if (!done0) {
-                const float dx = pxl0 - a.x;
+#pragma unroll
+            for (int q = 0; q < PX; q++) {
+                if (done[q]) continue;
+                const float dx = pxl[q] - a.x;
                 const float qs = quad(dx, a.z, Bdy, Cdy2);
-                if (qs >= kQsMin) {
-                    const float alpha = fminf(kAlphaMax, ex2_approx(qs + c.y));
-                    if (alpha >= kAlphaMin) {
-                        const float tn = fmaf(-alpha, T0, T0);
-                        if (tn < kTStop) {
-                            done0 = true;
-                            walk0 = b0 + k + 1;
-                        } else {
-                            const float w = alpha * T0;
-                            const float2 e = s2[k];
-                            c00 = fmaf(w, c.z, c00);
-                            c01 = fmaf(w, c.w, c01);
-                            c02 = fmaf(w, e.x, c02);
-                            D0 = fmaf(w, e.y, D0);
-                            A0 += w;
-                            T0 = tn;
-                            last0 = b0 + k + 1;
-                        }
-                    }
-                }
-            }
-            if (!done1) {
-                const float dx = pxl1 - a.x;
-                const float qs = quad(dx, a.z, Bdy, Cdy2);
-                if (qs >= kQsMin) {
-                    const float alpha = fminf(kAlphaMax, ex2_approx(qs + c.y));
-                    if (alpha >= kAlphaMin) {
-                        const float tn = fmaf(-alpha, T1, T1);
-                        if (tn < kTStop) {
-                            done1 = true;
-                            walk1 = b0 + k + 1;
-                        } else {
-                            const float w = alpha * T1;
-                            const float2 e = s2[k];
-                            c10 = fmaf(w, c.z, c10);
-                            c11 = fmaf(w, c.w, c11);
-                            c12 = fmaf(w, e.x, c12);
-                            D1 = fmaf(w, e.y, D1);
-                            A1 += w;
-                            T1 = tn;
-                            last1 = b0 + k + 1;
-                        }
-                    }
+                if (qs < kQsMin) continue;
+                const float alpha = fminf(kAlphaMax, ex2_approx(qs + c.y));
+                if (alpha < kAlphaMin) continue;
+                const float tn = fmaf(-alpha, T[q], T[q]);
+                if (tn < kTStop) {
+                    done[q] = true;
+                    walk[q] = b0 + k + 1;
+                } else {
+                    const float w = alpha * T[q];
+                    const float2 e = s2[k];
+                    cr[q] = fmaf(w, c.z, cr[q]);
+                    cg[q] = fmaf(w, c.w, cg[q]);
+                    cb[q] = fmaf(w, e.x, cb[q]);
+                    D[q] = fmaf(w, e.y, D[q]);
+                    A[q] += w;
+                    T[q] = tn;
+                    last[q] = b0 + k + 1;
                 }
             }
         }
@@ -161,21 +153,21 @@ __device__ __forceinline__ void blend_tile_fwd(const BlendView &v, int tile, con
     }
     const int HWimg = W * H;
 #pragma unroll
-    for (int q = 0; q < 2; q++) {
-        if (!(q ? in1 : in0)) continue;
-        const int p = gy * W + (q ? gx1 : gx0);
-        const float T = q ? T1 : T0, Dd = q ? D1 : D0, Aa = q ? A1 : A0;
-        v.image[p] = (q ? c10 : c00) + binf[0] * (1.f - T * bfar[0]);
-        v.image[HWimg + p] = (q ? c11 : c01) + binf[1] * (1.f - T * bfar[1]);
-        v.image[2 * HWimg + p] = (q ? c12 : c02) + binf[2] * (1.f - T * bfar[2]);
-        const float z = Aa > 0.f ? Dd / Aa : zfar;
+    for (int q = 0; q < PX; q++) {
+        const int gx = x0 + col + q * HW;
+        if (!(gy < H && gx < W)) continue;
+        const int p = gy * W + gx;
+        v.image[p] = cr[q] + binf[0] * (1.f - T[q] * bfar[0]);
+        v.image[HWimg + p] = cg[q] + binf[1] * (1.f - T[q] * bfar[1]);
+        v.image[2 * HWimg + p] = cb[q] + binf[2] * (1.f - T[q] * bfar[2]);
+        const float z = A[q] > 0.f ? D[q] / A[q] : zfar;
         if (v.depth) v.depth[p] = z;
         if (v.depth01) v.depth01[p] = 2.f / (1.f + expf(-0.1f * z)) - 1.f;
-        v.final_T[p] = T;
-        v.acc_alpha[p] = Aa;
+        v.final_T[p] = T[q];
+        v.acc_alpha[p] = A[q];
         v.zhat[p] = z;
-        v.n_last[p] = (uint32_t)(q ? last1 : last0);
-        v.n_walk[p] = (uint32_t)(q ? walk1 : walk0);
+        v.n_last[p] = (uint32_t)last[q];
+        v.n_walk[p] = (uint32_t)walk[q];
     }
 }
 
@@ -273,13 +265,14 @@ __device__ __forceinline__ bool pix_grad(PixB &p, int j, float dx, float dy, flo
 template <int TW, int TH, int NB>
 __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, const float *__restrict__ medium)
 {
-    constexpr int NT = Tile<TW, TH>::NT, HW = Tile<TW, TH>::HW;
+    constexpr int PX = kPxBwd;
+    constexpr int NT = Tile<TW, TH, PX>::NT, HW = Tile<TW, TH, PX>::HW;
     constexpr int NW = NT / 32;
     __shared__ float4 s0[NB];
     __shared__ float4 s1[NB];
     __shared__ float2 s2[NB];
     __shared__ uint32_t s_id[NB];
-    __shared__ float s_g[10][NB];
+    __shared__ float s_g[10][NB + 1];  // padded: the ten fields of one Gaussian fall in ten banks
     __shared__ float s_med[NW][6];
     __shared__ int s_maxlast;
 
@@ -290,10 +283,8 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int row = tid / HW, col = tid - row * HW;
     const float pyl = (float)(y0 - oy + row) + 0.5f;
-    const float pxl0 = (float)(x0 - ox + col) + 0.5f, pxl1 = (float)(x0 - ox + col + HW) + 0.5f;
     const int W = cam.W, H = cam.H;
-    const int gy = y0 + row, gx0 = x0 + col, gx1 = x0 + col + HW;
-    const bool in0 = gy < H && gx0 < W, in1 = gy < H && gx1 < W;
+    const int gy = y0 + row;
     const uint2 rg = v.ranges[tile];
     const int HWimg = W * H;
     const float zfar = cam.zfar;
@@ -308,14 +299,17 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
     // per-pixel set-up; medium terms that do not go through any Gaussian:
     //   dC/dB_inf = 1 - T_f b_far, dC/dbeta_B = B_inf T_f z_far b_far
     float mB[3] = {0.f, 0.f, 0.f}, mBB[3] = {0.f, 0.f, 0.f};
-    PixB P[2];
+    float pxl[PX];
+    PixB P[PX];
+    int mylast = 0;
 #pragma unroll
-    for (int q = 0; q < 2; q++) {
-        const bool in = q ? in1 : in0;
+    for (int q = 0; q < PX; q++) {
+        const int gx = x0 + col + q * HW;
+        pxl[q] = (float)(x0 - ox + col + q * HW) + 0.5f;
         PixB &p = P[q];
         p.T = 1.f; p.S = 0.f; p.G0 = p.G1 = p.G2 = p.gD = p.gA = 0.f; p.last = 0;
-        if (!in) continue;
-        const int pix = gy * W + (q ? gx1 : gx0);
+        if (!(gy < H && gx < W)) continue;
+        const int pix = gy * W + gx;
         p.T = v.final_T[pix];
         p.last = (int)v.n_last[pix];
         p.G0 = v.dL_dimage[pix];
@@ -340,6 +334,7 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
             S -= Gc[ch] * binf[ch] * bfar[ch] * p.T;  // the water behind the last Gaussian
         }
         p.S = S;
+        mylast = max(mylast, p.last);
     }
     // per-tile medium partials {beta_B[3], B_inf[3]}, reduced now so that the
     // accumulators do not stay live through the main loop
@@ -357,7 +352,7 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
         }
     }
     __syncthreads();
-    atomicMax(&s_maxlast, max(P[0].last, P[1].last));
+    atomicMax(&s_maxlast, mylast);
     if (tid < 6) {
         float acc = 0.f;
 #pragma unroll
@@ -381,7 +376,7 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
 #pragma unroll
             for (int f = 0; f < 10; f++) s_g[f][sl] = 0.f;
         __syncthreads();
-        if (__any_sync(0xffffffffu, P[0].last > b0 || P[1].last > b0)) {
+        if (__any_sync(0xffffffffu, mylast > b0)) {
             for (int k = nb - 1; k >= 0; k--) {
                 const int j = b0 + k;
                 const float4 a = s0[k];
@@ -391,8 +386,10 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
                 const float Bdy = a.w * dy;
                 const float Cdy2 = c.x * dy * dy;
                 float acc[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                bool any = pix_grad(P[0], j, pxl0 - a.x, dy, a.z, a.w, c.x, Bdy, Cdy2, c.y, c.z, c.w, e.x, e.y, acc);
-                any |= pix_grad(P[1], j, pxl1 - a.x, dy, a.z, a.w, c.x, Bdy, Cdy2, c.y, c.z, c.w, e.x, e.y, acc);
+                bool any = false;
+#pragma unroll
+                for (int q = 0; q < PX; q++)
+                    any |= pix_grad(P[q], j, pxl[q] - a.x, dy, a.z, a.w, c.x, Bdy, Cdy2, c.y, c.z, c.w, e.x, e.y, acc);
                 if (__any_sync(0xffffffffu, any)) {
                     const float r = warp_reduce10(acc, lane);
                     if (my_field >= 0) atomicAdd(&s_g[my_field][k], r);
@@ -420,13 +417,13 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
 // Kernels.
 
 template <int TW, int TH, int NB>
-__global__ void __launch_bounds__(128, 10) k_blend_fwd(BlendView v, const float *__restrict__ medium)
+__global__ void __launch_bounds__(fwd_threads<TW, TH>(), 1280 / fwd_threads<TW, TH>()) k_blend_fwd(BlendView v, const float *__restrict__ medium)
 {
     blend_tile_fwd<TW, TH, NB>(v, blockIdx.x, medium);
 }
 
 template <int TW, int TH, int NB>
-__global__ void __launch_bounds__(128, 8) k_blend_bwd(BlendView v, const float *__restrict__ medium)
+__global__ void __launch_bounds__(bwd_threads<TW, TH>(), 640 / bwd_threads<TW, TH>()) k_blend_bwd(BlendView v, const float *__restrict__ medium)
 {
     blend_tile_bwd<TW, TH, NB>(v, blockIdx.x, medium);
 }
@@ -445,7 +442,7 @@ __device__ __forceinline__ bool next_item(int *counter, const uint32_t *n_items,
 }
 
 template <int TW, int TH, int NB>
-__global__ void __launch_bounds__(128, 9) k_blend_fwd_persistent(const BlendView *__restrict__ views,
+__global__ void __launch_bounds__(fwd_threads<TW, TH>(), 1152 / fwd_threads<TW, TH>()) k_blend_fwd_persistent(const BlendView *__restrict__ views,
                                                                   const uint32_t *__restrict__ items,
                                                                   const uint32_t *__restrict__ n_items, int *counter,
                                                                   const float *__restrict__ medium)
@@ -458,7 +455,7 @@ __global__ void __launch_bounds__(128, 9) k_blend_fwd_persistent(const BlendView
 }
 
 template <int TW, int TH, int NB>
-__global__ void __launch_bounds__(128, 8) k_blend_bwd_persistent(const BlendView *__restrict__ views,
+__global__ void __launch_bounds__(bwd_threads<TW, TH>(), 640 / bwd_threads<TW, TH>()) k_blend_bwd_persistent(const BlendView *__restrict__ views,
                                                                  const uint32_t *__restrict__ items,
                                                                  const uint32_t *__restrict__ n_items, int *counter,
                                                                  const float *__restrict__ medium)
@@ -494,7 +491,7 @@ template <int TW, int TH, int NB>
 struct FwdPlain {
     static void run(const BlendView &v, const float *medium, cudaStream_t s)
     {
-        k_blend_fwd<TW, TH, NB><<<v.tg.tx * v.tg.ty, 128, 0, s>>>(v, medium);
+        k_blend_fwd<TW, TH, NB><<<v.tg.tx * v.tg.ty, fwd_threads<TW, TH>(), 0, s>>>(v, medium);
         count_launch();
     }
 };
@@ -502,7 +499,7 @@ template <int TW, int TH, int NB>
 struct BwdPlain {
     static void run(const BlendView &v, const float *medium, cudaStream_t s)
     {
-        k_blend_bwd<TW, TH, NB><<<v.tg.tx * v.tg.ty, 128, 0, s>>>(v, medium);
+        k_blend_bwd<TW, TH, NB><<<v.tg.tx * v.tg.ty, bwd_threads<TW, TH>(), 0, s>>>(v, medium);
         count_launch();
     }
 };
@@ -511,7 +508,7 @@ struct FwdPersistent {
     static void run(const BlendView *v, const uint32_t *items, const uint32_t *n, int *counter, const float *medium,
                     int ctas, cudaStream_t s)
     {
-        k_blend_fwd_persistent<TW, TH, NB><<<ctas, 128, 0, s>>>(v, items, n, counter, medium);
+        k_blend_fwd_persistent<TW, TH, NB><<<ctas, fwd_threads<TW, TH>(), 0, s>>>(v, items, n, counter, medium);
         count_launch();
     }
 };
@@ -520,7 +517,7 @@ struct BwdPersistent {
     static void run(const BlendView *v, const uint32_t *items, const uint32_t *n, int *counter, const float *medium,
                     int ctas, cudaStream_t s)
     {
-        k_blend_bwd_persistent<TW, TH, NB><<<ctas, 128, 0, s>>>(v, items, n, counter, medium);
+        k_blend_bwd_persistent<TW, TH, NB><<<ctas, bwd_threads<TW, TH>(), 0, s>>>(v, items, n, counter, medium);
         count_launch();
     }
 };
@@ -532,9 +529,9 @@ struct Occupancy {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (backward)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_blend_bwd_persistent<TW, TH, NB>, 128, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_blend_bwd_persistent<TW, TH, NB>, bwd_threads<TW, TH>(), 0);
         else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_blend_fwd_persistent<TW, TH, NB>, 128, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_blend_fwd_persistent<TW, TH, NB>, fwd_threads<TW, TH>(), 0);
         *out = sms * (per > 0 ? per : 1);
     }
 };

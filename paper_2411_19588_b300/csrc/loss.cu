@@ -8,7 +8,8 @@
 //           dL/dSSIM_p = -lam / count; block partial sums of |x-y| and SSIM.
 //   pass 2: dL/dx = blur(d_mu) + 2 x blur(d_xx) + y blur(d_xy) + sign(x-y)/count
 //           (the window is symmetric, so the adjoint blur is the same blur).
-// Both passes are HBM-bound streams over a few [C,H,W] maps.
+// Each 1-D window pass is register-blocked: a thread slides the 11 taps over
+// four consecutive outputs, so a few shared loads feed many FMAs.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -18,8 +19,10 @@ namespace splash {
 namespace {
 
 constexpr int kR = 5;             // window radius
-constexpr int kTX = 32, kTY = 16; // output tile
-constexpr int kHX = kTX + 2 * kR, kHY = kTY + 2 * kR;
+constexpr int kTX = 32, kTY = 32; // output tile
+constexpr int kHX = kTX + 2 * kR, kHY = kTY + 2 * kR;  // haloed tile (42 x 42)
+constexpr int kSX = 44;           // row stride of the haloed tile: float4 rows, conflict-free
+constexpr int kRun = 4;           // consecutive outputs per thread in each 1-D pass
 constexpr float kC1 = 0.01f * 0.01f, kC2 = 0.03f * 0.03f;
 
 struct Win {
@@ -28,57 +31,112 @@ struct Win {
 
 __device__ __forceinline__ float load0(const float *p, int x, int y, int W, int H)
 {
-    return (x >= 0 && x < W && y >= 0 && y < H) ? p[y * W + x] : 0.f;
+    return (x >= 0 && x < W && y >= 0 && y < H) ? p[(size_t)y * W + x] : 0.f;
 }
 
+// kRun horizontal window sums starting at column 4j of row r of a haloed tile:
+// the 14 inputs come in as four float4 loads.
+__device__ __forceinline__ void hrun(const float (*t)[kSX], int r, int j, float (&u)[16])
+{
+    const float4 *row = reinterpret_cast<const float4 *>(&t[r][4 * j]);
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const float4 v = row[i];
+        u[4 * i] = v.x;
+        u[4 * i + 1] = v.y;
+        u[4 * i + 2] = v.z;
+        u[4 * i + 3] = v.w;
+    }
+}
+
+// Pass 1: blurred statistics (separable, register-blocked), per-pixel SSIM
+// and its partials w.r.t. (mu_x, E[x^2], E[xy]) scaled by dL/dSSIM_p, block
+// sums of |x - y| and SSIM.
 __global__ void __launch_bounds__(256) k_ssim_pass1(const float *__restrict__ X, const float *__restrict__ Y, int W, int H,
                                                     Win win, float wscale, float *__restrict__ d_mu,
                                                     float *__restrict__ d_xx, float *__restrict__ d_xy,
                                                     float *__restrict__ partial)
 {
-    __shared__ float sx[kHY][kHX], sy[kHY][kHX];
-    __shared__ float h[5][kHY][kTX];
+    __shared__ __align__(16) float sx[kHY][kSX];
+    __shared__ __align__(16) float sy[kHY][kSX];
+    __shared__ float h[5][kHY][kTX + 1];
     __shared__ float s_red[2][8];
     const int c = blockIdx.z;
     const float *x = X + (size_t)c * W * H, *y = Y + (size_t)c * W * H;
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
     const int tid = threadIdx.x;
-    for (int e = tid; e < kHY * kHX; e += 256) {
-        const int r = e / kHX, q = e - r * kHX;
-        sx[r][q] = load0(x, x0 - kR + q, y0 - kR + r, W, H);
-        sy[r][q] = load0(y, x0 - kR + q, y0 - kR + r, W, H);
-    }
-    __syncthreads();
-    for (int e = tid; e < kHY * kTX; e += 256) {
-        const int r = e / kTX, q = e - r * kTX;
-        float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
+    {  // haloed tiles: every load of this thread in flight before any store
+        constexpr int NL = (kHY * kSX + 255) / 256;
+        float lx[NL], ly[NL];
 #pragma unroll
-        for (int k = 0; k <= 2 * kR; k++) {
-            const float u = sx[r][q + k], v = sy[r][q + k], w = win.w[k];
-            a = fmaf(w, u, a);
-            b = fmaf(w, v, b);
-            aa = fmaf(w, u * u, aa);
-            bb = fmaf(w, v * v, bb);
-            ab = fmaf(w, u * v, ab);
+        for (int t = 0; t < NL; t++) {
+            const int e = tid + 256 * t, r = e / kSX, q = e - r * kSX;
+            const bool in = e < kHY * kSX && q < kHX;
+            lx[t] = in ? load0(x, x0 - kR + q, y0 - kR + r, W, H) : 0.f;
+            ly[t] = in ? load0(y, x0 - kR + q, y0 - kR + r, W, H) : 0.f;
         }
-        h[0][r][q] = a; h[1][r][q] = b; h[2][r][q] = aa; h[3][r][q] = bb; h[4][r][q] = ab;
+#pragma unroll
+        for (int t = 0; t < NL; t++) {
+            const int e = tid + 256 * t, r = e / kSX, q = e - r * kSX;
+            if (e < kHY * kSX) {
+                sx[r][q] = lx[t];
+                sy[r][q] = ly[t];
+            }
+        }
     }
     __syncthreads();
+    // horizontal: kHY rows x (kTX / kRun) runs
+    for (int e = tid; e < kHY * (kTX / kRun); e += 256) {
+        const int r = e / (kTX / kRun), j = e - r * (kTX / kRun);
+        float u[16], v[16], uu[16], vv[16], uv[16];
+        hrun(sx, r, j, u);
+        hrun(sy, r, j, v);
+#pragma unroll
+        for (int i = 0; i < kRun + 2 * kR; i++) {
+            uu[i] = u[i] * u[i];
+            vv[i] = v[i] * v[i];
+            uv[i] = u[i] * v[i];
+        }
+#pragma unroll
+        for (int i = 0; i < kRun; i++) {
+            float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
+#pragma unroll
+            for (int k = 0; k <= 2 * kR; k++) {
+                const float w = win.w[k];
+                a = fmaf(w, u[i + k], a);
+                b = fmaf(w, v[i + k], b);
+                aa = fmaf(w, uu[i + k], aa);
+                bb = fmaf(w, vv[i + k], bb);
+                ab = fmaf(w, uv[i + k], ab);
+            }
+            const int q = kRun * j + i;
+            h[0][r][q] = a; h[1][r][q] = b; h[2][r][q] = aa; h[3][r][q] = bb; h[4][r][q] = ab;
+        }
+    }
+    __syncthreads();
+    // vertical: thread (column q, run b) makes rows kRun b .. kRun b + kRun - 1
+    const int q = tid & (kTX - 1), rb = tid / kTX;
+    float st[5][kRun];
+#pragma unroll
+    for (int m = 0; m < 5; m++) {
+        float col[kRun + 2 * kR];
+#pragma unroll
+        for (int i = 0; i < kRun + 2 * kR; i++) col[i] = h[m][kRun * rb + i][q];
+#pragma unroll
+        for (int i = 0; i < kRun; i++) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k <= 2 * kR; k++) acc = fmaf(win.w[k], col[i + k], acc);
+            st[m][i] = acc;
+        }
+    }
     float l1 = 0.f, ss = 0.f;
-    for (int e = tid; e < kTY * kTX; e += 256) {
-        const int r = e / kTX, q = e - r * kTX;
-        const int gx = x0 + q, gy = y0 + r;
-        if (gx >= W || gy >= H) continue;
-        float m1 = 0.f, m2 = 0.f, e11 = 0.f, e22 = 0.f, e12 = 0.f;
+    const int gx = x0 + q;
 #pragma unroll
-        for (int k = 0; k <= 2 * kR; k++) {
-            const float w = win.w[k];
-            m1 = fmaf(w, h[0][r + k][q], m1);
-            m2 = fmaf(w, h[1][r + k][q], m2);
-            e11 = fmaf(w, h[2][r + k][q], e11);
-            e22 = fmaf(w, h[3][r + k][q], e22);
-            e12 = fmaf(w, h[4][r + k][q], e12);
-        }
+    for (int i = 0; i < kRun; i++) {
+        const int r = kRun * rb + i, gy = y0 + r;
+        if (gx >= W || gy >= H) continue;
+        const float m1 = st[0][i], m2 = st[1][i], e11 = st[2][i], e22 = st[3][i], e12 = st[4][i];
         const float sxx = e11 - m1 * m1, syy = e22 - m2 * m2, sxy = e12 - m1 * m2;
         const float A1 = 2.f * m1 * m2 + kC1, A2 = 2.f * sxy + kC2;
         const float B1 = m1 * m1 + m2 * m2 + kC1, B2 = sxx + syy + kC2;
@@ -114,55 +172,83 @@ __global__ void __launch_bounds__(256) k_ssim_pass1(const float *__restrict__ X,
     }
 }
 
+// Pass 2: dL/dx = blur(d_mu) + 2 x blur(d_xx) + y blur(d_xy) + sign(x - y) / count
+// (the window is symmetric, so the adjoint blur is the same blur).
 __global__ void __launch_bounds__(256) k_ssim_pass2(const float *__restrict__ X, const float *__restrict__ Y, int W, int H,
                                                     Win win, float l1scale, const float *__restrict__ d_mu,
                                                     const float *__restrict__ d_xx, const float *__restrict__ d_xy,
                                                     float *__restrict__ grad)
 {
-    __shared__ float s[3][kHY][kHX];
-    __shared__ float h[3][kHY][kTX];
+    __shared__ __align__(16) float s[3][kHY][kSX];
+    __shared__ float h[3][kHY][kTX + 1];
     const int c = blockIdx.z;
     const size_t off = (size_t)c * W * H;
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
     const int tid = threadIdx.x;
-    for (int e = tid; e < kHY * kHX; e += 256) {
-        const int r = e / kHX, q = e - r * kHX;
-        const int gx = x0 - kR + q, gy = y0 - kR + r;
-        s[0][r][q] = load0(d_mu + off, gx, gy, W, H);
-        s[1][r][q] = load0(d_xx + off, gx, gy, W, H);
-        s[2][r][q] = load0(d_xy + off, gx, gy, W, H);
-    }
-    __syncthreads();
-    for (int e = tid; e < kHY * kTX; e += 256) {
-        const int r = e / kTX, q = e - r * kTX;
-        float a = 0.f, b = 0.f, d = 0.f;
+    {  // haloed tiles: every load of this thread in flight before any store
+        constexpr int NL = (kHY * kSX + 255) / 256;
+        float l0[NL], l1[NL], l2[NL];
 #pragma unroll
-        for (int k = 0; k <= 2 * kR; k++) {
-            const float w = win.w[k];
-            a = fmaf(w, s[0][r][q + k], a);
-            b = fmaf(w, s[1][r][q + k], b);
-            d = fmaf(w, s[2][r][q + k], d);
+        for (int t = 0; t < NL; t++) {
+            const int e = tid + 256 * t, r = e / kSX, q = e - r * kSX;
+            const int gx = x0 - kR + q, gy = y0 - kR + r;
+            const bool in = e < kHY * kSX && q < kHX;
+            l0[t] = in ? load0(d_mu + off, gx, gy, W, H) : 0.f;
+            l1[t] = in ? load0(d_xx + off, gx, gy, W, H) : 0.f;
+            l2[t] = in ? load0(d_xy + off, gx, gy, W, H) : 0.f;
         }
-        h[0][r][q] = a; h[1][r][q] = b; h[2][r][q] = d;
+#pragma unroll
+        for (int t = 0; t < NL; t++) {
+            const int e = tid + 256 * t, r = e / kSX, q = e - r * kSX;
+            if (e < kHY * kSX) {
+                s[0][r][q] = l0[t];
+                s[1][r][q] = l1[t];
+                s[2][r][q] = l2[t];
+            }
+        }
     }
     __syncthreads();
-    for (int e = tid; e < kTY * kTX; e += 256) {
-        const int r = e / kTX, q = e - r * kTX;
-        const int gx = x0 + q, gy = y0 + r;
+    for (int e = tid; e < kHY * (kTX / kRun); e += 256) {
+        const int r = e / (kTX / kRun), j = e - r * (kTX / kRun);
+#pragma unroll
+        for (int m = 0; m < 3; m++) {
+            float u[16];
+            hrun(s[m], r, j, u);
+#pragma unroll
+            for (int i = 0; i < kRun; i++) {
+                float a = 0.f;
+#pragma unroll
+                for (int k = 0; k <= 2 * kR; k++) a = fmaf(win.w[k], u[i + k], a);
+                h[m][r][kRun * j + i] = a;
+            }
+        }
+    }
+    __syncthreads();
+    const int q = tid & (kTX - 1), rb = tid / kTX;
+    float bl[3][kRun];
+#pragma unroll
+    for (int m = 0; m < 3; m++) {
+        float col[kRun + 2 * kR];
+#pragma unroll
+        for (int i = 0; i < kRun + 2 * kR; i++) col[i] = h[m][kRun * rb + i][q];
+#pragma unroll
+        for (int i = 0; i < kRun; i++) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k <= 2 * kR; k++) acc = fmaf(win.w[k], col[i + k], acc);
+            bl[m][i] = acc;
+        }
+    }
+    const int gx = x0 + q;
+#pragma unroll
+    for (int i = 0; i < kRun; i++) {
+        const int gy = y0 + kRun * rb + i;
         if (gx >= W || gy >= H) continue;
-        float a = 0.f, b = 0.f, d = 0.f;
-#pragma unroll
-        for (int k = 0; k <= 2 * kR; k++) {
-            const float w = win.w[k];
-            a = fmaf(w, h[0][r + k][q], a);
-            b = fmaf(w, h[1][r + k][q], b);
-            d = fmaf(w, h[2][r + k][q], d);
-        }
         const size_t p = off + (size_t)gy * W + gx;
         const float xv = X[p], yv = Y[p];
         const float diff = xv - yv;
         const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
-        grad[p] = a + 2.f * xv * b + yv * d + sgn * l1scale;
+        grad[p] = bl[0][i] + 2.f * xv * bl[1][i] + yv * bl[2][i] + sgn * l1scale;
     }
 }
 

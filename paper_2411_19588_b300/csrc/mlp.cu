@@ -510,9 +510,11 @@ bool make_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// N tile: the largest multiple of 16 up to 128 that divides N
-int pick_nt(int N)
+// N tile: 256 when that still gives every SM a tile, else the largest
+// multiple of 16 up to 128 that divides N (small GEMMs spread over more CTAs)
+int pick_nt(int M, int N)
 {
+    if (N % 256 == 0 && (int64_t)(M / kBM) * (N / 256) >= 148) return 256;
     for (int nt = 128; nt >= 16; nt -= 16)
         if (N % nt == 0) return nt;
     return 0;
@@ -551,7 +553,7 @@ bool setup_gemm(Gemm &g, const void *A, int64_t lda, const void *B, int64_t ldb,
     g.N = N;
     g.K = K;
     g.args = GemmArgs{};
-    g.args.nt = pick_nt(N);
+    g.args.nt = pick_nt(M, N);
     g.args.nk = K / kBK;
     g.args.tcols = tmem_cols(g.args.nt);
     g.args.status = status;

@@ -684,6 +684,8 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_preprocess_bwd_adam(
         reinterpret_cast<float4 *>(ad.v[2])[i] = v;
         adam_update(ologits[i], glogit, ad.m[3][i], ad.v[3][i], ad.lr[3], ad.h);
     }
+    // the medium partials first, so that they are not live through the SH step
+    medium_partial(gmed, s_med, block_medium);
     __syncwarp();
     {  // warp-cooperative step of this warp's SH block
         const float *gsrc = s_sh[warp];
@@ -693,30 +695,45 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_preprocess_bwd_adam(
         const float lr = ad.lr[4];
         if (((reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(M) | reinterpret_cast<uintptr_t>(Vv)) & 15) == 0) {
             const int n4 = total >> 2;
-            for (int e = lane; e < n4; e += 32) {
-                float4 p = reinterpret_cast<float4 *>(P)[e];
-                float4 m = reinterpret_cast<float4 *>(M)[e];
-                float4 v = reinterpret_cast<float4 *>(Vv)[e];
-                float g[4];
+            float4 *P4 = reinterpret_cast<float4 *>(P), *M4 = reinterpret_cast<float4 *>(M);
+            float4 *V4 = reinterpret_cast<float4 *>(Vv);
+            // four 16-byte slots per lane per round: all twelve loads issue before any update
+            constexpr int U = 4;
+            for (int e0 = lane; e0 < n4; e0 += 32 * U) {
+                float4 p[U], m[U], v[U];
 #pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    const int f = 4 * e + k;
-                    g[k] = gsrc[(f / KC) * ROW + (f % KC)];
+                for (int u = 0; u < U; u++) {
+                    const int e = e0 + 32 * u;
+                    if (e < n4) {
+                        p[u] = P4[e];
+                        m[u] = M4[e];
+                        v[u] = V4[e];
+                    }
                 }
-                adam_update(p.x, g[0], m.x, v.x, lr, ad.h);
-                adam_update(p.y, g[1], m.y, v.y, lr, ad.h);
-                adam_update(p.z, g[2], m.z, v.z, lr, ad.h);
-                adam_update(p.w, g[3], m.w, v.w, lr, ad.h);
-                reinterpret_cast<float4 *>(P)[e] = p;
-                reinterpret_cast<float4 *>(M)[e] = m;
-                reinterpret_cast<float4 *>(Vv)[e] = v;
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int e = e0 + 32 * u;
+                    if (e >= n4) continue;
+                    float g[4];
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        const int f = 4 * e + k;
+                        g[k] = gsrc[(f / KC) * ROW + (f % KC)];
+                    }
+                    adam_update(p[u].x, g[0], m[u].x, v[u].x, lr, ad.h);
+                    adam_update(p[u].y, g[1], m[u].y, v[u].y, lr, ad.h);
+                    adam_update(p[u].z, g[2], m[u].z, v[u].z, lr, ad.h);
+                    adam_update(p[u].w, g[3], m[u].w, v[u].w, lr, ad.h);
+                    P4[e] = p[u];
+                    M4[e] = m[u];
+                    V4[e] = v[u];
+                }
             }
             done = n4 * 4;
         }
         for (int f = done + lane; f < total; f += 32)
             adam_update(P[f], gsrc[(f / KC) * ROW + (f % KC)], M[f], Vv[f], lr, ad.h);
     }
-    medium_partial(gmed, s_med, block_medium);
 }
 
 // Final stage of the medium-gradient reduction: d_medium[j] = column sums of

@@ -28,7 +28,7 @@ def _bf16(rng, shape, scale=1.0):
 
 
 @pytest.mark.parametrize("M_,N_,K_", [(128, 16, 64), (256, 128, 3136), (128, 3136, 256), (384, 208, 192),
-                                      (128, 256, 1024), (512, 48, 640)])
+                                      (128, 256, 1024), (512, 48, 640), (2048, 2560, 128)])
 def test_gemm_matches_fp64(r, M_, N_, K_):
     rng = np.random.default_rng(M_ + N_ + K_)
     A, a = _bf16(rng, (M_, K_))
