@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(fwd_threads<TW, TH>(), 1280 / fwd_threads<TW, 
 }
 
 template <int TW, int TH, int NB>
-__global__ void __launch_bounds__(bwd_threads<TW, TH>(), 640 / bwd_threads<TW, TH>()) k_blend_bwd(BlendView v, const float *__restrict__ medium)
+__global__ void __launch_bounds__(bwd_threads<TW, TH>(), 768 / bwd_threads<TW, TH>()) k_blend_bwd(BlendView v, const float *__restrict__ medium)
 {
     blend_tile_bwd<TW, TH, NB>(v, blockIdx.x, medium);
 }
@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(fwd_threads<TW, TH>(), 1152 / fwd_threads<TW, 
 }
 
 template <int TW, int TH, int NB>
-__global__ void __launch_bounds__(bwd_threads<TW, TH>(), 640 / bwd_threads<TW, TH>()) k_blend_bwd_persistent(const BlendView *__restrict__ views,
+__global__ void __launch_bounds__(bwd_threads<TW, TH>(), 768 / bwd_threads<TW, TH>()) k_blend_bwd_persistent(const BlendView *__restrict__ views,
                                                                  const uint32_t *__restrict__ items,
                                                                  const uint32_t *__restrict__ n_items, int *counter,
                                                                  const float *__restrict__ medium)

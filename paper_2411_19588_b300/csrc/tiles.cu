@@ -98,29 +98,63 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(int64_t n, const uin
     }
 }
 
+// One warp per 32 consecutive depth-ordered Gaussians. Their runs of pairs are
+// consecutive in the output, so the warp writes the whole range together with
+// coalesced stores: output slot s belongs to the last lane whose run starts at
+// or before s (a 5-step shuffle search), and is the k-th tile of that lane's
+// rectangle in row-major order. A Gaussian whose run does not fit the
+// capacity writes nothing and is reported.
 __global__ void __launch_bounds__(256) k_emit(int64_t n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ offsets,
                                               const uint32_t *__restrict__ tt, const uint2 *__restrict__ rect, int tiles_x,
                                               uint32_t *__restrict__ tile_ids, uint32_t *__restrict__ gauss_ids,
                                               uint64_t capacity, uint32_t *__restrict__ status)
 {
+    constexpr uint32_t kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    const uint32_t g = order[r];
-    const uint64_t cnt = tt[g];
-    if (cnt == 0) return;  // culled or off-image
-    const uint2 rc = rect[g];
-    const uint32_t tx0 = rc.x & 0xffffu, tx1 = rc.x >> 16, ty0 = rc.y & 0xffffu, ty1 = rc.y >> 16;
-    uint64_t off = offsets[r];
-    if (off + cnt > capacity) {
-        atomicOr(status, kStatusCapacity);
-        return;
-    }
-    for (uint32_t ty = ty0; ty <= ty1; ty++)
-        for (uint32_t tx = tx0; tx <= tx1; tx++) {
-            tile_ids[off] = ty * (uint32_t)tiles_x + tx;
-            gauss_ids[off] = g;
-            ++off;
+    if (r - lane >= n) return;  // the whole warp is past the end
+    uint32_t g = 0, cnt = 0, tx0 = 0, ty0 = 0, w = 1, fit = 0;
+    uint32_t off0 = 0;
+    if (r < n) {
+        g = order[r];
+        cnt = tt[g];
+        const uint32_t off = offsets[r];
+        if (cnt) {
+            const uint2 rc = rect[g];
+            tx0 = rc.x & 0xffffu;
+            ty0 = rc.y & 0xffffu;
+            w = (rc.x >> 16) - tx0 + 1;
+            fit = (uint64_t)off + cnt <= capacity;
+            if (!fit) atomicOr(status, kStatusCapacity);
         }
+        off0 = off;
+    }
+    off0 = __shfl_sync(kFull, off0, 0);  // offsets[first Gaussian of the warp]
+    // warp-local start of each lane's run: exclusive scan of the counts
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const uint32_t loc = incl - cnt;
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t s = base + lane;
+        int j = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t lj = __shfl_sync(kFull, loc, j + step);
+            if (lj <= s) j += step;
+        }
+        const uint32_t og = __shfl_sync(kFull, g, j), otx0 = __shfl_sync(kFull, tx0, j), oty0 = __shfl_sync(kFull, ty0, j);
+        const uint32_t ow = __shfl_sync(kFull, w, j), ofit = __shfl_sync(kFull, fit, j), oloc = __shfl_sync(kFull, loc, j);
+        if (s < total && ofit) {
+            const uint32_t k = s - oloc, dy = k / ow, dx = k - dy * ow;
+            tile_ids[(uint64_t)off0 + s] = (oty0 + dy) * (uint32_t)tiles_x + otx0 + dx;
+            gauss_ids[(uint64_t)off0 + s] = og;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(256) k_ranges(int64_t k_host, const uint32_t *__restrict__ k_dev,
