@@ -36,6 +36,9 @@ LR = {"means": 1.6e-4, "log_scales": 5e-3, "quats": 1e-3, "opacity_logits": 5e-2
 # algorithmic work per unit (see the design notes): FP32 FLOP per walked pixel-Gaussian pair
 FLOP_PER_PAIR_FWD = 18
 FLOP_PER_PAIR_BWD = 50
+# DRAM bytes (read + write) of one launch at the default workload (1.5M Gaussians, 1920x1280,
+# 16x16 tiles), from an ncu capture of the current kernel; used for the roofline's `traffic`
+KERNEL_DRAM_BYTES = {"blend_bwd": 103.13e6}
 SM_COUNT_FALLBACK = 148
 
 
@@ -412,7 +415,9 @@ def run_ours(args, world, rank, local):
         "fps": round(world * 1000.0 / fwd_ms, 2),
         "fwd_ms": round(fwd_ms, 4),
         "roofline": {"kernel": dom, "bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 2),
-                     "unit": unit, "frac": round(achieved / peak, 4), "traffic": None, "peak_source": note},
+                     "unit": unit, "frac": round(achieved / peak, 4),
+                     "traffic": KERNEL_DRAM_BYTES.get(dom) if (args.n == N_GAUSS and args.tile == "16x16") else None,
+                     "peak_source": note},
         "stages_ms": stages_ms,
         "stage_roofline": stage_roofline,
         "pairs": {"walked_fwd": int(walk), "walked_bwd": int(last), "keys": int(n_keys)},
