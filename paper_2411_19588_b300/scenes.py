@@ -440,3 +440,36 @@ def patch_scene_device(n: int, seed: int, z_range=(1.0, 8.0), width=1280, height
     return {"means": f32(torch.cat([s_means, f_means])[perm]), "log_scales": f32(torch.cat([s_log, f_log])[perm]),
             "quats": f32(torch.cat([s_quats, f_quats])[perm]),
             "opacity_logits": f32(torch.cat([s_logits, f_logits])[perm]), "sh": f32(sh), "sh_degree": sh_degree}
+
+
+def water_view(seed: int, width: int, height: int, z_range=(1.5, 12.0), z_far: float = 20.0, shadow_frac: float = 0.03,
+               shadow_block: int = 4):
+    """Maps of one synthetic underwater view for the backscatter estimator:
+    depth [H,W] (a seabed sloping from z_range[1] at the top to z_range[0]
+    at the bottom, a few rocks standing closer, and open water at exactly
+    z_far in the top corner), albedo [3,H,W] in [0.15, 1] (smooth colour
+    fields plus texture), and a shadow mask [H,W] (bool; square blocks of
+    shadow_block pixels covering about shadow_frac of the view, where the
+    direct signal is absent). Also the drawn medium. The image itself is
+    composed by the caller."""
+    rng = np.random.default_rng(seed)
+    yy, xx = np.mgrid[0:height, 0:width].astype(np.float64)
+    v = yy / max(1, height - 1)
+    z0, z1 = z_range
+    depth = z1 + (z0 - z1) * v
+    for _ in range(6):
+        cx, cy = rng.uniform(0, width), rng.uniform(0.3 * height, height)
+        rad = rng.uniform(0.05, 0.15) * width
+        bump = np.exp(-((xx - cx) ** 2 + (yy - cy) ** 2) / (2 * rad * rad))
+        depth = depth - rng.uniform(0.2, 0.5) * (depth - z0 * 0.7) * bump
+    depth[: height // 6, : width // 4] = z_far
+    alb = np.stack([0.55 + 0.3 * np.sin(xx / rng.uniform(20, 60) + yy / rng.uniform(20, 60) + c) for c in range(3)])
+    alb = np.clip(alb + rng.normal(0, 0.08, alb.shape), 0.15, 1.0)
+    shadow = np.zeros((height, width), bool)
+    bh, bw = max(1, height // shadow_block), max(1, width // shadow_block)
+    n_blocks = max(1, int(round(shadow_frac * bh * bw)))
+    picks = rng.choice(bh * bw, n_blocks, replace=False)
+    for p in picks:
+        by, bx = divmod(int(p), bw)
+        shadow[by * shadow_block:(by + 1) * shadow_block, bx * shadow_block:(bx + 1) * shadow_block] = True
+    return depth.astype(np.float32), alb.astype(np.float32), shadow, random_medium(rng)
