@@ -137,7 +137,12 @@ splash_status splash_render_backward(splash_ctx *ctx, splash_state *st, const sp
  * the medium parameters are clamped at >= medium_min after the step.
  * Every Gaussian steps (a zero gradient still moves its moments), as in
  * dense Adam. grad_medium (device float[9], may be NULL) receives the medium
- * gradient. Upstream gradients as in splash_render_backward. */
+ * gradient. Upstream gradients as in splash_render_backward. With `prior`
+ * non-NULL (device float[6] = beta_B_hat[3], B_inf_hat[3], e.g. the first six
+ * floats of a splash_backscatter_result), the gradient of Eq. 9's
+ * lambda_est L_best term, lambda_est sign(medium[3+j] - prior[j]) (sign(0) =
+ * 0), is added to medium[3..8]'s gradient before the step (and to
+ * grad_medium). */
 typedef struct {
     float *means;
     float *log_scales;
@@ -154,6 +159,8 @@ typedef struct {
     int32_t step;
     int32_t clamp_medium;
     float medium_min;
+    const float *prior; /* device [6] or NULL: the L_best estimate */
+    float lambda_est;   /* weight of L_best (Eq. 9; 0.1 in the paper) */
 } splash_adam_config;
 splash_status splash_render_backward_adam(splash_ctx *ctx, splash_state *st, const splash_param_buffers *params,
                                           int64_t n, int32_t sh_degree, const splash_camera *cam,
@@ -282,7 +289,8 @@ typedef enum {
     SPLASH_STAGE_PREPROCESS_BWD = 8,
     SPLASH_STAGE_MEDIUM_REDUCE = 9,
     SPLASH_STAGE_LOSS = 10,
-    SPLASH_STAGE_COUNT = 11
+    SPLASH_STAGE_BACKSCATTER = 11,
+    SPLASH_STAGE_COUNT = 12
 } splash_stage;
 splash_status splash_profile_enable(splash_ctx *ctx, int32_t on);
 splash_status splash_profile_read(splash_ctx *ctx, double *ms, int64_t *counts);
@@ -378,6 +386,73 @@ splash_status splash_mlp_predict(splash_mlp *mlp, const uint16_t *rows, int32_t 
 splash_status splash_mlp_step(splash_mlp *mlp, const uint16_t *bank, int64_t n_rows, const int32_t *idx,
                               const float *targets, int32_t batch, const splash_mlp_adam *adam, float *loss, splash_mlp_params *grads,
                               void *stream);
+
+/* ---- Backscatter estimate and the L_best prior (Sec. IV-B, Eq. 7-9;
+ * appendix Alg. 1 "Estimate Backscatter" and Alg. 2) -----------------------
+ * splash_backscatter_estimate turns an observed image and the expected depth
+ * of the current scene at the same view (Eq. 6) into per-channel estimates
+ * beta_B_hat and B_inf_hat of the backscatter B_inf (1 - exp(-beta_B z)):
+ *  1. image and depth are area-averaged to resized_height rows and
+ *     w = floor((2 W rh + H) / (2 H)) columns (at least 1): output row o
+ *     covers source rows [o H / rh, (o+1) H / rh), each weighted by its
+ *     overlap length (columns alike); the exact weighted mean (FP64
+ *     accumulation) is rounded once to FP32 and negative values become 0;
+ *  2. edges e_i = zmin + ((zmax - zmin) i) / (edges - 1) (FP64) over the
+ *     resized depth; a pixel's cluster is the largest i <= edges - 2 with
+ *     z >= e_i; of a cluster of n pixels the ceil(p_dark n) darkest are kept,
+ *     ranked by fl32(fl32(R + G) + B) with ties to the smaller row-major
+ *     index;
+ *  3. over the kept pixels' depths, bounds f_i = lo + ((hi - lo) i) /
+ *     (intervals - 1); per channel and per non-empty interval (the largest
+ *     i <= intervals - 2 with z >= f_i) the kept pixel with the smallest
+ *     value (ties: smaller index) gives one point (its depth, its value);
+ *  4. per channel, min sum_j (m_j - B (1 - exp(-beta z_j)))^2 over
+ *     B in [0, b_max], beta in [0, beta_max]: an FP32 scan of 1024 betas
+ *     brackets the minimum, then the zero of the derivative of the profiled
+ *     residual (B = the clipped linear least-squares value for each beta) is
+ *     found in FP64.
+ * image: device [3,H,W] FP32; depth: device [H,W] FP32; finite values.
+ * opt: NULL = the paper's values (300, 10, 25, 0.01, 1, 5). result: device,
+ * 16-byte aligned; its first six floats (beta_b, then b_inf) line up with
+ * medium[3..8] and serve as the `prior` of the calls below. resized
+ * (device, nullable) receives [4, h, w] FP32: the resized R, G, B and depth;
+ * dark (device, nullable) receives [h w] bytes, 1 for kept pixels. The
+ * scratch is owned by the context (grow-only), so estimates sharing a
+ * context must be stream-ordered. SPLASH_ERR_INVALID_ARG for a null
+ * pointer, a size below 1, a resized image above 2^24 pixels or options out
+ * of range (edges and intervals in 2..65, p_dark in (0, 1], positive bounds,
+ * resized_height in 1..4096). */
+#define SPLASH_BS_MAX_POINTS 64
+typedef struct {
+    int32_t resized_height; /* rows after the resize (300) */
+    int32_t edges;          /* depth edges of Alg. 2 (10, i.e. 9 clusters) */
+    int32_t intervals;      /* interval bounds of Alg. 1 (25, i.e. 24 intervals) */
+    int32_t pad;
+    double p_dark;          /* fraction of each cluster kept (0.01) */
+    float b_max, beta_max;  /* fit bounds (1 and 5 per metre) */
+} splash_backscatter_options;
+typedef struct {
+    float beta_b[3];       /* beta_B_hat (1/m) */
+    float b_inf[3];        /* B_inf_hat */
+    float residual[3];     /* sum of squared residuals of each channel's fit */
+    int32_t n_points[3];   /* fitted points per channel (0: nothing kept; then 0, 0) */
+    int32_t n_dark;        /* kept pixels */
+    int32_t width, height; /* resized size */
+    int32_t pad;
+    float point_z[3][SPLASH_BS_MAX_POINTS]; /* points in interval order */
+    float point_v[3][SPLASH_BS_MAX_POINTS];
+} splash_backscatter_result;
+splash_status splash_backscatter_estimate(splash_ctx *ctx, const float *image, const float *depth, int32_t width,
+                                          int32_t height, const splash_backscatter_options *opt,
+                                          splash_backscatter_result *result, float *resized, uint8_t *dark,
+                                          void *stream);
+/* Eq. 9's prior term for the unfused backward: with medium (device [9]) and
+ * prior (device [6] = beta_B_hat, B_inf_hat), adds lambda_est (|beta_B -
+ * beta_B_hat|_1 + |B_inf - B_inf_hat|_1) to *loss (device, nullable) and
+ * lambda_est sign(medium[3+j] - prior[j]) (sign(0) = 0) to grad_medium[3+j]
+ * (device [9], nullable). */
+splash_status splash_backscatter_prior(const float *medium, const float *prior, float lambda_est, float *grad_medium,
+                                       float *loss, void *stream);
 
 /* Synchronise `stream` and report any error a kernel recorded since the last check. */
 splash_status splash_sync_status(splash_ctx *ctx, void *stream);

@@ -111,7 +111,10 @@ def bounds(lo: float, hi: float, count: int) -> np.ndarray:
 def bucket(z: np.ndarray, b: np.ndarray) -> np.ndarray:
     """Largest i in 0..len(b)-2 with z >= b[i] (z >= b[0] assumed)."""
     z = np.asarray(z, np.float64)
-    return sum((z >= b[i]).astype(np.int64) for i in range(1, len(b) - 1))
+    out = np.zeros(z.shape, np.int64)
+    for i in range(1, len(b) - 1):
+        out += z >= b[i]
+    return out
 
 
 def dark_mask(img32: np.ndarray, z32: np.ndarray, p_dark: float = P_DARK, edges: int = EDGES):

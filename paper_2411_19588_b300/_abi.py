@@ -73,7 +73,24 @@ class AdamConfig(ctypes.Structure):
                 ("lr_log_scales", ctypes.c_float), ("lr_quats", ctypes.c_float), ("lr_opacity_logits", ctypes.c_float),
                 ("lr_sh", ctypes.c_float), ("lr_medium", ctypes.c_float), ("beta1", ctypes.c_float),
                 ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("step", ctypes.c_int32),
-                ("clamp_medium", ctypes.c_int32), ("medium_min", ctypes.c_float)]
+                ("clamp_medium", ctypes.c_int32), ("medium_min", ctypes.c_float), ("prior", ctypes.c_void_p),
+                ("lambda_est", ctypes.c_float)]
+
+
+BS_MAX_POINTS = 64
+
+
+class BackscatterOptions(ctypes.Structure):
+    _fields_ = [("resized_height", ctypes.c_int32), ("edges", ctypes.c_int32), ("intervals", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("p_dark", ctypes.c_double), ("b_max", ctypes.c_float),
+                ("beta_max", ctypes.c_float)]
+
+
+class BackscatterResult(ctypes.Structure):
+    _fields_ = [("beta_b", ctypes.c_float * 3), ("b_inf", ctypes.c_float * 3), ("residual", ctypes.c_float * 3),
+                ("n_points", ctypes.c_int32 * 3), ("n_dark", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("point_z", (ctypes.c_float * BS_MAX_POINTS) * 3), ("point_v", (ctypes.c_float * BS_MAX_POINTS) * 3)]
 
 
 ADAM_MAX_GROUPS = 8
@@ -136,6 +153,11 @@ _SIGS = {
     "splash_mlp_predict": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p],
     "splash_mlp_step": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                         ctypes.POINTER(MlpAdam), ctypes.c_void_p, ctypes.POINTER(MlpParams), ctypes.c_void_p],
+    "splash_backscatter_estimate": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.POINTER(BackscatterOptions), ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p],
+    "splash_backscatter_prior": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p],
     "splash_sort_pairs_u32_noalloc": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p],
 }
@@ -143,7 +165,7 @@ _SIGS = {
 NOALLOC_MAX_PAIRS = 1 << 20
 
 STAGES = ["preprocess", "depth_sort", "scan", "emit", "tile_sort", "ranges", "blend_fwd", "blend_bwd",
-          "preprocess_bwd", "medium_reduce", "loss"]
+          "preprocess_bwd", "medium_reduce", "loss", "backscatter"]
 
 FIELDS = {"tile_ids": 0, "gauss_ids": 1, "ranges": 2, "depth_keys": 3, "tiles_touched": 4, "records": 5,
           "final_T": 6, "acc_alpha": 7, "n_last": 8, "n_walk": 9, "rects": 10}

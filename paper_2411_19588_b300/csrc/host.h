@@ -173,6 +173,7 @@ struct splash_ctx {
     uint32_t *d_status = nullptr;  // kernel-reported error bits
     splash_host::Prof prof;
     splash_host::Buf feat_counts;  // featuriser histogram counters (kept zero between calls)
+    splash_host::Buf bs_scratch;   // backscatter estimate: counters, keys, clusters, kept list, resized maps
 };
 
 struct splash_state {

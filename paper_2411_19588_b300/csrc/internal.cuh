@@ -160,7 +160,7 @@ void launch_medium_reduce(const float *tile_medium, int ntiles, const float *blo
 void launch_preprocess_bwd_adam(int64_t n, int sh_degree, const splash_param_buffers &p, const float *medium,
                                 const CamK &cam, const GAcc *acc, const uint32_t *dk, const splash_adam_config &cfg,
                                 float *block_medium, int *n_blocks_out, cudaStream_t s);
-void launch_medium_adam(float *medium, const float *grad, const splash_adam_config &cfg, cudaStream_t s);
+void launch_medium_adam(float *medium, float *grad, const splash_adam_config &cfg, cudaStream_t s);
 int preprocess_bwd_blocks(int64_t n);
 int preprocess_bwd_multi_blocks(int64_t n);
 void launch_preprocess_bwd_multi(int64_t n, int V, const splash_gaussians &g, const float *medium, const BlendView *views,

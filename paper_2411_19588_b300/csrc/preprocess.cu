@@ -752,13 +752,21 @@ __global__ void k_medium_final(const float *__restrict__ part_tile, const float 
 }
 
 // Adam step on the 9 medium parameters from their reduced gradient.
-__global__ void k_medium_adam(float *__restrict__ medium, const float *__restrict__ grad, float *__restrict__ m,
-                              float *__restrict__ v, float lr, AdamHyper h, int clamp, float lo)
+// With a backscatter prior (Eq. 9), lambda_est sign(p - prior) joins the
+// gradient of beta_B and B_inf (medium[3..8]) before the step.
+__global__ void k_medium_adam(float *__restrict__ medium, float *__restrict__ grad, float *__restrict__ m,
+                              float *__restrict__ v, float lr, AdamHyper h, int clamp, float lo,
+                              const float *__restrict__ prior, float lambda_est)
 {
     const int j = threadIdx.x;
     if (j < 9) {
-        float p = medium[j], mm = m[j], vv = v[j];
-        adam_update(p, grad[j], mm, vv, lr, h);
+        float p = medium[j], mm = m[j], vv = v[j], g = grad[j];
+        if (prior && j >= 3) {
+            const float d = p - prior[j - 3];
+            g += d > 0.f ? lambda_est : (d < 0.f ? -lambda_est : 0.f);
+            grad[j] = g;
+        }
+        adam_update(p, g, mm, vv, lr, h);
         if (clamp) p = fmaxf(p, lo);
         medium[j] = p;
         m[j] = mm;
@@ -891,11 +899,11 @@ void launch_preprocess_bwd_adam(int64_t n, int sh_degree, const splash_param_buf
     }
 }
 
-void launch_medium_adam(float *medium, const float *grad, const splash_adam_config &cfg, cudaStream_t s)
+void launch_medium_adam(float *medium, float *grad, const splash_adam_config &cfg, cudaStream_t s)
 {
     k_medium_adam<<<1, 32, 0, s>>>(medium, grad, cfg.m.medium, cfg.v.medium, cfg.lr_medium,
                                    make_adam_hyper(cfg.beta1, cfg.beta2, cfg.eps, cfg.step), cfg.clamp_medium,
-                                   cfg.medium_min);
+                                   cfg.medium_min, cfg.prior, cfg.lambda_est);
     count_launch();
 }
 

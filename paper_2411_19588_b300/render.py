@@ -164,10 +164,14 @@ class Renderer:
 
     def backward_adam(self, st: State, params: dict, medium: torch.Tensor, cam: scenes.Camera, dL_dimage,
                       m: dict, v: dict, lr: dict, step: int, betas=(0.9, 0.999), eps: float = 1e-15,
-                      medium_min: float | None = 0.0, dL_ddepth=None, dL_ddepth01=None, grad_medium=None):
+                      medium_min: float | None = 0.0, dL_ddepth=None, dL_ddepth01=None, grad_medium=None,
+                      prior: torch.Tensor | None = None, lambda_est: float = 0.1):
         """Fused training-step backward: gradients of the last forward on `st`
         followed by one Adam step applied in place to params/medium and the
-        moment dicts m, v (keys PARAM_NAMES + 'medium')."""
+        moment dicts m, v (keys PARAM_NAMES + 'medium'). With `prior` (device
+        float32[6] = beta_B_hat, B_inf_hat, e.g. backscatter.prior_of(result)),
+        the L_best term of Eq. 9 weighted by lambda_est joins the medium
+        gradient."""
         H, W = cam.height, cam.width
         _check_tensor(dL_dimage, "dL_dimage", (3, H, W))
         names = PARAM_NAMES + ("medium",)
@@ -183,7 +187,10 @@ class Renderer:
                               float(lr["means"]), float(lr["log_scales"]), float(lr["quats"]),
                               float(lr["opacity_logits"]), float(lr["sh"]), float(lr["medium"]),
                               float(betas[0]), float(betas[1]), float(eps), int(step),
-                              0 if medium_min is None else 1, float(medium_min or 0.0))
+                              0 if medium_min is None else 1, float(medium_min or 0.0), _abi.ptr(prior),
+                              float(lambda_est))
+        if prior is not None:
+            _check_tensor(prior, "prior", (6,))
         c = camera_struct(cam)
         rc = _abi.lib().splash_render_backward_adam(self._ctx, st.handle, ctypes.byref(pb), params["means"].shape[0],
                                                     int(params["sh_degree"]), ctypes.byref(c), dL_dimage.data_ptr(),

@@ -67,6 +67,16 @@ def test_dark_mask_hand_worked():
     assert np.nonzero(keep)[0].tolist() == [1, 2, 4, 5, 8, 9, 12, 13, 15, 17, 19]
 
 
+def test_two_bounds_make_one_bucket():
+    """edges = 2 (or intervals = 2): a single cluster (interval) holds every pixel."""
+    z = np.array([[3.0, 1.0, 2.0, 5.0]], np.float32)
+    img = np.stack([np.array([[0.4, 0.3, 0.1, 0.2]], np.float32)] * 3)
+    keep, cl, _ = BS.dark_mask(img, z, p_dark=0.5, edges=2)
+    assert cl.tolist() == [0, 0, 0, 0] and np.nonzero(keep)[0].tolist() == [2, 3]
+    pts = BS.depth_minima(img, z, np.ones(4, bool), intervals=2)
+    assert all(p[0].tolist() == [2.0] for p in pts)
+
+
 def test_dark_mask_constant_depth_is_one_top_cluster():
     img = np.random.default_rng(3).uniform(0, 1, (3, 10, 30)).astype(np.float32)
     z = np.full((10, 30), 4.0, np.float32)
