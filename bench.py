@@ -54,12 +54,13 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--views", type=int, default=N_VIEWS, help="arc views (targets rendered up front)")
     ap.add_argument("--gemm-size", type=int, default=8192, help="gemm: M = N = K")
-    ap.add_argument("--workload", choices=["train", "batch", "warmstart", "gemm"], default="train",
+    ap.add_argument("--workload", choices=["train", "batch", "warmstart", "gemm", "backscatter"], default="train",
                     help="train: the training step (the headline metric); batch: 64 uneven views forward+backward, "
                          "sequential plain launches vs one persistent launch each way under a CUDA graph; "
                          "warmstart: MLP trained on generated renders, then the 1.5M fit from its predicted medium "
                          "vs from the default medium; gemm: the tensor-core BF16 GEMM the MLP runs on, "
-                         "at M = N = K = --gemm-size")
+                         "at M = N = K = --gemm-size; backscatter: the Alg. 1/2 estimate behind the L_best prior "
+                         "on one 1920x1280 view")
     ap.add_argument("--ws-scenes", type=int, default=200, help="warmstart: generated 300k-Gaussian scenes")
     ap.add_argument("--ws-views", type=int, default=100, help="warmstart: (medium, view) draws per scene")
     ap.add_argument("--ws-epochs", type=int, default=30)
@@ -670,6 +671,126 @@ def run_gemm(args, world, rank, local):
         print(json.dumps(out), flush=True)
 
 
+def run_backscatter(args, world, rank, local):
+    """The backscatter estimate behind Eq. 9's L_best prior (Alg. 1 and
+    Alg. 2), as the training loop runs it every 500 iterations: one observed
+    view (the target render of the 1.5M-Gaussian scene through its
+    ground-truth water) and the expected depth rendered from the current
+    scene at that view, 1920x1280 -> resized to 300x450 (FP64 area means),
+    dark pixels per depth cluster, interval minima, per-channel bounded fit.
+    Views cycle through the arc, so each call's 39 MB of inputs come from HBM
+    (all views' inputs: ~4 GB > L2)."""
+    import torch
+
+    from oracle import backscatter as obs
+    from paper_2411_19588_b300 import backscatter as BSC
+    from paper_2411_19588_b300 import render as R
+
+    torch.cuda.set_device(local)
+    r = R.Renderer()
+    params, med, gt, med_gt, cams = build_workload(args.n, rank, args.views)
+    nv = len(cams)
+    H, W = cams[0].height, cams[0].width
+    st = r.state()
+    targets, depths = [], []
+    for cam in cams:
+        targets.append(r.forward(st, gt, med_gt, cam)[0].clone())
+        depths.append(r.forward(st, params, med, cam)[1].clone())
+    del gt, st
+    res = BSC.new_result()
+    view = lambda i: (i * 7 + rank * 13) % nv
+    warm = max(3, args.warmup)
+    for i in range(warm):
+        BSC.estimate(r, targets[view(i)], depths[view(i)], result=res)
+    torch.cuda.synchronize()
+    barrier(world)
+    steps = args.steps
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = R.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(steps):
+        BSC.estimate(r, targets[view(i)], depths[view(i)], result=res)
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = R.kernel_launches() - l0
+    r.sync_status()
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, world)
+    # per-kernel durations of the same calls, from the library's stage events
+    r.profile(True)
+    r.profile_read()
+    for i in range(steps):
+        BSC.estimate(r, targets[view(i)], depths[view(i)], result=res)
+    torch.cuda.synchronize()
+    prof = r.profile_read()
+    r.profile(False)
+    t_resize = prof["bs_resize"][0] / max(1, prof["bs_resize"][1])
+    t_rest = prof["backscatter"][0] / max(1, prof["backscatter"][1])
+    est = BSC.read(res)
+    # e2e: host (pinned) image + depth in, result record out, every call
+    e2e = None
+    if not args.no_e2e:
+        h_img = targets[0].cpu().pin_memory()
+        h_dep = depths[0].cpu().pin_memory()
+        d_img, d_dep = torch.empty_like(targets[0]), torch.empty_like(depths[0])
+        h_res = torch.empty(BSC.RESULT_BYTES, dtype=torch.uint8).pin_memory()
+        reps = max(5, steps // 2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            d_img.copy_(h_img, non_blocking=True)
+            d_dep.copy_(h_dep, non_blocking=True)
+            BSC.estimate(r, d_img, d_dep, result=res)
+            h_res.copy_(res, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / reps
+        e2e = {"value": round(world / e2e_s, 2), "unit": "estimates/s",
+               "h2d_bytes_per_step": int(h_img.numel() * 4 + h_dep.numel() * 4),
+               "d2h_bytes_per_step": int(BSC.RESULT_BYTES)}
+    peaks, src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    # the resize: bytes (read image + depth, write the four resized maps and the keys) and FP64 work
+    # (one multiply-add per overlapping source pixel and channel, one per overlapping row to combine)
+    w, h = BSC.resized_size(W, H)
+    resize_bytes = 16 * H * W + 20 * h * w
+    span = lambda n_in, n_out, o: min(n_in, -(-((o + 1) * n_in) // n_out)) - (o * n_in) // n_out
+    rows = sum(span(H, h, o) for o in range(h))
+    cols = sum(span(W, w, p) + 1 for p in range(w))
+    resize_flop = 2 * 4 * rows * cols
+    fp64_peak = 1250.0  # GFLOP/s: nominal B300 FP64 rate (no measured FP64 peak on this pool)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        img_np, dep_np = targets[0].cpu().numpy(), depths[0].cpu().numpy()
+        t0 = time.perf_counter()
+        obs.estimate(img_np, dep_np)
+        t_cpu = time.perf_counter() - t0
+        cpu = {"value": round(1.0 / t_cpu, 4), "unit": "estimates/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "one full estimate of one 1920x1280 view (FP64 resize, dark pixels, minima, multi-start "
+                         "trust-region fit)"}
+    out = {"metric": "backscatter estimates/s (Alg. 1/2) at 1920x1280 -> 300x450", "value": round(world * 1e3 / ms, 2),
+           "unit": "estimates/s", "n_gpus": world, "steps": steps, "warmup": warm, "ms_per_step": round(ms, 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32",
+           "data": "synthetic",
+           "config": {"workload": "backscatter estimate: target render of the 1.5M-Gaussian scene + rendered depth, "
+                                  "1920x1280 -> 300x450, 9 clusters, 24 intervals, p_dark 0.01",
+                      "l2": f"inputs cycle over {nv} views ({nv * 39} MB > L2)"},
+           "stages_ms": {"bs_resize": round(t_resize, 4), "cluster+select+minima+fit": round(t_rest, 4)},
+           "roofline": {"kernel": "k_bs_resize", "bound": "alu", "achieved": round(resize_flop / (t_resize * 1e-3) / 1e9, 1),
+                        "peak": fp64_peak, "unit": "GFLOP/s (FP64)",
+                        "frac": round(resize_flop / (t_resize * 1e-3) / 1e9 / fp64_peak, 4),
+                        "traffic": None, "peak_source": "nominal FP64 rate (148 SMs at 2032 MHz)",
+                        "hbm": {"achieved": round(resize_bytes / (t_resize * 1e-3) / 1e9, 1), "peak": hbm,
+                                "unit": "GB/s", "frac": round(resize_bytes / (t_resize * 1e-3) / 1e9 / hbm, 4),
+                                "peak_source": f"{src} copy bandwidth"}},
+           "estimate": {"beta_b": est["beta_b"].tolist(), "b_inf": est["b_inf"].tolist(), "n_dark": est["n_dark"],
+                        "true_beta_b": med_gt[3:6].tolist(), "true_b_inf": med_gt[6:9].tolist()},
+           "gpu_launches": int(launches), "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def cpu_baseline(budget_s: float = 20.0, n: int = N_GAUSS) -> dict:
     """The FP64 oracle (as it stands) on a bounded sample of the training
     step: projection of all Gaussians, forward and adjoint at a random
@@ -746,6 +867,8 @@ def main():
         run_warmstart(args, world, rank, local)
     elif args.workload == "gemm":
         run_gemm(args, world, rank, local)
+    elif args.workload == "backscatter":
+        run_backscatter(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

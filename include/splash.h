@@ -289,8 +289,9 @@ typedef enum {
     SPLASH_STAGE_PREPROCESS_BWD = 8,
     SPLASH_STAGE_MEDIUM_REDUCE = 9,
     SPLASH_STAGE_LOSS = 10,
-    SPLASH_STAGE_BACKSCATTER = 11,
-    SPLASH_STAGE_COUNT = 12
+    SPLASH_STAGE_BACKSCATTER = 11, /* cluster, select, minima and fit of the backscatter estimate */
+    SPLASH_STAGE_BS_RESIZE = 12,   /* the estimate's resize */
+    SPLASH_STAGE_COUNT = 13
 } splash_stage;
 splash_status splash_profile_enable(splash_ctx *ctx, int32_t on);
 splash_status splash_profile_read(splash_ctx *ctx, double *ms, int64_t *counts);

@@ -165,7 +165,8 @@ _SIGS = {
 NOALLOC_MAX_PAIRS = 1 << 20
 
 STAGES = ["preprocess", "depth_sort", "scan", "emit", "tile_sort", "ranges", "blend_fwd", "blend_bwd",
-          "preprocess_bwd", "medium_reduce", "loss", "backscatter"]
+          "preprocess_bwd", "medium_reduce", "loss", "backscatter",
+          "bs_resize"]
 
 FIELDS = {"tile_ids": 0, "gauss_ids": 1, "ranges": 2, "depth_keys": 3, "tiles_touched": 4, "records": 5,
           "final_T": 6, "acc_alpha": 7, "n_last": 8, "n_walk": 9, "rects": 10}

@@ -6,12 +6,14 @@
 //
 //   k_bs_resize  -- area-average resize of image + depth (FP64 accumulation,
 //                   one rounding to FP32), darkness keys, depth min/max
-//   k_bs_cluster -- depth cluster of every pixel, cluster sizes
-//   k_bs_select  -- one block per cluster: radix select of the
+//   k_bs_cluster -- depth cluster of every pixel, per-block cluster counts
+//   k_bs_offsets -- where each (block, cluster) run starts in the partition
+//   k_bs_scatter -- stable partition of (darkness key, index) by cluster
+//   k_bs_select  -- one block per cluster segment: radix select of the
 //                   ceil(p_dark n)-th darkest key, then the kept pixels
-//   k_bs_minima  -- interval minima of the kept pixels -> fit points
-//   k_bs_fit     -- one block per channel: FP32 scan over beta, FP64
-//                   root of the profiled residual's derivative
+//   k_bs_fit     -- one block per channel: interval minima of the kept
+//                   pixels (the fit points), then an FP32 residual scan over
+//                   beta and two sign scans of the profiled derivative
 //   k_bs_prior   -- Eq. 9's lambda_est L_best loss and gradient
 //
 // The estimate runs once every few hundred training iterations on a
@@ -42,7 +44,8 @@ struct BsCounters {      // cleared by one memset per estimate
     uint32_t zmin_inv;   // max of ~bits, i.e. ~(min bits)
     uint32_t n_dark;
     uint32_t pad;
-    uint32_t count[kMaxClusters];
+    uint32_t count[kMaxClusters];  // cluster sizes
+    uint32_t start[kMaxClusters];  // segment starts of the cluster-major partition
 };
 
 __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
@@ -126,10 +129,16 @@ __device__ __forceinline__ float bound_ru(double lo, double hi, int i, int count
     return __double2float_ru(e);
 }
 
-// Alg. 2: cluster = the largest i <= E-2 with z >= e_i.
-__global__ void __launch_bounds__(256) k_bs_cluster(const float *__restrict__ z, int64_t N, int E,
-                                                    BsCounters *__restrict__ cnt, uint8_t *__restrict__ cl,
-                                                    uint8_t *__restrict__ dark)
+constexpr int kPartThreads = 256;
+constexpr int kPartItems = 4;
+constexpr int kPartTile = kPartThreads * kPartItems;  // pixels per partition block
+
+// Alg. 2: cluster = the largest i <= E-2 with z >= e_i. One block per 1024
+// consecutive pixels; also its per-cluster counts (for the stable partition)
+// and the cluster sizes.
+__global__ void __launch_bounds__(kPartThreads) k_bs_cluster(const float *__restrict__ z, int64_t N, int E,
+                                                             BsCounters *__restrict__ cnt, uint8_t *__restrict__ cl,
+                                                             uint32_t *__restrict__ blk_cnt, uint8_t *__restrict__ dark)
 {
     __shared__ float s_t[kMaxClusters];
     __shared__ uint32_t s_cnt[kMaxClusters];
@@ -137,17 +146,91 @@ __global__ void __launch_bounds__(256) k_bs_cluster(const float *__restrict__ z,
     if ((int)threadIdx.x < E - 2) s_t[threadIdx.x] = bound_ru(zmin, zmax, threadIdx.x + 1, E);
     if ((int)threadIdx.x < E - 1) s_cnt[threadIdx.x] = 0;
     __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) {
-        const float zi = z[i];
-        int c = 0;
-        for (int k = 0; k < E - 2; k++) c += zi >= s_t[k];
-        cl[i] = (uint8_t)c;
-        if (dark) dark[i] = 0;
-        atomicAdd(&s_cnt[c], 1u);
+    const int64_t base = (int64_t)blockIdx.x * kPartTile;
+#pragma unroll
+    for (int r = 0; r < kPartItems; r++) {
+        const int64_t i = base + r * kPartThreads + threadIdx.x;
+        if (i < N) {
+            const float zi = z[i];
+            int c = 0;
+            for (int k = 0; k < E - 2; k++) c += zi >= s_t[k];
+            cl[i] = (uint8_t)c;
+            if (dark) dark[i] = 0;
+            // one shared atomic per distinct cluster in the warp
+            const unsigned peers = __match_any_sync(__activemask(), c);
+            if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&s_cnt[c], (uint32_t)__popc(peers));
+        }
     }
     __syncthreads();
-    if ((int)threadIdx.x < E - 1 && s_cnt[threadIdx.x]) atomicAdd(&cnt->count[threadIdx.x], s_cnt[threadIdx.x]);
+    if ((int)threadIdx.x < E - 1) {
+        const uint32_t v = s_cnt[threadIdx.x];
+        blk_cnt[(int64_t)blockIdx.x * (E - 1) + threadIdx.x] = v;
+        if (v) atomicAdd(&cnt->count[threadIdx.x], v);
+    }
+}
+
+// Start of every (block, cluster) run in the cluster-major partition: warp c
+// scans column c of blk_cnt over the blocks, after the sizes of the clusters
+// before c. Also the segment start of each cluster.
+__global__ void __launch_bounds__(1024) k_bs_offsets(int nblk, int E, BsCounters *__restrict__ cnt,
+                                                     uint32_t *__restrict__ blk_cnt)
+{
+    const int lane = threadIdx.x & 31;
+    for (int c = threadIdx.x >> 5; c < E - 1; c += 32) {
+    uint32_t carry = 0;
+    for (int k = 0; k < c; k++) carry += cnt->count[k];
+    if (lane == 0) cnt->start[c] = carry;
+    for (int b0 = 0; b0 < nblk; b0 += 32) {
+        const int b = b0 + lane;
+        const uint32_t v = b < nblk ? blk_cnt[(int64_t)b * (E - 1) + c] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (b < nblk) blk_cnt[(int64_t)b * (E - 1) + c] = carry + x - v;
+        carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+    }
+}
+
+// Stable partition by cluster: every pixel's (key, index) goes to its
+// cluster's segment, in index order.
+__global__ void __launch_bounds__(kPartThreads) k_bs_scatter(const uint32_t *__restrict__ key, const uint8_t *__restrict__ cl,
+                                                             int64_t N, int E, const uint32_t *__restrict__ blk_off,
+                                                             uint32_t *__restrict__ seg_key, uint32_t *__restrict__ seg_idx)
+{
+    constexpr int kWarps = kPartThreads / 32;
+    __shared__ uint32_t s_run[kMaxClusters];           // pixels of each cluster placed so far
+    __shared__ uint32_t s_wc[kWarps][kMaxClusters];    // this round's count per warp and cluster
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if ((int)threadIdx.x < E - 1) s_run[threadIdx.x] = blk_off[(int64_t)blockIdx.x * (E - 1) + threadIdx.x];
+    const int64_t base = (int64_t)blockIdx.x * kPartTile;
+    for (int r = 0; r < kPartItems; r++) {
+        for (int k = threadIdx.x; k < kWarps * kMaxClusters; k += kPartThreads) (&s_wc[0][0])[k] = 0;
+        __syncthreads();
+        const int64_t i = base + r * kPartThreads + threadIdx.x;
+        const bool ok = i < N;
+        int c = ok ? cl[i] : kMaxClusters;  // past the end: a cluster no pixel has
+        const unsigned peers = __match_any_sync(0xffffffffu, c);
+        const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+        if (ok && lane == __ffs(peers) - 1) s_wc[wid][c] = __popc(peers);
+        __syncthreads();
+        if (ok) {
+            uint32_t pos = s_run[c] + rank;
+            for (int w2 = 0; w2 < wid; w2++) pos += s_wc[w2][c];
+            seg_key[pos] = key[i];
+            seg_idx[pos] = (uint32_t)i;
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < E - 1) {
+            uint32_t t = 0;
+            for (int w2 = 0; w2 < kWarps; w2++) t += s_wc[w2][threadIdx.x];
+            s_run[threadIdx.x] += t;
+        }
+        __syncthreads();
+    }
 }
 
 constexpr int kSelThreads = 1024;
@@ -179,12 +262,13 @@ __device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t *s_w)
 }
 
 // Block c keeps the k = ceil(p_dark n_c) smallest (key, index) pairs of
-// cluster c: three radix rounds (11, 11, 10 bits) find the k-th smallest key
-// t, then every key < t is kept together with the first (in index order)
-// keys == t needed to reach k.
-__global__ void __launch_bounds__(kSelThreads) k_bs_select(const uint32_t *__restrict__ key, const uint8_t *__restrict__ cl,
-                                                           int64_t N, double p_dark, BsCounters *__restrict__ cnt,
-                                                           uint32_t *__restrict__ list, uint8_t *__restrict__ dark)
+// cluster c's segment (index order): three radix rounds (11, 11, 10 bits)
+// find the k-th smallest key t, then every key < t is kept together with the
+// first keys == t needed to reach k.
+__global__ void __launch_bounds__(kSelThreads) k_bs_select(const uint32_t *__restrict__ seg_key,
+                                                           const uint32_t *__restrict__ seg_idx, double p_dark,
+                                                           BsCounters *__restrict__ cnt, uint32_t *__restrict__ list,
+                                                           uint8_t *__restrict__ dark)
 {
     __shared__ uint32_t hist[2048];
     __shared__ uint32_t s_w[32];
@@ -192,6 +276,8 @@ __global__ void __launch_bounds__(kSelThreads) k_bs_select(const uint32_t *__res
     const int c = blockIdx.x;
     const uint32_t n = cnt->count[c];
     if (n == 0) return;
+    const uint32_t *keys = seg_key + cnt->start[c];
+    const uint32_t *idxs = seg_idx + cnt->start[c];
     uint32_t krem = (uint32_t)ceil(__dmul_rn(p_dark, (double)n));
     krem = min(max(krem, 1u), n);
     uint32_t prefix = 0, pmask = 0;
@@ -200,10 +286,14 @@ __global__ void __launch_bounds__(kSelThreads) k_bs_select(const uint32_t *__res
         const uint32_t dmask = round == 2 ? 0x3ffu : 0x7ffu;
         for (int b = threadIdx.x; b < 2048; b += kSelThreads) hist[b] = 0;
         __syncthreads();
-        for (int64_t i = threadIdx.x; i < N; i += kSelThreads) {
-            if (cl[i] != c) continue;
-            const uint32_t u = key[i];
-            if ((u & pmask) == prefix) atomicAdd(&hist[(u >> shift) & dmask], 1u);
+        for (uint32_t j0 = 0; j0 < n; j0 += kSelThreads) {
+            const uint32_t j = j0 + threadIdx.x;
+            const uint32_t u = j < n ? keys[j] : 0u;
+            const bool in = j < n && (u & pmask) == prefix;
+            const uint32_t d = in ? (u >> shift) & dmask : 0xffffffffu;
+            // one shared atomic per distinct digit in the warp (neighbouring keys share digits)
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (in && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[d], (uint32_t)__popc(peers));
         }
         __syncthreads();
         // thread t owns bins 2t, 2t+1; find the bin where the running count reaches krem
@@ -222,230 +312,198 @@ __global__ void __launch_bounds__(kSelThreads) k_bs_select(const uint32_t *__res
         __syncthreads();
     }
     const uint32_t t = prefix, need = krem;  // keys < t all kept; `need` of the keys == t
-    const int64_t chunk = (N + kSelThreads - 1) / kSelThreads;
-    const int64_t a = min64(N, (int64_t)threadIdx.x * chunk), b = min64(N, a + chunk);
+    const uint32_t chunk = (n + kSelThreads - 1) / kSelThreads;
+    const uint32_t a = min(n, threadIdx.x * chunk), b = min(n, a + chunk);
     uint32_t ties = 0;
-    for (int64_t i = a; i < b; i++) ties += (cl[i] == c && key[i] == t);
+    for (uint32_t j = a; j < b; j++) ties += keys[j] == t;
     uint32_t before = block_incl_scan(ties, s_w) - ties;
-    for (int64_t i = a; i < b; i++) {
-        if (cl[i] != c) continue;
-        const uint32_t u = key[i];
+    for (uint32_t j = a; j < b; j++) {
+        const uint32_t u = keys[j];
         bool take = u < t;
         if (u == t) take = before++ < need;
         if (take) {
-            list[atomicAdd(&cnt->n_dark, 1u)] = (uint32_t)i;
+            const uint32_t i = idxs[j];
+            list[atomicAdd(&cnt->n_dark, 1u)] = i;
             if (dark) dark[i] = 1;
         }
     }
 }
 
-// Alg. 1 steps 6-8: interval bounds over the kept depths; per channel and
-// interval, the kept pixel with the smallest (value, index).
-__global__ void __launch_bounds__(1024) k_bs_minima(const float *__restrict__ res, int64_t N, int w, int h, int M,
-                                                    const BsCounters *__restrict__ cnt, const uint32_t *__restrict__ list,
-                                                    splash_backscatter_result *__restrict__ out)
+// Profiled residual of one channel: for a given beta the best B is the
+// clipped linear least-squares value B(beta) = clip(sum m f / sum f f), and
+// by the envelope theorem dS/dbeta = -2 B (sum m f' - B sum f f'), with
+// f = 1 - exp(-beta z) and f' = z exp(-beta z). FP32; one thread per beta.
+__device__ __forceinline__ float dS32(float beta, const float *z, const float *m, int n, float bmax)
 {
-    __shared__ uint32_t s_red[32];
-    __shared__ float s_f[kMaxIntervals];
-    __shared__ unsigned long long s_best[3][kMaxIntervals];
-    const uint32_t nd = cnt->n_dark;
-    const float *zres = res + 3 * N;
-    uint32_t hi = 0, loinv = 0;
-    for (uint32_t j = threadIdx.x; j < nd; j += blockDim.x) {
-        const uint32_t zb = __float_as_uint(zres[list[j]]);
-        hi = max(hi, zb);
-        loinv = max(loinv, ~zb);
+    float smf = 0.f, sff = 0.f, smp = 0.f, sfp = 0.f;
+    for (int j = 0; j < n; j++) {
+        const float em1 = expm1f(-beta * z[j]), f = -em1, fp = z[j] * (1.f + em1);
+        smf = fmaf(m[j], f, smf);
+        sff = fmaf(f, f, sff);
+        smp = fmaf(m[j], fp, smp);
+        sfp = fmaf(f, fp, sfp);
     }
-    hi = block_max_u32(hi, s_red);
-    loinv = block_max_u32(loinv, s_red);
-    if ((int)threadIdx.x < M - 2) s_f[threadIdx.x] = bound_ru(__uint_as_float(~loinv), __uint_as_float(hi), threadIdx.x + 1, M);
-    for (int k = threadIdx.x; k < 3 * kMaxIntervals; k += blockDim.x) (&s_best[0][0])[k] = ~0ull;
+    const float B = sff > 0.f ? fminf(bmax, fmaxf(0.f, smf / sff)) : 0.f;
+    return -2.f * B * (smp - B * sfp);
+}
+
+__device__ __forceinline__ float B32(float beta, const float *z, const float *m, int n, float bmax)
+{
+    float smf = 0.f, sff = 0.f;
+    for (int j = 0; j < n; j++) {
+        const float f = -expm1f(-beta * z[j]);
+        smf = fmaf(m[j], f, smf);
+        sff = fmaf(f, f, sff);
+    }
+    return sff > 0.f ? fminf(bmax, fmaxf(0.f, smf / sff)) : 0.f;
+}
+
+__device__ __forceinline__ float S32(float beta, float B, const float *z, const float *m, int n)
+{
+    float S = 0.f;
+    for (int j = 0; j < n; j++) {
+        const float r = m[j] + B * expm1f(-beta * z[j]);
+        S = fmaf(r, r, S);
+    }
+    return S;
+}
+
+// Block-wide: the first thread whose flag is set (kGrid if none), and
+// whether any thread's `any` is set.
+__device__ __forceinline__ int block_first(bool flag, bool any, int *s_i, int *s_any)
+{
+    int v = __reduce_min_sync(0xffffffffu, flag ? (int)threadIdx.x : kGrid);
+    const unsigned a = __reduce_or_sync(0xffffffffu, any ? 1u : 0u);
+    if ((threadIdx.x & 31) == 0) {
+        s_i[threadIdx.x >> 5] = v;
+        s_any[threadIdx.x >> 5] = (int)a;
+    }
     __syncthreads();
-    for (uint32_t j = threadIdx.x; j < nd; j += blockDim.x) {
+    int r = kGrid, an = 0;
+    for (int w = 0; w < kGrid / 32; w++) {
+        r = min(r, s_i[w]);
+        an |= s_any[w];
+    }
+    __syncthreads();
+    return an ? r : -1;
+}
+
+// Bounded fit of one channel (block = channel): level 1 scans the residual
+// at kGrid betas over [0, beta_max] for the global minimum; levels 2 and 3
+// scan the sign of dS/dbeta at kGrid betas inside the best cell pair and
+// then inside the bracketing sub-cell, locating the zero to about the FP32
+// noise of dS (a few 1e-6 relative). Where dS keeps one sign across a cell
+// the minimum is on the cell's edge (a bound of the box, or the level-1
+// point when dS vanishes identically).
+__global__ void __launch_bounds__(kGrid) k_bs_fit(const float *__restrict__ res, int64_t N, int w, int h, int M,
+                                                  const BsCounters *__restrict__ cnt, const uint32_t *__restrict__ list,
+                                                  splash_backscatter_result *__restrict__ out, float bmax, float beta_max)
+{
+    __shared__ float s_z[kMaxIntervals], s_m[kMaxIntervals];
+    __shared__ unsigned long long s_min[32];
+    __shared__ unsigned long long s_best[kMaxIntervals];
+    __shared__ float s_f[kMaxIntervals];
+    __shared__ uint32_t s_red[32];
+    __shared__ int s_i[32], s_any[32];
+    __shared__ int s_g, s_n;
+    const int ch = blockIdx.x, t = threadIdx.x;
+    // Alg. 1 steps 6-8 for this channel: interval bounds over the kept
+    // depths, then per interval the kept pixel with the smallest (value, index)
+    const uint32_t nd = cnt->n_dark;
+    const float *zres = res + 3 * N, *vres = res + ch * N;
+    uint32_t hi_b = 0, lo_inv = 0;
+    for (uint32_t j = t; j < nd; j += blockDim.x) {
+        const uint32_t zb = __float_as_uint(zres[list[j]]);
+        hi_b = max(hi_b, zb);
+        lo_inv = max(lo_inv, ~zb);
+    }
+    hi_b = block_max_u32(hi_b, s_red);
+    lo_inv = block_max_u32(lo_inv, s_red);
+    if (t < M - 2) s_f[t] = bound_ru(__uint_as_float(~lo_inv), __uint_as_float(hi_b), t + 1, M);
+    if (t < kMaxIntervals) s_best[t] = ~0ull;
+    __syncthreads();
+    for (uint32_t j = t; j < nd; j += blockDim.x) {
         const uint32_t idx = list[j];
         const float zi = zres[idx];
         int iv = 0;
         for (int k = 0; k < M - 2; k++) iv += zi >= s_f[k];
-#pragma unroll
-        for (int ch = 0; ch < 3; ch++) {
-            const unsigned long long v = ((unsigned long long)__float_as_uint(res[ch * N + idx]) << 32) | idx;
-            atomicMin(&s_best[ch][iv], v);
-        }
+        atomicMin(&s_best[iv], ((unsigned long long)__float_as_uint(vres[idx]) << 32) | idx);
     }
     __syncthreads();
-    if (threadIdx.x < 3) {
-        const int ch = threadIdx.x;
+    if (t == 0) {
         int np = 0;
         for (int iv = 0; iv < M - 1; iv++) {
-            const unsigned long long b = s_best[ch][iv];
+            const unsigned long long b = s_best[iv];
             if (b == ~0ull) continue;
-            const uint32_t idx = (uint32_t)(b & 0xffffffffu);
-            out->point_z[ch][np] = zres[idx];
-            out->point_v[ch][np] = __uint_as_float((uint32_t)(b >> 32));
+            s_z[np] = zres[(uint32_t)(b & 0xffffffffu)];
+            s_m[np] = __uint_as_float((uint32_t)(b >> 32));
             np++;
         }
+        s_n = np;
         out->n_points[ch] = np;
-    }
-    if (threadIdx.x == 0) {
-        out->n_dark = (int32_t)nd;
-        out->width = w;
-        out->height = h;
-        out->pad = 0;
-    }
-}
-
-// Profiled residual of one channel: for a given beta the best B is the
-// clipped linear least-squares value, and by the envelope theorem
-// dS/dbeta = -2 B (sum m f' - B sum f f'), f = 1 - exp(-beta z),
-// f' = z exp(-beta z). Lanes hold the points; FP64.
-struct Prof64 {
-    double B, dS;
-};
-
-__device__ Prof64 profile64(double beta, const float *z, const float *m, int n, double bmax)
-{
-    double smf = 0, sff = 0, smp = 0, sfp = 0;
-    for (int j = threadIdx.x & 31; j < n; j += 32) {
-        const double zj = z[j], mj = m[j];
-        const double e = exp(-beta * zj), f = 1.0 - e, fp = zj * e;
-        smf = fma(mj, f, smf);
-        sff = fma(f, f, sff);
-        smp = fma(mj, fp, smp);
-        sfp = fma(f, fp, sfp);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        smf += __shfl_xor_sync(0xffffffffu, smf, o);
-        sff += __shfl_xor_sync(0xffffffffu, sff, o);
-        smp += __shfl_xor_sync(0xffffffffu, smp, o);
-        sfp += __shfl_xor_sync(0xffffffffu, sfp, o);
-    }
-    Prof64 r;
-    r.B = sff > 0 ? fmin(bmax, fmax(0.0, smf / sff)) : 0.0;
-    r.dS = -2.0 * r.B * (smp - r.B * sfp);
-    return r;
-}
-
-__global__ void __launch_bounds__(kGrid) k_bs_fit(splash_backscatter_result *__restrict__ out, float bmax, float beta_max)
-{
-    __shared__ float s_z[kMaxIntervals], s_m[kMaxIntervals];
-    __shared__ unsigned long long s_min[32];
-    __shared__ int s_g;
-    const int ch = blockIdx.x;
-    const int n = out->n_points[ch];
-    if (n <= 0) {
-        if (threadIdx.x == 0) out->beta_b[ch] = out->b_inf[ch] = out->residual[ch] = 0.f;
-        return;
-    }
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        s_z[j] = out->point_z[ch][j];
-        s_m[j] = out->point_v[ch][j];
+        if (ch == 0) {
+            out->n_dark = (int32_t)nd;
+            out->width = w;
+            out->height = h;
+            out->pad = 0;
+        }
     }
     __syncthreads();
-    // FP32 scan: beta_g = beta_max g / (kGrid - 1), residual with the best B
+    const int n = s_n;
+    for (int j = t; j < kMaxIntervals; j += blockDim.x) {
+        out->point_z[ch][j] = j < n ? s_z[j] : 0.f;
+        out->point_v[ch][j] = j < n ? s_m[j] : 0.f;
+    }
+    if (n <= 0) {
+        if (t == 0) out->beta_b[ch] = out->b_inf[ch] = out->residual[ch] = 0.f;
+        return;
+    }
+    // level 1: residual at beta_g = beta_max g / (kGrid - 1)
+    auto grid1 = [&](int g) { return beta_max * (float)g / (float)(kGrid - 1); };
     {
-        const int g = threadIdx.x;
-        const float beta = beta_max * (float)g / (float)(kGrid - 1);
-        float smf = 0.f, sff = 0.f;
-        for (int j = 0; j < n; j++) {
-            const float f = -expm1f(-beta * s_z[j]);
-            smf = fmaf(s_m[j], f, smf);
-            sff = fmaf(f, f, sff);
-        }
-        const float B = sff > 0.f ? fminf(bmax, fmaxf(0.f, smf / sff)) : 0.f;
-        float S = 0.f;
-        for (int j = 0; j < n; j++) {
-            const float r = s_m[j] + B * expm1f(-beta * s_z[j]);
-            S = fmaf(r, r, S);
-        }
-        unsigned long long v = ((unsigned long long)__float_as_uint(S) << 32) | (uint32_t)g;
+        const float beta = grid1(t);
+        const float S = S32(beta, B32(beta, s_z, s_m, n, bmax), s_z, s_m, n);
+        unsigned long long v = ((unsigned long long)__float_as_uint(S) << 32) | (uint32_t)t;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-        if ((threadIdx.x & 31) == 0) s_min[threadIdx.x >> 5] = v;
+        if ((t & 31) == 0) s_min[t >> 5] = v;
         __syncthreads();
-        if (threadIdx.x < 32) {
-            unsigned long long u = s_min[threadIdx.x];
+        if (t < 32) {
+            unsigned long long u = s_min[t];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) u = min(u, __shfl_xor_sync(0xffffffffu, u, o));
-            if (threadIdx.x == 0) s_g = (int)(u & 0xffffffffu);
+            if (t == 0) s_g = (int)(u & 0xffffffffu);
         }
         __syncthreads();
     }
-    if (threadIdx.x >= 32) return;
-    // FP64: zero of dS/dbeta next to the best scan point (the bracket moves
-    // outward one scan cell at a time if the FP32 scan was off by a cell)
-    const double bm = bmax, top = beta_max;
-    auto grid = [&](int g) { return top * (double)g / (double)(kGrid - 1); };
-    int g = s_g;
-    double x = grid(g);
-    Prof64 px = profile64(x, s_z, s_m, n, bm);
-    double beta = x;
-    if (px.dS != 0.0) {
-        double lo, hi, flo, fhi;
-        bool bracketed = false;
-        if (px.dS < 0.0) {  // descending at x: the minimum lies to the right
-            lo = x, flo = px.dS;
-            int gh = g;
-            hi = x, fhi = px.dS;
-            while (gh < kGrid - 1) {
-                hi = grid(++gh);
-                fhi = profile64(hi, s_z, s_m, n, bm).dS;
-                if (fhi > 0.0) { bracketed = true; break; }
-                if (fhi == 0.0) break;
-                lo = hi, flo = fhi;
-            }
-            if (!bracketed) beta = hi;  // at the upper bound, or an exact stationary point
-        } else {
-            hi = x, fhi = px.dS;
-            int gl = g;
-            lo = x, flo = px.dS;
-            while (gl > 0) {
-                lo = grid(--gl);
-                flo = profile64(lo, s_z, s_m, n, bm).dS;
-                if (flo < 0.0) { bracketed = true; break; }
-                if (flo == 0.0) break;
-                hi = lo, fhi = flo;
-            }
-            if (!bracketed) beta = lo;
+    const int g = s_g;
+    float lo = grid1(max(g - 1, 0)), hi = grid1(min(g + 1, kGrid - 1));
+    float beta = grid1(g);
+    // levels 2 and 3: first point of the cell where dS > 0
+    for (int level = 0; level < 2; level++) {
+        const float b = lo + (hi - lo) * (float)t / (float)(kGrid - 1);
+        const float d = dS32(b, s_z, s_m, n, bmax);
+        const int first = block_first(d > 0.f, d != 0.f, s_i, s_any);
+        if (first < 0) break;  // dS vanishes on the whole cell: keep the level-1 point
+        if (first == 0) {      // rising from the left edge: the minimum is at that edge
+            beta = lo;
+            break;
         }
-        if (bracketed) {
-            // Illinois regula falsi on flo < 0 < fhi
-            int side = 0;
-            for (int it = 0; it < 200; it++) {
-                double c = hi - fhi * (hi - lo) / (fhi - flo);
-                if (!(c > lo && c < hi)) c = 0.5 * (lo + hi);
-                if (!(c > lo && c < hi)) break;  // no representable point left inside
-                const double fc = profile64(c, s_z, s_m, n, bm).dS;
-                if (fc == 0.0) {
-                    lo = hi = c;
-                    break;
-                }
-                if (fc < 0.0) {
-                    lo = c, flo = fc;
-                    if (side == -1) fhi *= 0.5;
-                    side = -1;
-                } else {
-                    hi = c, fhi = fc;
-                    if (side == 1) flo *= 0.5;
-                    side = 1;
-                }
-                if (hi - lo <= 2e-16 * hi) break;
-            }
-            beta = -flo <= fhi ? lo : hi;
+        const float l2 = lo + (hi - lo) * (float)(first - 1) / (float)(kGrid - 1);
+        const float h2 = first == kGrid ? hi : lo + (hi - lo) * (float)first / (float)(kGrid - 1);
+        if (first == kGrid) {  // falling across the whole cell: the minimum is at the right edge
+            beta = hi;
+            break;
         }
+        lo = l2;
+        hi = h2;
+        beta = 0.5f * (lo + hi);
     }
-    const Prof64 pf = profile64(beta, s_z, s_m, n, bm);
-    double S = 0.0;
-    for (int j = threadIdx.x; j < n; j += 32) {
-        const double r = (double)s_m[j] - pf.B * (1.0 - exp(-beta * (double)s_z[j]));
-        S = fma(r, r, S);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
-    if (threadIdx.x == 0) {
-        out->beta_b[ch] = (float)beta;
-        out->b_inf[ch] = (float)pf.B;
-        out->residual[ch] = (float)S;
+    if (t == 0) {
+        const float B = B32(beta, s_z, s_m, n, bmax);
+        out->beta_b[ch] = beta;
+        out->b_inf[ch] = B;
+        out->residual[ch] = S32(beta, B, s_z, s_m, n);
     }
 }
 
@@ -492,27 +550,37 @@ extern "C" splash_status splash_backscatter_estimate(splash_ctx *ctx, const floa
     const int64_t N = (int64_t)h * w;
     if (N > ((int64_t)1 << 24)) return fail(SPLASH_ERR_INVALID_ARG, "resized image above 2^24 pixels");
     cudaStream_t s = (cudaStream_t)stream;
-    // scratch: counters | keys [N] | clusters [N] | kept list [N] | resized [4N] (when not given)
+    // scratch: counters | keys [N] | clusters [N] | kept list [N] | partition keys, indices [N] |
+    // per-block cluster counts | resized [4N] (when not given)
+    const int nblk = (int)((N + kPartTile - 1) / kPartTile);
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t off_key = up(sizeof(BsCounters)), off_cl = off_key + up(4 * N), off_list = off_cl + up(N),
-                 off_res = off_list + up(4 * N), total = off_res + (resized ? 0 : up(16 * N));
+                 off_sk = off_list + up(4 * N), off_si = off_sk + up(4 * N), off_blk = off_si + up(4 * N),
+                 off_res = off_blk + up(4 * (size_t)nblk * (o.edges - 1)), total = off_res + (resized ? 0 : up(16 * N));
     ENSURE(ctx->bs_scratch, total);
     char *base = ctx->bs_scratch.as<char>();
     BsCounters *cnt = reinterpret_cast<BsCounters *>(base);
     uint32_t *key = reinterpret_cast<uint32_t *>(base + off_key);
     uint8_t *cl = reinterpret_cast<uint8_t *>(base + off_cl);
     uint32_t *list = reinterpret_cast<uint32_t *>(base + off_list);
+    uint32_t *seg_key = reinterpret_cast<uint32_t *>(base + off_sk);
+    uint32_t *seg_idx = reinterpret_cast<uint32_t *>(base + off_si);
+    uint32_t *blk = reinterpret_cast<uint32_t *>(base + off_blk);
     float *res = resized ? resized : reinterpret_cast<float *>(base + off_res);
+    const unsigned blocks = (unsigned)((N + 255) / 256);
+    {
+        Stage t(ctx->prof, SPLASH_STAGE_BS_RESIZE, s);
+        SPLASH_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(BsCounters), s));
+        k_bs_resize<<<blocks, 256, 0, s>>>(image, depth, width, height, w, h, res, key, cnt);
+    }
     {
         Stage t(ctx->prof, SPLASH_STAGE_BACKSCATTER, s);
-        SPLASH_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(BsCounters), s));
-        const unsigned blocks = (unsigned)((N + 255) / 256);
-        k_bs_resize<<<blocks, 256, 0, s>>>(image, depth, width, height, w, h, res, key, cnt);
-        k_bs_cluster<<<blocks, 256, 0, s>>>(res + 3 * N, N, o.edges, cnt, cl, dark);
-        k_bs_select<<<o.edges - 1, kSelThreads, 0, s>>>(key, cl, N, o.p_dark, cnt, list, dark);
-        k_bs_minima<<<1, 1024, 0, s>>>(res, N, w, h, o.intervals, cnt, list, result);
-        k_bs_fit<<<3, kGrid, 0, s>>>(result, o.b_max, o.beta_max);
-        count_launch(5);
+        k_bs_cluster<<<nblk, kPartThreads, 0, s>>>(res + 3 * N, N, o.edges, cnt, cl, blk, dark);
+        k_bs_offsets<<<1, 1024, 0, s>>>(nblk, o.edges, cnt, blk);
+        k_bs_scatter<<<nblk, kPartThreads, 0, s>>>(key, cl, N, o.edges, blk, seg_key, seg_idx);
+        k_bs_select<<<o.edges - 1, kSelThreads, 0, s>>>(seg_key, seg_idx, o.p_dark, cnt, list, dark);
+        k_bs_fit<<<3, kGrid, 0, s>>>(res, N, w, h, o.intervals, cnt, list, result, o.b_max, o.beta_max);
+        count_launch(6);
     }
     SPLASH_CUDA_TRY(cudaGetLastError());
     return SPLASH_OK;

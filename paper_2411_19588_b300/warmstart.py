@@ -20,6 +20,7 @@ import time
 import numpy as np
 import torch
 
+from . import backscatter as BSC
 from . import mlp as M
 from . import render as R
 from . import scenes
@@ -121,9 +122,14 @@ def log_error(pred, truth) -> float:
 class Fit:
     """The plain fit: forward, L1 + lam (1 - SSIM), fused backward + Adam on
     every Gaussian and medium parameter (medium clamped at 0), one view per
-    iteration in a fixed shuffled order."""
+    iteration in a fixed shuffled order. With lambda_est > 0 the loss also
+    carries Eq. 9's lambda_est L_best term: every estimate_every iterations
+    (and at the first) the backscatter estimate (Alg. 1/2) is recomputed
+    from the iteration's target image and the depth just rendered at that
+    view, and the prior's gradient joins the medium step."""
 
-    def __init__(self, renderer: R.Renderer, params: dict, medium, cams, targets, lam: float = 0.2, lr=None):
+    def __init__(self, renderer: R.Renderer, params: dict, medium, cams, targets, lam: float = 0.2, lr=None,
+                 lambda_est: float = 0.0, estimate_every: int = 500):
         self.r = renderer
         self.params = {k: (v.clone() if isinstance(v, torch.Tensor) else v) for k, v in params.items()}
         self.medium = torch.as_tensor(np.asarray(medium, np.float32)).cuda().contiguous()
@@ -141,14 +147,24 @@ class Fit:
         self.depth01 = torch.empty((H, W), device="cuda")
         self.it = 0
         self.order = np.random.default_rng(0).permutation(len(cams))
+        self.lambda_est, self.estimate_every = float(lambda_est), int(estimate_every)
+        self.estimate = BSC.new_result() if self.lambda_est > 0 else None
+        self.estimates_done = 0
 
     def step(self):
         k = int(self.order[self.it % len(self.cams)])
         cam = self.cams[k]
         self.r.forward(self.st, self.params, self.medium, cam, self.image, self.depth, self.depth01)
+        prior = None
+        if self.estimate is not None:
+            if self.it % self.estimate_every == 0:
+                BSC.estimate(self.r, self.targets[k], self.depth, result=self.estimate)
+                self.estimates_done += 1
+            prior = BSC.prior_of(self.estimate)
         loss, gimg = self.r.loss(self.st, self.image, self.targets[k], self.lam)
         self.it += 1
-        self.r.backward_adam(self.st, self.params, self.medium, cam, gimg, self.m, self.v, self.lr, self.it)
+        self.r.backward_adam(self.st, self.params, self.medium, cam, gimg, self.m, self.v, self.lr, self.it,
+                             prior=prior, lambda_est=self.lambda_est)
         return loss
 
     def psnr(self, views) -> float:

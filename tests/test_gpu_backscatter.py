@@ -65,9 +65,26 @@ def _check(gpu, resized, dark, ora, unique=True, label=""):
         # the GPU minimum is no worse than the oracle's (float32 parameters)
         assert BS.residual(gB, gbeta, oz, ov) <= S * (1 + 1e-5) + 1e-11, f"{label}: channel {k} residual"
         assert gS == pytest.approx(S, rel=1e-4, abs=1e-11)
-        if unique:
+        if unique and _well_determined(oz, ov, beta, S):
             assert gbeta == pytest.approx(beta, rel=2e-5, abs=1e-6), f"{label}: beta of channel {k}"
             assert gB == pytest.approx(B, rel=2e-5, abs=1e-6), f"{label}: B_inf of channel {k}"
+
+
+def _profile(z, m, beta):
+    """Residual with the best B in [0, 1] for this beta (FP64)."""
+    f = 1.0 - np.exp(-beta * z)
+    ff = f @ f
+    B = min(1.0, max(0.0, (m @ f) / ff)) if ff > 0 else 0.0
+    return BS.residual(B, beta, z, m)
+
+
+def _well_determined(z, m, beta, S):
+    """The parameters are compared only where the residual pins them: moving
+    beta by 0.1% (inside the box) must raise the profiled residual by more
+    than FP32 can resolve (1e-5 relative); otherwise both answers are minima
+    to FP32 resolution and the residual comparison above is the check."""
+    rises = [_profile(z, m, b) - S for b in (beta * 0.999, beta * 1.001) if 0.0 <= b <= 5.0]
+    return len(rises) == 2 and min(rises) > 1e-5 * S + 1e-12
 
 
 @pytest.mark.parametrize("W,H,seed", [(1920, 1280, 11), (1280, 854, 12)])
@@ -171,3 +188,33 @@ def test_fused_adam_applies_the_prior(renderer):
     np.testing.assert_allclose(d[:3], 0.0, atol=1e-7)
     np.testing.assert_allclose(d[3:], 0.1 * sign, atol=1e-6 + 1e-6 * np.abs(grads[0][3:]).max())
     assert sign[1] == 0.0
+
+
+def test_fit_re_estimates_on_schedule_and_tracks_the_water(renderer):
+    """The fit with L_best re-estimates at iterations 0, 5, 10 (estimate_every
+    = 5) from the iteration's target and the depth it just rendered; in
+    between the prior stays fixed. (How close the estimate comes to the true
+    water depends on the scene having unlit surfaces: the patch scenes have
+    none, so only the bounds are checked here; the shadowed water views
+    above check the recovery.)"""
+    from paper_2411_19588_b300 import scenes, warmstart
+    g, med, _ = scenes.patch_scene(60_000, 22, (2.0, 15.0), 480, 320, 450.0)
+    cams = scenes.arc_cameras(20, 22, width=480, height=320, fx=450.0)
+    gt = R.params_to_device(g)
+    med_gt = torch.tensor(med.as_array(), device="cuda")
+    tgt = [renderer.render(gt, med_gt, c)[0].clone() for c in cams]
+    fit = warmstart.Fit(renderer, gt, warmstart.DEFAULT_MEDIUM, cams, tgt, lambda_est=0.1, estimate_every=5)
+    priors = []
+    for _ in range(12):
+        fit.step()
+        priors.append(GB.prior_of(fit.estimate).cpu().numpy().copy())
+    renderer.sync_status()
+    assert fit.estimates_done == 3
+    for i in (1, 2, 3, 4, 6, 7, 8, 9, 11):
+        assert np.array_equal(priors[i], priors[i - 1 if i not in (5, 10) else i])
+    assert not np.array_equal(priors[4], priors[5]) and not np.array_equal(priors[9], priors[10])
+    est = GB.read(fit.estimate)
+    print({"beta_b": est["beta_b"].tolist(), "b_inf": est["b_inf"].tolist(), "true_beta_b": med.beta_b.tolist(),
+           "true_b_inf": med.b_inf.tolist()})
+    assert np.all((est["b_inf"] >= 0) & (est["b_inf"] <= 1)) and np.all((est["beta_b"] >= 0) & (est["beta_b"] <= 5))
+    assert est["n_dark"] > 0 and min(est["n_points"]) > 0
