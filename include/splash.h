@@ -455,6 +455,19 @@ splash_status splash_backscatter_estimate(splash_ctx *ctx, const float *image, c
 splash_status splash_backscatter_prior(const float *medium, const float *prior, float lambda_est, float *grad_medium,
                                        float *loss, void *stream);
 
+/* ---- Water removal (the application of Sec. I / Sec. V) -------------------
+ * The clean render of a scene, its colour with the water taken away, is
+ * splash_render_forward with a zero medium: Eq. 5 with beta_D = beta_B =
+ * B_inf = 0 is the plain composite of Eq. 1. splash_restore removes the water
+ * from an image instead, given a depth map (e.g. the Eq. 6 depth of the
+ * reconstructed scene) and the medium: per pixel and channel,
+ *   out = max(I - B_inf (1 - exp(-beta_B z)), 0) exp(beta_D z),
+ * the inverse of Eq. 5 with the direct signal clipped at 0. image, out: device
+ * [3,H,W] FP32 (out may equal image); depth: device [H,W]; medium: device
+ * [9] (beta_D, beta_B, B_inf). Asynchronous on `stream`. */
+splash_status splash_restore(const float *image, const float *depth, const float *medium, int32_t width,
+                             int32_t height, float *out, void *stream);
+
 /* Synchronise `stream` and report any error a kernel recorded since the last check. */
 splash_status splash_sync_status(splash_ctx *ctx, void *stream);
 

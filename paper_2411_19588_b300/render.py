@@ -141,6 +141,25 @@ class Renderer:
         st = self.state()
         return self.forward(st, params, medium, cam)
 
+    def render_clean(self, params: dict, cam: scenes.Camera):
+        """The scene without water: Eq. 5 with beta_D = beta_B = B_inf = 0,
+        i.e. the plain composite of Eq. 1. Returns (image, depth, depth01)."""
+        return self.render(params, torch.zeros(9, device="cuda"), cam)
+
+    def restore(self, image: torch.Tensor, depth: torch.Tensor, medium: torch.Tensor, out=None) -> torch.Tensor:
+        """Water removed from `image` [3,H,W] given a depth map [H,W] and the
+        medium [9]: max(I - B_inf (1 - e^{-beta_B z}), 0) e^{beta_D z}."""
+        _check_tensor(image, "image")
+        H, W = image.shape[1:]
+        _check_tensor(depth, "depth", (H, W))
+        _check_tensor(medium, "medium", (9,))
+        out = torch.empty_like(image) if out is None else out
+        _check_tensor(out, "out", (3, H, W))
+        rc = _abi.lib().splash_restore(image.data_ptr(), depth.data_ptr(), medium.data_ptr(), int(W), int(H),
+                                       out.data_ptr(), _stream())
+        _abi.check(rc, "splash_restore")
+        return out
+
     def backward(self, st: State, params: dict, medium: torch.Tensor, cam: scenes.Camera, dL_dimage,
                  dL_ddepth=None, dL_ddepth01=None, grads: dict | None = None) -> dict:
         H, W = cam.height, cam.width
