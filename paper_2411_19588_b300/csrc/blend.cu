@@ -37,6 +37,15 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
+// 1/x for x in [0.01, 1] (x = 1 - alpha with alpha <= 0.99): the hardware
+// approximation, relative error below 2^-22
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // qs = A dx^2 + B dx dy + C dy^2 with the dy terms precomputed; used by both
 // passes so that they take identical decisions
 __device__ __forceinline__ float quad(float dx, float A, float Bdy, float Cdy2) { return fmaf(dx, fmaf(A, dx, Bdy), Cdy2); }
@@ -230,9 +239,13 @@ __device__ __forceinline__ int reduce10_field(int lane)
     return nreal > 0 ? base : -1;
 }
 
-// adjoint of one pixel at one Gaussian; returns false if it does not contribute
-__device__ __forceinline__ bool pix_grad(PixB &p, int j, float dx, float dy, float A, float B, float C, float Bdy,
-                                         float Cdy2, float lo, float ctr, float ctg, float ctb, float d, float *acc)
+// adjoint of one pixel at one Gaussian; returns false if it does not contribute.
+// The exponent's gradient gqs enters the centre and conic gradients only
+// through its moments: acc[5] = sum gqs, acc[0] = sum gqs dx, acc[2] = sum
+// gqs dx^2 over the thread's pixels (one row, so dy is shared); the dy
+// moments and the conic coefficients are applied once per Gaussian.
+__device__ __forceinline__ bool pix_grad(PixB &p, int j, float dx, float A, float Bdy, float Cdy2, float lo, float ctr,
+                                         float ctg, float ctb, float d, float *acc)
 {
     if (j >= p.last) return false;
     const float qs = quad(dx, A, Bdy, Cdy2);
@@ -240,23 +253,21 @@ __device__ __forceinline__ bool pix_grad(PixB &p, int j, float dx, float dy, flo
     const float araw = ex2_approx(qs + lo);
     const float alpha = fminf(kAlphaMax, araw);
     if (alpha < kAlphaMin) return false;
-    const float inv = __frcp_rn(1.f - alpha);
+    const float inv = rcp_approx(1.f - alpha);
     const float Tj = p.T * inv;  // transmittance in front of this Gaussian
     const float w = alpha * Tj;
     const float u = fmaf(p.G0, ctr, fmaf(p.G1, ctg, fmaf(p.G2, ctb, fmaf(p.gD, d, p.gA))));
     // dL/dalpha = T_j u - S / (1 - alpha)
     const float galpha = fmaf(Tj, u, -p.S * inv);
     const float gqs = araw < kAlphaMax ? galpha * alpha * kLn2 : 0.f;
-    acc[0] += gqs * -fmaf(2.f * A, dx, B * dy);
-    acc[1] += gqs * -fmaf(B, dx, 2.f * C * dy);
-    acc[2] += gqs * dx * dx;
-    acc[3] += gqs * dx * dy;
-    acc[4] += gqs * dy * dy;
+    const float gx = gqs * dx;
+    acc[0] += gx;
+    acc[2] = fmaf(gx, dx, acc[2]);
     acc[5] += gqs;
-    acc[6] += p.gD * w;
-    acc[7] += p.G0 * w;
-    acc[8] += p.G1 * w;
-    acc[9] += p.G2 * w;
+    acc[6] = fmaf(p.gD, w, acc[6]);
+    acc[7] = fmaf(p.G0, w, acc[7]);
+    acc[8] = fmaf(p.G1, w, acc[8]);
+    acc[9] = fmaf(p.G2, w, acc[9]);
     p.S = fmaf(w, u, p.S);
     p.T = Tj;
     return true;
@@ -389,8 +400,12 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
                 bool any = false;
 #pragma unroll
                 for (int q = 0; q < PX; q++)
-                    any |= pix_grad(P[q], j, pxl[q] - a.x, dy, a.z, a.w, c.x, Bdy, Cdy2, c.y, c.z, c.w, e.x, e.y, acc);
+                    any |= pix_grad(P[q], j, pxl[q] - a.x, a.z, Bdy, Cdy2, c.y, c.z, c.w, e.x, e.y, acc);
                 if (__any_sync(0xffffffffu, any)) {
+                    // moments in y from the row's dy: sum gqs dy, sum gqs dx dy, sum gqs dy^2
+                    acc[1] = acc[5] * dy;
+                    acc[3] = acc[0] * dy;
+                    acc[4] = acc[5] * (dy * dy);
                     const float r = warp_reduce10(acc, lane);
                     if (my_field >= 0) atomicAdd(&s_g[my_field][k], r);
                 }
@@ -404,8 +419,12 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
 #pragma unroll
             for (int f = 0; f < 10; f++) nz |= g[f] != 0.f;
             if (nz) {
+                // centre gradient from the moments: dqs/dx = 2A dx + B dy, dqs/dy = B dx + 2C dy
+                const float A = s0[sl].z, B = s0[sl].w, C = s1[sl].x;
+                const float gmx = -fmaf(2.f * A, g[0], B * g[1]);
+                const float gmy = -fmaf(B, g[0], 2.f * C * g[1]);
                 GAcc *dst = v.gacc + s_id[sl];
-                atomicAdd(&dst->a0, make_float4(g[0], g[1], g[2], g[3]));
+                atomicAdd(&dst->a0, make_float4(gmx, gmy, g[2], g[3]));
                 atomicAdd(&dst->a1, make_float4(g[4], g[5], g[6], 0.f));
                 atomicAdd(&dst->a2, make_float4(g[7], g[8], g[9], 0.f));
             }
