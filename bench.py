@@ -38,7 +38,8 @@ FLOP_PER_PAIR_FWD = 18
 FLOP_PER_PAIR_BWD = 50
 # DRAM bytes (read + write) of one launch at the default workload (1.5M Gaussians, 1920x1280,
 # 16x16 tiles), from an ncu capture of the current kernel; used for the roofline's `traffic`
-KERNEL_DRAM_BYTES = {"blend_bwd": 103.13e6}
+# (empty while no capture of the current kernel exists)
+KERNEL_DRAM_BYTES = {}
 SM_COUNT_FALLBACK = 148
 
 
@@ -339,23 +340,48 @@ def run_ours(args, world, rank, local):
     last /= args.steps
     n_keys = r.info(st)["n_keys"]
 
-    # --- end to end through the public API with host buffers
+    # --- end to end through the public API with host buffers: every step's target comes from
+    # pinned host memory (copied on a side stream one step ahead, into one of two device
+    # buffers) and every step's loss is read back to the host (one step behind)
     e2e = None
     if not args.no_e2e:
         nb = min(8, nv)
         host_t = [targets[view_of(args.warmup + i)].cpu().pin_memory() for i in range(nb)]
-        host_loss = torch.empty(1, dtype=torch.float32).pin_memory()
-        dev_t = torch.empty_like(targets[0])
+        host_loss = torch.empty(args.steps, dtype=torch.float32).pin_memory()
+        dev_t = [torch.empty_like(targets[0]) for _ in range(2)]
+        copy_s = torch.cuda.Stream()
+        ready = [torch.cuda.Event() for _ in range(2)]
+        freed = [torch.cuda.Event() for _ in range(2)]
+        got = [torch.cuda.Event() for _ in range(args.steps)]
+        losses = []
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        with torch.cuda.stream(copy_s):
+            dev_t[0].copy_(host_t[0], non_blocking=True)
+            ready[0].record(copy_s)
         for i in range(args.steps):
-            dev_t.copy_(host_t[i % nb], non_blocking=True)
-            loss = step(args.warmup + i, target=dev_t)
-            host_loss.copy_(loss, non_blocking=True)
-            torch.cuda.current_stream().synchronize()
+            b = i & 1
+            if i + 1 < args.steps:  # prefetch the next target once step i-1 is done with its buffer
+                with torch.cuda.stream(copy_s):
+                    if i >= 1:
+                        copy_s.wait_event(freed[1 - b])
+                    dev_t[1 - b].copy_(host_t[(i + 1) % nb], non_blocking=True)
+                    ready[1 - b].record(copy_s)
+            stream.wait_event(ready[b])
+            loss = step(args.warmup + i, target=dev_t[b])
+            freed[b].record(stream)
+            host_loss[i:i + 1].copy_(loss, non_blocking=True)
+            got[i].record(stream)
+            if i >= 1:
+                got[i - 1].synchronize()
+                losses.append(float(host_loss[i - 1]))
+        got[args.steps - 1].synchronize()
+        losses.append(float(host_loss[args.steps - 1]))
         e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
-        e2e = {"value": round(world / e2e_s, 3), "unit": "iters/s", "h2d_bytes_per_step": int(dev_t.numel() * 4),
-               "d2h_bytes_per_step": 4}
+        assert all(math.isfinite(x) for x in losses)
+        e2e = {"value": round(world / e2e_s, 3), "unit": "iters/s", "h2d_bytes_per_step": int(dev_t[0].numel() * 4),
+               "d2h_bytes_per_step": 4, "overlap": "target of step i+1 copied on a side stream during step i; "
+                                                   "loss of step i read on the host during step i+1"}
 
     # --- roofline of the dominant kernel
     peaks, peak_src = measured_peaks()
