@@ -114,19 +114,20 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
         k[j] = ok ? kin[idx] : 0xffffffffu;  // past the end: largest digit, ranked last
         v[j] = ok ? (vin ? vin[idx] : (uint32_t)idx) : 0u;
     }
-    // stable rank within the warp: lanes with equal digits via match.any
+    // stable rank within the warp: lanes with equal digits, from one ballot per digit bit
     uint32_t *wh = s_whist[warp];
 #pragma unroll
     for (int j = 0; j < kSortItems; j++) {
         const uint32_t d = (k[j] >> shift) & mask;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const int leader = 31 - __clz(peers);
-        uint32_t old = 0;
-        if (lane == leader) {
-            old = wh[d];
-            wh[d] = old + __popc(peers);
+        uint32_t peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b < kRadixBits; b++) {
+            const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? bal : ~bal;
         }
-        old = __shfl_sync(0xffffffffu, old, leader);
+        const uint32_t old = wh[d];  // every peer reads the same word (a broadcast)
+        __syncwarp();
+        if (lane == 31 - __clz(peers)) wh[d] = old + __popc(peers);
         rank[j] = old + __popc(peers & lt);
         __syncwarp();
     }
