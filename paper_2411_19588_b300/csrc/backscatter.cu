@@ -51,6 +51,18 @@ struct BsCounters {      // cleared by one memset per estimate
 __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
 __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
 
+// Lanes of the (full) warp whose `bits`-bit value equals this lane's: one
+// ballot per bit (cheaper than match.any on this GPU).
+__device__ __forceinline__ unsigned peers_of(uint32_t v, int bits)
+{
+    unsigned peers = 0xffffffffu;
+    for (int b = 0; b < bits; b++) {
+        const unsigned bal = __ballot_sync(0xffffffffu, (v >> b) & 1u);
+        peers &= ((v >> b) & 1u) ? bal : ~bal;
+    }
+    return peers;
+}
+
 __device__ __forceinline__ uint32_t block_max_u32(uint32_t v, uint32_t *s_red)
 {
     v = __reduce_max_sync(0xffffffffu, v);
@@ -150,16 +162,17 @@ __global__ void __launch_bounds__(kPartThreads) k_bs_cluster(const float *__rest
 #pragma unroll
     for (int r = 0; r < kPartItems; r++) {
         const int64_t i = base + r * kPartThreads + threadIdx.x;
+        int c = kMaxClusters;  // past the end: a cluster no pixel has
         if (i < N) {
             const float zi = z[i];
-            int c = 0;
+            c = 0;
             for (int k = 0; k < E - 2; k++) c += zi >= s_t[k];
             cl[i] = (uint8_t)c;
             if (dark) dark[i] = 0;
-            // one shared atomic per distinct cluster in the warp
-            const unsigned peers = __match_any_sync(__activemask(), c);
-            if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&s_cnt[c], (uint32_t)__popc(peers));
         }
+        // one shared atomic per distinct cluster in the warp
+        const unsigned peers = peers_of((uint32_t)c, 7);
+        if (c < kMaxClusters && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&s_cnt[c], (uint32_t)__popc(peers));
     }
     __syncthreads();
     if ((int)threadIdx.x < E - 1) {
@@ -213,7 +226,7 @@ __global__ void __launch_bounds__(kPartThreads) k_bs_scatter(const uint32_t *__r
         const int64_t i = base + r * kPartThreads + threadIdx.x;
         const bool ok = i < N;
         int c = ok ? cl[i] : kMaxClusters;  // past the end: a cluster no pixel has
-        const unsigned peers = __match_any_sync(0xffffffffu, c);
+        const unsigned peers = peers_of((uint32_t)c, 7);
         const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
         if (ok && lane == __ffs(peers) - 1) s_wc[wid][c] = __popc(peers);
         __syncthreads();
@@ -292,7 +305,7 @@ __global__ void __launch_bounds__(kSelThreads) k_bs_select(const uint32_t *__res
             const bool in = j < n && (u & pmask) == prefix;
             const uint32_t d = in ? (u >> shift) & dmask : 0xffffffffu;
             // one shared atomic per distinct digit in the warp (neighbouring keys share digits)
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const unsigned peers = peers_of(in ? d : 0x800u, 12);
             if (in && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[d], (uint32_t)__popc(peers));
         }
         __syncthreads();
