@@ -240,10 +240,12 @@ __device__ __forceinline__ int reduce10_field(int lane)
 }
 
 // adjoint of one pixel at one Gaussian; returns false if it does not contribute.
+// DG: the loss has a depth term (gD, gA non-zero); without it those terms vanish.
 // The exponent's gradient gqs enters the centre and conic gradients only
 // through its moments: acc[5] = sum gqs, acc[0] = sum gqs dx, acc[2] = sum
 // gqs dx^2 over the thread's pixels (one row, so dy is shared); the dy
 // moments and the conic coefficients are applied once per Gaussian.
+template <bool DG>
 __device__ __forceinline__ bool pix_grad(PixB &p, int j, float dx, float A, float Bdy, float Cdy2, float lo, float ctr,
                                          float ctg, float ctb, float d, float *acc)
 {
@@ -256,7 +258,8 @@ __device__ __forceinline__ bool pix_grad(PixB &p, int j, float dx, float A, floa
     const float inv = rcp_approx(1.f - alpha);
     const float Tj = p.T * inv;  // transmittance in front of this Gaussian
     const float w = alpha * Tj;
-    const float u = fmaf(p.G0, ctr, fmaf(p.G1, ctg, fmaf(p.G2, ctb, fmaf(p.gD, d, p.gA))));
+    const float u = DG ? fmaf(p.G0, ctr, fmaf(p.G1, ctg, fmaf(p.G2, ctb, fmaf(p.gD, d, p.gA))))
+                       : fmaf(p.G0, ctr, fmaf(p.G1, ctg, p.G2 * ctb));
     // dL/dalpha = T_j u - S / (1 - alpha)
     const float galpha = fmaf(Tj, u, -p.S * inv);
     const float gqs = araw < kAlphaMax ? galpha * alpha * kLn2 : 0.f;
@@ -264,7 +267,7 @@ __device__ __forceinline__ bool pix_grad(PixB &p, int j, float dx, float A, floa
     acc[0] += gx;
     acc[2] = fmaf(gx, dx, acc[2]);
     acc[5] += gqs;
-    acc[6] = fmaf(p.gD, w, acc[6]);
+    if (DG) acc[6] = fmaf(p.gD, w, acc[6]);
     acc[7] = fmaf(p.G0, w, acc[7]);
     acc[8] = fmaf(p.G1, w, acc[8]);
     acc[9] = fmaf(p.G2, w, acc[9]);
@@ -273,7 +276,7 @@ __device__ __forceinline__ bool pix_grad(PixB &p, int j, float dx, float A, floa
     return true;
 }
 
-template <int TW, int TH, int NB>
+template <int TW, int TH, int NB, bool DG>
 __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, const float *__restrict__ medium)
 {
     constexpr int PX = kPxBwd;
@@ -326,15 +329,17 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
         p.G0 = v.dL_dimage[pix];
         p.G1 = v.dL_dimage[HWimg + pix];
         p.G2 = v.dL_dimage[2 * HWimg + pix];
-        const float A = v.acc_alpha[pix], z = v.zhat[pix];
-        float gz = v.dL_ddepth ? v.dL_ddepth[pix] : 0.f;
-        if (v.dL_ddepth01) {
-            const float e = expf(-0.1f * z);
-            gz += v.dL_ddepth01[pix] * 0.2f * e / ((1.f + e) * (1.f + e));
-        }
-        if (A > 0.f) {
-            p.gD = gz / A;  // z = D / A
-            p.gA = -gz * z / A;
+        if (DG) {
+            const float A = v.acc_alpha[pix], z = v.zhat[pix];
+            float gz = v.dL_ddepth ? v.dL_ddepth[pix] : 0.f;
+            if (v.dL_ddepth01) {
+                const float e = expf(-0.1f * z);
+                gz += v.dL_ddepth01[pix] * 0.2f * e / ((1.f + e) * (1.f + e));
+            }
+            if (A > 0.f) {
+                p.gD = gz / A;  // z = D / A
+                p.gA = -gz * z / A;
+            }
         }
         const float Gc[3] = {p.G0, p.G1, p.G2};
         float S = 0.f;
@@ -400,7 +405,7 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
                 bool any = false;
 #pragma unroll
                 for (int q = 0; q < PX; q++)
-                    any |= pix_grad(P[q], j, pxl[q] - a.x, a.z, Bdy, Cdy2, c.y, c.z, c.w, e.x, e.y, acc);
+                    any |= pix_grad<DG>(P[q], j, pxl[q] - a.x, a.z, Bdy, Cdy2, c.y, c.z, c.w, e.x, e.y, acc);
                 if (__any_sync(0xffffffffu, any)) {
                     // moments in y from the row's dy: sum gqs dy, sum gqs dx dy, sum gqs dy^2
                     acc[1] = acc[5] * dy;
@@ -441,10 +446,12 @@ __global__ void __launch_bounds__(fwd_threads<TW, TH>(), 1280 / fwd_threads<TW, 
     blend_tile_fwd<TW, TH, NB>(v, blockIdx.x, medium);
 }
 
-template <int TW, int TH, int NB>
-__global__ void __launch_bounds__(bwd_threads<TW, TH>(), 768 / bwd_threads<TW, TH>()) k_blend_bwd(BlendView v, const float *__restrict__ medium)
+// occupancy target: 14 blocks of 64 threads per SM without the depth terms
+// (72 registers), 12 with them (80)
+template <int TW, int TH, int NB, bool DG>
+__global__ void __launch_bounds__(bwd_threads<TW, TH>(), (DG ? 768 : 896) / bwd_threads<TW, TH>()) k_blend_bwd(BlendView v, const float *__restrict__ medium)
 {
-    blend_tile_bwd<TW, TH, NB>(v, blockIdx.x, medium);
+    blend_tile_bwd<TW, TH, NB, DG>(v, blockIdx.x, medium);
 }
 
 // Persistent: one wave of CTAs; each takes the next (view, tile) item from the
@@ -482,7 +489,7 @@ __global__ void __launch_bounds__(bwd_threads<TW, TH>(), 768 / bwd_threads<TW, T
     int it;
     while (next_item(counter, n_items, it)) {
         const uint32_t code = items[it];
-        blend_tile_bwd<TW, TH, NB>(views[code >> 24], (int)(code & 0xffffffu), medium);
+        blend_tile_bwd<TW, TH, NB, false>(views[code >> 24], (int)(code & 0xffffffu), medium);  // no depth loss in batches
     }
 }
 
@@ -518,7 +525,10 @@ template <int TW, int TH, int NB>
 struct BwdPlain {
     static void run(const BlendView &v, const float *medium, cudaStream_t s)
     {
-        k_blend_bwd<TW, TH, NB><<<v.tg.tx * v.tg.ty, bwd_threads<TW, TH>(), 0, s>>>(v, medium);
+        if (v.dL_ddepth || v.dL_ddepth01)
+            k_blend_bwd<TW, TH, NB, true><<<v.tg.tx * v.tg.ty, bwd_threads<TW, TH>(), 0, s>>>(v, medium);
+        else
+            k_blend_bwd<TW, TH, NB, false><<<v.tg.tx * v.tg.ty, bwd_threads<TW, TH>(), 0, s>>>(v, medium);
         count_launch();
     }
 };
