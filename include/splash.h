@@ -388,6 +388,29 @@ splash_status splash_mlp_step(splash_mlp *mlp, const uint16_t *bank, int64_t n_r
                               const float *targets, int32_t batch, const splash_mlp_adam *adam, float *loss, splash_mlp_params *grads,
                               void *stream);
 
+/* ---- The pixel form of the water (Eq. 5 as printed, with the Eq. 6 depth) ----
+ * C = J exp(-beta_D z) + B_inf (1 - exp(-beta_B z)) per pixel and channel, with
+ * J = sum_i c_i alpha_i T_i the plain composite and z the expected depth (z_far
+ * where nothing composites); the default calls above instead attenuate every
+ * Gaussian at its own depth and add the backscatter of every water segment.
+ * splash_render_forward_pixel takes the same arguments as
+ * splash_render_forward: it renders J and z (the render with a zero medium)
+ * and applies Eq. 5; depth and depth01 are the same Eq. 6 outputs. The state
+ * keeps J for the backward. splash_render_backward_pixel is its adjoint with
+ * the arguments of splash_render_backward: dL/dJ = G exp(-beta_D z), dL/dz
+ * gains sum_ch G (B_inf beta_B exp(-beta_B z) - beta_D J exp(-beta_D z)) where
+ * something composites (it reaches every contributing Gaussian through
+ * alpha and d), and grads->medium receives sum over pixels of G (-z J
+ * exp(-beta_D z)), G B_inf z exp(-beta_B z) and G (1 - exp(-beta_B z)).
+ * SPLASH_ERR_STATE if the state's last forward was not the pixel form. */
+splash_status splash_render_forward_pixel(splash_ctx *ctx, splash_state *st, const splash_gaussians *g,
+                                          const float *medium_dev, const splash_camera *cam, float *image, float *depth,
+                                          float *depth01, void *stream);
+splash_status splash_render_backward_pixel(splash_ctx *ctx, splash_state *st, const splash_gaussians *g,
+                                           const float *medium_dev, const splash_camera *cam,
+                                           const float *dL_dimage, const float *dL_ddepth,
+                                           const float *dL_ddepth01, const splash_grads *grads, void *stream);
+
 /* ---- Backscatter estimate and the L_best prior (Sec. IV-B, Eq. 7-9;
  * appendix Alg. 1 "Estimate Backscatter" and Alg. 2) -----------------------
  * splash_backscatter_estimate turns an observed image and the expected depth

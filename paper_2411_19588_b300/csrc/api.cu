@@ -141,6 +141,7 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
     if (!medium || !image) return fail(SPLASH_ERR_INVALID_ARG, "null medium or image");
     cudaStream_t s = (cudaStream_t)stream;
     st->has_forward = false;
+    st->pixel_forward = false;
 
     const int64_t n = g->n;
     TileGeom tg{ctx->opt.tile_w, ctx->opt.tile_h, 0, 0};
@@ -253,10 +254,13 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
     return SPLASH_OK;
 }
 
-splash_status splash_render_backward(splash_ctx *ctx, splash_state *st, const splash_gaussians *g,
-                                     const float *medium, const splash_camera *cam, const float *dL_dimage,
-                                     const float *dL_ddepth, const float *dL_ddepth01, const splash_grads *grads,
-                                     void *stream)
+}  // extern "C"
+
+// C++ linkage: called by the C ABI entry points of this file and of pixel.cu
+splash_status render_backward_impl(splash_ctx *ctx, splash_state *st, const splash_gaussians *g,
+                                   const float *medium, const splash_camera *cam, const float *dL_dimage,
+                                   const float *dL_ddepth, const float *dL_ddepth01, const splash_grads *grads,
+                                   void *stream)
 {
     if (!ctx || !st || st->ctx != ctx) return fail(SPLASH_ERR_INVALID_ARG, "bad context or state");
     splash_status rc;
@@ -297,6 +301,18 @@ splash_status splash_render_backward(splash_ctx *ctx, splash_state *st, const sp
     return SPLASH_OK;
 }
 
+extern "C" {
+
+splash_status splash_render_backward(splash_ctx *ctx, splash_state *st, const splash_gaussians *g,
+                                     const float *medium, const splash_camera *cam, const float *dL_dimage,
+                                     const float *dL_ddepth, const float *dL_ddepth01, const splash_grads *grads,
+                                     void *stream)
+{
+    if (st && st->pixel_forward)
+        return fail(SPLASH_ERR_STATE, "the last forward on this state was the pixel form: use splash_render_backward_pixel");
+    return render_backward_impl(ctx, st, g, medium, cam, dL_dimage, dL_ddepth, dL_ddepth01, grads, stream);
+}
+
 splash_status splash_render_backward_adam(splash_ctx *ctx, splash_state *st, const splash_param_buffers *params,
                                           int64_t n, int32_t sh_degree, const splash_camera *cam,
                                           const float *dL_dimage, const float *dL_ddepth, const float *dL_ddepth01,
@@ -320,6 +336,8 @@ splash_status splash_render_backward_adam(splash_ctx *ctx, splash_state *st, con
     }
     if (!st->has_forward || st->n != n || st->W != cam->width || st->H != cam->height)
         return fail(SPLASH_ERR_STATE, "backward does not match the last forward on this state");
+    if (st->pixel_forward)
+        return fail(SPLASH_ERR_STATE, "the last forward on this state was the pixel form: use splash_render_backward_pixel");
     cudaStream_t s = (cudaStream_t)stream;
     const int ntiles = st->tg.tx * st->tg.ty;
     const int nblocks = preprocess_bwd_blocks(std::max<int64_t>(n, 1));

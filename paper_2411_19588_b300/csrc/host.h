@@ -174,6 +174,7 @@ struct splash_ctx {
     splash_host::Prof prof;
     splash_host::Buf feat_counts;  // featuriser histogram counters (kept zero between calls)
     splash_host::Buf bs_scratch;   // backscatter estimate: counters, keys, clusters, kept list, resized maps
+    splash_host::Buf zero16;       // 16 zeros: the medium of the pixel form's inner render
 };
 
 struct splash_state {
@@ -189,6 +190,9 @@ struct splash_state {
     splash_host::Buf gacc, tile_med, block_med, gmed, red_scratch;
     // loss / standalone sort
     splash_host::Buf loss_scratch, tmp_k, tmp_v;
+    // pixel form of the water (Eq. 5): J, the zero-medium upstream, per-block medium sums
+    splash_host::Buf pixJ, pixG, pixgz, pixmed;
+    bool pixel_forward = false;  // the last forward was splash_render_forward_pixel
     splash_host::Buf small;       // [0] = pair count K, [1..] spare
     uint32_t *h_small = nullptr;  // pinned: K, status
     // what the last forward produced
@@ -201,3 +205,10 @@ struct splash_state {
     const uint32_t *tile_ids = nullptr;  // sorted pairs
     const uint32_t *gauss_ids = nullptr;
 };
+
+// splash_render_backward without its check that the last forward was not the
+// pixel form (the pixel form's own backward runs it on the zero-medium render)
+splash_status render_backward_impl(splash_ctx *ctx, splash_state *st, const splash_gaussians *g,
+                                   const float *medium, const splash_camera *cam, const float *dL_dimage,
+                                   const float *dL_ddepth, const float *dL_ddepth01, const splash_grads *grads,
+                                   void *stream);

@@ -122,7 +122,9 @@ class Renderer:
 
     # -- render
     def forward(self, st: State, params: dict, medium: torch.Tensor, cam: scenes.Camera, image=None, depth=None,
-                depth01=None):
+                depth01=None, pixel: bool = False):
+        """Render (image, depth, depth01). pixel=True: Eq. 5 applied per pixel
+        with the Eq. 6 depth instead of per Gaussian and water segment."""
         _check_tensor(medium, "medium", (9,))
         H, W = cam.height, cam.width
         dev = medium.device
@@ -131,9 +133,10 @@ class Renderer:
         depth01 = torch.empty((H, W), device=dev, dtype=torch.float32) if depth01 is None else depth01
         g = gaussians_struct(params)
         c = camera_struct(cam)
-        rc = _abi.lib().splash_render_forward(self._ctx, st.handle, ctypes.byref(g), medium.data_ptr(), ctypes.byref(c),
-                                              image.data_ptr(), _abi.ptr(depth), _abi.ptr(depth01), _stream())
-        _abi.check(rc, "splash_render_forward")
+        fn = "splash_render_forward_pixel" if pixel else "splash_render_forward"
+        rc = getattr(_abi.lib(), fn)(self._ctx, st.handle, ctypes.byref(g), medium.data_ptr(), ctypes.byref(c),
+                                     image.data_ptr(), _abi.ptr(depth), _abi.ptr(depth01), _stream())
+        _abi.check(rc, fn)
         st.shape = (params["means"].shape[0], H, W)
         return image, depth, depth01
 
@@ -161,7 +164,7 @@ class Renderer:
         return out
 
     def backward(self, st: State, params: dict, medium: torch.Tensor, cam: scenes.Camera, dL_dimage,
-                 dL_ddepth=None, dL_ddepth01=None, grads: dict | None = None) -> dict:
+                 dL_ddepth=None, dL_ddepth01=None, grads: dict | None = None, pixel: bool = False) -> dict:
         H, W = cam.height, cam.width
         _check_tensor(dL_dimage, "dL_dimage", (3, H, W))
         if dL_ddepth is not None:
@@ -175,10 +178,11 @@ class Renderer:
                           for k in PARAM_NAMES + ("medium",)))
         g = gaussians_struct(params)
         c = camera_struct(cam)
-        rc = _abi.lib().splash_render_backward(self._ctx, st.handle, ctypes.byref(g), medium.data_ptr(),
-                                               ctypes.byref(c), dL_dimage.data_ptr(), _abi.ptr(dL_ddepth),
-                                               _abi.ptr(dL_ddepth01), ctypes.byref(gs), _stream())
-        _abi.check(rc, "splash_render_backward")
+        fn = "splash_render_backward_pixel" if pixel else "splash_render_backward"
+        rc = getattr(_abi.lib(), fn)(self._ctx, st.handle, ctypes.byref(g), medium.data_ptr(), ctypes.byref(c),
+                                     dL_dimage.data_ptr(), _abi.ptr(dL_ddepth), _abi.ptr(dL_ddepth01),
+                                     ctypes.byref(gs), _stream())
+        _abi.check(rc, fn)
         return grads
 
     def backward_adam(self, st: State, params: dict, medium: torch.Tensor, cam: scenes.Camera, dL_dimage,
