@@ -68,6 +68,9 @@ def parse_args():
     ap.add_argument("--batch-views", type=int, default=64)
     ap.add_argument("--step", choices=["fused", "unfused"], default="fused",
                     help="fused: backward and Adam in one kernel; unfused: backward, then the multi-group Adam")
+    ap.add_argument("--form", choices=["segment", "pixel"], default="segment",
+                    help="segment: water per Gaussian and water segment (the default step); pixel: Eq. 5 per pixel "
+                         "with the Eq. 6 depth (implies --step unfused)")
     ap.add_argument("--profile-region", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -247,6 +250,9 @@ def run_ours(args, world, rank, local):
     from paper_2411_19588_b300 import render as R
 
     torch.cuda.set_device(local)
+    pixel = args.form == "pixel"  # the pixel form has no fused backward + Adam
+    if pixel:
+        args.step = "unfused"
     tw, th = (int(x) for x in args.tile.split("x"))
     r = R.Renderer(tile=(tw, th))
     params, med, gt, med_gt, cams = build_workload(args.n, rank, args.views)
@@ -256,7 +262,7 @@ def run_ours(args, world, rank, local):
     st_t = r.state()
     targets = []
     for cam in cams:
-        img, _, _ = r.forward(st_t, gt, med_gt, cam)
+        img, _, _ = r.forward(st_t, gt, med_gt, cam, pixel=pixel)
         targets.append(img.clone())
     del gt
     torch.cuda.synchronize()
@@ -280,13 +286,13 @@ def run_ours(args, world, rank, local):
     def step(i, target=None):
         """forward, loss, then the fused backward + Adam (parameters updated in place)"""
         cam = cams[view_of(i)]
-        r.forward(st, params, med, cam, image, depth, depth01)
+        r.forward(st, params, med, cam, image, depth, depth01, pixel=pixel)
         loss, gimg = r.loss(st, image, targets[view_of(i)] if target is None else target, LAMBDA_SSIM)
         step_no[0] += 1
         if grads is None:
             r.backward_adam(st, params, med, cam, gimg, mom, vel, LR, step_no[0])
         else:
-            r.backward(st, params, med, cam, gimg, None, None, grads)
+            r.backward(st, params, med, cam, gimg, None, None, grads, pixel=pixel)
             R.adam_step(groups, step_no[0])
         return loss
 
@@ -324,7 +330,7 @@ def run_ours(args, world, rank, local):
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
     for i in range(args.steps):
-        r.forward(st, params, med, cams[view_of(i)], image, depth, depth01)
+        r.forward(st, params, med, cams[view_of(i)], image, depth, depth01, pixel=pixel)
     f1.record(stream)
     torch.cuda.synchronize()
     fwd_ms = max_over_ranks(f0.elapsed_time(f1) / args.steps, world)
@@ -332,7 +338,7 @@ def run_ours(args, world, rank, local):
     # --- algorithmic work of the blend launches in the timed region (same views)
     walk, last = 0.0, 0.0
     for i in range(args.steps):
-        r.forward(st, params, med, cams[view_of(args.warmup + i)], image, depth, depth01)
+        r.forward(st, params, med, cams[view_of(args.warmup + i)], image, depth, depth01, pixel=pixel)
         walk += float(r.state_array(st, "n_walk").to(torch.int64).sum())
         last += float(r.state_array(st, "n_last").to(torch.int64).sum())
     walk /= args.steps
@@ -435,7 +441,7 @@ def run_ours(args, world, rank, local):
         "data": "synthetic (seeded surface-patch scenes standing in for the paper's underwater captures)",
         "config": {"workload": "train step: 1.5M Gaussians (SH3, 2-15 m), 1920x1280, 100-view arc, "
                                "fwd + L1+0.2(1-SSIM) + bwd + Adam",
-                   "n_gaussians": args.n, "width": W, "height": H, "views": nv, "tile": args.tile, "step": args.step,
+                   "n_gaussians": args.n, "width": W, "height": H, "views": nv, "tile": args.tile, "step": args.step, "form": args.form,
                    "parallelism": f"replicas x{world}",
                    "l2": "working set (params+grads+Adam moments ~1.4 GB) larger than L2; no flush"},
         "fps": round(world * 1000.0 / fwd_ms, 2),
