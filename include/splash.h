@@ -388,6 +388,13 @@ splash_status splash_mlp_step(splash_mlp *mlp, const uint16_t *bank, int64_t n_r
                               const float *targets, int32_t batch, const splash_mlp_adam *adam, float *loss, splash_mlp_params *grads,
                               void *stream);
 
+/* Opacity reset of the training schedule (appendix: every 3,000 iterations):
+ * logits[i] = min(logits[i], logit(max_opacity)) for n opacity logits
+ * (device), and the opacity group's Adam moments adam_m, adam_v (device,
+ * nullable) set to zero. max_opacity in (0, 1); the paper's value is 0.01. */
+splash_status splash_opacity_reset(float *logits, float *adam_m, float *adam_v, int64_t n, float max_opacity,
+                                   void *stream);
+
 /* ---- The pixel form of the water (Eq. 5 as printed, with the Eq. 6 depth) ----
  * C = J exp(-beta_D z) + B_inf (1 - exp(-beta_B z)) per pixel and channel, with
  * J = sum_i c_i alpha_i T_i the plain composite and z the expected depth (z_far

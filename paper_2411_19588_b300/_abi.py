@@ -164,6 +164,8 @@ _SIGS = {
                                     ctypes.c_void_p, ctypes.c_void_p],
     "splash_backscatter_prior": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_void_p],
+    "splash_opacity_reset": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_float,
+                             ctypes.c_void_p],
     "splash_restore": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                        ctypes.c_void_p, ctypes.c_void_p],
     "splash_sort_pairs_u32_noalloc": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,

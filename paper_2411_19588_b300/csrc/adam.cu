@@ -98,3 +98,39 @@ extern "C" splash_status splash_adam_step(const splash_adam_group *groups, int32
     SPLASH_CUDA_TRY(cudaGetLastError());
     return SPLASH_OK;
 }
+
+// Opacity reset of the appendix's schedule (every 3,000 iterations in the
+// paper, as in 3DGS): opacities above max_opacity are set to it (a cap on the
+// logit), and the opacity group's Adam moments restart at zero.
+namespace {
+__global__ void k_opacity_reset(float *__restrict__ logits, float *__restrict__ m, float *__restrict__ v, int64_t n,
+                                float cap)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        logits[i] = fminf(logits[i], cap);
+        if (m) m[i] = 0.f;
+        if (v) v[i] = 0.f;
+    }
+}
+}  // namespace
+
+extern "C" splash_status splash_opacity_reset(float *logits, float *adam_m, float *adam_v, int64_t n, float max_opacity,
+                                              void *stream)
+{
+    using namespace splash;
+    if (n < 0 || (n > 0 && !logits)) {
+        splash_set_error("splash_opacity_reset: null logits or negative n");
+        return SPLASH_ERR_INVALID_ARG;
+    }
+    if (!(max_opacity > 0.f && max_opacity < 1.f)) {
+        splash_set_error("splash_opacity_reset: max_opacity must be in (0, 1)");
+        return SPLASH_ERR_INVALID_ARG;
+    }
+    if (n == 0) return SPLASH_OK;
+    const float cap = (float)log((double)max_opacity / (1.0 - (double)max_opacity));
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 8);
+    k_opacity_reset<<<blocks, 256, 0, (cudaStream_t)stream>>>(logits, adam_m, adam_v, n, cap);
+    count_launch();
+    SPLASH_CUDA_TRY(cudaGetLastError());
+    return SPLASH_OK;
+}

@@ -340,6 +340,19 @@ def kernel_launches() -> int:
     return int(_abi.lib().splash_kernel_launches())
 
 
+def opacity_reset(logits: torch.Tensor, m: torch.Tensor | None = None, v: torch.Tensor | None = None,
+                  max_opacity: float = 0.01):
+    """The schedule's opacity reset: opacities capped at max_opacity, the
+    opacity group's Adam moments (if given) set to zero. In place."""
+    _check_tensor(logits, "logits")
+    for t, name in ((m, "m"), (v, "v")):
+        if t is not None:
+            _check_tensor(t, name, tuple(logits.shape))
+    rc = _abi.lib().splash_opacity_reset(logits.data_ptr(), _abi.ptr(m), _abi.ptr(v), logits.numel(),
+                                         float(max_opacity), _stream())
+    _abi.check(rc, "splash_opacity_reset")
+
+
 def adam_step(groups, step: int, betas=(0.9, 0.999), eps: float = 1e-15):
     """groups: list of dicts {param, grad, m, v, lr, clamp_min (optional)}."""
     if len(groups) > _abi.ADAM_MAX_GROUPS:

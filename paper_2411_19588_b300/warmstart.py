@@ -24,6 +24,7 @@ from . import backscatter as BSC
 from . import mlp as M
 from . import render as R
 from . import scenes
+from . import schedule as SCH
 
 DEFAULT_MEDIUM = [0.1] * 9
 # learning rates of the fit (3DGS values the paper keeps, appendix "Experimental Setup")
@@ -126,10 +127,14 @@ class Fit:
     carries Eq. 9's lambda_est L_best term: every estimate_every iterations
     (and at the first) the backscatter estimate (Alg. 1/2) is recomputed
     from the iteration's target image and the depth just rendered at that
-    view, and the prior's gradient joins the medium step."""
+    view, and the prior's gradient joins the medium step. With schedule=True
+    the appendix's schedule applies: the position learning rate decays
+    (schedule.position_lr) and the opacities are reset every
+    reset_every iterations."""
 
     def __init__(self, renderer: R.Renderer, params: dict, medium, cams, targets, lam: float = 0.2, lr=None,
-                 lambda_est: float = 0.0, estimate_every: int = 500):
+                 lambda_est: float = 0.0, estimate_every: int = 500, schedule: bool = False,
+                 reset_every: int = SCH.OPACITY_RESET_EVERY):
         self.r = renderer
         self.params = {k: (v.clone() if isinstance(v, torch.Tensor) else v) for k, v in params.items()}
         self.medium = torch.as_tensor(np.asarray(medium, np.float32)).cuda().contiguous()
@@ -150,8 +155,15 @@ class Fit:
         self.lambda_est, self.estimate_every = float(lambda_est), int(estimate_every)
         self.estimate = BSC.new_result() if self.lambda_est > 0 else None
         self.estimates_done = 0
+        self.schedule, self.reset_every, self.resets_done = bool(schedule), int(reset_every), 0
 
     def step(self):
+        if self.schedule:
+            self.lr["means"] = SCH.position_lr(self.it)
+            if self.it > 0 and self.it % self.reset_every == 0:
+                R.opacity_reset(self.params["opacity_logits"], self.m["opacity_logits"], self.v["opacity_logits"],
+                                SCH.OPACITY_RESET_VALUE)
+                self.resets_done += 1
         k = int(self.order[self.it % len(self.cams)])
         cam = self.cams[k]
         self.r.forward(self.st, self.params, self.medium, cam, self.image, self.depth, self.depth01)
