@@ -161,6 +161,7 @@ typedef struct {
     float medium_min;
     const float *prior; /* device [6] or NULL: the L_best estimate */
     float lambda_est;   /* weight of L_best (Eq. 9; 0.1 in the paper) */
+    float *densify_stats; /* device [n][2] or NULL: densification statistics, += */
 } splash_adam_config;
 splash_status splash_render_backward_adam(splash_ctx *ctx, splash_state *st, const splash_param_buffers *params,
                                           int64_t n, int32_t sh_degree, const splash_camera *cam,
@@ -387,6 +388,37 @@ splash_status splash_mlp_predict(splash_mlp *mlp, const uint16_t *rows, int32_t 
 splash_status splash_mlp_step(splash_mlp *mlp, const uint16_t *bank, int64_t n_rows, const int32_t *idx,
                               const float *targets, int32_t batch, const splash_mlp_adam *adam, float *loss, splash_mlp_params *grads,
                               void *stream);
+
+/* Densification (appendix: every 100 iterations from 1,500 to 15,000;
+ * gradient threshold 0.0002, minimum opacity 0.1; the 3DGS procedure).
+ * Statistics: with adam->densify_stats set, each fused training step adds,
+ * for every Gaussian in the view, the NDC norm of its screen-space centre
+ * gradient, |(g_x W/2, g_y H/2)|, and 1 (the count) to stats[i][0..1].
+ * splash_densify_plan decides per Gaussian (FP32 decisions): prune if its
+ * opacity logit < logit(min_opacity); otherwise, if stats[i][0] /
+ * max(stats[i][1], 1) >= grad_threshold, split if its largest log-scale >
+ * log(percent_dense * extent), else clone; otherwise keep. It synchronises
+ * `stream` and returns the new count in *n_new (host). The plan is kept in
+ * the context for the next splash_densify_apply with the same n, which
+ * writes the new arrays (caller-allocated for n_new Gaussians; same layouts;
+ * the medium members are ignored): survivors and a clone's original in
+ * place of order with their Adam moments, a clone's copy right after it with
+ * zero moments, a split Gaussian's two samples mu + R diag(exp(log_scales))
+ * noise[i][k] (noise: device [n][2][3] standard normals) with log-scales
+ * lowered by log(1.6) and zero moments. */
+typedef struct {
+    float grad_threshold; /* 0.0002 */
+    float min_opacity;    /* 0.1 */
+    float percent_dense;  /* 0.01 */
+    float extent;         /* scene extent (m) */
+} splash_densify_options;
+splash_status splash_densify_plan(splash_ctx *ctx, const float *log_scales, const float *opacity_logits,
+                                  const float *stats, int64_t n, const splash_densify_options *opt, int64_t *n_new,
+                                  void *stream);
+splash_status splash_densify_apply(splash_ctx *ctx, const splash_param_buffers *params, const splash_param_buffers *m,
+                                   const splash_param_buffers *v, int64_t n, int32_t sh_degree, const float *noise,
+                                   const splash_param_buffers *new_params, const splash_param_buffers *new_m,
+                                   const splash_param_buffers *new_v, int64_t n_new, void *stream);
 
 /* Opacity reset of the training schedule (appendix: every 3,000 iterations):
  * logits[i] = min(logits[i], logit(max_opacity)) for n opacity logits

@@ -49,16 +49,20 @@ def stat_increment(g_proj_xy, width: int, height: int) -> np.ndarray:
 
 
 def classify(log_scales, opacity_logits, stats, threshold=THRESHOLD, min_opacity=MIN_OPACITY, dense=1.0):
-    ls = np.asarray(log_scales, np.float64)
-    p = 1.0 / (1.0 + np.exp(-np.asarray(opacity_logits, np.float64)))
-    st = np.asarray(stats, np.float64)
-    avg = st[:, 0] / np.maximum(st[:, 1], 1.0)
-    big = np.exp(ls.max(axis=1)) > dense
-    sel = avg >= threshold
-    act = np.full(len(p), KEEP, np.int64)
+    """Action per Gaussian. The three integer decisions are taken in FP32
+    on the stored values (the kernel's precision): opacity below
+    min_opacity as logit < fl32(logit(min_opacity)), size as max log-scale >
+    fl32(log(dense)), selection as fl32(accum / max(count, 1)) >= fl32(threshold)."""
+    ls = np.asarray(log_scales, np.float32)
+    lg = np.asarray(opacity_logits, np.float32)
+    st = np.asarray(stats, np.float32)
+    avg = st[:, 0] / np.maximum(st[:, 1], np.float32(1.0))
+    big = ls.max(axis=1) > np.float32(math.log(dense))
+    sel = avg >= np.float32(threshold)
+    act = np.full(len(lg), KEEP, np.int64)
     act[sel & ~big] = CLONE
     act[sel & big] = SPLIT
-    act[p < min_opacity] = PRUNE
+    act[lg < np.float32(math.log(min_opacity / (1.0 - min_opacity)))] = PRUNE
     return act
 
 

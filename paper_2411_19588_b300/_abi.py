@@ -74,7 +74,12 @@ class AdamConfig(ctypes.Structure):
                 ("lr_sh", ctypes.c_float), ("lr_medium", ctypes.c_float), ("beta1", ctypes.c_float),
                 ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("step", ctypes.c_int32),
                 ("clamp_medium", ctypes.c_int32), ("medium_min", ctypes.c_float), ("prior", ctypes.c_void_p),
-                ("lambda_est", ctypes.c_float)]
+                ("lambda_est", ctypes.c_float), ("densify_stats", ctypes.c_void_p)]
+
+
+class DensifyOptions(ctypes.Structure):
+    _fields_ = [("grad_threshold", ctypes.c_float), ("min_opacity", ctypes.c_float), ("percent_dense", ctypes.c_float),
+                ("extent", ctypes.c_float)]
 
 
 BS_MAX_POINTS = 64
@@ -164,6 +169,12 @@ _SIGS = {
                                     ctypes.c_void_p, ctypes.c_void_p],
     "splash_backscatter_prior": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_void_p],
+    "splash_densify_plan": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                            ctypes.POINTER(DensifyOptions), ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p],
+    "splash_densify_apply": [ctypes.c_void_p, ctypes.POINTER(ParamBuffers), ctypes.POINTER(ParamBuffers),
+                             ctypes.POINTER(ParamBuffers), ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                             ctypes.POINTER(ParamBuffers), ctypes.POINTER(ParamBuffers), ctypes.POINTER(ParamBuffers),
+                             ctypes.c_int64, ctypes.c_void_p],
     "splash_opacity_reset": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_float,
                              ctypes.c_void_p],
     "splash_restore": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,

@@ -175,6 +175,9 @@ struct splash_ctx {
     splash_host::Buf feat_counts;  // featuriser histogram counters (kept zero between calls)
     splash_host::Buf bs_scratch;   // backscatter estimate: counters, keys, clusters, kept list, resized maps
     splash_host::Buf zero16;       // 16 zeros: the medium of the pixel form's inner render
+    // densification plan: output counts, actions, output offsets (for dens_n Gaussians)
+    splash_host::Buf dens_count, dens_action, dens_off, dens_iota, dens_sums, dens_total;
+    int64_t dens_n = -1;
 };
 
 struct splash_state {

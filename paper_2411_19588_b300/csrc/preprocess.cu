@@ -634,6 +634,7 @@ struct AdamK {
     float *v[5];
     float lr[5];
     AdamHyper h;
+    float *dstat;  // densification statistics [n][2] (NDC centre-gradient norm, count), or null
 };
 
 // The same adjoint, followed by one Adam step on the Gaussian's parameters
@@ -665,6 +666,13 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_preprocess_bwd_adam(
     } else if (i < n) {
 #pragma unroll
         for (int k = 0; k < KC; k++) row[k] = 0.f;
+    }
+    if (ad.dstat && i < n && depth_key[i] != 0xffffffffu) {  // in the view: ga was loaded by has_grad
+        const float gx = ga.a0.x * (0.5f * (float)cam.W), gy = ga.a0.y * (0.5f * (float)cam.H);
+        float2 st = reinterpret_cast<float2 *>(ad.dstat)[i];
+        st.x += sqrtf(fmaf(gx, gx, gy * gy));
+        st.y += 1.f;
+        reinterpret_cast<float2 *>(ad.dstat)[i] = st;
     }
     if (i < n) {  // every Gaussian steps (zero gradient still moves its moments), as in plain Adam
 #pragma unroll
@@ -891,6 +899,7 @@ void launch_preprocess_bwd_adam(int64_t n, int sh_degree, const splash_param_buf
     ad.lr[3] = cfg.lr_opacity_logits;
     ad.lr[4] = cfg.lr_sh;
     ad.h = make_adam_hyper(cfg.beta1, cfg.beta2, cfg.eps, cfg.step);
+    ad.dstat = cfg.densify_stats;
     switch (sh_degree) {
     case 0: pre_bwd_adam<0>(n, p, medium, cam, acc, dk, ad, bm, s); break;
     case 1: pre_bwd_adam<1>(n, p, medium, cam, acc, dk, ad, bm, s); break;

@@ -188,13 +188,15 @@ class Renderer:
     def backward_adam(self, st: State, params: dict, medium: torch.Tensor, cam: scenes.Camera, dL_dimage,
                       m: dict, v: dict, lr: dict, step: int, betas=(0.9, 0.999), eps: float = 1e-15,
                       medium_min: float | None = 0.0, dL_ddepth=None, dL_ddepth01=None, grad_medium=None,
-                      prior: torch.Tensor | None = None, lambda_est: float = 0.1):
+                      prior: torch.Tensor | None = None, lambda_est: float = 0.1,
+                      densify_stats: torch.Tensor | None = None):
         """Fused training-step backward: gradients of the last forward on `st`
         followed by one Adam step applied in place to params/medium and the
         moment dicts m, v (keys PARAM_NAMES + 'medium'). With `prior` (device
         float32[6] = beta_B_hat, B_inf_hat, e.g. backscatter.prior_of(result)),
         the L_best term of Eq. 9 weighted by lambda_est joins the medium
-        gradient."""
+        gradient. densify_stats ([n, 2] float32) accumulates the densification
+        statistics (see densify_plan)."""
         H, W = cam.height, cam.width
         _check_tensor(dL_dimage, "dL_dimage", (3, H, W))
         names = PARAM_NAMES + ("medium",)
@@ -211,7 +213,9 @@ class Renderer:
                               float(lr["opacity_logits"]), float(lr["sh"]), float(lr["medium"]),
                               float(betas[0]), float(betas[1]), float(eps), int(step),
                               0 if medium_min is None else 1, float(medium_min or 0.0), _abi.ptr(prior),
-                              float(lambda_est))
+                              float(lambda_est), _abi.ptr(densify_stats))
+        if densify_stats is not None:
+            _check_tensor(densify_stats, "densify_stats", (params["means"].shape[0], 2))
         if prior is not None:
             _check_tensor(prior, "prior", (6,))
         c = camera_struct(cam)
@@ -338,6 +342,37 @@ class Batch:
 
 def kernel_launches() -> int:
     return int(_abi.lib().splash_kernel_launches())
+
+
+def densify(renderer: "Renderer", params: dict, m: dict, v: dict, stats: torch.Tensor, noise: torch.Tensor,
+            extent: float, grad_threshold: float = 0.0002, min_opacity: float = 0.1, percent_dense: float = 0.01):
+    """One densification step (prune / clone / split, see splash_densify_plan):
+    returns new (params, m, v) dicts for the Gaussian groups (medium and other
+    entries of the dicts are carried over unchanged). noise: [n, 2, 3] standard
+    normals for the split samples. Synchronises the stream (the new count)."""
+    n = params["means"].shape[0]
+    _check_tensor(stats, "stats", (n, 2))
+    _check_tensor(noise, "noise", (n, 2, 3))
+    opt = _abi.DensifyOptions(float(grad_threshold), float(min_opacity), float(percent_dense), float(extent))
+    n_new = ctypes.c_int64()
+    L = _abi.lib()
+    _abi.check(L.splash_densify_plan(renderer._ctx, params["log_scales"].data_ptr(), params["opacity_logits"].data_ptr(),
+                                     stats.data_ptr(), n, ctypes.byref(opt), ctypes.byref(n_new), _stream()),
+               "splash_densify_plan")
+    nn = int(n_new.value)
+    deg = int(params["sh_degree"])
+    shapes = {"means": (nn, 3), "log_scales": (nn, 3), "quats": (nn, 4), "opacity_logits": (nn,),
+              "sh": (nn, (deg + 1) ** 2, 3)}
+    new = [{k: torch.empty(sh, device="cuda") for k, sh in shapes.items()} for _ in range(3)]
+    buf = lambda d: _abi.ParamBuffers(*(d[k].data_ptr() for k in PARAM_NAMES), None)
+    _abi.check(L.splash_densify_apply(renderer._ctx, ctypes.byref(buf(params)), ctypes.byref(buf(m)), ctypes.byref(buf(v)),
+                                      n, deg, noise.data_ptr(), ctypes.byref(buf(new[0])), ctypes.byref(buf(new[1])),
+                                      ctypes.byref(buf(new[2])), nn, _stream()), "splash_densify_apply")
+    for src, dst in zip((params, m, v), new):
+        for k, val in src.items():
+            if k not in shapes:
+                dst[k] = val
+    return tuple(new)
 
 
 def opacity_reset(logits: torch.Tensor, m: torch.Tensor | None = None, v: torch.Tensor | None = None,

@@ -130,11 +130,15 @@ class Fit:
     view, and the prior's gradient joins the medium step. With schedule=True
     the appendix's schedule applies: the position learning rate decays
     (schedule.position_lr) and the opacities are reset every
-    reset_every iterations."""
+    reset_every iterations. With densify (a dict: start, stop, every,
+    grad_threshold, min_opacity, percent_dense; defaults from
+    schedule.DENSIFY) the fit gathers the densification statistics while the
+    (1-based) iteration is below stop and densifies at every multiple of
+    `every` above start."""
 
     def __init__(self, renderer: R.Renderer, params: dict, medium, cams, targets, lam: float = 0.2, lr=None,
                  lambda_est: float = 0.0, estimate_every: int = 500, schedule: bool = False,
-                 reset_every: int = SCH.OPACITY_RESET_EVERY):
+                 reset_every: int = SCH.OPACITY_RESET_EVERY, densify: dict | None = None, seed: int = 0):
         self.r = renderer
         self.params = {k: (v.clone() if isinstance(v, torch.Tensor) else v) for k, v in params.items()}
         self.medium = torch.as_tensor(np.asarray(medium, np.float32)).cuda().contiguous()
@@ -156,6 +160,14 @@ class Fit:
         self.estimate = BSC.new_result() if self.lambda_est > 0 else None
         self.estimates_done = 0
         self.schedule, self.reset_every, self.resets_done = bool(schedule), int(reset_every), 0
+        self.densify = None if densify is None else {**SCH.DENSIFY, **densify}
+        self.densify_steps, self.counts = 0, [self.params["means"].shape[0]]
+        self.stats = None
+        if self.densify is not None:
+            self.stats = torch.zeros((self.params["means"].shape[0], 2), device="cuda")
+            centres = np.stack([-c.world_to_cam[:, :3].T @ c.world_to_cam[:, 3] for c in cams])
+            self.extent = 1.1 * float(np.linalg.norm(centres - centres.mean(0), axis=1).max())
+            self.gen = torch.Generator(device="cuda").manual_seed(seed)
 
     def step(self):
         if self.schedule:
@@ -175,9 +187,24 @@ class Fit:
             prior = BSC.prior_of(self.estimate)
         loss, gimg = self.r.loss(self.st, self.image, self.targets[k], self.lam)
         self.it += 1
+        d = self.densify
+        gather = d is not None and self.it < d["stop"]  # 1-based iteration, as in 3DGS
         self.r.backward_adam(self.st, self.params, self.medium, cam, gimg, self.m, self.v, self.lr, self.it,
-                             prior=prior, lambda_est=self.lambda_est)
+                             prior=prior, lambda_est=self.lambda_est, densify_stats=self.stats if gather else None)
+        if gather and self.it > d["start"] and self.it % d["every"] == 0:
+            self._densify()
         return loss
+
+    def _densify(self):
+        d = self.densify
+        n = self.params["means"].shape[0]
+        noise = torch.randn((n, 2, 3), generator=self.gen, device="cuda")
+        p, m, v = R.densify(self.r, self.params, self.m, self.v, self.stats, noise, self.extent, d["grad_threshold"],
+                            d["min_opacity"], d["percent_dense"])
+        self.params, self.m, self.v = p, m, v
+        self.stats = torch.zeros((p["means"].shape[0], 2), device="cuda")
+        self.densify_steps += 1
+        self.counts.append(p["means"].shape[0])
 
     def psnr(self, views) -> float:
         """Mean PSNR (images clipped to [0, 1]) over the given views."""

@@ -1,0 +1,109 @@
+"""GPU parity of the densification step (appendix schedule; the 3DGS
+procedure): the statistics gathered by the fused training step, the plan
+(prune / keep / clone / split) and the new arrays, against the FP64 oracle;
+and the fit loop densifying on its schedule."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import densify as OD
+from paper_2411_19588_b300 import render as R
+from paper_2411_19588_b300 import scenes, warmstart
+
+from parity import GMARGIN, MARGIN, medium_tensor
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def renderer(cuda_lib):
+    return R.Renderer()
+
+
+def test_statistics_match_the_oracle_screen_gradients(renderer):
+    g, m, cam = scenes.tiny_scene(3)
+    params = R.params_to_device(g)
+    med = medium_tensor(m)
+    st = renderer.state()
+    renderer.forward(st, params, med, cam)
+    ora = oracle.render(g, m, cam)
+    keep = (ora["margin"] >= MARGIN) & (ora["gmargin"] >= GMARGIN) & (ora["tie"] == 0)
+    G = np.float64(np.float32(np.random.default_rng(3).standard_normal((3, cam.height, cam.width)) * keep))
+    names = R.PARAM_NAMES + ("medium",)
+    tens = dict(params)
+    tens["medium"] = med
+    mo = {k: torch.zeros_like(tens[k]) for k in names}
+    ve = {k: torch.zeros_like(tens[k]) for k in names}
+    stats = torch.zeros((g.n, 2), device="cuda")
+    stats[:, 0] = 0.5  # accumulates (+=)
+    renderer.backward_adam(st, params, med, cam, torch.tensor(G, dtype=torch.float32, device="cuda"), mo, ve,
+                           warmstart.FIT_LR, 1, densify_stats=stats)
+    got = stats.cpu().numpy().astype(np.float64)
+    ref = oracle.backward(g, m, cam, G)
+    # in the view: inside (z_near, z_far] and opaque enough ever to reach alpha >= 1/255
+    vis = (oracle.project(g, m, cam)["vis"] > 0) & (1 / (1 + np.exp(-g.opacity_logits.astype(np.float64))) >= 1 / 255)
+    want = OD.stat_increment(ref["proj"][:, 0:2], cam.width, cam.height)
+    assert np.array_equal(got[:, 1], vis.astype(np.float64))           # in-view count
+    np.testing.assert_allclose(got[vis, 0] - 0.5, want[vis], rtol=1e-3, atol=1e-5 * want.max())
+    assert np.all(got[~vis, 0] == 0.5)
+
+
+def _random_set(n, rng, deg=3):
+    k = (deg + 1) ** 2
+    p = {"means": rng.normal(0, 2, (n, 3)), "log_scales": rng.normal(-4.0, 0.8, (n, 3)),
+         "quats": rng.normal(0, 1, (n, 4)), "opacity_logits": rng.normal(-1.0, 2.0, n),
+         "sh": rng.normal(0, 0.5, (n, k, 3))}
+    p = {k2: v.astype(np.float32) for k2, v in p.items()}
+    mo = {k2: rng.normal(0, 1e-3, v.shape).astype(np.float32) for k2, v in p.items()}
+    ve = {k2: rng.uniform(0, 1e-5, v.shape).astype(np.float32) for k2, v in p.items()}
+    stats = np.stack([rng.uniform(0, 0.01, n), rng.integers(0, 30, n)], 1).astype(np.float32)
+    return p, mo, ve, stats
+
+
+@pytest.mark.parametrize("n", [1, 777, 20_000])
+def test_plan_and_apply_match_oracle(renderer, n):
+    rng = np.random.default_rng(n)
+    p, mo, ve, stats = _random_set(n, rng)
+    noise = rng.standard_normal((n, 2, 3)).astype(np.float32)
+    extent = 3.0
+    t = lambda d: {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in d.items()}
+    gp, gm, gv = t(p), t(mo), t(ve)
+    gp["sh_degree"] = 3
+    P, M, V = R.densify(renderer, gp, gm, gv, torch.from_numpy(stats).cuda(), torch.from_numpy(noise).cuda(), extent)
+    renderer.sync_status()
+    act = OD.classify(p["log_scales"], p["opacity_logits"], stats, dense=0.01 * extent)
+    if n > 100:
+        assert set(np.unique(act)) == {OD.PRUNE, OD.KEEP, OD.CLONE, OD.SPLIT}
+    oP, oM, oV = OD.apply(p, mo, ve, act, noise)
+    assert P["means"].shape[0] == oP["means"].shape[0]
+    split_rows = np.concatenate([[a == OD.SPLIT] * (2 if a in (OD.CLONE, OD.SPLIT) else 1)
+                                 for a in act if a != OD.PRUNE]) if len(oP["means"]) else np.zeros(0, bool)
+    for k in R.PARAM_NAMES:
+        g_k = P[k].cpu().numpy()
+        if k in ("means", "log_scales"):  # split samples are computed: FP32 against FP64
+            np.testing.assert_array_equal(g_k[~split_rows], np.float32(oP[k][~split_rows]))
+            np.testing.assert_allclose(g_k[split_rows], oP[k][split_rows], rtol=2e-6, atol=2e-6)
+        else:
+            np.testing.assert_array_equal(g_k, np.float32(oP[k]))
+        np.testing.assert_array_equal(M[k].cpu().numpy(), np.float32(oM[k]))
+        np.testing.assert_array_equal(V[k].cpu().numpy(), np.float32(oV[k]))
+
+
+def test_fit_densifies_on_schedule(renderer):
+    g, med, _ = scenes.patch_scene(20_000, 6, (2.0, 12.0), 320, 214, 300.0)
+    cams = scenes.arc_cameras(8, 6, width=320, height=214, fx=300.0)
+    gt = R.params_to_device(g)
+    m = torch.tensor(med.as_array(), device="cuda")
+    tgt = [renderer.render(gt, m, c)[0].clone() for c in cams]
+    start, _ = scenes.perturb(g, med, seed=7)
+    fit = warmstart.Fit(renderer, R.params_to_device(start), warmstart.DEFAULT_MEDIUM, cams, tgt,
+                        densify={"start": 2, "stop": 9, "every": 3, "grad_threshold": 1e-4})
+    losses = [fit.step().item() for _ in range(12)]
+    renderer.sync_status()
+    assert fit.densify_steps == 2 and len(fit.counts) == 3   # at iterations 3 and 6 (9 is past stop)
+    assert fit.counts[1] != fit.counts[0]
+    assert all(math.isfinite(x) for x in losses)
+    assert fit.params["means"].shape[0] == fit.m["means"].shape[0] == fit.counts[-1]
