@@ -54,13 +54,13 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--views", type=int, default=N_VIEWS, help="arc views (targets rendered up front)")
     ap.add_argument("--gemm-size", type=int, default=8192, help="gemm: M = N = K")
-    ap.add_argument("--workload", choices=["train", "batch", "warmstart", "gemm", "backscatter"], default="train",
+    ap.add_argument("--workload", choices=["train", "batch", "warmstart", "gemm", "backscatter", "loop"], default="train",
                     help="train: the training step (the headline metric); batch: 64 uneven views forward+backward, "
                          "sequential plain launches vs one persistent launch each way under a CUDA graph; "
                          "warmstart: MLP trained on generated renders, then the 1.5M fit from its predicted medium "
                          "vs from the default medium; gemm: the tensor-core BF16 GEMM the MLP runs on, "
                          "at M = N = K = --gemm-size; backscatter: the Alg. 1/2 estimate behind the L_best prior "
-                         "on one 1920x1280 view")
+                         "on one 1920x1280 view; loop: the training loop's densification and opacity reset")
     ap.add_argument("--ws-scenes", type=int, default=200, help="warmstart: generated 300k-Gaussian scenes")
     ap.add_argument("--ws-views", type=int, default=100, help="warmstart: (medium, view) draws per scene")
     ap.add_argument("--ws-epochs", type=int, default=30)
@@ -835,6 +835,78 @@ def run_backscatter(args, world, rank, local):
         print(json.dumps(out), flush=True)
 
 
+def run_loop(args, world, rank, local):
+    """The training loop's schedule pieces at the full size (1.5M Gaussians,
+    1920x1280): the fused step with and without the densification statistics,
+    one densification step (plan + gather; the statistics from the timed
+    steps), and the opacity reset."""
+    import torch
+
+    from paper_2411_19588_b300 import render as R
+
+    torch.cuda.set_device(local)
+    r = R.Renderer()
+    params, med, gt, med_gt, cams = build_workload(args.n, rank, args.views)
+    nv = len(cams)
+    H, W = cams[0].height, cams[0].width
+    st = r.state()
+    targets = [r.forward(st, gt, med_gt, c)[0].clone() for c in cams]
+    del gt
+    tensors = {k: params[k] for k in R.PARAM_NAMES}
+    tensors["medium"] = med
+    mom = {k: torch.zeros_like(v) for k, v in tensors.items()}
+    vel = {k: torch.zeros_like(v) for k, v in tensors.items()}
+    image = torch.empty((3, H, W), device="cuda")
+    stats = torch.zeros((args.n, 2), device="cuda")
+    it = [0]
+
+    def step(i, with_stats):
+        cam = cams[(i * 7 + rank * 13) % nv]
+        r.forward(st, params, med, cam, image)
+        _, gimg = r.loss(st, image, targets[(i * 7 + rank * 13) % nv], LAMBDA_SSIM)
+        it[0] += 1
+        r.backward_adam(st, params, med, cam, gimg, mom, vel, LR, it[0], densify_stats=stats if with_stats else None)
+
+    def timed(fn, reps):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for j in range(reps):
+            fn(j)
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    for i in range(max(3, args.warmup)):
+        step(i, True)
+    steps = max(5, args.steps)
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_plain = timed(lambda j: step(j, False), steps)
+    t_stats = timed(lambda j: step(j, True), steps)
+    noise = torch.randn((args.n, 2, 3), device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    p2, m2, v2 = R.densify(r, params, mom, vel, stats, noise, extent=9.35)
+    torch.cuda.synchronize()
+    t_dens = (time.perf_counter() - t0) * 1e3
+    logits = params["opacity_logits"].clone()
+    t_reset = timed(lambda j: R.opacity_reset(logits, None, None, 0.01), 20)
+    clk = clocks.stop()
+    r.sync_status()
+    out = {"metric": "training-loop schedule pieces at 1.5M Gaussians 1920x1280 (ms)", "value": round(t_stats, 4),
+           "unit": "ms per step with densification statistics", "n_gpus": world, "steps": steps,
+           "warmup": max(3, args.warmup), "ms_per_step": round(t_stats, 4), "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "loop: fused step +- densification statistics, one densification step, opacity "
+                                  "reset", "n_gaussians": args.n},
+           "step_ms_without_stats": round(t_plain, 4), "densify_step_ms": round(t_dens, 3),
+           "densify_counts": [args.n, int(p2["means"].shape[0])], "opacity_reset_ms": round(t_reset, 4),
+           "clocks": clk}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def cpu_baseline(budget_s: float = 20.0, n: int = N_GAUSS) -> dict:
     """The FP64 oracle (as it stands) on a bounded sample of the training
     step: projection of all Gaussians, forward and adjoint at a random
@@ -913,6 +985,8 @@ def main():
         run_gemm(args, world, rank, local)
     elif args.workload == "backscatter":
         run_backscatter(args, world, rank, local)
+    elif args.workload == "loop":
+        run_loop(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

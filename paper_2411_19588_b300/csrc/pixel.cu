@@ -96,14 +96,17 @@ __global__ void __launch_bounds__(kPixThreads) k_pixel_adjoint(
     }
 }
 
-// d_medium[j] = sum over blocks of block_med[b][j], in block order
-__global__ void k_pixel_medium_final(const float *__restrict__ block_med, int nblocks, float *__restrict__ d_medium)
+// d_medium[j] = sum over blocks of block_med[b][j]: warp j, lane l adds
+// blocks l, l + 32, ... in order, then a fixed butterfly (deterministic)
+__global__ void __launch_bounds__(9 * 32) k_pixel_medium_final(const float *__restrict__ block_med, int nblocks,
+                                                               float *__restrict__ d_medium)
 {
-    const int j = threadIdx.x;
-    if (j >= 9) return;
+    const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float v = 0.f;
-    for (int b = 0; b < nblocks; b++) v += block_med[b * 9 + j];
-    d_medium[j] = v;
+    for (int b = lane; b < nblocks; b += 32) v += block_med[b * 9 + j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) d_medium[j] = v;
 }
 
 int pixel_blocks(int64_t HW) { return (int)std::min<int64_t>((HW + kPixThreads - 1) / kPixThreads, kPixBlocksMax); }
@@ -174,7 +177,7 @@ extern "C" splash_status splash_render_backward_pixel(splash_ctx *ctx, splash_st
                                    &gs, stream)) != SPLASH_OK)
         return rc;
     if (grads->medium) {
-        k_pixel_medium_final<<<1, 32, 0, s>>>(st->pixmed.as<float>(), nb, grads->medium);
+        k_pixel_medium_final<<<1, 9 * 32, 0, s>>>(st->pixmed.as<float>(), nb, grads->medium);
         count_launch();
     }
     SPLASH_CUDA_TRY(cudaGetLastError());
