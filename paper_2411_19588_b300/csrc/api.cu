@@ -113,7 +113,8 @@ splash_status splash_state_create(splash_ctx *ctx, splash_state **out)
     if (!ctx || !out) return fail(SPLASH_ERR_INVALID_ARG, "null argument");
     splash_state *s = new splash_state();
     s->ctx = ctx;
-    if (cudaMallocHost(&s->h_small, 16 * sizeof(uint32_t)) != cudaSuccess || !s->small.ensure(64)) {
+    if (cudaMallocHost(&s->h_small, 16 * sizeof(uint32_t)) != cudaSuccess || !s->small.ensure(64) ||
+        cudaEventCreateWithFlags(&s->k_ready, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         delete s;
         return fail(SPLASH_ERR_OOM, "splash_state_create: allocation failed");
@@ -126,6 +127,7 @@ splash_status splash_state_destroy(splash_state *st)
 {
     if (!st) return SPLASH_OK;
     if (st->h_small) cudaFreeHost(st->h_small);
+    if (st->k_ready) cudaEventDestroy(st->k_ready);
     delete st;
     return SPLASH_OK;
 }
@@ -177,6 +179,13 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
         launch_preprocess_fwd(n, *g, medium, ck, tg, st->rec.as<Rec>(), st->depth_key.as<uint32_t>(),
                               st->tt.as<uint32_t>(), st->rect.as<uint2>(), s);
     }
+    // the pair count K is the sum of the tile counts: read it back (with the
+    // status word) while the depth sort and the scan run, so that the host
+    // knows K before the GPU runs out of queued work
+    launch_pair_total(n, st->tt.as<uint32_t>(), dK, s);
+    SPLASH_CUDA_TRY(cudaMemcpyAsync(st->h_small, dK, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    SPLASH_CUDA_TRY(cudaMemcpyAsync(st->h_small + 1, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    SPLASH_CUDA_TRY(cudaEventRecord(st->k_ready, s));
     const uint32_t *order = nullptr;
     if (n > 0) {
         Stage t(ctx->prof, SPLASH_STAGE_DEPTH_SORT, s);
@@ -187,10 +196,17 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
     }
     {
         Stage t(ctx->prof, SPLASH_STAGE_SCAN, s);
-        launch_count_scan(n, order, st->tt.as<uint32_t>(), st->offsets.as<uint32_t>(), st->scan_sums.as<uint32_t>(), dK, s);
+        launch_count_scan(n, order, st->tt.as<uint32_t>(), st->offsets.as<uint32_t>(), st->scan_sums.as<uint32_t>(),
+                          dK + 2, s);  // its total equals K
     }
     SPLASH_CUDA_TRY(cudaGetLastError());
-    if ((rc = read_status(ctx, st, s, true)) != SPLASH_OK) return rc;
+    SPLASH_CUDA_TRY(cudaEventSynchronize(st->k_ready));
+    if (const uint32_t status = st->h_small[1]) {
+        SPLASH_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), s));
+        if (status & kStatusTimeout) return fail(SPLASH_ERR_TIMEOUT, "a device-side wait gave up (spin limit reached)");
+        if (status & kStatusCapacity) return fail(SPLASH_ERR_CAPACITY, "tile/Gaussian pairs exceeded the workspace");
+        if (status & kStatusIndex) return fail(SPLASH_ERR_INVALID_ARG, "a row index was outside the feature bank");
+    }
     const int64_t K = st->h_small[0];
     if (K >= ((int64_t)1 << 30)) return fail(SPLASH_ERR_CAPACITY, "more than 2^30 tile/Gaussian pairs");
 

@@ -198,6 +198,7 @@ struct splash_state {
     bool pixel_forward = false;  // the last forward was splash_render_forward_pixel
     splash_host::Buf small;       // [0] = pair count K, [1..] spare
     uint32_t *h_small = nullptr;  // pinned: K, status
+    cudaEvent_t k_ready = nullptr;  // K and the status word have reached h_small
     // what the last forward produced
     bool has_forward = false;
     int64_t n = 0;

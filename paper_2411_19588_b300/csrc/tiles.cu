@@ -170,7 +170,25 @@ __global__ void __launch_bounds__(256) k_ranges(int64_t k_host, const uint32_t *
     }
 }
 
+// total of the tile counts (the pair count K), one atomic per warp
+__global__ void __launch_bounds__(256) k_sum_u32(const uint32_t *__restrict__ v, int64_t n, uint32_t *__restrict__ total)
+{
+    uint32_t acc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) acc += v[i];
+    acc = __reduce_add_sync(0xffffffffu, acc);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(total, acc);
+}
+
 }  // namespace
+
+void launch_pair_total(int64_t n, const uint32_t *tt, uint32_t *total, cudaStream_t s)
+{
+    cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
+    if (n <= 0) return;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 4);
+    k_sum_u32<<<blocks, 256, 0, s>>>(tt, n, total);
+    count_launch();
+}
 
 void launch_count_scan(int64_t n, const uint32_t *order, const uint32_t *tt, uint32_t *offsets, uint32_t *sums,
                        uint32_t *total, cudaStream_t s)
