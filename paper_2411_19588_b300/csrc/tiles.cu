@@ -157,17 +157,35 @@ __global__ void __launch_bounds__(256) k_emit(int64_t n, const uint32_t *__restr
     }
 }
 
+__device__ __forceinline__ void range_ends(int64_t i, uint32_t t, uint32_t prev, uint32_t next, int64_t k,
+                                           uint2 *__restrict__ ranges, uint32_t ntiles)
+{
+    if (t >= ntiles) return;  // only after a capacity overflow (reported through the status word)
+    if (i == 0 || prev != t) ranges[t].x = (uint32_t)i;
+    if (i == k - 1 || next != t) ranges[t].y = (uint32_t)(i + 1);
+}
+
+// Starts and ends of the runs of equal tile ids: four ids per thread from one
+// 16-byte load (when the buffer is 16-byte aligned), plus the two neighbours.
 __global__ void __launch_bounds__(256) k_ranges(int64_t k_host, const uint32_t *__restrict__ k_dev,
                                                 const uint32_t *__restrict__ tile_ids, uint2 *__restrict__ ranges,
                                                 uint32_t ntiles)
 {
     const int64_t k = k_dev ? (int64_t)*k_dev : k_host;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t t = tile_ids[i];
-        if (t >= ntiles) continue;  // only after a capacity overflow (reported through the status word)
-        if (i == 0 || tile_ids[i - 1] != t) ranges[t].x = (uint32_t)i;
-        if (i == k - 1 || tile_ids[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t k4 = (reinterpret_cast<uintptr_t>(tile_ids) & 15) ? 0 : k / 4;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < k4; q += stride) {
+        const uint4 v = reinterpret_cast<const uint4 *>(tile_ids)[q];
+        const int64_t i = 4 * q;
+        const uint32_t prev = i > 0 ? tile_ids[i - 1] : 0u;
+        const uint32_t next = i + 4 < k ? tile_ids[i + 4] : 0u;
+        range_ends(i, v.x, prev, v.y, k, ranges, ntiles);
+        range_ends(i + 1, v.y, v.x, v.z, k, ranges, ntiles);
+        range_ends(i + 2, v.z, v.y, v.w, k, ranges, ntiles);
+        range_ends(i + 3, v.w, v.z, next, k, ranges, ntiles);
     }
+    for (int64_t i = 4 * k4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride)
+        range_ends(i, tile_ids[i], i > 0 ? tile_ids[i - 1] : 0u, i + 1 < k ? tile_ids[i + 1] : 0u, k, ranges, ntiles);
 }
 
 // total of the tile counts (the pair count K), one atomic per warp
@@ -220,7 +238,7 @@ void launch_ranges(int64_t k_host, const uint32_t *k_dev, const uint32_t *tile_i
 {
     cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)ntiles, s);
     if (k_host <= 0) return;
-    const int blocks = (int)std::min<int64_t>((k_host + 255) / 256, 148 * 32);
+    const int blocks = (int)std::min<int64_t>((k_host / 4 + 255) / 256 + 1, 148 * 16);
     k_ranges<<<blocks, 256, 0, s>>>(k_host, k_dev, tile_ids, ranges, (uint32_t)ntiles);
     count_launch();
 }
