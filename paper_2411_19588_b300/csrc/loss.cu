@@ -254,15 +254,22 @@ __global__ void __launch_bounds__(256) k_ssim_pass2(const float *__restrict__ X,
 
 // Final stage: the kColsumParts partial rows of (sum |x-y|, sum SSIM) in a
 // fixed order, then the loss.
+// one warp: lane l adds partial rows l, l + 32, ... (FP64), then a fixed
+// butterfly; the FP64 add chain stays short on this GPU's narrow FP64 pipe
 __global__ void k_loss_final(const float *__restrict__ part, double inv_count, float lam, float *__restrict__ loss)
 {
-    if (threadIdx.x != 0) return;
+    const int lane = threadIdx.x;
     double l1 = 0.0, ss = 0.0;
-    for (int p = 0; p < kColsumParts; p++) {
+    for (int p = lane; p < kColsumParts; p += 32) {
         l1 += part[2 * p];
         ss += part[2 * p + 1];
     }
-    *loss = (float)(l1 * inv_count + (double)lam * (1.0 - ss * inv_count));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+        ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    }
+    if (lane == 0) *loss = (float)(l1 * inv_count + (double)lam * (1.0 - ss * inv_count));
 }
 
 Win make_window()

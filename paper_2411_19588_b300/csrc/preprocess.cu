@@ -747,16 +747,19 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_preprocess_bwd_adam(
 // Final stage of the medium-gradient reduction: d_medium[j] = column sums of
 // the stage-1 partial rows of the per-tile table (pixel terms: beta_B[3],
 // B_inf[3]) and of the per-block table (Gaussian terms, 9), in a fixed order.
-__global__ void k_medium_final(const float *__restrict__ part_tile, const float *__restrict__ part_block,
-                               float *__restrict__ d_medium)
+// (warp j, lane l: partial rows l, l + 32, ... of column j, then a fixed butterfly)
+__global__ void __launch_bounds__(9 * 32) k_medium_final(const float *__restrict__ part_tile,
+                                                         const float *__restrict__ part_block,
+                                                         float *__restrict__ d_medium)
 {
-    const int j = threadIdx.x;
-    if (j >= 9) return;
+    const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float v = 0.f;
-    for (int p = 0; p < kColsumParts; p++) v += part_block[9 * p + j];
+    for (int p = lane; p < kColsumParts; p += 32) v += part_block[9 * p + j];
     if (j >= 3)
-        for (int p = 0; p < kColsumParts; p++) v += part_tile[6 * p + (j - 3)];
-    d_medium[j] = v;
+        for (int p = lane; p < kColsumParts; p += 32) v += part_tile[6 * p + (j - 3)];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) d_medium[j] = v;
 }
 
 // Adam step on the 9 medium parameters from their reduced gradient.
@@ -873,7 +876,7 @@ void launch_medium_reduce(const float *tile_medium, int ntiles, const float *blo
     float *part_tile = scratch, *part_block = scratch + 6 * kColsumParts;
     launch_colsum_partial(tile_medium, ntiles, 6, part_tile, s);
     launch_colsum_partial(block_medium, nblocks, 9, part_block, s);
-    k_medium_final<<<1, 32, 0, s>>>(part_tile, part_block, d_medium);
+    k_medium_final<<<1, 9 * 32, 0, s>>>(part_tile, part_block, d_medium);
     count_launch();
 }
 
