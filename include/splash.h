@@ -296,6 +296,10 @@ typedef enum {
 } splash_stage;
 splash_status splash_profile_enable(splash_ctx *ctx, int32_t on);
 splash_status splash_profile_read(splash_ctx *ctx, double *ms, int64_t *counts);
+/* Restrict the timing to the stages whose bit (1 << splash_stage) is set in
+ * stage_mask (all stages by default); each timed stage costs two event
+ * records on the stream. */
+splash_status splash_profile_mask(splash_ctx *ctx, uint32_t stage_mask);
 
 /* Number of kernels this library has launched in this process so far. */
 uint64_t splash_kernel_launches(void);

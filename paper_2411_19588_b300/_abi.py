@@ -142,6 +142,7 @@ _SIGS = {
     "splash_state_copy": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p],
     "splash_profile_enable": [ctypes.c_void_p, ctypes.c_int32],
     "splash_profile_read": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
+    "splash_profile_mask": [ctypes.c_void_p, ctypes.c_uint32],
     "splash_batch_create": [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(Camera), ctypes.POINTER(ctypes.c_void_p)],
     "splash_batch_destroy": [ctypes.c_void_p],
     "splash_batch_calibrate": [ctypes.c_void_p, ctypes.POINTER(Gaussians), ctypes.c_void_p, ctypes.c_float,

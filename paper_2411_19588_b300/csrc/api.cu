@@ -490,6 +490,13 @@ splash_status splash_profile_enable(splash_ctx *ctx, int32_t on)
     return rc;
 }
 
+splash_status splash_profile_mask(splash_ctx *ctx, uint32_t stage_mask)
+{
+    if (!ctx) return fail(SPLASH_ERR_INVALID_ARG, "null context");
+    ctx->prof.mask = stage_mask;
+    return SPLASH_OK;
+}
+
 splash_status splash_profile_read(splash_ctx *ctx, double *ms, int64_t *counts)
 {
     if (!ctx || !ms || !counts) return fail(SPLASH_ERR_INVALID_ARG, "null argument");

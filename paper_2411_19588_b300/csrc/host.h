@@ -46,6 +46,7 @@ struct Buf {
 // Per-stage CUDA-event timing (tracing aid)
 struct Prof {
     bool on = false;
+    uint32_t mask = ~0u;  // stages timed while on
     struct Rec {
         int stage;
         cudaEvent_t a, b;
@@ -86,7 +87,7 @@ struct Stage {
     cudaEvent_t a = nullptr;
     Stage(Prof &p_, int stage_, cudaStream_t s_) : p(p_), stage(stage_), s(s_)
     {
-        if (p.on && (a = p.take())) cudaEventRecord(a, s);
+        if (p.on && ((p.mask >> stage) & 1u) && (a = p.take())) cudaEventRecord(a, s);
     }
     ~Stage()
     {

@@ -269,7 +269,11 @@ class Renderer:
         _abi.check(rc, "splash_sort_pairs_u32")
         return ko, vo
 
-    def profile(self, on: bool = True):
+    def profile(self, on: bool = True, stages=None):
+        """Stage timing on (clears the totals); `stages` (names from
+        _abi.STAGES) restricts it to those stages, None times all."""
+        mask = 0xFFFFFFFF if stages is None else sum(1 << _abi.STAGES.index(s) for s in stages)
+        _abi.check(_abi.lib().splash_profile_mask(self._ctx, mask), "splash_profile_mask")
         _abi.check(_abi.lib().splash_profile_enable(self._ctx, int(on)), "splash_profile_enable")
 
     def profile_read(self) -> dict:
