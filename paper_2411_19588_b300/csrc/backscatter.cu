@@ -52,7 +52,8 @@ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? 
 __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
 
 // Lanes of the (full) warp whose `bits`-bit value equals this lane's: one
-// ballot per bit (cheaper than match.any on this GPU).
+// ballot per bit (cheaper than match.any on this GPU for a few bits; the
+// 11-bit digits of the select use match.any).
 __device__ __forceinline__ unsigned peers_of(uint32_t v, int bits)
 {
     unsigned peers = 0xffffffffu;
@@ -305,7 +306,8 @@ __global__ void __launch_bounds__(kSelThreads) k_bs_select(const uint32_t *__res
             const bool in = j < n && (u & pmask) == prefix;
             const uint32_t d = in ? (u >> shift) & dmask : 0xffffffffu;
             // one shared atomic per distinct digit in the warp (neighbouring keys share digits)
-            const unsigned peers = peers_of(in ? d : 0x800u, 12);
+            // (11-bit digits: one match.any beats twelve ballots here)
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
             if (in && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[d], (uint32_t)__popc(peers));
         }
         __syncthreads();
