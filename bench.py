@@ -70,7 +70,7 @@ def parse_args():
                     help="fused: backward and Adam in one kernel; unfused: backward, then the multi-group Adam")
     ap.add_argument("--form", choices=["segment", "pixel"], default="segment",
                     help="segment: water per Gaussian and water segment (the default step); pixel: Eq. 5 per pixel "
-                         "with the Eq. 6 depth (implies --step unfused)")
+                         "with the Eq. 6 depth")
     ap.add_argument("--profile-region", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -250,9 +250,7 @@ def run_ours(args, world, rank, local):
     from paper_2411_19588_b300 import render as R
 
     torch.cuda.set_device(local)
-    pixel = args.form == "pixel"  # the pixel form has no fused backward + Adam
-    if pixel:
-        args.step = "unfused"
+    pixel = args.form == "pixel"
     tw, th = (int(x) for x in args.tile.split("x"))
     r = R.Renderer(tile=(tw, th))
     params, med, gt, med_gt, cams = build_workload(args.n, rank, args.views)
@@ -290,7 +288,7 @@ def run_ours(args, world, rank, local):
         loss, gimg = r.loss(st, image, targets[view_of(i)] if target is None else target, LAMBDA_SSIM)
         step_no[0] += 1
         if grads is None:
-            r.backward_adam(st, params, med, cam, gimg, mom, vel, LR, step_no[0])
+            r.backward_adam(st, params, med, cam, gimg, mom, vel, LR, step_no[0], pixel=pixel)
         else:
             r.backward(st, params, med, cam, gimg, None, None, grads, pixel=pixel)
             R.adam_step(groups, step_no[0])

@@ -453,6 +453,15 @@ splash_status splash_render_backward_pixel(splash_ctx *ctx, splash_state *st, co
                                            const float *medium_dev, const splash_camera *cam,
                                            const float *dL_dimage, const float *dL_ddepth,
                                            const float *dL_ddepth01, const splash_grads *grads, void *stream);
+/* The fused training step of the pixel form: its adjoint followed by one Adam
+ * step in place, with the arguments and conventions of
+ * splash_render_backward_adam (prior and densification statistics
+ * included). */
+splash_status splash_render_backward_adam_pixel(splash_ctx *ctx, splash_state *st, const splash_param_buffers *params,
+                                                int64_t n, int32_t sh_degree, const splash_camera *cam,
+                                                const float *dL_dimage, const float *dL_ddepth,
+                                                const float *dL_ddepth01, const splash_adam_config *adam,
+                                                float *grad_medium, void *stream);
 
 /* ---- Backscatter estimate and the L_best prior (Sec. IV-B, Eq. 7-9;
  * appendix Alg. 1 "Estimate Backscatter" and Alg. 2) -----------------------

@@ -127,6 +127,10 @@ _SIGS = {
     "splash_render_backward_pixel": [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(Gaussians), ctypes.c_void_p,
                                      ctypes.POINTER(Camera), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.POINTER(Grads), ctypes.c_void_p],
+    "splash_render_backward_adam_pixel": [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ParamBuffers),
+                                          ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Camera), ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(AdamConfig),
+                                          ctypes.c_void_p, ctypes.c_void_p],
     "splash_state_get_info": [ctypes.c_void_p, ctypes.POINTER(StateInfo)],
     "splash_render_backward_adam": [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ParamBuffers), ctypes.c_int64,
                                     ctypes.c_int32, ctypes.POINTER(Camera), ctypes.c_void_p, ctypes.c_void_p,

@@ -329,10 +329,14 @@ splash_status splash_render_backward(splash_ctx *ctx, splash_state *st, const sp
     return render_backward_impl(ctx, st, g, medium, cam, dL_dimage, dL_ddepth, dL_ddepth01, grads, stream);
 }
 
-splash_status splash_render_backward_adam(splash_ctx *ctx, splash_state *st, const splash_param_buffers *params,
-                                          int64_t n, int32_t sh_degree, const splash_camera *cam,
-                                          const float *dL_dimage, const float *dL_ddepth, const float *dL_ddepth01,
-                                          const splash_adam_config *adam, float *grad_medium, void *stream)
+}  // extern "C"
+
+// C++ linkage: the fused backward + Adam of both water forms
+splash_status backward_adam_impl(splash_ctx *ctx, splash_state *st, const splash_param_buffers *params, int64_t n,
+                                 int32_t sh_degree, const splash_camera *cam, const float *dL_dimage,
+                                 const float *dL_ddepth, const float *dL_ddepth01, const splash_adam_config *adam,
+                                 float *grad_medium, void *stream, const float *chain_medium,
+                                 const float *pixel_partials, int pixel_blocks)
 {
     if (!ctx || !st || st->ctx != ctx) return fail(SPLASH_ERR_INVALID_ARG, "bad context or state");
     if (!params || !adam || !dL_dimage) return fail(SPLASH_ERR_INVALID_ARG, "null params, adam config or dL_dimage");
@@ -352,8 +356,6 @@ splash_status splash_render_backward_adam(splash_ctx *ctx, splash_state *st, con
     }
     if (!st->has_forward || st->n != n || st->W != cam->width || st->H != cam->height)
         return fail(SPLASH_ERR_STATE, "backward does not match the last forward on this state");
-    if (st->pixel_forward)
-        return fail(SPLASH_ERR_STATE, "the last forward on this state was the pixel form: use splash_render_backward_pixel");
     cudaStream_t s = (cudaStream_t)stream;
     const int ntiles = st->tg.tx * st->tg.ty;
     const int nblocks = preprocess_bwd_blocks(std::max<int64_t>(n, 1));
@@ -367,25 +369,42 @@ splash_status splash_render_backward_adam(splash_ctx *ctx, splash_state *st, con
     const CamK ck = make_cam(*cam);
     {
         Stage t(ctx->prof, SPLASH_STAGE_BLEND_BWD, s);
-        launch_blend_bwd(backward_view(st, ck, dL_dimage, dL_ddepth, dL_ddepth01), params->medium,
+        launch_blend_bwd(backward_view(st, ck, dL_dimage, dL_ddepth, dL_ddepth01), chain_medium,
                          ctx->opt.gaussian_batch, s);
     }
     int nb = 0;
     {
         Stage t(ctx->prof, SPLASH_STAGE_PREPROCESS_BWD, s);
-        launch_preprocess_bwd_adam(n, sh_degree, *params, params->medium, ck, st->gacc.as<GAcc>(),
+        launch_preprocess_bwd_adam(n, sh_degree, *params, chain_medium, ck, st->gacc.as<GAcc>(),
                                    st->depth_key.as<uint32_t>(), *adam, st->block_med.as<float>(), &nb, s);
     }
     {
         Stage t(ctx->prof, SPLASH_STAGE_MEDIUM_REDUCE, s);
-        launch_medium_reduce(st->tile_med.as<float>(), ntiles, st->block_med.as<float>(), nb, st->gmed.as<float>(),
-                             st->red_scratch.as<float>(), s);
+        if (pixel_partials)  // the pixel form's medium gradient (its chain ran with a zero medium)
+            launch_pixel_medium_final(pixel_partials, pixel_blocks, st->gmed.as<float>(), s);
+        else
+            launch_medium_reduce(st->tile_med.as<float>(), ntiles, st->block_med.as<float>(), nb, st->gmed.as<float>(),
+                                 st->red_scratch.as<float>(), s);
         launch_medium_adam(params->medium, st->gmed.as<float>(), *adam, s);
     }
     if (grad_medium)
         SPLASH_CUDA_TRY(cudaMemcpyAsync(grad_medium, st->gmed.p, 9 * sizeof(float), cudaMemcpyDeviceToDevice, s));
     SPLASH_CUDA_TRY(cudaGetLastError());
     return SPLASH_OK;
+}
+
+extern "C" {
+
+splash_status splash_render_backward_adam(splash_ctx *ctx, splash_state *st, const splash_param_buffers *params,
+                                          int64_t n, int32_t sh_degree, const splash_camera *cam,
+                                          const float *dL_dimage, const float *dL_ddepth, const float *dL_ddepth01,
+                                          const splash_adam_config *adam, float *grad_medium, void *stream)
+{
+    if (st && st->pixel_forward)
+        return fail(SPLASH_ERR_STATE, "the last forward on this state was the pixel form: use splash_render_backward_adam_pixel");
+    if (!params) return fail(SPLASH_ERR_INVALID_ARG, "null params");
+    return backward_adam_impl(ctx, st, params, n, sh_degree, cam, dL_dimage, dL_ddepth, dL_ddepth01, adam, grad_medium,
+                              stream, params->medium, nullptr, 0);
 }
 
 splash_status splash_state_get_info(const splash_state *st, splash_state_info *out)

@@ -217,3 +217,12 @@ splash_status render_backward_impl(splash_ctx *ctx, splash_state *st, const spla
                                    const float *medium, const splash_camera *cam, const float *dL_dimage,
                                    const float *dL_ddepth, const float *dL_ddepth01, const splash_grads *grads,
                                    void *stream);
+
+// splash_render_backward_adam with the medium its chain sees given explicitly
+// (the pixel form passes zeros) and, when pixel_partials is set, the medium
+// gradient taken from those per-block sums instead of the segment terms
+splash_status backward_adam_impl(splash_ctx *ctx, splash_state *st, const splash_param_buffers *params, int64_t n,
+                                 int32_t sh_degree, const splash_camera *cam, const float *dL_dimage,
+                                 const float *dL_ddepth, const float *dL_ddepth01, const splash_adam_config *adam,
+                                 float *grad_medium, void *stream, const float *chain_medium,
+                                 const float *pixel_partials, int pixel_blocks);

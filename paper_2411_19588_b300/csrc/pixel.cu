@@ -122,6 +122,13 @@ splash_status zero_medium(splash_ctx *ctx, cudaStream_t s, const float **out)
 }
 
 }  // namespace
+
+void launch_pixel_medium_final(const float *partials, int nblocks, float *d_medium, cudaStream_t s)
+{
+    k_pixel_medium_final<<<1, 9 * 32, 0, s>>>(partials, nblocks, d_medium);
+    count_launch();
+}
+
 }  // namespace splash
 
 using namespace splash;
@@ -176,10 +183,37 @@ extern "C" splash_status splash_render_backward_pixel(splash_ctx *ctx, splash_st
     if ((rc = render_backward_impl(ctx, st, g, zero, cam, st->pixG.as<float>(), st->pixgz.as<float>(), dL_ddepth01,
                                    &gs, stream)) != SPLASH_OK)
         return rc;
-    if (grads->medium) {
-        k_pixel_medium_final<<<1, 9 * 32, 0, s>>>(st->pixmed.as<float>(), nb, grads->medium);
-        count_launch();
-    }
+    if (grads->medium) launch_pixel_medium_final(st->pixmed.as<float>(), nb, grads->medium, s);
     SPLASH_CUDA_TRY(cudaGetLastError());
     return SPLASH_OK;
+}
+
+extern "C" splash_status splash_render_backward_adam_pixel(splash_ctx *ctx, splash_state *st,
+                                                           const splash_param_buffers *params, int64_t n,
+                                                           int32_t sh_degree, const splash_camera *cam,
+                                                           const float *dL_dimage, const float *dL_ddepth,
+                                                           const float *dL_ddepth01, const splash_adam_config *adam,
+                                                           float *grad_medium, void *stream)
+{
+    if (!ctx || !st || st->ctx != ctx) return fail(SPLASH_ERR_INVALID_ARG, "bad context or state");
+    if (!params || !params->medium || !dL_dimage || !cam || !adam)
+        return fail(SPLASH_ERR_INVALID_ARG, "null params, medium, dL_dimage, camera or adam config");
+    if (!st->has_forward || !st->pixel_forward || st->W != cam->width || st->H != cam->height)
+        return fail(SPLASH_ERR_STATE, "backward does not match the last pixel-form forward on this state");
+    cudaStream_t s = (cudaStream_t)stream;
+    const float *zero = nullptr;
+    splash_status rc;
+    if ((rc = zero_medium(ctx, s, &zero)) != SPLASH_OK) return rc;
+    const int64_t HW = (int64_t)cam->width * cam->height;
+    const int nb = pixel_blocks(HW);
+    ENSURE(st->pixG, 12 * (size_t)HW);
+    ENSURE(st->pixgz, 4 * (size_t)HW);
+    ENSURE(st->pixmed, 4 * 9 * (size_t)nb);
+    k_pixel_adjoint<<<nb, kPixThreads, 0, s>>>(dL_dimage, dL_ddepth, st->pixJ.as<float>(), st->zh.as<float>(),
+                                               st->aA.as<float>(), params->medium, HW, st->pixG.as<float>(),
+                                               st->pixgz.as<float>(), st->pixmed.as<float>());
+    count_launch();
+    SPLASH_CUDA_TRY(cudaGetLastError());
+    return backward_adam_impl(ctx, st, params, n, sh_degree, cam, st->pixG.as<float>(), st->pixgz.as<float>(),
+                              dL_ddepth01, adam, grad_medium, stream, zero, st->pixmed.as<float>(), nb);
 }

@@ -189,7 +189,7 @@ class Renderer:
                       m: dict, v: dict, lr: dict, step: int, betas=(0.9, 0.999), eps: float = 1e-15,
                       medium_min: float | None = 0.0, dL_ddepth=None, dL_ddepth01=None, grad_medium=None,
                       prior: torch.Tensor | None = None, lambda_est: float = 0.1,
-                      densify_stats: torch.Tensor | None = None):
+                      densify_stats: torch.Tensor | None = None, pixel: bool = False):
         """Fused training-step backward: gradients of the last forward on `st`
         followed by one Adam step applied in place to params/medium and the
         moment dicts m, v (keys PARAM_NAMES + 'medium'). With `prior` (device
@@ -219,11 +219,12 @@ class Renderer:
         if prior is not None:
             _check_tensor(prior, "prior", (6,))
         c = camera_struct(cam)
-        rc = _abi.lib().splash_render_backward_adam(self._ctx, st.handle, ctypes.byref(pb), params["means"].shape[0],
-                                                    int(params["sh_degree"]), ctypes.byref(c), dL_dimage.data_ptr(),
-                                                    _abi.ptr(dL_ddepth), _abi.ptr(dL_ddepth01), ctypes.byref(cfg),
-                                                    _abi.ptr(grad_medium), _stream())
-        _abi.check(rc, "splash_render_backward_adam")
+        fn = "splash_render_backward_adam_pixel" if pixel else "splash_render_backward_adam"
+        rc = getattr(_abi.lib(), fn)(self._ctx, st.handle, ctypes.byref(pb), params["means"].shape[0],
+                                     int(params["sh_degree"]), ctypes.byref(c), dL_dimage.data_ptr(),
+                                     _abi.ptr(dL_ddepth), _abi.ptr(dL_ddepth01), ctypes.byref(cfg),
+                                     _abi.ptr(grad_medium), _stream())
+        _abi.check(rc, fn)
 
     def state_array(self, st: State, field: str, dtype=torch.int32, shape=None) -> torch.Tensor:
         """Copy of one forward-state buffer (see splash_state_copy)."""

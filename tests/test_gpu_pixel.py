@@ -130,3 +130,39 @@ def test_pixel_and_segment_agree_for_an_opaque_single_surface(renderer):
     fx, fy = cam.fx * g.means[0, 0] / g.means[0, 2] + cam.cx, cam.fy * g.means[0, 1] / g.means[0, 2] + cam.cy
     ix, iy = int(fx), int(fy)
     assert n > 1 and np.allclose(a[:, iy, ix], b[:, iy, ix], rtol=0, atol=4e-3)
+
+
+def test_fused_pixel_step_equals_backward_then_adam(renderer):
+    """The fused pixel-form training step updates every parameter as the
+    pixel-form backward followed by the multi-group Adam does, and reports
+    the same medium gradient."""
+    from paper_2411_19588_b300 import warmstart
+    g, m, cam = _box_scene(85, 1500, 100, 75, 90.0, 3, eye=(0.3, -0.2, -0.4), target=(0.1, 0.05, 4.0))
+    lr = dict(warmstart.FIT_LR)
+    G = torch.tensor(np.random.default_rng(2).standard_normal((3, cam.height, cam.width)) * 0.1, dtype=torch.float32,
+                     device="cuda")
+    names = R.PARAM_NAMES + ("medium",)
+    out = []
+    for fused in (True, False):
+        params = R.params_to_device(g)
+        med = medium_tensor(m)
+        tens = dict(params)
+        tens["medium"] = med
+        mo = {k: torch.zeros_like(tens[k]) for k in names}
+        ve = {k: torch.zeros_like(tens[k]) for k in names}
+        st = renderer.state()
+        renderer.forward(st, params, med, cam, pixel=True)
+        gm = torch.zeros(9, device="cuda")
+        if fused:
+            renderer.backward_adam(st, params, med, cam, G, mo, ve, lr, 1, grad_medium=gm, pixel=True)
+        else:
+            grads = renderer.backward(st, params, med, cam, G, pixel=True)
+            gm.copy_(grads["medium"])
+            groups = [{"param": tens[k], "grad": grads[k], "m": mo[k], "v": ve[k], "lr": lr[k],
+                       "clamp_min": 0.0 if k == "medium" else None} for k in names]
+            R.adam_step(groups, 1)
+        torch.cuda.synchronize()
+        out.append(({k: tens[k].cpu().numpy() for k in names}, gm.cpu().numpy()))
+    for k in names:
+        np.testing.assert_allclose(out[0][0][k], out[1][0][k], rtol=1e-6, atol=1e-7, err_msg=k)
+    np.testing.assert_allclose(out[0][1], out[1][1], rtol=1e-6, atol=1e-6)
