@@ -138,7 +138,8 @@ class Fit:
 
     def __init__(self, renderer: R.Renderer, params: dict, medium, cams, targets, lam: float = 0.2, lr=None,
                  lambda_est: float = 0.0, estimate_every: int = 500, schedule: bool = False,
-                 reset_every: int = SCH.OPACITY_RESET_EVERY, densify: dict | None = None, seed: int = 0):
+                 reset_every: int = SCH.OPACITY_RESET_EVERY, densify: dict | None = None, seed: int = 0,
+                 pixel: bool = False):
         self.r = renderer
         self.params = {k: (v.clone() if isinstance(v, torch.Tensor) else v) for k, v in params.items()}
         self.medium = torch.as_tensor(np.asarray(medium, np.float32)).cuda().contiguous()
@@ -160,6 +161,7 @@ class Fit:
         self.estimate = BSC.new_result() if self.lambda_est > 0 else None
         self.estimates_done = 0
         self.schedule, self.reset_every, self.resets_done = bool(schedule), int(reset_every), 0
+        self.pixel = bool(pixel)  # Eq. 5 per pixel instead of per Gaussian and water segment
         self.densify = None if densify is None else {**SCH.DENSIFY, **densify}
         self.densify_steps, self.counts = 0, [self.params["means"].shape[0]]
         self.stats = None
@@ -178,7 +180,7 @@ class Fit:
                 self.resets_done += 1
         k = int(self.order[self.it % len(self.cams)])
         cam = self.cams[k]
-        self.r.forward(self.st, self.params, self.medium, cam, self.image, self.depth, self.depth01)
+        self.r.forward(self.st, self.params, self.medium, cam, self.image, self.depth, self.depth01, pixel=self.pixel)
         prior = None
         if self.estimate is not None:
             if self.it % self.estimate_every == 0:
@@ -190,7 +192,8 @@ class Fit:
         d = self.densify
         gather = d is not None and self.it < d["stop"]  # 1-based iteration, as in 3DGS
         self.r.backward_adam(self.st, self.params, self.medium, cam, gimg, self.m, self.v, self.lr, self.it,
-                             prior=prior, lambda_est=self.lambda_est, densify_stats=self.stats if gather else None)
+                             prior=prior, lambda_est=self.lambda_est, densify_stats=self.stats if gather else None,
+                             pixel=self.pixel)
         if gather and self.it > d["start"] and self.it % d["every"] == 0:
             self._densify()
         return loss
@@ -210,7 +213,8 @@ class Fit:
         """Mean PSNR (images clipped to [0, 1]) over the given views."""
         vals = []
         for k in views:
-            self.r.forward(self.st, self.params, self.medium, self.cams[k], self.image, self.depth, self.depth01)
+            self.r.forward(self.st, self.params, self.medium, self.cams[k], self.image, self.depth, self.depth01,
+                           pixel=self.pixel)
             mse = torch.mean((self.image.clamp(0, 1) - self.targets[k].clamp(0, 1)) ** 2)
             vals.append(mse)
         mse = torch.stack(vals)

@@ -166,3 +166,19 @@ def test_fused_pixel_step_equals_backward_then_adam(renderer):
     for k in names:
         np.testing.assert_allclose(out[0][0][k], out[1][0][k], rtol=1e-6, atol=1e-7, err_msg=k)
     np.testing.assert_allclose(out[0][1], out[1][1], rtol=1e-6, atol=1e-6)
+
+
+def test_fit_in_the_pixel_form_lowers_the_loss(renderer):
+    from paper_2411_19588_b300 import warmstart
+    g, med, _ = scenes.patch_scene(20_000, 9, (2.0, 10.0), 320, 214, 300.0)
+    cams = scenes.arc_cameras(6, 9, width=320, height=214, fx=300.0)
+    gt = R.params_to_device(g)
+    m = torch.tensor(med.as_array(), device="cuda")
+    tgt = [renderer.forward(renderer.state(), gt, m, c, pixel=True)[0].clone() for c in cams]
+    start, _ = scenes.perturb(g, med, seed=10)
+    fit = warmstart.Fit(renderer, R.params_to_device(start), warmstart.DEFAULT_MEDIUM, cams, tgt, pixel=True)
+    first = fit.psnr(range(6))
+    for _ in range(60):
+        fit.step()
+    renderer.sync_status()
+    assert fit.psnr(range(6)) > first + 1.0
