@@ -105,6 +105,40 @@ struct BlendView {
 // device status word bits
 enum : uint32_t { kStatusTimeout = 1u, kStatusCapacity = 2u, kStatusIndex = 4u };
 
+// ---- two FP32 lanes in one 64-bit register pair (packed f32x2 arithmetic,
+// sm_100 and later): one issue slot yields two IEEE round-to-nearest results,
+// each bit-identical to the scalar operation on its lane (no flush to zero,
+// like the rest of the library). The FP32 pipe's rate is unchanged; what is
+// saved is issue slots, which is what bounds the windowed and blending loops.
+struct F2 {
+    uint64_t r;
+};
+__device__ __forceinline__ F2 f2(float x, float y)
+{
+    F2 v;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(v.r) : "f"(x), "f"(y));
+    return v;
+}
+__device__ __forceinline__ void f2_split(F2 v, float &x, float &y) { asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(v.r)); }
+__device__ __forceinline__ F2 f2_fma(F2 a, F2 b, F2 c)
+{
+    F2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.r) : "l"(a.r), "l"(b.r), "l"(c.r));
+    return d;
+}
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b)
+{
+    F2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
+    return d;
+}
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b)
+{
+    F2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
+    return d;
+}
+
 // ---- onesweep radix sort (sort.cu)
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;

@@ -9,7 +9,8 @@
 //   pass 2: dL/dx = blur(d_mu) + 2 x blur(d_xx) + y blur(d_xy) + sign(x-y)/count
 //           (the window is symmetric, so the adjoint blur is the same blur).
 // Each 1-D window pass is register-blocked: a thread slides the 11 taps over
-// four consecutive outputs, so a few shared loads feed many FMAs.
+// four consecutive outputs, so a few shared loads feed many FMAs; pairs of
+// statistics share one packed FP32x2 FMA per tap.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -34,24 +35,27 @@ __device__ __forceinline__ float load0(const float *p, int x, int y, int W, int 
     return (x >= 0 && x < W && y >= 0 && y < H) ? p[(size_t)y * W + x] : 0.f;
 }
 
-// kRun horizontal window sums starting at column 4j of row r of a haloed tile:
-// the 14 inputs come in as four float4 loads.
-__device__ __forceinline__ void hrun(const float (*t)[kSX], int r, int j, float (&u)[16])
-{
-    const float4 *row = reinterpret_cast<const float4 *>(&t[r][4 * j]);
+// The window's taps as packed pairs (w_k, w_k); the window is symmetric
+// (w_k = w_{2R-k} exactly), so six pairs serve all eleven taps.
+struct WinPairs {
+    F2 p[kR + 1];
+    __device__ __forceinline__ explicit WinPairs(const Win &win)
+    {
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-        const float4 v = row[i];
-        u[4 * i] = v.x;
-        u[4 * i + 1] = v.y;
-        u[4 * i + 2] = v.z;
-        u[4 * i + 3] = v.w;
+        for (int k = 0; k <= kR; k++) p[k] = f2(win.w[k], win.w[k]);
     }
-}
+    __device__ __forceinline__ F2 operator[](int k) const { return p[k <= kR ? k : 2 * kR - k]; }
+};
+
+// The 1-D passes are written in scatter form: each input is read (and its
+// products formed) once and added into the kRun outputs it feeds. Every
+// output still sums its taps in the order k = 0 .. 2R from zero, so the
+// result is the same as the gather form, tap by tap.
 
 // Pass 1: blurred statistics (separable, register-blocked), per-pixel SSIM
 // and its partials w.r.t. (mu_x, E[x^2], E[xy]) scaled by dL/dSSIM_p, block
-// sums of |x - y| and SSIM.
+// sums of |x - y| and SSIM. The x and y statistics travel as packed pairs
+// (mu_x, mu_y) and (E[x^2], E[y^2]); E[xy] is the scalar fifth.
 __global__ void __launch_bounds__(256) k_ssim_pass1(const float *__restrict__ X, const float *__restrict__ Y, int W, int H,
                                                     Win win, float wscale, float *__restrict__ d_mu,
                                                     float *__restrict__ d_xx, float *__restrict__ d_xy,
@@ -59,12 +63,15 @@ __global__ void __launch_bounds__(256) k_ssim_pass1(const float *__restrict__ X,
 {
     __shared__ __align__(16) float sx[kHY][kSX];
     __shared__ __align__(16) float sy[kHY][kSX];
-    __shared__ float h[5][kHY][kTX + 1];
+    __shared__ F2 hm[kHY][kTX + 1];   // horizontal (mu_x, mu_y)
+    __shared__ F2 hs[kHY][kTX + 1];   // horizontal (E[x^2], E[y^2])
+    __shared__ float hc[kHY][kTX + 1];  // horizontal E[xy]
     __shared__ float s_red[2][8];
     const int c = blockIdx.z;
     const float *x = X + (size_t)c * W * H, *y = Y + (size_t)c * W * H;
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
     const int tid = threadIdx.x;
+    const WinPairs w2(win);
     {  // haloed tiles: every load of this thread in flight before any store
         constexpr int NL = (kHY * kSX + 255) / 256;
         float lx[NL], ly[NL];
@@ -85,49 +92,70 @@ __global__ void __launch_bounds__(256) k_ssim_pass1(const float *__restrict__ X,
         }
     }
     __syncthreads();
-    // horizontal: kHY rows x (kTX / kRun) runs
+    // horizontal: kHY rows x (kTX / kRun) runs; the 14 inputs of a run come
+    // in as float4 loads (conflict-free at the 44-float row stride)
     for (int e = tid; e < kHY * (kTX / kRun); e += 256) {
         const int r = e / (kTX / kRun), j = e - r * (kTX / kRun);
-        float u[16], v[16], uu[16], vv[16], uv[16];
-        hrun(sx, r, j, u);
-        hrun(sy, r, j, v);
+        const float4 *rx = reinterpret_cast<const float4 *>(&sx[r][4 * j]);
+        const float4 *ry = reinterpret_cast<const float4 *>(&sy[r][4 * j]);
+        F2 a[kRun], b[kRun];
+        float ab[kRun];
 #pragma unroll
-        for (int i = 0; i < kRun + 2 * kR; i++) {
-            uu[i] = u[i] * u[i];
-            vv[i] = v[i] * v[i];
-            uv[i] = u[i] * v[i];
+        for (int i = 0; i < kRun; i++) {
+            a[i] = b[i] = f2(0.f, 0.f);
+            ab[i] = 0.f;
+        }
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            const float4 fu = rx[t], fv = ry[t];
+            const float u4[4] = {fu.x, fu.y, fu.z, fu.w}, v4[4] = {fv.x, fv.y, fv.z, fv.w};
+#pragma unroll
+            for (int l = 0; l < 4; l++) {
+                const int jj = 4 * t + l;  // input column 4j + jj of the haloed row
+                if (jj >= kRun + 2 * kR) continue;
+                const F2 uv = f2(u4[l], v4[l]);
+                const F2 sq = f2_mul(uv, uv);
+                const float cr = u4[l] * v4[l];
+#pragma unroll
+                for (int i = 0; i < kRun; i++) {
+                    const int k = jj - i;
+                    if (k < 0 || k > 2 * kR) continue;
+                    a[i] = f2_fma(w2[k], uv, a[i]);
+                    b[i] = f2_fma(w2[k], sq, b[i]);
+                    ab[i] = fmaf(win.w[k], cr, ab[i]);
+                }
+            }
         }
 #pragma unroll
         for (int i = 0; i < kRun; i++) {
-            float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
-#pragma unroll
-            for (int k = 0; k <= 2 * kR; k++) {
-                const float w = win.w[k];
-                a = fmaf(w, u[i + k], a);
-                b = fmaf(w, v[i + k], b);
-                aa = fmaf(w, uu[i + k], aa);
-                bb = fmaf(w, vv[i + k], bb);
-                ab = fmaf(w, uv[i + k], ab);
-            }
             const int q = kRun * j + i;
-            h[0][r][q] = a; h[1][r][q] = b; h[2][r][q] = aa; h[3][r][q] = bb; h[4][r][q] = ab;
+            hm[r][q] = a[i];
+            hs[r][q] = b[i];
+            hc[r][q] = ab[i];
         }
     }
     __syncthreads();
     // vertical: thread (column q, run b) makes rows kRun b .. kRun b + kRun - 1
     const int q = tid & (kTX - 1), rb = tid / kTX;
-    float st[5][kRun];
+    F2 mu[kRun], sq[kRun];
+    float cr[kRun];
 #pragma unroll
-    for (int m = 0; m < 5; m++) {
-        float col[kRun + 2 * kR];
+    for (int i = 0; i < kRun; i++) {
+        mu[i] = sq[i] = f2(0.f, 0.f);
+        cr[i] = 0.f;
+    }
 #pragma unroll
-        for (int i = 0; i < kRun + 2 * kR; i++) col[i] = h[m][kRun * rb + i][q];
+    for (int jj = 0; jj < kRun + 2 * kR; jj++) {
+        const int rr = kRun * rb + jj;
+        const F2 a = hm[rr][q], b = hs[rr][q];
+        const float cc = hc[rr][q];
 #pragma unroll
         for (int i = 0; i < kRun; i++) {
-            float acc = 0.f;
-#pragma unroll
-            for (int k = 0; k <= 2 * kR; k++) acc = fmaf(win.w[k], col[i + k], acc);
-            st[m][i] = acc;
+            const int k = jj - i;
+            if (k < 0 || k > 2 * kR) continue;
+            mu[i] = f2_fma(w2[k], a, mu[i]);
+            sq[i] = f2_fma(w2[k], b, sq[i]);
+            cr[i] = fmaf(win.w[k], cc, cr[i]);
         }
     }
     float l1 = 0.f, ss = 0.f;
@@ -136,7 +164,10 @@ __global__ void __launch_bounds__(256) k_ssim_pass1(const float *__restrict__ X,
     for (int i = 0; i < kRun; i++) {
         const int r = kRun * rb + i, gy = y0 + r;
         if (gx >= W || gy >= H) continue;
-        const float m1 = st[0][i], m2 = st[1][i], e11 = st[2][i], e22 = st[3][i], e12 = st[4][i];
+        float m1, m2, e11, e22;
+        f2_split(mu[i], m1, m2);
+        f2_split(sq[i], e11, e22);
+        const float e12 = cr[i];
         const float sxx = e11 - m1 * m1, syy = e22 - m2 * m2, sxy = e12 - m1 * m2;
         const float A1 = 2.f * m1 * m2 + kC1, A2 = 2.f * sxy + kC2;
         const float B1 = m1 * m1 + m2 * m2 + kC1, B2 = sxx + syy + kC2;
@@ -173,18 +204,21 @@ __global__ void __launch_bounds__(256) k_ssim_pass1(const float *__restrict__ X,
 }
 
 // Pass 2: dL/dx = blur(d_mu) + 2 x blur(d_xx) + y blur(d_xy) + sign(x - y) / count
-// (the window is symmetric, so the adjoint blur is the same blur).
+// (the window is symmetric, so the adjoint blur is the same blur). d_mu and
+// d_xx are blurred as one packed pair, d_xy as the scalar third.
 __global__ void __launch_bounds__(256) k_ssim_pass2(const float *__restrict__ X, const float *__restrict__ Y, int W, int H,
                                                     Win win, float l1scale, const float *__restrict__ d_mu,
                                                     const float *__restrict__ d_xx, const float *__restrict__ d_xy,
                                                     float *__restrict__ grad)
 {
     __shared__ __align__(16) float s[3][kHY][kSX];
-    __shared__ float h[3][kHY][kTX + 1];
+    __shared__ F2 hp[kHY][kTX + 1];     // horizontal (d_mu, d_xx)
+    __shared__ float hq[kHY][kTX + 1];  // horizontal d_xy
     const int c = blockIdx.z;
     const size_t off = (size_t)c * W * H;
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
     const int tid = threadIdx.x;
+    const WinPairs w2(win);
     {  // haloed tiles: every load of this thread in flight before any store
         constexpr int NL = (kHY * kSX + 255) / 256;
         float l0[NL], l1[NL], l2[NL];
@@ -210,33 +244,61 @@ __global__ void __launch_bounds__(256) k_ssim_pass2(const float *__restrict__ X,
     __syncthreads();
     for (int e = tid; e < kHY * (kTX / kRun); e += 256) {
         const int r = e / (kTX / kRun), j = e - r * (kTX / kRun);
+        const float4 *r0 = reinterpret_cast<const float4 *>(&s[0][r][4 * j]);
+        const float4 *r1 = reinterpret_cast<const float4 *>(&s[1][r][4 * j]);
+        const float4 *r2 = reinterpret_cast<const float4 *>(&s[2][r][4 * j]);
+        F2 a[kRun];
+        float b[kRun];
 #pragma unroll
-        for (int m = 0; m < 3; m++) {
-            float u[16];
-            hrun(s[m], r, j, u);
+        for (int i = 0; i < kRun; i++) {
+            a[i] = f2(0.f, 0.f);
+            b[i] = 0.f;
+        }
 #pragma unroll
-            for (int i = 0; i < kRun; i++) {
-                float a = 0.f;
+        for (int t = 0; t < 4; t++) {
+            const float4 f0 = r0[t], f1 = r1[t], f2v = r2[t];
+            const float v0[4] = {f0.x, f0.y, f0.z, f0.w}, v1[4] = {f1.x, f1.y, f1.z, f1.w},
+                        v2[4] = {f2v.x, f2v.y, f2v.z, f2v.w};
 #pragma unroll
-                for (int k = 0; k <= 2 * kR; k++) a = fmaf(win.w[k], u[i + k], a);
-                h[m][r][kRun * j + i] = a;
+            for (int l = 0; l < 4; l++) {
+                const int jj = 4 * t + l;
+                if (jj >= kRun + 2 * kR) continue;
+                const F2 pr = f2(v0[l], v1[l]);
+#pragma unroll
+                for (int i = 0; i < kRun; i++) {
+                    const int k = jj - i;
+                    if (k < 0 || k > 2 * kR) continue;
+                    a[i] = f2_fma(w2[k], pr, a[i]);
+                    b[i] = fmaf(win.w[k], v2[l], b[i]);
+                }
             }
+        }
+#pragma unroll
+        for (int i = 0; i < kRun; i++) {
+            hp[r][kRun * j + i] = a[i];
+            hq[r][kRun * j + i] = b[i];
         }
     }
     __syncthreads();
     const int q = tid & (kTX - 1), rb = tid / kTX;
-    float bl[3][kRun];
+    F2 bp[kRun];
+    float bq[kRun];
 #pragma unroll
-    for (int m = 0; m < 3; m++) {
-        float col[kRun + 2 * kR];
+    for (int i = 0; i < kRun; i++) {
+        bp[i] = f2(0.f, 0.f);
+        bq[i] = 0.f;
+    }
 #pragma unroll
-        for (int i = 0; i < kRun + 2 * kR; i++) col[i] = h[m][kRun * rb + i][q];
+    for (int jj = 0; jj < kRun + 2 * kR; jj++) {
+        const int rr = kRun * rb + jj;
+        const F2 a = hp[rr][q];
+        const float bb = hq[rr][q];
 #pragma unroll
         for (int i = 0; i < kRun; i++) {
-            float acc = 0.f;
-#pragma unroll
-            for (int k = 0; k <= 2 * kR; k++) acc = fmaf(win.w[k], col[i + k], acc);
-            bl[m][i] = acc;
+            const int k = jj - i;
+            if (k < 0 || k > 2 * kR) continue;
+            bp[i] = f2_fma(w2[k], a, bp[i]);
+            bq[i] = fmaf(win.w[k], bb, bq[i]);
         }
     }
     const int gx = x0 + q;
@@ -248,7 +310,9 @@ __global__ void __launch_bounds__(256) k_ssim_pass2(const float *__restrict__ X,
         const float xv = X[p], yv = Y[p];
         const float diff = xv - yv;
         const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
-        grad[p] = bl[0][i] + 2.f * xv * bl[1][i] + yv * bl[2][i] + sgn * l1scale;
+        float b0, b1;
+        f2_split(bp[i], b0, b1);
+        grad[p] = b0 + 2.f * xv * b1 + yv * bq[i] + sgn * l1scale;
     }
 }
 
