@@ -145,6 +145,31 @@ __device__ __forceinline__ DF pinhole(float f, DF a, DF b, float c)
 
 __device__ __forceinline__ float clampf(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
 
+// non-binding fetch of the line holding p into L2 (no register, no wait)
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// One Gaussian's geometric and opacity parameters, loaded together (one
+// round trip) before anything that depends on them.
+struct GPar {
+    float m[3];
+    float4 q;
+    float ls[3];
+    float logit;
+};
+__device__ __forceinline__ GPar load_gpar(int i, const float *__restrict__ means, const float *__restrict__ log_scales,
+                                          const float *__restrict__ quats, const float *__restrict__ ologits)
+{
+    GPar g;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        g.m[k] = means[3 * i + k];
+        g.ls[k] = log_scales[3 * i + k];
+    }
+    g.q = reinterpret_cast<const float4 *>(quats)[i];
+    g.logit = ologits[i];
+    return g;
+}
+
 constexpr int kPreThreads = 128;
 
 // Stage one warp's SH rows (32 Gaussians x K*3 floats, contiguous in HBM)
@@ -154,15 +179,24 @@ template <int KC>
 __device__ __forceinline__ void stage_sh(const float *__restrict__ sh, int64_t wbase, int cnt, int lane, float *dst)
 {
     constexpr int ROW = KC + 1;
+    constexpr int PER_LANE = (32 * KC / 4 + 31) / 32;  // 16-byte loads per lane for a full warp
     const float *src = sh + wbase * KC;
     const int total = cnt * KC;
     int done = 0;
     if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
         const int n4 = total >> 2;
         const float4 *s4 = reinterpret_cast<const float4 *>(src);
-        for (int e = lane; e < n4; e += 32) {
-            const float4 v = __ldg(s4 + e);
-            const float vv[4] = {v.x, v.y, v.z, v.w};
+        float4 buf[PER_LANE];  // every load in flight before the first shared store
+#pragma unroll
+        for (int u = 0; u < PER_LANE; u++) {
+            const int e = lane + 32 * u;
+            if (e < n4) buf[u] = __ldg(s4 + e);
+        }
+#pragma unroll
+        for (int u = 0; u < PER_LANE; u++) {
+            const int e = lane + 32 * u;
+            if (e >= n4) continue;
+            const float vv[4] = {buf[u].x, buf[u].y, buf[u].z, buf[u].w};
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 const int f = 4 * e + k;
@@ -214,15 +248,17 @@ __global__ void __launch_bounds__(kPreThreads) k_preprocess_fwd(
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t wbase = (int64_t)blockIdx.x * kPreThreads + warp * 32;
     const int cnt = (int)max((int64_t)0, min((int64_t)32, (int64_t)n - wbase));
+    const int i = (int)(wbase + lane);
+    // the lane's own parameters and the warp's SH block in one round trip
+    const GPar gp = i < n ? load_gpar(i, means, log_scales, quats, ologits) : GPar{};
     stage_sh<KC>(sh, wbase, cnt, lane, s_sh[warp]);
     __syncwarp();
-    const int i = (int)(wbase + lane);
     if (i >= n) return;
 
-    const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
+    const float mx = gp.m[0], my = gp.m[1], mz = gp.m[2];
     const DF tzd = dot3_plus(cam.R + 6, mx, my, mz, cam.t[2]);
     const float tz = tzd.hi;
-    const float opac = 1.f / (1.f + expf(-ologits[i]));
+    const float opac = 1.f / (1.f + expf(-gp.logit));
     // culled: outside (z_near, z_far], or too transparent ever to reach alpha >= 1/255
     if (!(tz > cam.znear && tz <= cam.zfar && opac >= kAlphaMin)) {
         depth_key[i] = 0xffffffffu;
@@ -235,13 +271,13 @@ __global__ void __launch_bounds__(kPreThreads) k_preprocess_fwd(
     const float tx = txd.hi, ty = tyd.hi;
 
     // Gaussian rotation from the normalised quaternion (w, x, y, z)
-    const float4 q4 = reinterpret_cast<const float4 *>(quats)[i];
+    const float4 q4 = gp.q;
     const float qinv = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
     const float qw = q4.x * qinv, qx = q4.y * qinv, qy = q4.z * qinv, qz = q4.w * qinv;
     const float Rq[9] = {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
                          2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
                          2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
-    const float s0 = expf(log_scales[3 * i]), s1 = expf(log_scales[3 * i + 1]), s2 = expf(log_scales[3 * i + 2]);
+    const float s0 = expf(gp.ls[0]), s1 = expf(gp.ls[1]), s2 = expf(gp.ls[2]);
     // V = W Rq S: the scaled Gaussian axes in camera coordinates
     float V[9];
 #pragma unroll
@@ -311,7 +347,7 @@ __global__ void __launch_bounds__(kPreThreads) k_preprocess_fwd(
     for (int ch = 0; ch < 3; ch++)
         ct[ch] = col[ch] * expf(-__ldg(medium + ch) * tz) - __ldg(medium + 6 + ch) * expf(-__ldg(medium + 3 + ch) * tz);
     // log2(sigmoid(o)) = -log2(1 + e^{-o})
-    const float lo = -log1pf(expf(-ologits[i])) * kLog2e;
+    const float lo = -log1pf(expf(-gp.logit)) * kLog2e;
 
     Rec r;
     r.r0 = make_float4(px.hi, py.hi, px.lo, py.lo);
@@ -332,26 +368,24 @@ constexpr int kBwdThreads = 128;
 // when ACC. gmed accumulates the Gaussian's share of the medium gradient
 // (through ct = c a - B b).
 template <int DEG, bool ACC = false>
-__device__ __forceinline__ void gaussian_chain(int i, const float *__restrict__ means, const float *__restrict__ log_scales,
-                                               const float *__restrict__ quats, const float *__restrict__ ologits,
-                                               const float *__restrict__ medium, const CamK &cam, const GAcc &ga,
-                                               const float *row, float *grow, float gmean[3], float gls[3], float gq[4],
-                                               float &glogit, float gmed[9])
+__device__ __forceinline__ void gaussian_chain(const GPar &gp, const float *__restrict__ medium, const CamK &cam,
+                                               const GAcc &ga, const float *row, float *grow, float gmean[3], float gls[3],
+                                               float gq[4], float &glogit, float gmed[9])
 {
     constexpr int K = (DEG + 1) * (DEG + 1);
-    const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
+    const float mx = gp.m[0], my = gp.m[1], mz = gp.m[2];
     // same rounding as the forward pass, so clamp decisions agree
     const float tx = dot3_plus(cam.R, mx, my, mz, cam.t[0]).hi;
     const float ty = dot3_plus(cam.R + 3, mx, my, mz, cam.t[1]).hi;
     const float tz = dot3_plus(cam.R + 6, mx, my, mz, cam.t[2]).hi;
-    const float4 q4 = reinterpret_cast<const float4 *>(quats)[i];
+    const float4 q4 = gp.q;
     const float qn2 = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
     const float qinv = rsqrtf(qn2);
     const float qw = q4.x * qinv, qx = q4.y * qinv, qy = q4.z * qinv, qz = q4.w * qinv;
     const float Rq[9] = {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
                          2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
                          2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
-    const float s[3] = {expf(log_scales[3 * i]), expf(log_scales[3 * i + 1]), expf(log_scales[3 * i + 2])};
+    const float s[3] = {expf(gp.ls[0]), expf(gp.ls[1]), expf(gp.ls[2])};
     float WR[9];  // W Rq
 #pragma unroll
     for (int r = 0; r < 3; r++)
@@ -481,18 +515,22 @@ __device__ __forceinline__ void gaussian_chain(int i, const float *__restrict__ 
     gmean[1] = cam.R[1] * gtx + cam.R[4] * gty + cam.R[7] * gtz + (gdir.y - dy * gdd) * vinv;
     gmean[2] = cam.R[2] * gtx + cam.R[5] * gty + cam.R[8] * gtz + (gdir.z - dz * gdd) * vinv;
     // lo = log2(sigmoid(o)): dlo/do = (1 - sigmoid(o)) / ln 2
-    const float opac = 1.f / (1.f + expf(-ologits[i]));
+    const float opac = 1.f / (1.f + expf(-gp.logit));
     glogit = ga.a1.y * (1.f - opac) * (1.f / kLn2);
 }
 
 // Whether a Gaussian got any blend gradient (culled ones never do).
+__device__ __forceinline__ bool any_grad(const GAcc &ga)
+{
+    return (ga.a0.x != 0.f) | (ga.a0.y != 0.f) | (ga.a0.z != 0.f) | (ga.a0.w != 0.f) | (ga.a1.x != 0.f) |
+           (ga.a1.y != 0.f) | (ga.a1.z != 0.f) | (ga.a2.x != 0.f) | (ga.a2.y != 0.f) | (ga.a2.z != 0.f);
+}
 __device__ __forceinline__ bool has_grad(int i, int n, const GAcc *__restrict__ acc, const uint32_t *__restrict__ depth_key,
                                          GAcc &ga)
 {
     if (i >= n || depth_key[i] == 0xffffffffu) return false;
     ga = acc[i];
-    return (ga.a0.x != 0.f) | (ga.a0.y != 0.f) | (ga.a0.z != 0.f) | (ga.a0.w != 0.f) | (ga.a1.x != 0.f) |
-           (ga.a1.y != 0.f) | (ga.a1.z != 0.f) | (ga.a2.x != 0.f) | (ga.a2.y != 0.f) | (ga.a2.z != 0.f);
+    return any_grad(ga);
 }
 
 // block partial of the 9 medium-gradient terms: warp shuffle, then one row per block
@@ -531,15 +569,23 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd(
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t wbase = (int64_t)blockIdx.x * kBwdThreads + warp * 32;
     const int cnt = (int)max((int64_t)0, min((int64_t)32, (int64_t)n - wbase));
+    const int i = (int)(wbase + lane);
+    // the lane's own loads and the warp's SH block in one round trip
+    uint32_t dk = 0xffffffffu;
+    GAcc ga{};
+    GPar gp{};
+    if (i < n) {
+        dk = depth_key[i];
+        ga = acc[i];
+        gp = load_gpar(i, means, log_scales, quats, ologits);
+    }
     stage_sh<KC>(sh, wbase, cnt, lane, s_sh[warp]);
     __syncwarp();
-    const int i = (int)(wbase + lane);
     float gmed[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float gmean[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, glogit = 0.f;
     float *row = s_sh[warp] + lane * ROW;  // SH coefficients in, their gradients out
-    GAcc ga;
-    if (has_grad(i, n, acc, depth_key, ga)) {
-        gaussian_chain<DEG>(i, means, log_scales, quats, ologits, medium, cam, ga, row, row, gmean, gls, gq, glogit, gmed);
+    if (dk != 0xffffffffu && any_grad(ga)) {
+        gaussian_chain<DEG>(gp, medium, cam, ga, row, row, gmean, gls, gq, glogit, gmed);
     } else if (i < n) {
 #pragma unroll
         for (int k = 0; k < KC; k++) row[k] = 0.f;
@@ -593,12 +639,12 @@ __global__ void __launch_bounds__(kMultiThreads) k_preprocess_bwd_multi(
     __syncwarp();
     float gmed[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float gmean[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, glogit = 0.f;
+    const GPar gp = i < n ? load_gpar(i, means, log_scales, quats, ologits) : GPar{};
     for (int v = 0; v < V; v++) {
         GAcc ga;
         if (!has_grad(i, n, gacc + (int64_t)v * n, depth_keys + (int64_t)v * key_stride, ga)) continue;
         float m3[3], l3[3], q4[4], lg;
-        gaussian_chain<DEG, true>(i, means, log_scales, quats, ologits, medium, views[v].cam, ga, row, grow, m3, l3, q4,
-                                  lg, gmed);
+        gaussian_chain<DEG, true>(gp, medium, views[v].cam, ga, row, grow, m3, l3, q4, lg, gmed);
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             gmean[k] += m3[k];
@@ -654,20 +700,35 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_preprocess_bwd_adam(
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t wbase = (int64_t)blockIdx.x * kBwdThreads + warp * 32;
     const int cnt = (int)max((int64_t)0, min((int64_t)32, (int64_t)n - wbase));
+    const int i = (int)(wbase + lane);
+    // the lane's own loads and the warp's SH block in one round trip; the
+    // moments of the eleven per-lane values are fetched into L2 meanwhile
+    uint32_t dk = 0xffffffffu;
+    GAcc ga{};
+    GPar gp{};
+    if (i < n) {
+        dk = depth_key[i];
+        ga = acc[i];
+        gp = load_gpar(i, means, log_scales, quats, ologits);
+#pragma unroll
+        for (int g = 0; g < 4; g++) {
+            const int64_t e = g < 2 ? 3 * (int64_t)i : (g == 2 ? 4 * (int64_t)i : (int64_t)i);
+            prefetch_l2(ad.m[g] + e);
+            prefetch_l2(ad.v[g] + e);
+        }
+    }
     stage_sh<KC>(sh, wbase, cnt, lane, s_sh[warp]);
     __syncwarp();
-    const int i = (int)(wbase + lane);
     float gmed[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float gmean[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, glogit = 0.f;
     float *row = s_sh[warp] + lane * ROW;
-    GAcc ga;
-    if (has_grad(i, n, acc, depth_key, ga)) {
-        gaussian_chain<DEG>(i, means, log_scales, quats, ologits, medium, cam, ga, row, row, gmean, gls, gq, glogit, gmed);
+    if (dk != 0xffffffffu && any_grad(ga)) {
+        gaussian_chain<DEG>(gp, medium, cam, ga, row, row, gmean, gls, gq, glogit, gmed);
     } else if (i < n) {
 #pragma unroll
         for (int k = 0; k < KC; k++) row[k] = 0.f;
     }
-    if (ad.dstat && i < n && depth_key[i] != 0xffffffffu) {  // in the view: ga was loaded by has_grad
+    if (ad.dstat && i < n && dk != 0xffffffffu) {  // in the view
         const float gx = ga.a0.x * (0.5f * (float)cam.W), gy = ga.a0.y * (0.5f * (float)cam.H);
         float2 st = reinterpret_cast<float2 *>(ad.dstat)[i];
         st.x += sqrtf(fmaf(gx, gx, gy * gy));
@@ -675,22 +736,48 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_preprocess_bwd_adam(
         reinterpret_cast<float2 *>(ad.dstat)[i] = st;
     }
     if (i < n) {  // every Gaussian steps (zero gradient still moves its moments), as in plain Adam
+        // the values are the ones loaded at the start; all 22 moment loads
+        // issue before any store (the compiler cannot know that the arrays do
+        // not alias)
+        float pm[3], mm[3], vm[3], ps[3], ms[3], vs[3];
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            adam_update(means[3 * i + k], gmean[k], ad.m[0][3 * i + k], ad.v[0][3 * i + k], ad.lr[0], ad.h);
-            adam_update(log_scales[3 * i + k], gls[k], ad.m[1][3 * i + k], ad.v[1][3 * i + k], ad.lr[1], ad.h);
+            pm[k] = gp.m[k];
+            mm[k] = ad.m[0][3 * i + k];
+            vm[k] = ad.v[0][3 * i + k];
+            ps[k] = gp.ls[k];
+            ms[k] = ad.m[1][3 * i + k];
+            vs[k] = ad.v[1][3 * i + k];
         }
-        float4 p = reinterpret_cast<float4 *>(quats)[i];
+        float4 p = gp.q;
         float4 m = reinterpret_cast<float4 *>(ad.m[2])[i];
         float4 v = reinterpret_cast<float4 *>(ad.v[2])[i];
+        float po = gp.logit, mo = ad.m[3][i], vo = ad.v[3][i];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            adam_update(pm[k], gmean[k], mm[k], vm[k], ad.lr[0], ad.h);
+            adam_update(ps[k], gls[k], ms[k], vs[k], ad.lr[1], ad.h);
+        }
         adam_update(p.x, gq[0], m.x, v.x, ad.lr[2], ad.h);
         adam_update(p.y, gq[1], m.y, v.y, ad.lr[2], ad.h);
         adam_update(p.z, gq[2], m.z, v.z, ad.lr[2], ad.h);
         adam_update(p.w, gq[3], m.w, v.w, ad.lr[2], ad.h);
+        adam_update(po, glogit, mo, vo, ad.lr[3], ad.h);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            means[3 * i + k] = pm[k];
+            ad.m[0][3 * i + k] = mm[k];
+            ad.v[0][3 * i + k] = vm[k];
+            log_scales[3 * i + k] = ps[k];
+            ad.m[1][3 * i + k] = ms[k];
+            ad.v[1][3 * i + k] = vs[k];
+        }
         reinterpret_cast<float4 *>(quats)[i] = p;
         reinterpret_cast<float4 *>(ad.m[2])[i] = m;
         reinterpret_cast<float4 *>(ad.v[2])[i] = v;
-        adam_update(ologits[i], glogit, ad.m[3][i], ad.v[3][i], ad.lr[3], ad.h);
+        ologits[i] = po;
+        ad.m[3][i] = mo;
+        ad.v[3][i] = vo;
     }
     // the medium partials first, so that they are not live through the SH step
     medium_partial(gmed, s_med, block_medium);
