@@ -239,22 +239,17 @@ __device__ __forceinline__ int reduce10_field(int lane)
     return nreal > 0 ? base : -1;
 }
 
-// adjoint of one pixel at one Gaussian; returns false if it does not contribute.
+// adjoint of one pixel at one Gaussian that contributes to it (alpha = the
+// clamped raw value araw, which is at least 1/255 here; dx its column offset).
 // DG: the loss has a depth term (gD, gA non-zero); without it those terms vanish.
 // The exponent's gradient gqs enters the centre and conic gradients only
 // through its moments: acc[5] = sum gqs, acc[0] = sum gqs dx, acc[2] = sum
 // gqs dx^2 over the thread's pixels (one row, so dy is shared); the dy
 // moments and the conic coefficients are applied once per Gaussian.
 template <bool DG>
-__device__ __forceinline__ bool pix_grad(PixB &p, int j, float dx, float A, float Bdy, float Cdy2, float lo, float ctr,
-                                         float ctg, float ctb, float d, float *acc)
+__device__ __forceinline__ void pix_grad(PixB &p, float dx, float araw, float ctr, float ctg, float ctb, float d, float *acc)
 {
-    if (j >= p.last) return false;
-    const float qs = quad(dx, A, Bdy, Cdy2);
-    if (qs < kQsMin) return false;
-    const float araw = ex2_approx(qs + lo);
     const float alpha = fminf(kAlphaMax, araw);
-    if (alpha < kAlphaMin) return false;
     const float inv = rcp_approx(1.f - alpha);
     const float Tj = p.T * inv;  // transmittance in front of this Gaussian
     const float w = alpha * Tj;
@@ -273,7 +268,6 @@ __device__ __forceinline__ bool pix_grad(PixB &p, int j, float dx, float A, floa
     acc[9] = fmaf(p.G2, w, acc[9]);
     p.S = fmaf(w, u, p.S);
     p.T = Tj;
-    return true;
 }
 
 template <int TW, int TH, int NB, bool DG>
@@ -402,10 +396,26 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
                 const float Bdy = a.w * dy;
                 const float Cdy2 = c.x * dy * dy;
                 float acc[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                // the exponent and raw alpha of all the thread's pixels first, without
+                // branches (independent chains the scheduler can overlap); a pixel
+                // takes part if the Gaussian is in front of its last one, within
+                // 3 sigma and at least 1/255 opaque there
+                float dxv[PX], arv[PX];
+                bool on[PX];
+#pragma unroll
+                for (int q = 0; q < PX; q++) {
+                    dxv[q] = pxl[q] - a.x;
+                    const float qs = quad(dxv[q], a.z, Bdy, Cdy2);
+                    arv[q] = ex2_approx(qs + c.y);
+                    on[q] = (j < P[q].last) & (qs >= kQsMin) & (fminf(kAlphaMax, arv[q]) >= kAlphaMin);
+                }
                 bool any = false;
 #pragma unroll
-                for (int q = 0; q < PX; q++)
-                    any |= pix_grad<DG>(P[q], j, pxl[q] - a.x, a.z, Bdy, Cdy2, c.y, c.z, c.w, e.x, e.y, acc);
+                for (int q = 0; q < PX; q++) {
+                    if (!on[q]) continue;
+                    pix_grad<DG>(P[q], dxv[q], arv[q], c.z, c.w, e.x, e.y, acc);
+                    any = true;
+                }
                 if (__any_sync(0xffffffffu, any)) {
                     // moments in y from the row's dy: sum gqs dy, sum gqs dx dy, sum gqs dy^2
                     acc[1] = acc[5] * dy;
