@@ -38,7 +38,7 @@ FLOP_PER_PAIR_FWD = 18
 FLOP_PER_PAIR_BWD = 50
 # DRAM bytes (read + write) of one launch at the default workload (1.5M Gaussians, 1920x1280,
 # 16x16 tiles), from an ncu capture of the current kernel; used for the roofline's `traffic`
-KERNEL_DRAM_BYTES = {"blend_bwd": 99.62e6 + 3.77e6}
+KERNEL_DRAM_BYTES = {"blend_bwd": 80.17e6 + 2.55e6}
 SM_COUNT_FALLBACK = 148
 
 
