@@ -185,7 +185,9 @@ def test_fused_adam_applies_the_prior(renderer):
         grads.append(gm.cpu().numpy())
     sign = np.sign(medium0.cpu().numpy()[3:] - pv.cpu().numpy())
     d = grads[1] - grads[0]
-    np.testing.assert_allclose(d[:3], 0.0, atol=1e-7)
+    # the two runs agree on beta_D up to the run-to-run rounding of the blend
+    # backward's float atomics (a few ulp of the gradient), not bit for bit
+    np.testing.assert_allclose(d[:3], 0.0, atol=1e-7 + 1e-6 * np.abs(grads[0][:3]).max())
     np.testing.assert_allclose(d[3:], 0.1 * sign, atol=1e-6 + 1e-6 * np.abs(grads[0][3:]).max())
     assert sign[1] == 0.0
 
