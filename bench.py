@@ -606,6 +606,10 @@ def run_warmstart(args, world, rank, local):
 
     torch.cuda.set_device(local)
     r = R.Renderer()
+    # the device scene generator's first call loads torch's linear-algebra libraries
+    # (tens of seconds on a fresh box): make it once, untimed, before the timed generation
+    from paper_2411_19588_b300 import scenes as S
+    S.patch_scene_device(1000, 1, (2.0, 12.0), 1280, 854, 1200.0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     bank, targets = W.generate(r, args.ws_scenes, args.ws_views)

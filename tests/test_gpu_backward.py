@@ -55,6 +55,18 @@ def test_ragged_gradients(renderer, seed, W, H, deg):
     print((W, H), compare_grads(got, ref, f"ragged{W}x{H}"))
 
 
+@pytest.mark.parametrize("tile", [(8, 32), (32, 8)])
+def test_other_tile_shapes_gradients(cuda_lib, tile):
+    """The plain backward with the autotuner's other tile shapes (64
+    threads of 4 pixels each, 2 or 8 threads per tile row) on a ragged image
+    with and without the depth terms."""
+    r = R.Renderer(tile=tile)
+    g, m, cam = _box_scene(71, 1500, 100, 75, 90.0, 3, eye=(0.3, -0.2, -0.4), target=(0.1, 0.05, 4.0))
+    for depth in (True, False):
+        got, ref, _ = _run(r, g, m, cam, 71, depth)
+        print(tile, depth, compare_grads(got, ref, f"tile{tile[0]}x{tile[1]}"))
+
+
 def test_dense_overlap_gradients(renderer):
     """Long per-pixel lists: checks the back-to-front recomputation of T
     from the stored final transmittance."""
