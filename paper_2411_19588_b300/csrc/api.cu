@@ -53,19 +53,12 @@ BlendView backward_view(splash_state *st, const CamK &ck, const float *gi, const
     return v;
 }
 
-splash_status read_status(splash_ctx *ctx, splash_state *st, cudaStream_t s, bool with_k)
+// the failure a non-zero device status word reports
+splash_status status_failure(uint32_t status)
 {
-    // K (when asked) and the status word in one round trip
-    if (with_k) SPLASH_CUDA_TRY(cudaMemcpyAsync(st->h_small, st->small.as<uint32_t>(), sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    SPLASH_CUDA_TRY(cudaMemcpyAsync(st->h_small + 1, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    SPLASH_CUDA_TRY(cudaStreamSynchronize(s));
-    const uint32_t status = st->h_small[1];
-    if (status) {
-        SPLASH_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), s));
-        if (status & kStatusTimeout) return fail(SPLASH_ERR_TIMEOUT, "a device-side wait gave up (spin limit reached)");
-        if (status & kStatusCapacity) return fail(SPLASH_ERR_CAPACITY, "tile/Gaussian pairs exceeded the workspace");
-        if (status & kStatusIndex) return fail(SPLASH_ERR_INVALID_ARG, "a row index was outside the feature bank");
-    }
+    if (status & kStatusTimeout) return fail(SPLASH_ERR_TIMEOUT, "a device-side wait gave up (spin limit reached)");
+    if (status & kStatusCapacity) return fail(SPLASH_ERR_CAPACITY, "tile/Gaussian pairs exceeded the workspace");
+    if (status & kStatusIndex) return fail(SPLASH_ERR_INVALID_ARG, "a row index was outside the feature bank");
     return SPLASH_OK;
 }
 
@@ -203,9 +196,7 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
     SPLASH_CUDA_TRY(cudaEventSynchronize(st->k_ready));
     if (const uint32_t status = st->h_small[1]) {
         SPLASH_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), s));
-        if (status & kStatusTimeout) return fail(SPLASH_ERR_TIMEOUT, "a device-side wait gave up (spin limit reached)");
-        if (status & kStatusCapacity) return fail(SPLASH_ERR_CAPACITY, "tile/Gaussian pairs exceeded the workspace");
-        if (status & kStatusIndex) return fail(SPLASH_ERR_INVALID_ARG, "a row index was outside the feature bank");
+        return status_failure(status);
     }
     const int64_t K = st->h_small[0];
     if (K >= ((int64_t)1 << 30)) return fail(SPLASH_ERR_CAPACITY, "more than 2^30 tile/Gaussian pairs");
@@ -380,12 +371,13 @@ splash_status backward_adam_impl(splash_ctx *ctx, splash_state *st, const splash
     }
     {
         Stage t(ctx->prof, SPLASH_STAGE_MEDIUM_REDUCE, s);
-        if (pixel_partials)  // the pixel form's medium gradient (its chain ran with a zero medium)
+        if (pixel_partials) {  // the pixel form's medium gradient (its chain ran with a zero medium)
             launch_pixel_medium_final(pixel_partials, pixel_blocks, st->gmed.as<float>(), s);
-        else
-            launch_medium_reduce(st->tile_med.as<float>(), ntiles, st->block_med.as<float>(), nb, st->gmed.as<float>(),
-                                 st->red_scratch.as<float>(), s);
-        launch_medium_adam(params->medium, st->gmed.as<float>(), *adam, s);
+            launch_medium_adam(params->medium, st->gmed.as<float>(), *adam, s);
+        } else {
+            launch_medium_reduce_adam(st->tile_med.as<float>(), ntiles, st->block_med.as<float>(), nb, params->medium,
+                                      st->gmed.as<float>(), st->red_scratch.as<float>(), *adam, s);
+        }
     }
     if (grad_medium)
         SPLASH_CUDA_TRY(cudaMemcpyAsync(grad_medium, st->gmed.p, 9 * sizeof(float), cudaMemcpyDeviceToDevice, s));
@@ -553,9 +545,7 @@ splash_status splash_sync_status(splash_ctx *ctx, void *stream)
     SPLASH_CUDA_TRY(cudaMemcpy(&status, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
     if (status) {
         SPLASH_CUDA_TRY(cudaMemset(ctx->d_status, 0, sizeof(uint32_t)));
-        if (status & kStatusTimeout) return fail(SPLASH_ERR_TIMEOUT, "a device-side wait gave up (spin limit reached)");
-        if (status & kStatusCapacity) return fail(SPLASH_ERR_CAPACITY, "tile/Gaussian pairs exceeded the workspace");
-        if (status & kStatusIndex) return fail(SPLASH_ERR_INVALID_ARG, "a row index was outside the feature bank");
+        return status_failure(status);
     }
     return SPLASH_OK;
 }

@@ -199,6 +199,10 @@ void launch_preprocess_bwd_adam(int64_t n, int sh_degree, const splash_param_buf
                                 const CamK &cam, const GAcc *acc, const uint32_t *dk, const splash_adam_config &cfg,
                                 float *block_medium, int *n_blocks_out, cudaStream_t s);
 void launch_medium_adam(float *medium, float *grad, const splash_adam_config &cfg, cudaStream_t s);
+// launch_medium_reduce followed by launch_medium_adam, in two launches
+void launch_medium_reduce_adam(const float *tile_medium, int ntiles, const float *block_medium, int nblocks,
+                               float *medium, float *d_medium, float *scratch, const splash_adam_config &cfg,
+                               cudaStream_t s);
 int preprocess_bwd_blocks(int64_t n);
 int preprocess_bwd_multi_blocks(int64_t n);
 void launch_preprocess_bwd_multi(int64_t n, int V, const splash_gaussians &g, const float *medium, const BlendView *views,
@@ -210,6 +214,9 @@ void launch_preprocess_bwd_multi(int64_t n, int V, const splash_gaussians &g, co
 // part[kColsumParts][cols].
 constexpr int kColsumParts = 64;
 void launch_colsum_partial(const float *data, int rows, int cols, float *part, cudaStream_t s);
+// the partial rows of a 6-column and a 9-column table in one launch
+void launch_colsum_pair_6_9(const float *a, int rows_a, float *part_a, const float *b, int rows_b, float *part_b,
+                            cudaStream_t s);
 
 void launch_ssim_loss(const float *img, const float *tgt, int C, int H, int W, float lam, float *loss,
                       float *grad, float *scratch, cudaStream_t s);

@@ -835,41 +835,68 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_preprocess_bwd_adam(
 // the stage-1 partial rows of the per-tile table (pixel terms: beta_B[3],
 // B_inf[3]) and of the per-block table (Gaussian terms, 9), in a fixed order.
 // (warp j, lane l: partial rows l, l + 32, ... of column j, then a fixed butterfly)
-__global__ void __launch_bounds__(9 * 32) k_medium_final(const float *__restrict__ part_tile,
-                                                         const float *__restrict__ part_block,
-                                                         float *__restrict__ d_medium)
+// one medium parameter's gradient from the partial rows (warp j, lane l:
+// partial rows l, l + 32, ... of column j, then a fixed butterfly)
+__device__ __forceinline__ float medium_column(const float *__restrict__ part_tile, const float *__restrict__ part_block,
+                                               int j, int lane)
 {
-    const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float v = 0.f;
     for (int p = lane; p < kColsumParts; p += 32) v += part_block[9 * p + j];
     if (j >= 3)
         for (int p = lane; p < kColsumParts; p += 32) v += part_tile[6 * p + (j - 3)];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(9 * 32) k_medium_final(const float *__restrict__ part_tile,
+                                                         const float *__restrict__ part_block,
+                                                         float *__restrict__ d_medium)
+{
+    const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float v = medium_column(part_tile, part_block, j, lane);
     if (lane == 0) d_medium[j] = v;
 }
 
-// Adam step on the 9 medium parameters from their reduced gradient.
-// With a backscatter prior (Eq. 9), lambda_est sign(p - prior) joins the
-// gradient of beta_B and B_inf (medium[3..8]) before the step.
+// Adam step of medium parameter j from its gradient g (written back to
+// grad[j] with the prior's term when there is one).
+__device__ __forceinline__ void medium_adam_one(int j, float g, float *__restrict__ medium, float *__restrict__ grad,
+                                                float *__restrict__ m, float *__restrict__ v, float lr, const AdamHyper &h,
+                                                int clamp, float lo, const float *__restrict__ prior, float lambda_est)
+{
+    float p = medium[j], mm = m[j], vv = v[j];
+    if (prior && j >= 3) {
+        const float d = p - prior[j - 3];
+        g += d > 0.f ? lambda_est : (d < 0.f ? -lambda_est : 0.f);
+    }
+    grad[j] = g;
+    adam_update(p, g, mm, vv, lr, h);
+    if (clamp) p = fmaxf(p, lo);
+    medium[j] = p;
+    m[j] = mm;
+    v[j] = vv;
+}
+
 __global__ void k_medium_adam(float *__restrict__ medium, float *__restrict__ grad, float *__restrict__ m,
                               float *__restrict__ v, float lr, AdamHyper h, int clamp, float lo,
                               const float *__restrict__ prior, float lambda_est)
 {
     const int j = threadIdx.x;
-    if (j < 9) {
-        float p = medium[j], mm = m[j], vv = v[j], g = grad[j];
-        if (prior && j >= 3) {
-            const float d = p - prior[j - 3];
-            g += d > 0.f ? lambda_est : (d < 0.f ? -lambda_est : 0.f);
-            grad[j] = g;
-        }
-        adam_update(p, g, mm, vv, lr, h);
-        if (clamp) p = fmaxf(p, lo);
-        medium[j] = p;
-        m[j] = mm;
-        v[j] = vv;
-    }
+    if (j < 9) medium_adam_one(j, grad[j], medium, grad, m, v, lr, h, clamp, lo, prior, lambda_est);
+}
+
+// the final stage of the medium reduction and the medium's Adam step in one
+// launch: warp j reduces column j, then its lane 0 steps parameter j
+__global__ void __launch_bounds__(9 * 32) k_medium_final_adam(const float *__restrict__ part_tile,
+                                                              const float *__restrict__ part_block,
+                                                              float *__restrict__ medium, float *__restrict__ grad,
+                                                              float *__restrict__ m, float *__restrict__ v, float lr,
+                                                              AdamHyper h, int clamp, float lo,
+                                                              const float *__restrict__ prior, float lambda_est)
+{
+    const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float g = medium_column(part_tile, part_block, j, lane);
+    if (lane == 0) medium_adam_one(j, g, medium, grad, m, v, lr, h, clamp, lo, prior, lambda_est);
 }
 
 template <int DEG>
@@ -961,9 +988,20 @@ void launch_medium_reduce(const float *tile_medium, int ntiles, const float *blo
 {
     // scratch: kColsumParts * (6 + 9) floats
     float *part_tile = scratch, *part_block = scratch + 6 * kColsumParts;
-    launch_colsum_partial(tile_medium, ntiles, 6, part_tile, s);
-    launch_colsum_partial(block_medium, nblocks, 9, part_block, s);
+    launch_colsum_pair_6_9(tile_medium, ntiles, part_tile, block_medium, nblocks, part_block, s);
     k_medium_final<<<1, 9 * 32, 0, s>>>(part_tile, part_block, d_medium);
+    count_launch();
+}
+
+void launch_medium_reduce_adam(const float *tile_medium, int ntiles, const float *block_medium, int nblocks,
+                               float *medium, float *d_medium, float *scratch, const splash_adam_config &cfg,
+                               cudaStream_t s)
+{
+    float *part_tile = scratch, *part_block = scratch + 6 * kColsumParts;
+    launch_colsum_pair_6_9(tile_medium, ntiles, part_tile, block_medium, nblocks, part_block, s);
+    k_medium_final_adam<<<1, 9 * 32, 0, s>>>(part_tile, part_block, medium, d_medium, cfg.m.medium, cfg.v.medium,
+                                             cfg.lr_medium, make_adam_hyper(cfg.beta1, cfg.beta2, cfg.eps, cfg.step),
+                                             cfg.clamp_medium, cfg.medium_min, cfg.prior, cfg.lambda_est);
     count_launch();
 }
 

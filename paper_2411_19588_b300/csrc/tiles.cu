@@ -72,12 +72,25 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_top(int nchunks, uint32_t
     if (threadIdx.x == 0) *total = carry;
 }
 
-// per chunk: exclusive offsets of each depth-ranked Gaussian's pairs
+// per chunk: exclusive offsets of each depth-ranked Gaussian's pairs. With
+// `own_prefix` the chunk adds up the sums of the chunks before it itself (a
+// fixed-order block sum; used when there are few chunks, in place of
+// k_scan_top) and the last chunk writes the total; otherwise sums[] holds the
+// exclusive prefixes k_scan_top wrote.
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(int64_t n, const uint32_t *__restrict__ order,
                                                           const uint32_t *__restrict__ tt, const uint32_t *__restrict__ sums,
-                                                          uint32_t *__restrict__ offsets)
+                                                          uint32_t *__restrict__ offsets, int own_prefix,
+                                                          uint32_t *__restrict__ total)
 {
     __shared__ uint32_t s_w[kScanThreads / 32];
+    uint32_t pre = 0;
+    if (own_prefix) {  // uniform over the grid
+        uint32_t a = 0;
+        for (int i = threadIdx.x; i < (int)blockIdx.x; i += kScanThreads) a += sums[i];
+        block_exclusive_scan(a, s_w, &pre);  // every thread gets the block total
+    } else {
+        pre = sums[blockIdx.x];
+    }
     // blocked arrangement: thread t owns items [t*kScanItems, (t+1)*kScanItems) of the chunk
     const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
     uint32_t c[kScanItems];
@@ -89,13 +102,14 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(int64_t n, const uin
         acc += c[j];
     }
     uint32_t tot;
-    uint32_t run = sums[blockIdx.x] + block_exclusive_scan(acc, s_w, &tot);
+    uint32_t run = pre + block_exclusive_scan(acc, s_w, &tot);
 #pragma unroll
     for (int j = 0; j < kScanItems; j++) {
         const int64_t i = base + j;
         if (i < n) offsets[i] = run;
         run += c[j];
     }
+    if (own_prefix && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *total = pre + tot;
 }
 
 // One warp per 32 consecutive depth-ordered Gaussians. Their runs of pairs are
@@ -218,9 +232,13 @@ void launch_count_scan(int64_t n, const uint32_t *order, const uint32_t *tt, uin
     }
     k_scan_reduce<<<nchunks, kScanThreads, 0, s>>>(n, order, tt, sums);
     count_launch();
-    k_scan_top<<<1, kScanThreads, 0, s>>>(nchunks, sums, total);
-    count_launch();
-    k_scan_down<<<nchunks, kScanThreads, 0, s>>>(n, order, tt, sums, offsets);
+    // up to 1024 chunks each chunk adds up its predecessors' sums itself
+    const int own = nchunks <= 1024;
+    if (!own) {
+        k_scan_top<<<1, kScanThreads, 0, s>>>(nchunks, sums, total);
+        count_launch();
+    }
+    k_scan_down<<<nchunks, kScanThreads, 0, s>>>(n, order, tt, sums, offsets, own, total);
     count_launch();
 }
 
