@@ -28,8 +28,32 @@ constexpr int kWarps = kSortThreads / 32;
 __device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) { return *reinterpret_cast<const volatile uint32_t *>(p); }
 __device__ __forceinline__ void st_volatile(uint32_t *p, uint32_t v) { *reinterpret_cast<volatile uint32_t *>(p) = v; }
 
+// exclusive scan of one pass's 256 digit counts by a 256-thread CTA (the
+// counts were added by other CTAs' atomics: read from L2, not L1)
+__device__ __forceinline__ void scan_digits(uint32_t *h, uint32_t *s_w)
+{
+    const uint32_t v = ld_volatile(h + threadIdx.x);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[w] = x;
+    __syncthreads();
+    uint32_t base = 0;
+    for (int i = 0; i < w; i++) base += s_w[i];
+    h[threadIdx.x] = base + x - v;
+    __syncthreads();
+}
+
+// Digit histograms of every pass. The last CTA to finish (a ticket taken
+// after its counts are flushed and fenced; nothing waits) turns them into
+// the per-pass exclusive digit offsets.
 __global__ void __launch_bounds__(256) k_hist(const uint32_t *__restrict__ keys, int64_t n_host,
-                                              const uint32_t *__restrict__ n_dev, int bits, uint32_t *__restrict__ hist)
+                                              const uint32_t *__restrict__ n_dev, int bits, uint32_t *__restrict__ hist,
+                                              uint32_t *__restrict__ done)
 {
     __shared__ uint32_t s[4][kRadix];
     const int passes = (bits + kRadixBits - 1) / kRadixBits;
@@ -58,26 +82,15 @@ __global__ void __launch_bounds__(256) k_hist(const uint32_t *__restrict__ keys,
         const uint32_t c = (&s[0][0])[e];
         if (c) atomicAdd(&hist[e], c);
     }
-}
-
-// exclusive scan of each pass's 256 digit counts (one block per pass)
-__global__ void __launch_bounds__(kRadix) k_hist_scan(uint32_t *__restrict__ hist)
-{
-    __shared__ uint32_t s_w[kRadix / 32];
-    uint32_t *h = hist + blockIdx.x * kRadix;
-    const uint32_t v = h[threadIdx.x];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_w[w] = x;
+    __threadfence();
+    __shared__ uint32_t s_last;
     __syncthreads();
-    uint32_t base = 0;
-    for (int i = 0; i < w; i++) base += s_w[i];
-    h[threadIdx.x] = base + x - v;
+    if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;  // uniform over the CTA
+    __threadfence();
+    __shared__ uint32_t s_w[256 / 32];
+    for (int p = 0; p < passes; p++) scan_digits(hist + p * kRadix, s_w);
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(
@@ -249,9 +262,7 @@ int sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *k0, u
     // look-back flags of every pass; pass p uses rows [p * parts, (p + 1) * parts)
     cudaMemsetAsync(s.lookback, 0, sizeof(uint32_t) * (size_t)passes * (size_t)parts * kRadix, stream);
     const int hblocks = (int)std::min<int64_t>((n_host / 4 + 255) / 256 + 1, 148 * 8);
-    k_hist<<<hblocks, 256, 0, stream>>>(keys_in, n_host, n_dev, bits, s.hist);
-    count_launch();
-    k_hist_scan<<<passes, kRadix, 0, stream>>>(s.hist);
+    k_hist<<<hblocks, 256, 0, stream>>>(keys_in, n_host, n_dev, bits, s.hist, s.counters + 4);  // zeroed above
     count_launch();
     const uint32_t *ki = keys_in, *vi = vals_in;
     for (int p = 0; p < passes; p++) {
