@@ -593,7 +593,7 @@ def run_batch(args, world, rank, local):
 def run_warmstart(args, world, rank, local):
     """Learned warm-start form: renders of generated 300k-Gaussian scenes with
     known water become feature rows; the BF16 MLP trains on them; the 1.5M
-    fit then starts once from the default medium (the plain fit, the judge)
+    fit then starts once from the default medium (the plain fit, the yardstick)
     and once from the medium the network predicts for five target views,
     and the warm fit counts iterations and fit time until it reaches the
     plain fit's final PSNR (fallback to the plain fit if it never does)."""
