@@ -84,7 +84,8 @@ typedef struct {
                                      wait of partition p + 1 runs out and the call reports
                                      SPLASH_ERR_TIMEOUT (results are then invalid) */
     int32_t gaussian_batch;       /* Gaussians staged in shared memory per blend step:
-                                     64, 128 (default, also for 0) or 256 */
+                                     64, 128 or 256 for both passes; 0 (default) = 64
+                                     forward, 128 backward */
 } splash_options;
 
 /* Context: options and a device status word. Allocates only the status

@@ -79,9 +79,8 @@ splash_status splash_create(const splash_options *opt, splash_ctx **out)
     if (o.spin_limit < 0 || o.test_stall_partition < 0)
         return fail(SPLASH_ERR_INVALID_ARG, "spin_limit and test_stall_partition must be >= 0");
     if (o.spin_limit == 0) o.spin_limit = 1 << 22;
-    if (o.gaussian_batch == 0) o.gaussian_batch = 128;
-    if (o.gaussian_batch != 64 && o.gaussian_batch != 128 && o.gaussian_batch != 256)
-        return fail(SPLASH_ERR_INVALID_ARG, "gaussian_batch must be 64, 128 or 256");
+    if (o.gaussian_batch != 0 && o.gaussian_batch != 64 && o.gaussian_batch != 128 && o.gaussian_batch != 256)
+        return fail(SPLASH_ERR_INVALID_ARG, "gaussian_batch must be 0 (per-pass defaults), 64, 128 or 256");
     splash_ctx *c = new splash_ctx();
     c->opt = o;
     if (cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess || cudaMemset(c->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
@@ -245,7 +244,7 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
         v.zhat = st->zh.as<float>();
         v.n_last = st->nlast.as<uint32_t>();
         v.n_walk = st->nwalk.as<uint32_t>();
-        launch_blend_fwd(v, medium, ctx->opt.gaussian_batch, s);
+        launch_blend_fwd(v, medium, fwd_batch(ctx->opt), s);
     }
     SPLASH_CUDA_TRY(cudaGetLastError());
 
@@ -291,7 +290,7 @@ splash_status render_backward_impl(splash_ctx *ctx, splash_state *st, const spla
     const CamK ck = make_cam(*cam);
     {
         Stage t(ctx->prof, SPLASH_STAGE_BLEND_BWD, s);
-        launch_blend_bwd(backward_view(st, ck, dL_dimage, dL_ddepth, dL_ddepth01), medium, ctx->opt.gaussian_batch, s);
+        launch_blend_bwd(backward_view(st, ck, dL_dimage, dL_ddepth, dL_ddepth01), medium, bwd_batch(ctx->opt), s);
     }
     int nb = 0;
     {
@@ -361,7 +360,7 @@ splash_status backward_adam_impl(splash_ctx *ctx, splash_state *st, const splash
     {
         Stage t(ctx->prof, SPLASH_STAGE_BLEND_BWD, s);
         launch_blend_bwd(backward_view(st, ck, dL_dimage, dL_ddepth, dL_ddepth01), chain_medium,
-                         ctx->opt.gaussian_batch, s);
+                         bwd_batch(ctx->opt), s);
     }
     int nb = 0;
     {

@@ -214,9 +214,9 @@ splash_status splash_batch_calibrate(splash_batch *b, const splash_gaussians *g,
     SPLASH_CUDA_TRY(cudaMemcpyAsync(b->item_meta.p, &nitems, 4, cudaMemcpyHostToDevice, s));
     SPLASH_CUDA_TRY(cudaMemcpyAsync(b->tiles_off_dev.p, b->tiles_off.data(), 8 * (V + 1), cudaMemcpyHostToDevice, s));
     SPLASH_CUDA_TRY(cudaStreamSynchronize(s));
-    const int tw = b->ctx->opt.tile_w, th = b->ctx->opt.tile_h, nb = b->ctx->opt.gaussian_batch;
-    b->ctas_fwd = blend_persistent_ctas(tw, th, nb, false);
-    b->ctas_bwd = blend_persistent_ctas(tw, th, nb, true);
+    const int tw = b->ctx->opt.tile_w, th = b->ctx->opt.tile_h;
+    b->ctas_fwd = blend_persistent_ctas(tw, th, fwd_batch(b->ctx->opt), false);
+    b->ctas_bwd = blend_persistent_ctas(tw, th, bwd_batch(b->ctx->opt), true);
     b->n = n;
     b->deg = g->sh_degree;
     b->calibrated = true;
@@ -329,7 +329,7 @@ splash_status splash_batch_forward(splash_batch *b, const splash_gaussians *g, c
     {
         Stage t(ctx->prof, SPLASH_STAGE_BLEND_FWD, s);
         SPLASH_CUDA_TRY(cudaMemsetAsync(meta + 1, 0, 4, s));
-        launch_blend_fwd_persistent(ctx->opt.tile_w, ctx->opt.tile_h, ctx->opt.gaussian_batch, b->views.as<BlendView>(),
+        launch_blend_fwd_persistent(ctx->opt.tile_w, ctx->opt.tile_h, fwd_batch(ctx->opt), b->views.as<BlendView>(),
                                     items, meta, reinterpret_cast<int *>(meta + 1), medium, b->ctas_fwd, s);
     }
     SPLASH_CUDA_TRY(cudaGetLastError());
@@ -362,7 +362,7 @@ splash_status splash_batch_backward(splash_batch *b, const splash_gaussians *g, 
     {
         Stage t(ctx->prof, SPLASH_STAGE_BLEND_BWD, s);
         SPLASH_CUDA_TRY(cudaMemsetAsync(meta + 1, 0, 4, s));
-        launch_blend_bwd_persistent(ctx->opt.tile_w, ctx->opt.tile_h, ctx->opt.gaussian_batch, b->views.as<BlendView>(),
+        launch_blend_bwd_persistent(ctx->opt.tile_w, ctx->opt.tile_h, bwd_batch(ctx->opt), b->views.as<BlendView>(),
                                     items, meta, reinterpret_cast<int *>(meta + 1), medium, b->ctas_bwd, s);
     }
     const int nb = preprocess_bwd_multi_blocks(std::max<int64_t>(n, 1));

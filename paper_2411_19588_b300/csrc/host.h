@@ -169,6 +169,12 @@ inline int bits_for(int64_t count)
         if (!(buf).ensure(bytes)) return splash_host::fail(SPLASH_ERR_OOM, "cudaMalloc failed for " #buf); \
     } while (0)
 
+// Gaussians staged in shared memory per blend step: an explicit option
+// applies to both passes; 0 picks each pass's measured best on the 1.5M
+// training workload (forward 64, backward 128)
+inline int fwd_batch(const splash_options &o) { return o.gaussian_batch ? o.gaussian_batch : 64; }
+inline int bwd_batch(const splash_options &o) { return o.gaussian_batch ? o.gaussian_batch : 128; }
+
 struct splash_ctx {
     splash_options opt;
     uint32_t *d_status = nullptr;  // kernel-reported error bits

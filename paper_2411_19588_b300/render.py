@@ -82,7 +82,7 @@ class State:
 
 
 class Renderer:
-    def __init__(self, tile=(16, 16), spin_limit: int = 0, test_stall_partition: int = 0, batch: int = 128):
+    def __init__(self, tile=(16, 16), spin_limit: int = 0, test_stall_partition: int = 0, batch: int = 0):
         L = _abi.lib()
         opt = _abi.Options(int(tile[0]), int(tile[1]), int(spin_limit), int(test_stall_partition), int(batch))
         h = ctypes.c_void_p()
