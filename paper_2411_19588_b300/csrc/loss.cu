@@ -35,6 +35,54 @@ __device__ __forceinline__ float load0(const float *p, int x, int y, int W, int 
     return (x >= 0 && x < W && y >= 0 && y < H) ? p[(size_t)y * W + x] : 0.f;
 }
 
+// Whether a CTA's haloed window lies inside the image with 16-byte aligned
+// rows (the maps' base addresses a, b, c included): then it is read as the
+// aligned columns x0 - 8 .. x0 + 39 (twelve 16-byte loads per row), with no
+// per-element bounds checks.
+__device__ __forceinline__ bool window_inside(int x0, int y0, int W, int H, const void *a, const void *b, const void *c)
+{
+    const uintptr_t base = reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(c);
+    return x0 >= 8 && x0 + kTX + 8 <= W && y0 >= kR && y0 + kTY + kR <= H && (W & 3) == 0 && (base & 15) == 0;
+}
+
+// The haloed window of NMAP maps of an inside CTA into shared memory: every
+// 16-byte load in flight before any store; element e of the load at aligned
+// column m lands in window column 4 m - 3 + e (kept while inside the row).
+template <int NMAP>
+__device__ __forceinline__ void load_window_inside(const float *const (&src)[NMAP], float (*const (&dst)[NMAP])[kSX],
+                                                   int x0, int y0, int W)
+{
+    constexpr int Q4 = 12;                  // 16-byte columns per window row
+    constexpr int NV = kHY * Q4;            // per map
+    constexpr int NI = (NV + 255) / 256;
+    const int tid = threadIdx.x;
+    float4 v[NMAP][NI];
+#pragma unroll
+    for (int t = 0; t < NI; t++) {
+        const int idx = tid + 256 * t;
+        if (idx >= NV) continue;
+        const int r = idx / Q4, m = idx - r * Q4;
+        const size_t o = (size_t)(y0 - kR + r) * W + (x0 - 8);
+#pragma unroll
+        for (int k = 0; k < NMAP; k++) v[k][t] = reinterpret_cast<const float4 *>(src[k] + o)[m];
+    }
+#pragma unroll
+    for (int t = 0; t < NI; t++) {
+        const int idx = tid + 256 * t;
+        if (idx >= NV) continue;
+        const int r = idx / Q4, m = idx - r * Q4;
+#pragma unroll
+        for (int k = 0; k < NMAP; k++) {
+            const float e4[4] = {v[k][t].x, v[k][t].y, v[k][t].z, v[k][t].w};
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int q = 4 * m - 3 + e;
+                if (q >= 0 && q < kSX) dst[k][r][q] = e4[e];
+            }
+        }
+    }
+}
+
 // The window's taps as packed pairs (w_k, w_k); the window is symmetric
 // (w_k = w_{2R-k} exactly), so six pairs serve all eleven taps.
 struct WinPairs {
@@ -72,7 +120,11 @@ __global__ void __launch_bounds__(256) k_ssim_pass1(const float *__restrict__ X,
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
     const int tid = threadIdx.x;
     const WinPairs w2(win);
-    {  // haloed tiles: every load of this thread in flight before any store
+    if (window_inside(x0, y0, W, H, x, y, y)) {  // uniform over the CTA
+        const float *const src[2] = {x, y};
+        float (*const dst[2])[kSX] = {sx, sy};
+        load_window_inside<2>(src, dst, x0, y0, W);
+    } else {  // haloed tiles with zero padding: every load in flight before any store
         constexpr int NL = (kHY * kSX + 255) / 256;
         float lx[NL], ly[NL];
 #pragma unroll
@@ -219,7 +271,23 @@ __global__ void __launch_bounds__(256) k_ssim_pass2(const float *__restrict__ X,
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
     const int tid = threadIdx.x;
     const WinPairs w2(win);
-    {  // haloed tiles: every load of this thread in flight before any store
+    // this thread's image and target values, fetched with the window
+    const int q = tid & (kTX - 1), rb = tid / kTX;
+    const int gx = x0 + q;
+    float xv[kRun], yv[kRun];
+#pragma unroll
+    for (int i = 0; i < kRun; i++) {
+        const int gy = y0 + kRun * rb + i;
+        const bool ok = gx < W && gy < H;
+        const size_t p = off + (size_t)(ok ? gy : 0) * W + (ok ? gx : 0);
+        xv[i] = ok ? X[p] : 0.f;
+        yv[i] = ok ? Y[p] : 0.f;
+    }
+    if (window_inside(x0, y0, W, H, d_mu + off, d_xx + off, d_xy + off)) {  // uniform over the CTA
+        const float *const src[3] = {d_mu + off, d_xx + off, d_xy + off};
+        float (*const dst[3])[kSX] = {s[0], s[1], s[2]};
+        load_window_inside<3>(src, dst, x0, y0, W);
+    } else {  // haloed tiles with zero padding: every load in flight before any store
         constexpr int NL = (kHY * kSX + 255) / 256;
         float l0[NL], l1[NL], l2[NL];
 #pragma unroll
@@ -280,7 +348,6 @@ __global__ void __launch_bounds__(256) k_ssim_pass2(const float *__restrict__ X,
         }
     }
     __syncthreads();
-    const int q = tid & (kTX - 1), rb = tid / kTX;
     F2 bp[kRun];
     float bq[kRun];
 #pragma unroll
@@ -301,18 +368,16 @@ __global__ void __launch_bounds__(256) k_ssim_pass2(const float *__restrict__ X,
             bq[i] = fmaf(win.w[k], bb, bq[i]);
         }
     }
-    const int gx = x0 + q;
 #pragma unroll
     for (int i = 0; i < kRun; i++) {
         const int gy = y0 + kRun * rb + i;
         if (gx >= W || gy >= H) continue;
         const size_t p = off + (size_t)gy * W + gx;
-        const float xv = X[p], yv = Y[p];
-        const float diff = xv - yv;
+        const float diff = xv[i] - yv[i];
         const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
         float b0, b1;
         f2_split(bp[i], b0, b1);
-        grad[p] = b0 + 2.f * xv * b1 + yv * bq[i] + sgn * l1scale;
+        grad[p] = b0 + 2.f * xv[i] * b1 + yv[i] * bq[i] + sgn * l1scale;
     }
 }
 
