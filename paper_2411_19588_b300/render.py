@@ -82,6 +82,13 @@ class State:
 
 
 class Renderer:
+    """One library context (splash_create). tile: pixel tile (16, 16), (8, 32)
+    or (32, 8); batch: Gaussians staged in shared memory per blend step, 64,
+    128 or 256 for both passes, or 0 for the per-pass defaults (forward 64,
+    backward 128); spin_limit: iterations before a device wait gives up (0:
+    the library default); test_stall_partition: testing aid of the sort's
+    bounded waits (0: off)."""
+
     def __init__(self, tile=(16, 16), spin_limit: int = 0, test_stall_partition: int = 0, batch: int = 0):
         L = _abi.lib()
         opt = _abi.Options(int(tile[0]), int(tile[1]), int(spin_limit), int(test_stall_partition), int(batch))
