@@ -16,13 +16,25 @@ def renderer(cuda_lib):
     return R.Renderer()
 
 
-@pytest.mark.parametrize("C,H,W", [(3, 130, 170), (3, 16, 32), (1, 45, 7), (3, 1280, 1920)])
-def test_loss_and_gradient_match_oracle(renderer, C, H, W):
+# 100x128: rows a multiple of 4 floats, so tiles whose haloed window lies inside the image
+# take the 16-byte load path and the others the checked one; "mis" offsets both buffers by
+# 4 bytes, which sends every tile down the checked path
+@pytest.mark.parametrize("C,H,W,mis", [(3, 130, 170, 0), (3, 16, 32, 0), (1, 45, 7, 0), (3, 100, 128, 0),
+                                       (3, 100, 128, 1), (3, 1280, 1920, 0)])
+def test_loss_and_gradient_match_oracle(renderer, C, H, W, mis):
     rng = np.random.default_rng(C * H + W)
     x = rng.uniform(0, 1, (C, H, W)).astype(np.float32)
     y = np.clip(x + rng.normal(0, 0.1, x.shape), 0, 1).astype(np.float32)
     st = renderer.state()
-    loss, grad = renderer.loss(st, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), 0.2)
+
+    def dev(a):
+        if not mis:
+            return torch.from_numpy(a).cuda()
+        buf = torch.empty(a.size + 1, device="cuda")
+        buf[1:] = torch.from_numpy(a.ravel()).cuda()
+        return buf[1:].view(a.shape)
+
+    loss, grad = renderer.loss(st, dev(x), dev(y), 0.2)
     torch.cuda.synchronize()
     if H * W > 1_000_000:  # the oracle on a crop far from the borders is exact for interior pixels
         ref_l, ref_g = oloss.loss_and_grad(x[:, 600:700, 900:1000], y[:, 600:700, 900:1000], 0.2)
