@@ -86,6 +86,26 @@ def test_empty_and_culled_scenes(renderer):
         np.testing.assert_allclose(out["depth"], 20.0)
 
 
+def test_culled_padding_keeps_the_image(renderer):
+    """4.4M Gaussians behind the camera added to a 3,000-Gaussian scene: they are
+    culled and list no tiles, so the image and depth stay bit for bit the same;
+    with more than 1,024 chunks of 4,096 depth-ordered Gaussians the count scan
+    takes its separate top-level pass."""
+    g, m, cam = _box_scene(91, 3000, 160, 120, 140.0, 1)
+    extra = 4_400_000
+    rng = np.random.default_rng(92)
+    pad = lambda a, b: np.ascontiguousarray(np.concatenate([a, b]), np.float32)
+    big = scenes.Gaussians(
+        pad(g.means, np.c_[rng.uniform(-2, 2, (extra, 2)), rng.uniform(-5.0, -0.5, extra)]),
+        pad(g.log_scales, np.full((extra, 3), -2.0)), pad(g.quats, np.tile([1.0, 0, 0, 0], (extra, 1))),
+        pad(g.opacity_logits, np.full(extra, 2.0)), pad(g.sh, np.zeros((extra,) + g.sh.shape[1:])), g.sh_degree)
+    a = gpu_forward(renderer, g, m, cam)
+    b = gpu_forward(renderer, big, m, cam)
+    assert big.n > 1024 * 4096
+    np.testing.assert_array_equal(a["image"], b["image"])
+    np.testing.assert_array_equal(a["depth"], b["depth"])
+
+
 def test_one_pixel_image(renderer):
     g, m, _ = scenes.tiny_scene(0)
     cam = scenes.Camera(1, 1, 120.0, 120.0, 0.5, 0.5, np.concatenate([np.eye(3), np.zeros((3, 1))], 1), 0.2, 20.0)
