@@ -951,67 +951,106 @@ def run_loop(args, world, rank, local):
         print(json.dumps(out), flush=True)
 
 
-def cpu_baseline(budget_s: float = 20.0, n: int = N_GAUSS) -> dict:
-    """The FP64 oracle (as it stands) on a bounded sample of the training
-    step: projection of all Gaussians, forward and adjoint at a random
-    sample of pixels, the loss and Adam on a sample of their elements;
-    scaled to one full step."""
-    import oracle
-    from oracle import adam as oadam
-    from oracle import loss as oloss
-    from paper_2411_19588_b300 import scenes
-    g, m, _ = scenes.patch_scene(n, 3, (2.0, 15.0), 1920, 1280, 1800.0)
-    cam = scenes.arc_cameras(N_VIEWS, seed=3)[N_VIEWS // 2]
-    H, W = cam.height, cam.width
-    rng = np.random.default_rng(0)
-    t = time.perf_counter()
-    oracle.project(g, m, cam)
-    t_proj = time.perf_counter() - t
-    S = 32
-    while True:
-        pix = rng.choice(H * W, S, replace=False)
+class _OracleStep:
+    """The FP64 oracle (as it stands) on the training workload, timed in pieces
+    and scaled to one full step: projection of all Gaussians (twice: forward
+    and adjoint), forward and adjoint at a random sample of pixels, the loss
+    on a crop and Adam on a sample of elements."""
+
+    def __init__(self, n: int = N_GAUSS):
+        import oracle
+        from oracle import adam as oadam
+        from oracle import loss as oloss
+        from paper_2411_19588_b300 import scenes
+        self.oracle = oracle
+        self.n = n
+        self.g, self.m, _ = scenes.patch_scene(n, 3, (2.0, 15.0), 1920, 1280, 1800.0)
+        self.cam = scenes.arc_cameras(N_VIEWS, seed=3)[N_VIEWS // 2]
+        self.H, self.W = self.cam.height, self.cam.width
+        self.rng = np.random.default_rng(0)
         t = time.perf_counter()
-        oracle.render(g, m, cam, pix=pix)
-        oracle.backward(g, m, cam, rng.standard_normal((3, S)), pix=pix)
-        t_pix = time.perf_counter() - t - 2 * t_proj
-        if t_pix + 2 * t_proj > budget_s * 0.6 or S >= 4096:
-            break
-        S *= 2
-    per_pixel = max(t_pix, 0.0) / S
-    crop = 256
-    x = rng.uniform(0, 1, (3, crop, crop))
-    t = time.perf_counter()
-    oloss.loss_and_grad(x, x * 0.9, LAMBDA_SSIM)
-    t_loss = (time.perf_counter() - t) * (H * W) / (crop * crop)
-    ne = 1_000_000
-    p = rng.standard_normal(ne)
-    t = time.perf_counter()
-    oadam.adam_step(p, p, np.zeros(ne), np.zeros(ne), 1, 1e-3)
-    t_adam = (time.perf_counter() - t) * (n * 59 + 9) / ne
-    t_step = 2 * t_proj + per_pixel * H * W + t_loss + t_adam
-    return {"value": 1.0 / t_step, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"projection of all {n} Gaussians + forward/adjoint at {S} random pixels (scaled by "
-                      f"{H * W}/{S}) + loss on a {crop}x{crop} crop and Adam on {ne} elements (scaled)",
+        oracle.project(self.g, self.m, self.cam)
+        self.t_proj = time.perf_counter() - t
+        self.crop = 256
+        x = self.rng.uniform(0, 1, (3, self.crop, self.crop))
+        t = time.perf_counter()
+        oloss.loss_and_grad(x, x * 0.9, LAMBDA_SSIM)
+        self.t_loss = (time.perf_counter() - t) * (self.H * self.W) / (self.crop * self.crop)
+        self.ne = 1_000_000
+        p = self.rng.standard_normal(self.ne)
+        t = time.perf_counter()
+        oadam.adam_step(p, p, np.zeros(self.ne), np.zeros(self.ne), 1, 1e-3)
+        self.t_adam = (time.perf_counter() - t) * (n * 59 + 9) / self.ne
+
+    def call_seconds(self, S: int) -> float:
+        """Wall time of the oracle's forward + adjoint calls at S random pixels."""
+        pix = self.rng.choice(self.H * self.W, S, replace=False)
+        t = time.perf_counter()
+        self.oracle.render(self.g, self.m, self.cam, pix=pix)
+        self.oracle.backward(self.g, self.m, self.cam, self.rng.standard_normal((3, S)), pix=pix)
+        return time.perf_counter() - t
+
+    def pixel_seconds(self, S: int) -> float:
+        """Seconds per pixel of forward + adjoint: an S-pixel call minus the calls'
+        fixed part (their projections and set-up, measured once with one pixel)."""
+        if not hasattr(self, "fixed"):
+            self.fixed = self.call_seconds(1)
+        return max(self.call_seconds(S) - self.fixed, 0.0) / S
+
+    def step_seconds(self, per_pixel: float) -> float:
+        return 2 * self.t_proj + per_pixel * self.H * self.W + self.t_loss + self.t_adam
+
+    def sample(self, S: int) -> str:
+        return (f"projection of all {self.n} Gaussians + forward/adjoint at {S} random pixels (scaled by "
+                f"{self.H * self.W}/{S}) + loss on a {self.crop}x{self.crop} crop and Adam on {self.ne} elements "
+                f"(scaled)")
+
+    def calibrate(self, budget_s: float) -> int:
+        """Pixel-sample size whose per-pixel part takes about budget_s (1024 .. 4096:
+        smaller samples leave the oracle's threads idle and overstate the per-pixel
+        cost)."""
+        S = 1024
+        while S < 4096 and self.pixel_seconds(S) * S < budget_s:
+            S *= 2
+        return S
+
+
+def cpu_baseline(budget_s: float = 20.0, n: int = N_GAUSS) -> dict:
+    """One bounded measurement of the oracle's training step (see _OracleStep)."""
+    o = _OracleStep(n)
+    S = o.calibrate(budget_s * 0.4)
+    t_step = o.step_seconds(o.pixel_seconds(S))
+    return {"value": 1.0 / t_step, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle", "sample": o.sample(S),
             "seconds_per_step": round(t_step, 1)}
 
 
 def run_reference(args, world, rank):
+    """The reference arm: the oracle on the same workload, each of the warm-up and
+    timed steps a bounded pixel sample; the workload, the projection, loss and Adam
+    timings are made once, and the sample is sized so that the whole run takes a few
+    minutes whatever --steps and --warmup are."""
     if rank != 0:
         return
-    budget = 4.0
+    o = _OracleStep(args.n)
+    # Each step costs the calls' fixed part (about 1.3-2.7 s) plus a 1,024-pixel sample.
+    # Every oracle step is the same work, so at most 20 steps are measured (and at most
+    # two untimed warm-up steps made): the run stays within a few minutes.
+    warm = min(args.warmup, 2)
+    measured = min(args.steps, 20)
+    S = o.calibrate(1.0)
     vals = []
-    for i in range(args.warmup + args.steps):
-        b = cpu_baseline(budget_s=budget, n=args.n)
-        if i >= args.warmup:
-            vals.append(b["value"])
+    for i in range(warm + measured):
+        v_i = 1.0 / o.step_seconds(o.pixel_seconds(S))
+        if i >= warm:
+            vals.append(v_i)
     v = float(np.median(vals))
     out = {"metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "impl": "reference",
+           "data": "synthetic", "impl": "reference", "measured_steps": measured,
            "config": {"workload": "train step: 1.5M Gaussians (SH3, 2-15 m), 1920x1280, 100-view arc, "
                                   "fwd + L1+0.2(1-SSIM) + bwd + Adam", "n_gaussians": args.n},
            "cpu_baseline": {"value": v, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
-                            "sample": b["sample"]},
+                            "sample": o.sample(S) + f", median of {measured} steps"},
            "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
