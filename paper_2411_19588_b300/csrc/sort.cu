@@ -93,6 +93,8 @@ __global__ void __launch_bounds__(256) k_hist(const uint32_t *__restrict__ keys,
     for (int p = 0; p < passes; p++) scan_digits(hist + p * kRadix, s_w);
 }
 
+// BITS: the digit width of this pass (its number of ballots per key)
+template <int BITS>
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t n_host, const uint32_t *__restrict__ n_dev, int shift, uint32_t mask,
@@ -134,7 +136,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
         const uint32_t d = (k[j] >> shift) & mask;
         uint32_t peers = 0xffffffffu;
 #pragma unroll
-        for (int b = 0; b < kRadixBits; b++) {
+        for (int b = 0; b < BITS; b++) {
             const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
             peers &= ((d >> b) & 1u) ? bal : ~bal;
         }
@@ -269,10 +271,20 @@ int sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *k0, u
         uint32_t *ko = (p & 1) ? k1 : k0, *vo = (p & 1) ? v1 : v0;
         const int pbits = std::min(kRadixBits, bits - kRadixBits * p);
         const uint32_t mask = (1u << pbits) - 1u;
-        k_onesweep<<<(unsigned)parts, kSortThreads, 0, stream>>>(ki, vi, ko, vo, n_host, n_dev, kRadixBits * p, mask,
-                                                                 s.hist + kRadix * p, s.lookback + (size_t)p * parts * kRadix,
-                                                                 s.counters + p, status, spin_limit,
-                                                                 (uint32_t)stall_part);
+        auto kern = k_onesweep<8>;
+        switch (pbits) {
+        case 1: kern = k_onesweep<1>; break;
+        case 2: kern = k_onesweep<2>; break;
+        case 3: kern = k_onesweep<3>; break;
+        case 4: kern = k_onesweep<4>; break;
+        case 5: kern = k_onesweep<5>; break;
+        case 6: kern = k_onesweep<6>; break;
+        case 7: kern = k_onesweep<7>; break;
+        default: break;
+        }
+        kern<<<(unsigned)parts, kSortThreads, 0, stream>>>(ki, vi, ko, vo, n_host, n_dev, kRadixBits * p, mask,
+                                                           s.hist + kRadix * p, s.lookback + (size_t)p * parts * kRadix,
+                                                           s.counters + p, status, spin_limit, (uint32_t)stall_part);
         count_launch();
         ki = ko;
         vi = vo;
