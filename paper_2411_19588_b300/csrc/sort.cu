@@ -170,11 +170,14 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     for (int w = 0; w < warp; w++) wpre += s_wsum[w];
     s_doff[d0] = wpre + x - total;
 
-    // decoupled look-back for this digit
+    // decoupled look-back for this digit (digits the pass cannot produce take no part:
+    // every partition of the pass skips the same ones)
     uint32_t *lb = lookback + (int64_t)part * kRadix + d0;
     uint32_t excl = 0;
     const bool publish = stall_part == 0u || part != stall_part;  // test hook: a partition that never reports
-    if (part == 0) {
+    if (d0 >= (1u << BITS)) {
+        // no key of this pass has digit d0
+    } else if (part == 0) {
         st_volatile(lb, kFlagInc | total);
     } else {
         if (publish) st_volatile(lb, kFlagAgg | total);
