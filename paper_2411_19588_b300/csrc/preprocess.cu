@@ -743,16 +743,16 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_preprocess_bwd_adam(
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             pm[k] = gp.m[k];
-            mm[k] = ad.m[0][3 * i + k];
-            vm[k] = ad.v[0][3 * i + k];
+            mm[k] = __ldcs(ad.m[0] + 3 * i + k);  // moments: streamed once, evict first
+            vm[k] = __ldcs(ad.v[0] + 3 * i + k);
             ps[k] = gp.ls[k];
-            ms[k] = ad.m[1][3 * i + k];
-            vs[k] = ad.v[1][3 * i + k];
+            ms[k] = __ldcs(ad.m[1] + 3 * i + k);
+            vs[k] = __ldcs(ad.v[1] + 3 * i + k);
         }
         float4 p = gp.q;
-        float4 m = reinterpret_cast<float4 *>(ad.m[2])[i];
-        float4 v = reinterpret_cast<float4 *>(ad.v[2])[i];
-        float po = gp.logit, mo = ad.m[3][i], vo = ad.v[3][i];
+        float4 m = __ldcs(reinterpret_cast<float4 *>(ad.m[2]) + i);
+        float4 v = __ldcs(reinterpret_cast<float4 *>(ad.v[2]) + i);
+        float po = gp.logit, mo = __ldcs(ad.m[3] + i), vo = __ldcs(ad.v[3] + i);
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             adam_update(pm[k], gmean[k], mm[k], vm[k], ad.lr[0], ad.h);
@@ -765,19 +765,19 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_preprocess_bwd_adam(
         adam_update(po, glogit, mo, vo, ad.lr[3], ad.h);
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            means[3 * i + k] = pm[k];
-            ad.m[0][3 * i + k] = mm[k];
-            ad.v[0][3 * i + k] = vm[k];
-            log_scales[3 * i + k] = ps[k];
-            ad.m[1][3 * i + k] = ms[k];
-            ad.v[1][3 * i + k] = vs[k];
+            __stcs(means + 3 * i + k, pm[k]);
+            __stcs(ad.m[0] + 3 * i + k, mm[k]);
+            __stcs(ad.v[0] + 3 * i + k, vm[k]);
+            __stcs(log_scales + 3 * i + k, ps[k]);
+            __stcs(ad.m[1] + 3 * i + k, ms[k]);
+            __stcs(ad.v[1] + 3 * i + k, vs[k]);
         }
-        reinterpret_cast<float4 *>(quats)[i] = p;
-        reinterpret_cast<float4 *>(ad.m[2])[i] = m;
-        reinterpret_cast<float4 *>(ad.v[2])[i] = v;
-        ologits[i] = po;
-        ad.m[3][i] = mo;
-        ad.v[3][i] = vo;
+        __stcs(reinterpret_cast<float4 *>(quats) + i, p);
+        __stcs(reinterpret_cast<float4 *>(ad.m[2]) + i, m);
+        __stcs(reinterpret_cast<float4 *>(ad.v[2]) + i, v);
+        __stcs(ologits + i, po);
+        __stcs(ad.m[3] + i, mo);
+        __stcs(ad.v[3] + i, vo);
     }
     // the medium partials first, so that they are not live through the SH step
     medium_partial(gmed, s_med, block_medium);
@@ -801,8 +801,8 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_preprocess_bwd_adam(
                     const int e = e0 + 32 * u;
                     if (e < n4) {
                         p[u] = P4[e];
-                        m[u] = M4[e];
-                        v[u] = V4[e];
+                        m[u] = __ldcs(M4 + e);  // streamed once: evict first
+                        v[u] = __ldcs(V4 + e);
                     }
                 }
 #pragma unroll
@@ -819,9 +819,9 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_preprocess_bwd_adam(
                     adam_update(p[u].y, g[1], m[u].y, v[u].y, lr, ad.h);
                     adam_update(p[u].z, g[2], m[u].z, v[u].z, lr, ad.h);
                     adam_update(p[u].w, g[3], m[u].w, v[u].w, lr, ad.h);
-                    P4[e] = p[u];
-                    M4[e] = m[u];
-                    V4[e] = v[u];
+                    __stcs(P4 + e, p[u]);
+                    __stcs(M4 + e, m[u]);
+                    __stcs(V4 + e, v[u]);
                 }
             }
             done = n4 * 4;
