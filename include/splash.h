@@ -89,7 +89,9 @@ typedef struct {
 } splash_options;
 
 /* Context: options and a device status word. Allocates only the status
- * word. opt may be NULL (defaults). */
+ * word, on the current device, which is the device of every call made with
+ * the context (it also sets the depth sort's shared-memory size there).
+ * opt may be NULL (defaults). */
 splash_status splash_create(const splash_options *opt, splash_ctx **out);
 splash_status splash_destroy(splash_ctx *ctx);
 

@@ -83,7 +83,8 @@ splash_status splash_create(const splash_options *opt, splash_ctx **out)
         return fail(SPLASH_ERR_INVALID_ARG, "gaussian_batch must be 0 (per-pass defaults), 64, 128 or 256");
     splash_ctx *c = new splash_ctx();
     c->opt = o;
-    if (cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess || cudaMemset(c->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
+    if (cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess || cudaMemset(c->d_status, 0, sizeof(uint32_t)) != cudaSuccess ||
+        sort_prepare_device() != cudaSuccess) {
         const std::string e = cudaGetErrorString(cudaGetLastError());
         delete c;
         return fail(SPLASH_ERR_CUDA, "splash_create: " + e);
@@ -183,7 +184,7 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
         Stage t(ctx->prof, SPLASH_STAGE_DEPTH_SORT, s);
         const int which = sort_pairs(st->depth_key.as<uint32_t>(), nullptr, st->dk0.as<uint32_t>(), st->dv0.as<uint32_t>(),
                                      st->dk1.as<uint32_t>(), st->dv1.as<uint32_t>(), n, nullptr, 32, ss, ctx->d_status,
-                                     ctx->opt.spin_limit, ctx->opt.test_stall_partition, s);
+                                     ctx->opt.spin_limit, ctx->opt.test_stall_partition, s, kDepthSortItems);
         order = which ? st->dv1.as<uint32_t>() : st->dv0.as<uint32_t>();
     }
     {

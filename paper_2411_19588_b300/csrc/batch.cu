@@ -275,7 +275,7 @@ splash_status splash_batch_forward(splash_batch *b, const splash_gaussians *g, c
             Stage t(ctx->prof, SPLASH_STAGE_DEPTH_SORT, s);
             const int which = sort_pairs(dk, nullptr, b->dk0.as<uint32_t>(), b->dv0.as<uint32_t>(), b->dk1.as<uint32_t>(),
                                          b->dv1.as<uint32_t>(), n, nullptr, 32, ss, ctx->d_status, ctx->opt.spin_limit,
-                                         ctx->opt.test_stall_partition, s);
+                                         ctx->opt.test_stall_partition, s, kDepthSortItems);
             order = which ? b->dv1.as<uint32_t>() : b->dv0.as<uint32_t>();
         }
         {

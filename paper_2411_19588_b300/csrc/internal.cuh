@@ -141,8 +141,15 @@ __device__ __forceinline__ F2 f2_add(F2 a, F2 b)
 
 // ---- onesweep radix sort (sort.cu)
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;   // keys per partition
+constexpr int kSortItems = 16;                         // keys per thread (pair sorts)
+constexpr int kSortTile = kSortThreads * kSortItems;   // keys per partition, the smallest used
+#ifndef SPLASH_DEPTH_SORT_ITEMS
+#define SPLASH_DEPTH_SORT_ITEMS 20
+#endif
+// keys per thread of the depth sort (keys only, one CTA wave at the bench's
+// sizes: wider partitions spread the per-partition cost over more keys)
+constexpr int kDepthSortItems = SPLASH_DEPTH_SORT_ITEMS;
+static_assert(kDepthSortItems >= kSortItems, "the scratch is sized for kSortTile partitions");
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 
@@ -153,14 +160,17 @@ struct SortScratch {
     int64_t max_parts;
 };
 size_t sort_scratch_bytes(int64_t n_max);
+// opts the wide (depth) sort kernels in to their shared memory on the
+// current device; once per device before the first depth sort
+cudaError_t sort_prepare_device();
 void sort_scratch_carve(void *base, int64_t n_max, SortScratch *s);
 // Sorts n pairs (n read from n_dev when non-null, else n_host) on bits
 // [0, bits). Ping-pongs between (k0,v0) and (k1,v1); returns which buffer
 // pair holds the result (0 or 1). grid is sized from n_host, which must be
-// >= the device count.
+// >= the device count. items: keys per thread, kSortItems or kDepthSortItems.
 int sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *k0, uint32_t *v0, uint32_t *k1,
                uint32_t *v1, int64_t n_host, const uint32_t *n_dev, int bits, const SortScratch &s,
-               uint32_t *status, int spin_limit, int stall_part, cudaStream_t stream);
+               uint32_t *status, int spin_limit, int stall_part, cudaStream_t stream, int items = kSortItems);
 
 // ---- kernels by stage (launch wrappers)
 void launch_preprocess_fwd(int64_t n, const splash_gaussians &g, const float *medium, const CamK &cam,

@@ -1,9 +1,9 @@
 // Stable LSD radix sort of (uint32 key, uint32 value) pairs, onesweep form:
 // one kernel reads all keys once to build the digit histograms of every
-// pass; then one kernel per 8-bit digit ranks a 4096-key partition in
-// shared memory, learns its global offset by decoupled look-back over the
-// partitions before it, and scatters. Each pass reads and writes every pair
-// once (16 B per pair per pass), which makes it HBM-bound.
+// pass; then one kernel per 8-bit digit ranks a partition of 256 x ITEMS
+// keys in shared memory, learns its global offset by decoupled look-back
+// over the partitions before it, and scatters. Each pass reads and writes
+// every pair once (16 B per pair per pass).
 //
 // The rasterizer needs the per-tile lists ordered by depth (Sec. III-A: the
 // Gaussians of a pixel are composited in increasing depth). It sorts the
@@ -93,8 +93,10 @@ __global__ void __launch_bounds__(256) k_hist(const uint32_t *__restrict__ keys,
     for (int p = 0; p < passes; p++) scan_digits(hist + p * kRadix, s_w);
 }
 
-// BITS: the digit width of this pass (its number of ballots per key)
-template <int BITS>
+// BITS: the digit width of this pass (its number of ballots per key);
+// ITEMS: keys per thread (the partition is kSortThreads * ITEMS keys, staged
+// for the scatter in dynamic shared memory)
+template <int BITS, int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t n_host, const uint32_t *__restrict__ n_dev, int shift, uint32_t mask,
@@ -105,25 +107,26 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     __shared__ uint32_t s_doff[kRadix];           // block-local exclusive digit offsets
     __shared__ uint32_t s_gbase[kRadix];          // global position of each digit's first key
     __shared__ uint32_t s_wsum[kWarps];
-    __shared__ uint32_t s_keys[kSortTile];
-    __shared__ uint32_t s_vals[kSortTile];
     __shared__ uint32_t s_part;
+    extern __shared__ uint32_t s_stage[];
+    constexpr int kTile = kSortThreads * ITEMS;
+    uint32_t *s_keys = s_stage, *s_vals = s_stage + kTile;
 
     if (threadIdx.x == 0) s_part = atomicAdd(counter, 1u);  // partitions start in ticket order
     for (int e = threadIdx.x; e < kWarps * kRadix; e += kSortThreads) (&s_whist[0][0])[e] = 0u;
     __syncthreads();
     const uint32_t part = s_part;
     const int64_t n = n_dev ? (int64_t)*n_dev : n_host;
-    const int64_t base = (int64_t)part * kSortTile;
+    const int64_t base = (int64_t)part * kTile;
     if (base >= n) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t wbase = base + (int64_t)warp * 32 * kSortItems;
+    const int64_t wbase = base + (int64_t)warp * 32 * ITEMS;
     const uint32_t lt = (1u << lane) - 1u;
 
     // warp-striped loads: item j of lane l is key wbase + 32 j + l (input order)
-    uint32_t k[kSortItems], v[kSortItems], rank[kSortItems];
+    uint32_t k[ITEMS], v[ITEMS], rank[ITEMS];
 #pragma unroll
-    for (int j = 0; j < kSortItems; j++) {
+    for (int j = 0; j < ITEMS; j++) {
         const int64_t idx = wbase + 32 * j + lane;
         const bool ok = idx < n;
         k[j] = ok ? kin[idx] : 0xffffffffu;  // past the end: largest digit, ranked last
@@ -132,7 +135,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     // stable rank within the warp: lanes with equal digits, from one ballot per digit bit
     uint32_t *wh = s_whist[warp];
 #pragma unroll
-    for (int j = 0; j < kSortItems; j++) {
+    for (int j = 0; j < ITEMS; j++) {
         const uint32_t d = (k[j] >> shift) & mask;
         uint32_t peers = 0xffffffffu;
 #pragma unroll
@@ -204,7 +207,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
 
     // scatter into shared memory in block-sorted order
 #pragma unroll
-    for (int j = 0; j < kSortItems; j++) {
+    for (int j = 0; j < ITEMS; j++) {
         const uint32_t d = (k[j] >> shift) & mask;
         const uint32_t slot = s_doff[d] + s_whist[warp][d] + rank[j];
         s_keys[slot] = k[j];
@@ -212,7 +215,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     }
     __syncthreads();
     // runs of equal digits go to consecutive global addresses
-    const int nvalid = (int)min((int64_t)kSortTile, n - base);
+    const int nvalid = (int)min((int64_t)kTile, n - base);
     for (int s = threadIdx.x; s < nvalid; s += kSortThreads) {
         const uint32_t kk = s_keys[s];
         const uint32_t d = (kk >> shift) & mask;
@@ -250,9 +253,50 @@ void sort_scratch_carve(void *base, int64_t n_max, SortScratch *s)
     s->max_parts = parts;
 }
 
+namespace {
+
+using OnesweepFn = void (*)(const uint32_t *, const uint32_t *, uint32_t *, uint32_t *, int64_t, const uint32_t *, int,
+                           uint32_t, const uint32_t *, uint32_t *, uint32_t *, uint32_t *, int, uint32_t);
+
+template <int ITEMS>
+OnesweepFn onesweep_for(int pbits)
+{
+    switch (pbits) {
+    case 1: return k_onesweep<1, ITEMS>;
+    case 2: return k_onesweep<2, ITEMS>;
+    case 3: return k_onesweep<3, ITEMS>;
+    case 4: return k_onesweep<4, ITEMS>;
+    case 5: return k_onesweep<5, ITEMS>;
+    case 6: return k_onesweep<6, ITEMS>;
+    case 7: return k_onesweep<7, ITEMS>;
+    default: return k_onesweep<8, ITEMS>;
+    }
+}
+
+// the partition's key and value staging (dynamic shared memory)
+OnesweepFn onesweep_kernel(int pbits, int items, size_t *smem)
+{
+    *smem = sizeof(uint32_t) * 2 * (size_t)kSortThreads * (size_t)items;
+    return items == kDepthSortItems ? onesweep_for<kDepthSortItems>(pbits) : onesweep_for<kSortItems>(pbits);
+}
+
+}  // namespace
+
+cudaError_t sort_prepare_device()
+{
+    // with its static arrays the wide form passes the default 48 KB window
+    const int smem = (int)(sizeof(uint32_t) * 2 * (size_t)kSortThreads * (size_t)kDepthSortItems);
+    for (int pbits = 1; pbits <= kRadixBits; pbits++) {
+        const cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(onesweep_for<kDepthSortItems>(pbits)),
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 int sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
                int64_t n_host, const uint32_t *n_dev, int bits, const SortScratch &s, uint32_t *status, int spin_limit,
-               int stall_part, cudaStream_t stream)
+               int stall_part, cudaStream_t stream, int items)
 {
     if (n_host <= 0) return 0;
     const int passes = (bits + kRadixBits - 1) / kRadixBits;
@@ -262,7 +306,9 @@ int sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *k0, u
         count_launch();
         return 0;
     }
-    const int64_t parts = (n_host + kSortTile - 1) / kSortTile;
+    if (items != kDepthSortItems) items = kSortItems;
+    const int64_t tile = (int64_t)kSortThreads * items;
+    const int64_t parts = (n_host + tile - 1) / tile;  // at most the scratch's kSortTile-sized count
     cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * (4 * kRadix + 64), stream);
     // look-back flags of every pass; pass p uses rows [p * parts, (p + 1) * parts)
     cudaMemsetAsync(s.lookback, 0, sizeof(uint32_t) * (size_t)passes * (size_t)parts * kRadix, stream);
@@ -274,20 +320,11 @@ int sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *k0, u
         uint32_t *ko = (p & 1) ? k1 : k0, *vo = (p & 1) ? v1 : v0;
         const int pbits = std::min(kRadixBits, bits - kRadixBits * p);
         const uint32_t mask = (1u << pbits) - 1u;
-        auto kern = k_onesweep<8>;
-        switch (pbits) {
-        case 1: kern = k_onesweep<1>; break;
-        case 2: kern = k_onesweep<2>; break;
-        case 3: kern = k_onesweep<3>; break;
-        case 4: kern = k_onesweep<4>; break;
-        case 5: kern = k_onesweep<5>; break;
-        case 6: kern = k_onesweep<6>; break;
-        case 7: kern = k_onesweep<7>; break;
-        default: break;
-        }
-        kern<<<(unsigned)parts, kSortThreads, 0, stream>>>(ki, vi, ko, vo, n_host, n_dev, kRadixBits * p, mask,
-                                                           s.hist + kRadix * p, s.lookback + (size_t)p * parts * kRadix,
-                                                           s.counters + p, status, spin_limit, (uint32_t)stall_part);
+        size_t smem = 0;
+        const OnesweepFn kern = onesweep_kernel(pbits, items, &smem);
+        kern<<<(unsigned)parts, kSortThreads, smem, stream>>>(ki, vi, ko, vo, n_host, n_dev, kRadixBits * p, mask,
+                                                              s.hist + kRadix * p, s.lookback + (size_t)p * parts * kRadix,
+                                                              s.counters + p, status, spin_limit, (uint32_t)stall_part);
         count_launch();
         ki = ko;
         vi = vo;
