@@ -312,7 +312,9 @@ int sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *k0, u
     cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * (4 * kRadix + 64), stream);
     // look-back flags of every pass; pass p uses rows [p * parts, (p + 1) * parts)
     cudaMemsetAsync(s.lookback, 0, sizeof(uint32_t) * (size_t)passes * (size_t)parts * kRadix, stream);
-    const int hblocks = (int)std::min<int64_t>((n_host / 4 + 255) / 256 + 1, 148 * 8);
+    // every CTA flushes up to 4 x 256 counters with global atomics onto the same
+    // addresses: 4 CTAs per SM keeps that contention below the cost of reading
+    const int hblocks = (int)std::min<int64_t>((n_host / 4 + 255) / 256 + 1, 148 * 4);
     k_hist<<<hblocks, 256, 0, stream>>>(keys_in, n_host, n_dev, bits, s.hist, s.counters + 4);  // zeroed above
     count_launch();
     const uint32_t *ki = keys_in, *vi = vals_in;

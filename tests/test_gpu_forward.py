@@ -112,11 +112,18 @@ def test_one_pixel_image(renderer):
     compare_forward(gpu_forward(renderer, g, m, cam), oracle.render(g, m, cam), label="1x1")
 
 
-def test_binning_and_sort_bit_exact(renderer):
+@pytest.mark.parametrize("n,z_step", [(4000, 0.0), (5 * 5120 + 77, 0.25)])
+def test_binning_and_sort_bit_exact(renderer, n, z_step):
     """Emitted pairs = the tiles of each Gaussian's rectangle; the sorted
     order equals a CPU stable sort of 64-bit (tile << 32 | depth bits) keys
-    emitted in Gaussian-index order; ranges equal a linear scan."""
-    g, m, cam = _box_scene(41, 4000, 203, 157, 150.0, 3, log_scale=-2.2)
+    emitted in Gaussian-index order; ranges equal a linear scan. The second
+    case spans several depth-sort partitions with a ragged last one, and its
+    depths sit on planes z_step apart (the camera looks down +z from the
+    origin), so that thousands of Gaussians share one depth key and their
+    order within a tile is decided by the sorts' stability alone."""
+    g, m, cam = _box_scene(41, n, 203, 157, 150.0, 3, log_scale=-2.2)
+    if z_step:
+        g.means[:, 2] = np.round(g.means[:, 2] / z_step) * z_step
     out = gpu_forward(renderer, g, m, cam)
     st = out["state"]
     info = renderer.info(st)
@@ -140,6 +147,8 @@ def test_binning_and_sort_bit_exact(renderer):
                 ids.append(i)
     keys = np.array(keys, np.uint64)
     ids = np.array(ids, np.uint32)
+    if z_step:
+        assert np.unique(dk[tt > 0]).size <= 25  # few distinct depth keys: many ties
     order = np.argsort(keys, kind="stable")
     assert info["n_keys"] == keys.size
     np.testing.assert_array_equal(tids, (keys[order] >> np.uint64(32)).astype(np.uint32))
