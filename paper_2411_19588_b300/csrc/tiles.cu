@@ -202,13 +202,21 @@ __global__ void __launch_bounds__(256) k_ranges(int64_t k_host, const uint32_t *
         range_ends(i, tile_ids[i], i > 0 ? tile_ids[i - 1] : 0u, i + 1 < k ? tile_ids[i + 1] : 0u, k, ranges, ntiles);
 }
 
-// total of the tile counts (the pair count K), one atomic per warp
+// total of the tile counts (the pair count K), one atomic per CTA (all of
+// them land on one address)
 __global__ void __launch_bounds__(256) k_sum_u32(const uint32_t *__restrict__ v, int64_t n, uint32_t *__restrict__ total)
 {
+    __shared__ uint32_t s_w[8];
     uint32_t acc = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) acc += v[i];
     acc = __reduce_add_sync(0xffffffffu, acc);
-    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(total, acc);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t x = threadIdx.x < 8 ? s_w[threadIdx.x] : 0u;
+        x = __reduce_add_sync(0xffffffffu, x);
+        if (threadIdx.x == 0 && x) atomicAdd(total, x);
+    }
 }
 
 }  // namespace
