@@ -30,7 +30,12 @@ PROJ_FIELDS = ["vis", "x", "y", "KA", "KB", "KC", "SA", "SB", "SC", "opac", "col
                "a_r", "a_g", "a_b", "b_r", "b_g", "b_b", "d", "raw_r", "raw_g", "raw_b", "cull_margin",
                "tx", "ty", "gmargin"]
 PIX_FIELDS = ["r", "g", "b", "depth", "depth01", "T_f", "n_contrib", "acc", "margin", "gmargin", "tie",
-              "n_cand", "dsum", "n_iter"]
+              "n_cand", "dsum", "n_iter", "n_near"]
+BRANCH_FIELDS = ["r", "g", "b", "depth", "depth01", "T_f", "n_contrib", "valid"]
+# A decision (3-sigma cut, alpha skip, transmittance stop, FP32 depth order)
+# whose FP64 quantity lies within NEAR (relative) of its threshold may be
+# taken either way by an FP32 evaluation of the same definition.
+NEAR = 1e-5
 
 
 def lib():
@@ -42,14 +47,18 @@ def lib():
         ip = ctypes.POINTER(ctypes.c_int64)
         i64, ci, cd = ctypes.c_int64, ctypes.c_int, ctypes.c_double
         L.oracle_project.argtypes = [i64, dp, dp, dp, dp, dp, ci, dp, dp, dp, ci]
-        L.oracle_render.argtypes = [i64, dp, dp, dp, dp, dp, ci, dp, dp, i64, ip, dp, ci]
-        L.oracle_backward.argtypes = [i64, dp, dp, dp, dp, dp, ci, dp, dp, i64, ip, dp, dp, dp, dp, dp, dp, dp, dp, ci]
+        L.oracle_render.argtypes = [i64, dp, dp, dp, dp, dp, ci, dp, dp, i64, ip, cd, dp, ci]
+        L.oracle_render_branches.argtypes = [i64, dp, dp, dp, dp, dp, ci, dp, dp, i64, ip, cd, dp, ci]
+        L.oracle_backward.argtypes = [i64, dp, dp, dp, dp, dp, ci, dp, dp, i64, ip, dp, ip, cd,
+                                      dp, dp, dp, dp, dp, dp, dp, ci]
         L.oracle_composite.argtypes = [i64, dp, dp, dp, dp, cd, dp]
         L.oracle_sh_basis.argtypes = [ci, dp, dp]
-        for f in (L.oracle_project, L.oracle_render, L.oracle_backward, L.oracle_composite, L.oracle_sh_basis):
+        for f in (L.oracle_project, L.oracle_render, L.oracle_render_branches, L.oracle_backward,
+                  L.oracle_composite, L.oracle_sh_basis):
             f.restype = ci
         _NPROJ, _NPIX, _NGP = L.oracle_nproj(), L.oracle_npix(), L.oracle_ngproj()
         assert _NPROJ == len(PROJ_FIELDS) and _NPIX == len(PIX_FIELDS)
+        assert L.oracle_nbf() == len(BRANCH_FIELDS)
         _lib = L
     return _lib
 
@@ -85,14 +94,15 @@ def _pix(cam, pix):
     return int(p.size), p, p.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
 
 
-def render(g, medium, cam, pix=None, nthreads: int = 0) -> dict:
+def render(g, medium, cam, pix=None, nthreads: int = 0, near: float = NEAR) -> dict:
     """Render every pixel (``pix=None``; arrays shaped (H, W), image (3, H, W))
-    or the listed linear pixel indices (arrays shaped (npix,), image (3, npix))."""
+    or the listed linear pixel indices (arrays shaped (npix,), image (3, npix)).
+    ``n_near`` counts each pixel's decisions within ``near`` of a threshold."""
     L = lib()
     arrs, med, c = _params(g, medium, cam)
     npix, p, pp = _pix(cam, pix)
     out = np.zeros((npix, _NPIX), np.float64)
-    rc = L.oracle_render(g.n, *[q for _, q in arrs], g.sh_degree, med[1], c[1], npix, pp,
+    rc = L.oracle_render(g.n, *[q for _, q in arrs], g.sh_degree, med[1], c[1], npix, pp, float(near),
                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nthreads)
     if rc != 0:
         raise RuntimeError(f"oracle_render failed: {rc}")
@@ -102,10 +112,36 @@ def render(g, medium, cam, pix=None, nthreads: int = 0) -> dict:
     return res
 
 
-def backward(g, medium, cam, dL_dimage, dL_ddepth=None, dL_ddepth01=None, pix=None, nthreads: int = 0) -> dict:
+def branches(g, medium, cam, pix, nthreads: int = 0, near: float = NEAR) -> dict:
+    """Every branch of the listed linear pixel indices: each field shaped
+    (npix, NBRANCH). Branch b takes near decision i (in the FP64 walk's order)
+    the other way when bit i of b is set; branch 0 is ``render``'s result.
+    ``valid`` marks the 2^k branches of a pixel with k <= log2(NBRANCH) near
+    decisions (branch 0 alone when it has more)."""
+    L = lib()
+    arrs, med, c = _params(g, medium, cam)
+    p = np.ascontiguousarray(pix, dtype=np.int64).reshape(-1)
+    nb = L.oracle_nbranch()
+    out = np.zeros((p.size, nb, len(BRANCH_FIELDS)), np.float64)
+    rc = L.oracle_render_branches(g.n, *[q for _, q in arrs], g.sh_degree, med[1], c[1], p.size,
+                                  p.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), float(near),
+                                  out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nthreads)
+    if rc != 0:
+        raise RuntimeError(f"oracle_render_branches failed: {rc}")
+    res = {k: out[:, :, i] for i, k in enumerate(BRANCH_FIELDS)}
+    res["image"] = np.stack([res["r"], res["g"], res["b"]])
+    res["valid"] = res["valid"] > 0
+    return res
+
+
+def backward(g, medium, cam, dL_dimage, dL_ddepth=None, dL_ddepth01=None, pix=None, nthreads: int = 0,
+             branch=None, near: float = NEAR) -> dict:
     """Gradients of L = <dL_dimage, C> + <dL_ddepth, z> + <dL_ddepth01, z01>
     with respect to every parameter (FP64 analytic adjoint). Upstream arrays
-    are (3, H, W)/(H, W) for ``pix=None`` or (3, npix)/(npix,) otherwise."""
+    are (3, H, W)/(H, W) for ``pix=None`` or (3, npix)/(npix,) otherwise.
+    ``branch`` (optional, one int per pixel, shaped like a depth map) picks the
+    branch of each pixel's near decisions whose adjoint is taken (see
+    ``branches``); 0 everywhere is the FP64 walk."""
     L = lib()
     arrs, med, c = _params(g, medium, cam)
     npix, p, pp = _pix(cam, pix)
@@ -120,8 +156,10 @@ def backward(g, medium, cam, dL_dimage, dL_ddepth=None, dL_ddepth01=None, pix=No
            "opacity_logits": np.zeros(g.n), "sh": np.zeros((g.n, K, 3)), "medium": np.zeros(9),
            "proj": np.zeros((g.n, _NGP))}
     ptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    br = None if branch is None else np.ascontiguousarray(np.asarray(branch).reshape(npix), np.int64)
+    bp = None if br is None else br.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
     rc = L.oracle_backward(g.n, *[q for _, q in arrs], g.sh_degree, med[1], c[1], npix, pp, ptr(gout),
-                           ptr(res["means"]), ptr(res["log_scales"]), ptr(res["quats"]), ptr(res["opacity_logits"]),
+                           bp, float(near), ptr(res["means"]), ptr(res["log_scales"]), ptr(res["quats"]), ptr(res["opacity_logits"]),
                            ptr(res["sh"]), ptr(res["medium"]), ptr(res["proj"]), nthreads)
     if rc != 0:
         raise RuntimeError(f"oracle_backward failed: {rc}")

@@ -48,21 +48,47 @@ def stat_increment(g_proj_xy, width: int, height: int) -> np.ndarray:
     return np.hypot(g[:, 0] * width / 2.0, g[:, 1] * height / 2.0)
 
 
-def classify(log_scales, opacity_logits, stats, threshold=THRESHOLD, min_opacity=MIN_OPACITY, dense=1.0):
-    """Action per Gaussian. The three integer decisions are taken in FP32
-    on the stored values (the kernel's precision): opacity below
-    min_opacity as logit < fl32(logit(min_opacity)), size as max log-scale >
-    fl32(log(dense)), selection as fl32(accum / max(count, 1)) >= fl32(threshold)."""
-    ls = np.asarray(log_scales, np.float32)
-    lg = np.asarray(opacity_logits, np.float32)
-    st = np.asarray(stats, np.float32)
-    avg = st[:, 0] / np.maximum(st[:, 1], np.float32(1.0))
-    big = ls.max(axis=1) > np.float32(math.log(dense))
-    sel = avg >= np.float32(threshold)
-    act = np.full(len(lg), KEEP, np.int64)
+def _decisions(log_scales, opacity_logits, stats, threshold, min_opacity, dense):
+    """The three decisions of every Gaussian, each taken in FP64 on its
+    definition, with its relative distance to the threshold:
+    low opacity sigmoid(o) < min_opacity, selection mean gradient >=
+    threshold, size max(exp(s)) > dense."""
+    ls = np.asarray(log_scales, np.float64)
+    lg = np.asarray(opacity_logits, np.float64)
+    st = np.asarray(stats, np.float64).reshape(-1, 2)
+    opac = 1.0 / (1.0 + np.exp(-lg))
+    avg = st[:, 0] / np.maximum(st[:, 1], 1.0)
+    size = np.exp(ls.max(axis=1)) if len(ls) else np.zeros(0)
+    take = np.stack([opac < min_opacity, avg >= threshold, size > dense], 1)
+    dist = np.stack([np.abs(opac - min_opacity) / min_opacity, np.abs(avg - threshold) / threshold,
+                     np.abs(size - dense) / dense], 1)
+    return take, dist
+
+
+LOW_OPACITY, SELECTED, LARGE = 1, 2, 4
+
+
+def decision_margins(log_scales, opacity_logits, stats, threshold=THRESHOLD, min_opacity=MIN_OPACITY, dense=1.0):
+    """[n, 3] relative distances of the low-opacity, selection and size
+    decisions to their thresholds (bits LOW_OPACITY, SELECTED, LARGE of a flip
+    mask, in that order)."""
+    return _decisions(log_scales, opacity_logits, stats, threshold, min_opacity, dense)[1]
+
+
+def classify(log_scales, opacity_logits, stats, threshold=THRESHOLD, min_opacity=MIN_OPACITY, dense=1.0, flip=None):
+    """Action per Gaussian from the three FP64 decisions. ``flip`` (optional,
+    one bit mask per Gaussian of LOW_OPACITY | SELECTED | LARGE) takes the
+    named decisions the other way: where a decision lies within rounding of
+    its threshold an FP32 evaluation may take either outcome."""
+    take, _ = _decisions(log_scales, opacity_logits, stats, threshold, min_opacity, dense)
+    if flip is not None:
+        f = np.asarray(flip, np.int64).reshape(-1)
+        take = take ^ np.stack([(f & LOW_OPACITY) > 0, (f & SELECTED) > 0, (f & LARGE) > 0], 1)
+    low, sel, big = take[:, 0], take[:, 1], take[:, 2]
+    act = np.full(len(take), KEEP, np.int64)
     act[sel & ~big] = CLONE
     act[sel & big] = SPLIT
-    act[lg < np.float32(math.log(min_opacity / (1.0 - min_opacity)))] = PRUNE
+    act[low] = PRUNE
     return act
 
 

@@ -14,8 +14,7 @@ Definitions (each is the plain statement of what the CUDA path computes):
   - an 8-bin histogram of z over [0, z_far]: bin = floor(fl32(fl32(8 z) /
     z_far)) clamped to [0, 7] (the integer decision is taken in FP32 on
     both sides), divided by H W;
-  - order: [channel][i][j] (3072 values), then the 8 bins, then a constant
-    1 (the bias input), then zeros up to K1 = 3136 columns; stored as BF16.
+  - order: [channel][i][j] (3072 values), then the 8 bins; stored as BF16.
 * MLP 3080 -> 128 -> 128 -> 9 with ReLU hidden layers. Every weight matrix
   carries its bias as one more input column that multiplies a constant 1.
   Weights are FP32 masters used as BF16 copies; products are summed in
@@ -39,9 +38,7 @@ GRID = 32
 N_BINS = 8
 N_IMG = 3 * GRID * GRID          # 3072
 N_IN = N_IMG + N_BINS            # 3080 features
-K1 = 3136                        # padded input width (features, bias 1, zeros)
 HID = 128
-K2 = 192                         # padded hidden width (128 units, bias 1, zeros)
 N_OUT = 9
 
 
@@ -98,12 +95,9 @@ def features(image, depth, z_far) -> np.ndarray:
     return np.concatenate([downsample(image).ravel(), depth_histogram(depth, z_far)])
 
 
-def feature_row(image, depth, z_far) -> np.ndarray:
-    """The stored row [K1]: BF16-rounded features, the bias input 1, zeros."""
-    row = np.zeros(K1)
-    row[:N_IN] = bf16_round(features(image, depth, z_far))
-    row[N_IN] = 1.0
-    return row
+def stored_features(image, depth, z_far) -> np.ndarray:
+    """The stored feature vector [3080]: the features rounded to BF16."""
+    return bf16_round(features(image, depth, z_far))
 
 
 # ----------------------------------------------------------------------- MLP

@@ -67,8 +67,10 @@ enum {
 /* per-pixel fields written by oracle_render */
 enum {
     O_R, O_G, O_B, O_DEPTH, O_DEPTH01, O_TF, O_NCONTRIB, O_ACC, O_MARGIN,
-    O_GMARGIN, O_TIE, O_NCAND, O_DSUM, O_NITER, NPIX
+    O_GMARGIN, O_TIE, O_NCAND, O_DSUM, O_NITER, O_NNEAR, NPIX
 };
+/* per-branch fields written by oracle_render_branches */
+enum { B_R, B_G, B_B, B_DEPTH, B_DEPTH01, B_TF, B_NCONTRIB, B_VALID, NBF };
 
 int oracle_nproj(void) { return NPROJ; }
 int oracle_npix(void) { return NPIX; }
@@ -370,6 +372,63 @@ static void scratch_reserve(scratch_t *s, int64_t need)
     s->cap = cap;
 }
 
+/* The discrete decisions a pixel takes: the 3-sigma cut of a Gaussian, the
+ * alpha < 1/255 skip, the transmittance stop, and the order of Gaussians
+ * whose depths are equal at FP32 resolution. A renderer that evaluates the
+ * same definition in FP32 may take a decision the other way when its FP64
+ * quantity lies within rounding of the threshold; either outcome is then a
+ * render of the definition at that precision. The oracle lists the decisions
+ * of a pixel whose quantity lies within a relative distance `rel` of the
+ * threshold ("near" decisions) and can evaluate the pixel under any
+ * combination of their outcomes (a branch; branch 0 takes every decision as
+ * FP64 does). For the order, the one alternative is the order of the FP32
+ * depths, ties to the lower index. */
+enum { D_CUT, D_SKIP, D_STOP, D_ORDER };
+#define NEAR_MAX 4
+#define NBR (1 << NEAR_MAX)
+typedef struct { int kind; int64_t id; } decision_t;
+typedef struct {
+    double rel;              /* relative distance to a threshold counted as near */
+    int n;                   /* near decisions found (may exceed NEAR_MAX) */
+    decision_t d[NEAR_MAX];  /* the first NEAR_MAX of them, in walk order */
+} near_t;
+typedef struct { int n; decision_t d[NEAR_MAX]; } flips_t;
+
+static int flipped(const flips_t *f, int kind, int64_t id)
+{
+    if (!f) return 0;
+    for (int i = 0; i < f->n; i++)
+        if (f->d[i].kind == kind && f->d[i].id == id) return 1;
+    return 0;
+}
+
+static void note_near(near_t *nr, int kind, int64_t id, double dist)
+{
+    if (!nr || !(dist < nr->rel)) return;
+    if (nr->n < NEAR_MAX) {
+        nr->d[nr->n].kind = kind;
+        nr->d[nr->n].id = id;
+    }
+    nr->n++;
+}
+
+/* the decisions a branch flips: bit i of b flips near decision i */
+static void branch_flips(const near_t *nr, int64_t b, flips_t *f)
+{
+    f->n = 0;
+    for (int i = 0; i < nr->n && i < NEAR_MAX; i++)
+        if ((b >> i) & 1) f->d[f->n++] = nr->d[i];
+}
+
+static int cand_cmp_f32(const void *pa, const void *pb)
+{
+    const cand_t *a = (const cand_t *)pa, *b = (const cand_t *)pb;
+    const float fa = (float)a->d, fb = (float)b->d;
+    if (fa < fb) return -1;
+    if (fa > fb) return 1;
+    return (a->id > b->id) - (a->id < b->id);
+}
+
 typedef struct {
     int64_t m;         /* contributors */
     int64_t ncand;     /* Gaussians within the 3-sigma ellipse */
@@ -381,18 +440,25 @@ typedef struct {
 } plist_t;
 
 /* Collect, sort and walk the Gaussians at pixel centre (px, py) with the
- * skip and stop rules; the contributors land in s->lst. */
+ * skip and stop rules; the contributors land in s->lst. `fl` (may be NULL)
+ * names the decisions taken the other way; `nr` (may be NULL) collects the
+ * near decisions of this walk. */
 static void pixel_list(const pg_t *P, const int64_t *vis, int64_t nvis, double px, double py, scratch_t *s,
-                       plist_t *out)
+                       plist_t *out, const flips_t *fl, near_t *nr)
 {
     int64_t nc = 0;
     double mg = INFINITY, gm = INFINITY;
+    if (nr) nr->n = 0;
     for (int64_t k = 0; k < nvis; k++) {
         const pg_t *g = &P[vis[k]];
         const double dx = px - g->x, dy = py - g->y;
         const double q = g->K[0] * dx * dx + 2.0 * g->K[1] * dx * dy + g->K[2] * dy * dy;
-        mg = fmin(mg, fabs(q - Q_MAX) / Q_MAX);
-        if (q <= Q_MAX) {
+        const double dist = fabs(q - Q_MAX) / Q_MAX;
+        mg = fmin(mg, dist);
+        note_near(nr, D_CUT, vis[k], dist);
+        int inside = q <= Q_MAX;
+        if (flipped(fl, D_CUT, vis[k])) inside = !inside;
+        if (inside) {
             scratch_reserve(s, nc + 1);
             s->cand[nc].d = g->d;
             s->cand[nc].id = vis[k];
@@ -402,7 +468,7 @@ static void pixel_list(const pg_t *P, const int64_t *vis, int64_t nvis, double p
             nc++;
         }
     }
-    qsort(s->cand, (size_t)nc, sizeof(cand_t), cand_cmp);
+    qsort(s->cand, (size_t)nc, sizeof(cand_t), flipped(fl, D_ORDER, -1) ? cand_cmp_f32 : cand_cmp);
     double T = 1.0, prev_d = -1.0;
     int64_t m = 0, it = 0, prev_id = -1;
     int tie = 0;
@@ -413,18 +479,29 @@ static void pixel_list(const pg_t *P, const int64_t *vis, int64_t nvis, double p
         const double alpha = araw < A_MAX ? araw : A_MAX;
         it++;
         gm = fmin(gm, fabs(araw - A_MAX) / A_MAX);
-        mg = fmin(mg, fabs(alpha - A_MIN) / A_MIN);
-        if (alpha < A_MIN) continue;
+        const double adist = fabs(alpha - A_MIN) / A_MIN;
+        mg = fmin(mg, adist);
+        note_near(nr, D_SKIP, cd->id, adist);
+        int skip = alpha < A_MIN;
+        if (flipped(fl, D_SKIP, cd->id)) skip = !skip;
+        if (skip) continue;
         /* An FP32 depth orders two Gaussians like their exact depths unless
          * both round to the same float, where ties go to the lower index
          * (rounding is monotonic). Flag the pixel when that index order
          * disagrees with the exact depth order of two alpha-valid neighbours. */
-        if (prev_id >= 0 && (float)cd->d == (float)prev_d && prev_id > cd->id) tie = 1;
+        if (prev_id >= 0 && (float)cd->d == (float)prev_d && prev_id > cd->id) {
+            if (!tie) note_near(nr, D_ORDER, -1, 0.0);
+            tie = 1;
+        }
         prev_d = cd->d;
         prev_id = cd->id;
         const double Tn = T * (1.0 - alpha);
-        mg = fmin(mg, fabs(Tn - T_STOP) / T_STOP);
-        if (Tn < T_STOP) break;
+        const double tdist = fabs(Tn - T_STOP) / T_STOP;
+        mg = fmin(mg, tdist);
+        note_near(nr, D_STOP, cd->id, tdist);
+        int stop = Tn < T_STOP;
+        if (flipped(fl, D_STOP, cd->id)) stop = !stop;
+        if (stop) break;
         gm = fmin(gm, g->gm);
         contrib_t *c = &s->lst[m++];
         c->id = cd->id;
@@ -495,9 +572,55 @@ static int64_t *visible_ids(const pg_t *P, int64_t n, int64_t *nvis)
     return vis;
 }
 
+/* Per-thread buffers of one pixel's composite. */
+typedef struct {
+    scratch_t s;
+    double *al, *co, *dd;
+    int64_t acap;
+} pixbuf_t;
+
+static void pixbuf_free(pixbuf_t *b)
+{
+    free(b->s.cand);
+    free(b->s.lst);
+    free(b->al);
+    free(b->co);
+    free(b->dd);
+}
+
+/* Walk one pixel (with the flipped decisions `fl`, collecting near ones into
+ * `nr`) and composite its contributors. res = r, g, b, depth, depth01, A, D. */
+static void render_pixel(const pg_t *P, const int64_t *vis, int64_t nvis, const cam_t *c, const double *med,
+                         int64_t p, const flips_t *fl, near_t *nr, pixbuf_t *b, plist_t *L, double *res)
+{
+    const double px = (double)(p % c->W) + 0.5, py = (double)(p / c->W) + 0.5;
+    pixel_list(P, vis, nvis, px, py, &b->s, L, fl, nr);
+    if (L->m > b->acap) {
+        b->acap = L->m * 2;
+        b->al = (double *)realloc(b->al, sizeof(double) * (size_t)b->acap);
+        b->co = (double *)realloc(b->co, sizeof(double) * 3 * (size_t)b->acap);
+        b->dd = (double *)realloc(b->dd, sizeof(double) * (size_t)b->acap);
+    }
+    for (int64_t i = 0; i < L->m; i++) {
+        const pg_t *g = &P[b->s.lst[i].id];
+        b->al[i] = b->s.lst[i].alpha;
+        b->dd[i] = g->d;
+        for (int ch = 0; ch < 3; ch++) b->co[3 * i + ch] = g->col[ch];
+    }
+    double Tf, D, A;
+    composite_segments(L->m, b->al, b->co, b->dd, med, c->zfar, res, &Tf, &D, &A);
+    res[3] = depth_of(D, A, c->zfar);
+    res[4] = logistic01(res[3]);
+    res[5] = A;
+    res[6] = D;
+}
+
+/* Render every pixel (pix = NULL) or the npix listed linear pixel indices.
+ * near_rel: the relative distance to a threshold that counts a decision as
+ * near (the O_NNEAR field). */
 int oracle_render(int64_t n, const double *means, const double *ls, const double *quats, const double *ologits,
                   const double *sh, int deg, const double *med, const double *cam, int64_t npix,
-                  const int64_t *pix, double *out, int nthreads)
+                  const int64_t *pix, double near_rel, double *out, int nthreads)
 {
     if (n < 0 || deg < 0 || deg > 3) return -1;
     cam_t c;
@@ -512,52 +635,89 @@ int oracle_render(int64_t n, const double *means, const double *ls, const double
 #pragma omp parallel num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
 #endif
     {
-        scratch_t s = {0};
-        double *al = NULL, *co = NULL, *dd = NULL;
-        int64_t acap = 0;
+        pixbuf_t b = {0};
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 16)
 #endif
         for (int64_t k = 0; k < npix; k++) {
-            const int64_t p = pix ? pix[k] : k;
-            const double px = (double)(p % c.W) + 0.5, py = (double)(p / c.W) + 0.5;
             plist_t L;
-            pixel_list(P, vis, nvis, px, py, &s, &L);
-            if (L.m > acap) {
-                acap = L.m * 2;
-                al = (double *)realloc(al, sizeof(double) * (size_t)acap);
-                co = (double *)realloc(co, sizeof(double) * 3 * (size_t)acap);
-                dd = (double *)realloc(dd, sizeof(double) * (size_t)acap);
-            }
-            for (int64_t i = 0; i < L.m; i++) {
-                const pg_t *g = &P[s.lst[i].id];
-                al[i] = s.lst[i].alpha;
-                dd[i] = g->d;
-                for (int ch = 0; ch < 3; ch++) co[3 * i + ch] = g->col[ch];
-            }
-            double rgb[3], Tf, D, A;
-            composite_segments(L.m, al, co, dd, med, c.zfar, rgb, &Tf, &D, &A);
+            near_t nr = {near_rel, 0, {{0, 0}}};
+            double res[7];
+            render_pixel(P, vis, nvis, &c, med, pix ? pix[k] : k, NULL, &nr, &b, &L, res);
             double *o = out + (size_t)NPIX * k;
-            o[O_R] = rgb[0];
-            o[O_G] = rgb[1];
-            o[O_B] = rgb[2];
-            o[O_DEPTH] = depth_of(D, A, c.zfar);
-            o[O_DEPTH01] = logistic01(o[O_DEPTH]);
-            o[O_TF] = Tf;
+            o[O_R] = res[0];
+            o[O_G] = res[1];
+            o[O_B] = res[2];
+            o[O_DEPTH] = res[3];
+            o[O_DEPTH01] = res[4];
+            o[O_TF] = L.Tf;
             o[O_NCONTRIB] = (double)L.m;
-            o[O_ACC] = A;
+            o[O_ACC] = res[5];
             o[O_MARGIN] = L.margin;
             o[O_GMARGIN] = L.gmargin;
             o[O_TIE] = L.tie;
             o[O_NCAND] = (double)L.ncand;
-            o[O_DSUM] = D;
+            o[O_DSUM] = res[6];
             o[O_NITER] = (double)L.niter;
+            o[O_NNEAR] = (double)nr.n;
         }
-        free(s.cand);
-        free(s.lst);
-        free(al);
-        free(co);
-        free(dd);
+        pixbuf_free(&b);
+    }
+    free(vis);
+    free(P);
+    return 0;
+}
+
+int oracle_nbranch(void) { return NBR; }
+int oracle_nbf(void) { return NBF; }
+
+/* Every branch of the listed pixels: out[k][b][NBF] for b < NBR. Branch b
+ * takes near decision i the other way when bit i of b is set; B_VALID is 1
+ * for the 2^k branches of a pixel with k <= NEAR_MAX near decisions (branch
+ * 0 alone when it has more). */
+int oracle_render_branches(int64_t n, const double *means, const double *ls, const double *quats,
+                           const double *ologits, const double *sh, int deg, const double *med, const double *cam,
+                           int64_t npix, const int64_t *pix, double near_rel, double *out, int nthreads)
+{
+    if (n < 0 || deg < 0 || deg > 3 || npix < 0 || (npix > 0 && !pix)) return -1;
+    cam_t c;
+    cam_load(cam, &c);
+    pg_t *P = (pg_t *)malloc(sizeof(pg_t) * (size_t)(n > 0 ? n : 1));
+    if (!P) return -2;
+    project_all(&c, n, means, ls, quats, ologits, sh, deg, med, P, nthreads);
+    int64_t nvis;
+    int64_t *vis = visible_ids(P, n, &nvis);
+    memset(out, 0, sizeof(double) * (size_t)npix * NBR * NBF);
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
+#endif
+    {
+        pixbuf_t b = {0};
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int64_t k = 0; k < npix; k++) {
+            plist_t L;
+            near_t nr = {near_rel, 0, {{0, 0}}};
+            double res[7];
+            render_pixel(P, vis, nvis, &c, med, pix[k], NULL, &nr, &b, &L, res);
+            const int64_t nb = nr.n <= NEAR_MAX ? ((int64_t)1 << nr.n) : 1;
+            for (int64_t br = 0; br < nb; br++) {
+                flips_t fl;
+                branch_flips(&nr, br, &fl);
+                render_pixel(P, vis, nvis, &c, med, pix[k], &fl, NULL, &b, &L, res);
+                double *o = out + ((size_t)k * NBR + (size_t)br) * NBF;
+                o[B_R] = res[0];
+                o[B_G] = res[1];
+                o[B_B] = res[2];
+                o[B_DEPTH] = res[3];
+                o[B_DEPTH01] = res[4];
+                o[B_TF] = L.Tf;
+                o[B_NCONTRIB] = (double)L.m;
+                o[B_VALID] = 1.0;
+            }
+        }
+        pixbuf_free(&b);
     }
     free(vis);
     free(P);
@@ -781,8 +941,9 @@ static void gaussian_backward(const cam_t *c, const pg_t *g, const double *gp, c
 
 int oracle_backward(int64_t n, const double *means, const double *ls, const double *quats, const double *ologits,
                     const double *sh, int deg, const double *med, const double *cam, int64_t npix,
-                    const int64_t *pix, const double *gout, double *g_means, double *g_ls, double *g_quats,
-                    double *g_ologits, double *g_sh, double *g_med, double *g_proj, int nthreads)
+                    const int64_t *pix, const double *gout, const int64_t *branch, double near_rel,
+                    double *g_means, double *g_ls, double *g_quats, double *g_ologits, double *g_sh, double *g_med,
+                    double *g_proj, int nthreads)
 {
     if (n < 0 || deg < 0 || deg > 3) return -1;
     cam_t c;
@@ -811,7 +972,17 @@ int oracle_backward(int64_t n, const double *means, const double *ls, const doub
             const int64_t p = pix ? pix[k] : k;
             const double px = (double)(p % c.W) + 0.5, py = (double)(p / c.W) + 0.5;
             plist_t L;
-            pixel_list(P, vis, nvis, px, py, &s, &L);
+            const int64_t br = branch ? branch[k] : 0;
+            if (br == 0) {
+                pixel_list(P, vis, nvis, px, py, &s, &L, NULL, NULL);
+            } else {
+                /* the branch's flips name near decisions of the FP64 walk */
+                near_t nr = {near_rel, 0, {{0, 0}}};
+                flips_t fl;
+                pixel_list(P, vis, nvis, px, py, &s, &L, NULL, &nr);
+                branch_flips(&nr, br, &fl);
+                pixel_list(P, vis, nvis, px, py, &s, &L, &fl, NULL);
+            }
             pixel_backward(P, s.lst, L.m, L.Tf, med, c.zfar, G, gp, gmed);
         }
 #ifdef _OPENMP

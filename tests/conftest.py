@@ -21,3 +21,21 @@ def cuda_lib():
         pytest.fail("gpu test collected but CUDA is not available")
     from paper_2411_19588_b300 import _abi
     return _abi.lib()
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    """Print every image/depth parity comparison of the session: pixels
+    compared, near decisions, pixels resolved to another branch, pixels two
+    branches match, excluded pixels and their fraction, gradient upstream
+    zeroed."""
+    mod = sys.modules.get("parity")
+    log = getattr(mod, "PARITY_LOG", None) if mod else None
+    if not log:
+        return
+    terminalreporter.section("parity: excluded and branch-resolved pixels")
+    for s in log:
+        terminalreporter.write_line(
+            f"{s['label']}: {s['pixels']} px, near {s['near']}, other branch {s['alt_branch']}, "
+            f"two branches {s['multi']}, excluded {s['excluded']} ({s['excluded_frac']:.2e}), "
+            f"grad upstream zeroed {s.get('grad_zeroed', '-')}, img max {s['img_max']:.2e}, "
+            f"depth rel max {s['depth_rel_max']:.2e}")

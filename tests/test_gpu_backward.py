@@ -1,6 +1,8 @@
 """Backward parity of the CUDA rasterizer against the oracle's FP64 adjoint
-(itself pinned by FP64 central differences). Upstream gradients are zeroed
-at pixels close to a discrete decision or a gradient kink, on both sides."""
+(itself pinned by FP64 central differences), taken on the branch of each
+pixel's near decisions that the GPU's forward matched. Upstream gradients
+are zeroed, on both sides, only at pixels two branches match and at pixels
+near a gradient kink (counted in the session's parity summary)."""
 import numpy as np
 import pytest
 import torch
@@ -9,7 +11,7 @@ import oracle
 from paper_2411_19588_b300 import render as R
 from paper_2411_19588_b300 import scenes
 
-from parity import GMARGIN, MARGIN, compare_grads, gpu_forward, grads_to_numpy, medium_tensor
+from parity import compare_forward, compare_grads, gpu_forward, grads_to_numpy, medium_tensor, upstream_keep
 from test_gpu_forward import _box_scene
 
 pytestmark = pytest.mark.gpu
@@ -20,38 +22,38 @@ def renderer(cuda_lib):
     return R.Renderer()
 
 
-def _upstream(rng, ora, H, W, depth=True):
-    keep = (ora["margin"] >= MARGIN) & (ora["gmargin"] >= GMARGIN) & (ora["tie"] == 0)
+def _upstream(rng, keep, H, W, depth=True):
     G = rng.standard_normal((3, H, W)) * keep
     Gz = rng.standard_normal((H, W)) * 0.05 * keep if depth else np.zeros((H, W))
     G01 = rng.standard_normal((H, W)) * 0.3 * keep if depth else np.zeros((H, W))
     return G, Gz, G01, keep
 
 
-def _run(renderer, g, m, cam, seed, depth=True):
+def _run(renderer, g, m, cam, seed, depth=True, label="bwd"):
     gpu = gpu_forward(renderer, g, m, cam)
     ora = oracle.render(g, m, cam)
+    fwd = compare_forward(gpu, ora, label=label, scene=(g, m, cam))
     rng = np.random.default_rng(seed)
-    G, Gz, G01, keep = _upstream(rng, ora, cam.height, cam.width, depth)
+    G, Gz, G01, keep = _upstream(rng, upstream_keep(ora, fwd), cam.height, cam.width, depth)
     t = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda").contiguous()
     # the oracle sees exactly the FP32 upstream values the GPU sees
     G, Gz, G01 = (np.float64(np.float32(a)) for a in (G, Gz, G01))
     grads = renderer.backward(gpu["state"], gpu["params"], gpu["medium"], cam, t(G), t(Gz), t(G01))
     torch.cuda.synchronize()
-    ref = oracle.backward(g, m, cam, G, Gz, G01)
+    ref = oracle.backward(g, m, cam, G, Gz, G01, branch=fwd["branch"])
     return grads_to_numpy(grads), ref, keep
 
 
 def test_tiny_scene_gradients(renderer):
     g, m, cam = scenes.tiny_scene(0)
-    got, ref, keep = _run(renderer, g, m, cam, 1)
+    got, ref, keep = _run(renderer, g, m, cam, 1, label="bwd tiny")
     print("tiny", compare_grads(got, ref, "tiny"), "kept", keep.mean())
 
 
 @pytest.mark.parametrize("seed,W,H,deg", [(51, 100, 75, 3), (52, 61, 47, 1)])
 def test_ragged_gradients(renderer, seed, W, H, deg):
     g, m, cam = _box_scene(seed, 1500, W, H, 0.9 * W, deg, eye=(0.3, -0.2, -0.4), target=(0.1, 0.05, 4.0))
-    got, ref, _ = _run(renderer, g, m, cam, seed)
+    got, ref, _ = _run(renderer, g, m, cam, seed, label=f"bwd ragged{W}x{H}")
     print((W, H), compare_grads(got, ref, f"ragged{W}x{H}"))
 
 
@@ -63,7 +65,7 @@ def test_other_tile_shapes_gradients(cuda_lib, tile):
     r = R.Renderer(tile=tile)
     g, m, cam = _box_scene(71, 1500, 100, 75, 90.0, 3, eye=(0.3, -0.2, -0.4), target=(0.1, 0.05, 4.0))
     for depth in (True, False):
-        got, ref, _ = _run(r, g, m, cam, 71, depth)
+        got, ref, _ = _run(r, g, m, cam, 71, depth, label=f"bwd tile{tile[0]}x{tile[1]} depth={depth}")
         print(tile, depth, compare_grads(got, ref, f"tile{tile[0]}x{tile[1]}"))
 
 
@@ -71,13 +73,13 @@ def test_dense_overlap_gradients(renderer):
     """Long per-pixel lists: checks the back-to-front recomputation of T
     from the stored final transmittance."""
     g, m, cam = _box_scene(61, 2500, 80, 60, 70.0, 3, log_scale=-1.7)
-    got, ref, _ = _run(renderer, g, m, cam, 61)
+    got, ref, _ = _run(renderer, g, m, cam, 61, label="bwd dense")
     print("dense", compare_grads(got, ref, "dense"))
 
 
 def test_image_only_upstream(renderer):
     g, m, cam = _box_scene(71, 1200, 64, 48, 60.0, 2)
-    got, ref, _ = _run(renderer, g, m, cam, 71, depth=False)
+    got, ref, _ = _run(renderer, g, m, cam, 71, depth=False, label="bwd image-only")
     compare_grads(got, ref, "image-only")
 
 
@@ -90,8 +92,9 @@ def test_full_scene_sparse_upstream(renderer):
     rng = np.random.default_rng(8)
     pix = rng.choice(cam.width * cam.height, 200, replace=False)
     ora = oracle.render(g, m, cam, pix=pix)
-    keep = (ora["margin"] >= MARGIN) & (ora["gmargin"] >= GMARGIN) & (ora["tie"] == 0)
-    pix = pix[keep]
+    fwd = compare_forward(gpu, ora, pix=pix, label="bwd full", scene=(g, m, cam))
+    keep = upstream_keep(ora, fwd)
+    pix, branch = pix[keep], fwd["branch"][keep]
     H, W = cam.height, cam.width
     Gs = np.float64(np.float32(rng.standard_normal((3, pix.size))))
     Gzs = np.float64(np.float32(rng.standard_normal(pix.size) * 0.05))
@@ -104,7 +107,7 @@ def test_full_scene_sparse_upstream(renderer):
     grads = renderer.backward(gpu["state"], gpu["params"], gpu["medium"], cam, t(G.reshape(3, H, W)),
                               t(Gz.reshape(H, W)), t(G01.reshape(H, W)))
     torch.cuda.synchronize()
-    ref = oracle.backward(g, m, cam, Gs, Gzs, G01s, pix=pix)
+    ref = oracle.backward(g, m, cam, Gs, Gzs, G01s, pix=pix, branch=branch)
     assert np.abs(ref["means"]).sum() > 0
     print("full", compare_grads(grads_to_numpy(grads), ref, "full-sparse"))
 

@@ -13,7 +13,7 @@ from oracle import densify as OD
 from paper_2411_19588_b300 import render as R
 from paper_2411_19588_b300 import scenes, warmstart
 
-from parity import GMARGIN, MARGIN, medium_tensor
+from parity import compare_forward, gpu_forward, medium_tensor, upstream_keep
 
 pytestmark = pytest.mark.gpu
 
@@ -25,12 +25,11 @@ def renderer(cuda_lib):
 
 def test_statistics_match_the_oracle_screen_gradients(renderer):
     g, m, cam = scenes.tiny_scene(3)
-    params = R.params_to_device(g)
-    med = medium_tensor(m)
-    st = renderer.state()
-    renderer.forward(st, params, med, cam)
+    out = gpu_forward(renderer, g, m, cam)
+    st, params, med = out["state"], out["params"], out["medium"]
     ora = oracle.render(g, m, cam)
-    keep = (ora["margin"] >= MARGIN) & (ora["gmargin"] >= GMARGIN) & (ora["tie"] == 0)
+    fwd = compare_forward(out, ora, label="densify stats", scene=(g, m, cam))
+    keep = upstream_keep(ora, fwd)
     G = np.float64(np.float32(np.random.default_rng(3).standard_normal((3, cam.height, cam.width)) * keep))
     names = R.PARAM_NAMES + ("medium",)
     tens = dict(params)
@@ -42,7 +41,7 @@ def test_statistics_match_the_oracle_screen_gradients(renderer):
     renderer.backward_adam(st, params, med, cam, torch.tensor(G, dtype=torch.float32, device="cuda"), mo, ve,
                            warmstart.FIT_LR, 1, densify_stats=stats)
     got = stats.cpu().numpy().astype(np.float64)
-    ref = oracle.backward(g, m, cam, G)
+    ref = oracle.backward(g, m, cam, G, branch=fwd["branch"])
     # in the view: inside (z_near, z_far] and opaque enough ever to reach alpha >= 1/255
     vis = (oracle.project(g, m, cam)["vis"] > 0) & (1 / (1 + np.exp(-g.opacity_logits.astype(np.float64))) >= 1 / 255)
     want = OD.stat_increment(ref["proj"][:, 0:2], cam.width, cam.height)
@@ -63,10 +62,38 @@ def _random_set(n, rng, deg=3):
     return p, mo, ve, stats
 
 
-@pytest.mark.parametrize("n", [1, 777, 20_000])
+DMARGIN = 1e-5   # a decision this close (relative) to its threshold may go either way in FP32
+
+
+def _edge_set(rng):
+    """64 Gaussians, a quarter of them on a threshold at FP32 resolution:
+    logit = fl32(logit(0.1)), max log-scale = fl32(log(dense)), mean
+    gradient fl32(threshold); the FP64 definitions decide these by the
+    rounding of the stored values."""
+    p, mo, ve, stats = _random_set(64, rng)
+    dense = 0.01 * 3.0
+    for i in range(0, 64, 4):
+        j = i // 4 % 3
+        if j == 0:
+            p["opacity_logits"][i] = np.float32(math.log(0.1 / 0.9))
+        elif j == 1:
+            p["log_scales"][i] = np.float32(math.log(dense)) - np.float32([0.5, 0.0, 0.7])
+            stats[i] = [0.01, 10]
+            p["opacity_logits"][i] = 2.0
+        else:
+            stats[i] = [np.float32(0.0002) * 7, 7]
+            p["opacity_logits"][i] = 2.0
+    return p, mo, ve, stats
+
+
+@pytest.mark.parametrize("n", [1, 777, 20_000, "edge"])
 def test_plan_and_apply_match_oracle(renderer, n):
-    rng = np.random.default_rng(n)
-    p, mo, ve, stats = _random_set(n, rng)
+    """The oracle decides in FP64 on the definitions; a decision within
+    DMARGIN of its threshold is accepted either way (its Gaussians counted).
+    Every other decision, and every output value, must match exactly."""
+    rng = np.random.default_rng(5 if n == "edge" else n)
+    p, mo, ve, stats = _edge_set(rng) if n == "edge" else _random_set(n, rng)
+    n = len(p["opacity_logits"])
     noise = rng.standard_normal((n, 2, 3)).astype(np.float32)
     extent = 3.0
     t = lambda d: {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in d.items()}
@@ -74,22 +101,43 @@ def test_plan_and_apply_match_oracle(renderer, n):
     gp["sh_degree"] = 3
     P, M, V = R.densify(renderer, gp, gm, gv, torch.from_numpy(stats).cuda(), torch.from_numpy(noise).cuda(), extent)
     renderer.sync_status()
-    act = OD.classify(p["log_scales"], p["opacity_logits"], stats, dense=0.01 * extent)
+    got = {k: P[k].cpu().numpy() for k in R.PARAM_NAMES}
+    cls = dict(dense=0.01 * extent)
+    margins = OD.decision_margins(p["log_scales"], p["opacity_logits"], stats, **cls)
+    near = margins < DMARGIN
+    bits = [(i, 1 << j) for i, j in zip(*np.nonzero(near))]
+    assert len(bits) <= 10, "too many near decisions to enumerate"
+    print(f"densify n={n}: {int(near.any(1).sum())} Gaussians with a near decision")
     if n > 100:
-        assert set(np.unique(act)) == {OD.PRUNE, OD.KEEP, OD.CLONE, OD.SPLIT}
-    oP, oM, oV = OD.apply(p, mo, ve, act, noise)
-    assert P["means"].shape[0] == oP["means"].shape[0]
-    split_rows = np.concatenate([[a == OD.SPLIT] * (2 if a in (OD.CLONE, OD.SPLIT) else 1)
-                                 for a in act if a != OD.PRUNE]) if len(oP["means"]) else np.zeros(0, bool)
-    for k in R.PARAM_NAMES:
-        g_k = P[k].cpu().numpy()
-        if k in ("means", "log_scales"):  # split samples are computed: FP32 against FP64
-            np.testing.assert_array_equal(g_k[~split_rows], np.float32(oP[k][~split_rows]))
-            np.testing.assert_allclose(g_k[split_rows], oP[k][split_rows], rtol=2e-6, atol=2e-6)
-        else:
-            np.testing.assert_array_equal(g_k, np.float32(oP[k]))
-        np.testing.assert_array_equal(M[k].cpu().numpy(), np.float32(oM[k]))
-        np.testing.assert_array_equal(V[k].cpu().numpy(), np.float32(oV[k]))
+        act0 = OD.classify(p["log_scales"], p["opacity_logits"], stats, **cls)
+        assert set(np.unique(act0)) == {OD.PRUNE, OD.KEEP, OD.CLONE, OD.SPLIT}
+    n_out = lambda a: int(np.sum(np.where(a == OD.PRUNE, 0, np.where(a == OD.KEEP, 1, 2))))
+    matched = None
+    for combo in range(1 << len(bits)):
+        flip = np.zeros(n, np.int64)
+        for b, (i, bit) in enumerate(bits):
+            if (combo >> b) & 1:
+                flip[i] |= bit
+        act = OD.classify(p["log_scales"], p["opacity_logits"], stats, flip=flip, **cls)
+        if n_out(act) != got["means"].shape[0]:
+            continue
+        oP, oM, oV = OD.apply(p, mo, ve, act, noise)
+        split_rows = np.concatenate([[a == OD.SPLIT] * (2 if a in (OD.CLONE, OD.SPLIT) else 1)
+                                     for a in act if a != OD.PRUNE]) if len(oP["means"]) else np.zeros(0, bool)
+        ok = True
+        for k in R.PARAM_NAMES:
+            g_k = got[k]
+            if k in ("means", "log_scales"):  # split samples are computed: FP32 against FP64
+                ok &= np.array_equal(g_k[~split_rows], np.float32(oP[k][~split_rows]))
+                ok &= np.allclose(g_k[split_rows], oP[k][split_rows], rtol=2e-6, atol=2e-6)
+            else:
+                ok &= np.array_equal(g_k, np.float32(oP[k]))
+            ok &= np.array_equal(M[k].cpu().numpy(), np.float32(oM[k]))
+            ok &= np.array_equal(V[k].cpu().numpy(), np.float32(oV[k]))
+        if ok:
+            matched = combo
+            break
+    assert matched is not None, f"no outcome of the {len(bits)} near decisions reproduces the GPU's step"
 
 
 def test_fit_densifies_on_schedule(renderer):

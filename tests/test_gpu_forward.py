@@ -36,7 +36,7 @@ def test_tiny_scene_matches_oracle(renderer):
     g, m, cam = scenes.tiny_scene(0)
     gpu = gpu_forward(renderer, g, m, cam)
     ora = oracle.render(g, m, cam)
-    stats = compare_forward(gpu, ora, label="tiny")
+    stats = compare_forward(gpu, ora, label="tiny", scene=(g, m, cam))
     print("tiny", stats)
 
 
@@ -46,7 +46,7 @@ def test_ragged_images_match_oracle(renderer, seed, W, H, deg):
     g, m, cam = _box_scene(seed, 2500, W, H, 0.9 * W, deg, eye=(0.3, -0.2, -0.4), target=(0.1, 0.05, 4.0))
     gpu = gpu_forward(renderer, g, m, cam)
     ora = oracle.render(g, m, cam)
-    print((W, H), compare_forward(gpu, ora, label=f"ragged{W}x{H}"))
+    print((W, H), compare_forward(gpu, ora, label=f"ragged{W}x{H}", scene=(g, m, cam)))
 
 
 def test_dense_overlap_matches_oracle(renderer):
@@ -55,7 +55,7 @@ def test_dense_overlap_matches_oracle(renderer):
     gpu = gpu_forward(renderer, g, m, cam)
     ora = oracle.render(g, m, cam)
     assert ora["n_contrib"].max() >= 20
-    print("dense", compare_forward(gpu, ora, label="dense"))
+    print("dense", compare_forward(gpu, ora, label="dense", scene=(g, m, cam)))
 
 
 @pytest.mark.parametrize("tile", [(8, 32), (32, 8)])
@@ -109,7 +109,7 @@ def test_culled_padding_keeps_the_image(renderer):
 def test_one_pixel_image(renderer):
     g, m, _ = scenes.tiny_scene(0)
     cam = scenes.Camera(1, 1, 120.0, 120.0, 0.5, 0.5, np.concatenate([np.eye(3), np.zeros((3, 1))], 1), 0.2, 20.0)
-    compare_forward(gpu_forward(renderer, g, m, cam), oracle.render(g, m, cam), label="1x1")
+    compare_forward(gpu_forward(renderer, g, m, cam), oracle.render(g, m, cam), label="1x1", scene=(g, m, cam))
 
 
 @pytest.mark.parametrize("n,z_step", [(4000, 0.0), (5 * 5120 + 77, 0.25)])
@@ -193,7 +193,7 @@ def test_mid_scene_sampled_pixels(renderer):
     rng = np.random.default_rng(5)
     pix = rng.choice(cam.width * cam.height, 400, replace=False)
     ora = oracle.render(g, m, cam, pix=pix)
-    print("mid", compare_forward(gpu, ora, pix=pix, label="mid", max_excluded=0.02))
+    print("mid", compare_forward(gpu, ora, pix=pix, label="mid", scene=(g, m, cam)))
 
 
 def test_full_scene_sampled_pixels(renderer):
@@ -204,6 +204,6 @@ def test_full_scene_sampled_pixels(renderer):
     rng = np.random.default_rng(6)
     pix = rng.choice(cam.width * cam.height, 200, replace=False)
     ora = oracle.render(g, m, cam, pix=pix)
-    print("full", compare_forward(gpu, ora, pix=pix, label="full", max_excluded=0.02))
+    print("full", compare_forward(gpu, ora, pix=pix, label="full", scene=(g, m, cam)))
     # every pixel is finite; the image stays in the physical range
     assert np.isfinite(gpu["image"]).all() and gpu["image"].min() >= -1e-6

@@ -64,7 +64,11 @@ def test_featurise_matches_oracle(r, w, h):
     row = M.featurise(r, torch.tensor(img, device="cuda"), torch.tensor(depth, device="cuda"), 20.0)
     r.sync_status()
     got = row.float().cpu().numpy().astype(np.float64)
-    ref = O.feature_row(img, depth, 20.0)
+    # the stored row's layout: the 3080 features, the bias input 1, zeros to the padded width
+    ref = np.zeros(M.ROW)
+    ref[:O.N_IN] = O.stored_features(img, depth, 20.0)
+    ref[O.N_IN] = 1.0
+    assert got.shape == (M.ROW,)
     # histogram, bias input and padding: decided in FP32 on both sides, bit-exact
     np.testing.assert_array_equal(got[O.N_IMG:], ref[O.N_IMG:])
     # cell means: equal BF16 unless the FP64 mean sits within 1e-5 (relative) of a rounding midpoint

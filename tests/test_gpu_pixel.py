@@ -10,7 +10,7 @@ from paper_2411_19588_b300 import _abi
 from paper_2411_19588_b300 import render as R
 from paper_2411_19588_b300 import scenes
 
-from parity import GMARGIN, MARGIN, compare_forward, compare_grads, grads_to_numpy, medium_tensor
+from parity import compare_forward, compare_grads, grads_to_numpy, medium_tensor, upstream_keep
 from test_gpu_forward import _box_scene
 
 pytestmark = pytest.mark.gpu
@@ -42,11 +42,10 @@ def test_pixel_forward_matches_oracle(renderer, case):
         g, m, cam = _box_scene(82, 2500, 80, 60, 70.0, 3, log_scale=-1.7)
     gpu, _, _, _ = _forward(renderer, g, m, cam)
     ora = OP.render(g, m, cam)
-    print(case, compare_forward(gpu, ora, label=f"pixel {case}"))
+    print(case, compare_forward(gpu, ora, label=f"pixel {case}", scene=(g, m, cam), branches=OP.branches))
 
 
-def _upstream(rng, ora, H, W, depth=True):
-    keep = (ora["margin"] >= MARGIN) & (ora["gmargin"] >= GMARGIN) & (ora["tie"] == 0)
+def _upstream(rng, keep, H, W, depth=True):
     G = rng.standard_normal((3, H, W)) * keep
     Gz = rng.standard_normal((H, W)) * 0.05 * keep if depth else None
     G01 = rng.standard_normal((H, W)) * 0.3 * keep if depth else None
@@ -64,13 +63,14 @@ def test_pixel_backward_matches_oracle(renderer, case, depth):
         g, m, cam = _box_scene(83, 1500, 61, 47, 55.0, 1, eye=(0.3, -0.2, -0.4), target=(0.1, 0.05, 4.0))
     else:
         g, m, cam = _box_scene(84, 2500, 80, 60, 70.0, 3, log_scale=-1.7)
-    _, st, params, med = _forward(renderer, g, m, cam)
+    gpu, st, params, med = _forward(renderer, g, m, cam)
     ora = OP.render(g, m, cam)
-    G, Gz, G01 = _upstream(np.random.default_rng(5), ora, cam.height, cam.width, depth)
+    fwd = compare_forward(gpu, ora, label=f"pixel bwd {case} depth={depth}", scene=(g, m, cam), branches=OP.branches)
+    G, Gz, G01 = _upstream(np.random.default_rng(5), upstream_keep(ora, fwd), cam.height, cam.width, depth)
     t = lambda a: None if a is None else torch.tensor(a, dtype=torch.float32, device="cuda").contiguous()
     grads = renderer.backward(st, params, med, cam, t(G), t(Gz), t(G01), pixel=True)
     torch.cuda.synchronize()
-    ref = OP.backward(g, m, cam, G, Gz, G01)
+    ref = OP.backward(g, m, cam, G, Gz, G01, branch=fwd["branch"])
     print(case, depth, compare_grads(grads_to_numpy(grads), ref, f"pixel {case}"))
 
 
@@ -82,14 +82,14 @@ def test_pixel_full_scene_sampled(renderer):
     rng = np.random.default_rng(9)
     pix = rng.choice(cam.width * cam.height, 200, replace=False)
     ora = OP.render(g, m, cam, pix=pix)
-    compare_forward(gpu, ora, pix=pix, label="pixel full", max_excluded=0.05)
-    keep = (ora["margin"] >= MARGIN) & (ora["gmargin"] >= GMARGIN) & (ora["tie"] == 0)
+    fwd = compare_forward(gpu, ora, pix=pix, label="pixel full", scene=(g, m, cam), branches=OP.branches)
+    keep = upstream_keep(ora, fwd)
     G = np.zeros((3, cam.height, cam.width))
     iy, ix = np.divmod(pix, cam.width)
     G[:, iy, ix] = np.float64(np.float32(rng.standard_normal((3, pix.size)) * keep))
     grads = renderer.backward(st, params, med, cam, torch.tensor(G, dtype=torch.float32, device="cuda"), pixel=True)
     torch.cuda.synchronize()
-    ref = OP.backward(g, m, cam, G[:, iy, ix], pix=pix)
+    ref = OP.backward(g, m, cam, G[:, iy, ix], pix=pix, branch=fwd["branch"])
     compare_grads(grads_to_numpy(grads), ref, "pixel full")
 
 

@@ -10,7 +10,7 @@ from oracle import adam as oadam
 from paper_2411_19588_b300 import render as R
 from paper_2411_19588_b300 import scenes
 
-from parity import GMARGIN, MARGIN, gpu_forward
+from parity import compare_forward, gpu_forward, upstream_keep
 from test_gpu_forward import _box_scene
 
 pytestmark = pytest.mark.gpu
@@ -34,8 +34,9 @@ def test_fused_step_matches_oracle_gradient_then_adam(cuda_lib, scene):
     r = R.Renderer()
     out = gpu_forward(r, g, med, cam)
     ora = oracle.render(g, med, cam)
+    fwd = compare_forward(out, ora, label=f"fused step {scene}", scene=(g, med, cam))
     rng = np.random.default_rng(5)
-    keep = (ora["margin"] >= MARGIN) & (ora["gmargin"] >= GMARGIN) & (ora["tie"] == 0)
+    keep = upstream_keep(ora, fwd)
     G = (rng.standard_normal((3, cam.height, cam.width)) * keep).astype(np.float32)
     shapes = {k: getattr(g, k).shape for k in R.PARAM_NAMES}
     shapes["medium"] = (9,)
@@ -47,7 +48,7 @@ def test_fused_step_matches_oracle_gradient_then_adam(cuda_lib, scene):
     r.backward_adam(out["state"], out["params"], out["medium"], cam, torch.from_numpy(G).cuda(), md, vd, LR, step,
                     medium_min=None, grad_medium=gmed)
     torch.cuda.synchronize()
-    ref = oracle.backward(g, med, cam, G.astype(np.float64))
+    ref = oracle.backward(g, med, cam, G.astype(np.float64), branch=fwd["branch"])
     p0 = {k: getattr(g, k).astype(np.float64) for k in R.PARAM_NAMES}
     p0["medium"] = med.as_array().astype(np.float64)
     for k in NAMES:

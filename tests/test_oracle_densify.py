@@ -26,6 +26,27 @@ def test_classify_hand_worked():
     assert act.tolist() == [D.CLONE, D.SPLIT, D.KEEP, D.PRUNE, D.KEEP]
 
 
+def test_classify_margins_and_flips():
+    """Relative distances of each decision to its threshold, and the action
+    when a decision is taken the other way (hand-worked)."""
+    ls = np.log(np.array([[0.01, 0.02, 0.01], [0.5, 0.1, 0.1], [0.2, 0.1, 0.1]]))
+    logits = np.array([0.0, math.log(0.1 / 0.9), 0.0])     # opacities 0.5, 0.1, 0.5
+    stats = np.array([[0.003, 10], [0.005, 10], [0.0004, 2]])
+    mg = D.decision_margins(ls, logits, stats, threshold=0.0002, min_opacity=0.1, dense=0.2)
+    np.testing.assert_allclose(mg[:, 0], [4.0, 0.0, 4.0], atol=1e-15)
+    np.testing.assert_allclose(mg[:, 1], [0.5, 1.5, 0.0], atol=1e-12)
+    np.testing.assert_allclose(mg[:, 2], [0.9, 1.5, 0.0], atol=1e-12)
+    # exactly on the thresholds: opacity 0.1 is not below 0.1, 0.0002 is selected, 0.2 is not larger than 0.2
+    assert D.classify(ls, logits, stats, threshold=0.0002, min_opacity=0.1, dense=0.2).tolist() == \
+        [D.CLONE, D.SPLIT, D.CLONE]
+    flip = [D.SELECTED, D.LOW_OPACITY, D.LARGE]
+    assert D.classify(ls, logits, stats, threshold=0.0002, min_opacity=0.1, dense=0.2, flip=flip).tolist() == \
+        [D.KEEP, D.PRUNE, D.SPLIT]
+    flip = [D.LOW_OPACITY | D.SELECTED, 0, D.SELECTED | D.LARGE]
+    assert D.classify(ls, logits, stats, threshold=0.0002, min_opacity=0.1, dense=0.2, flip=flip).tolist() == \
+        [D.PRUNE, D.SPLIT, D.KEEP]
+
+
 def test_rotation_matches_scipy():
     q = np.array([0.3, -0.5, 0.2, 0.9])
     want = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()  # scipy: (x, y, z, w)

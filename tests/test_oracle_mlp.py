@@ -51,11 +51,12 @@ def test_depth_histogram_closed_forms():
     assert abs(h.sum() - 1.0) < 1e-15 and 0.18 < h[7] < 0.22
 
 
-def test_feature_row_layout():
+def test_stored_feature_layout():
     img, depth = scenes.view_maps(4, 100, 60)
-    row = M.feature_row(img, depth, 20.0)
-    assert row.shape == (M.K1,) and row[M.N_IN] == 1.0 and not row[M.N_IN + 1:].any()
+    row = M.stored_features(img, depth, 20.0)
+    assert row.shape == (M.N_IN,)
     np.testing.assert_array_equal(row[:M.N_IMG], M.bf16_round(M.downsample(img).ravel()))
+    np.testing.assert_array_equal(row[M.N_IMG:], M.bf16_round(M.depth_histogram(depth, 20.0)))
     # channel-major order: channel 1, cell (0, 0) averages rows 0..1, cols 0..3 of a 60x100 image
     assert row[1024] == M.bf16_round(img[1, 0:2, 0:4].mean())
 
