@@ -304,6 +304,20 @@ splash_status splash_profile_read(splash_ctx *ctx, double *ms, int64_t *counts);
  * records on the stream. */
 splash_status splash_profile_mask(splash_ctx *ctx, uint32_t stage_mask);
 
+/* ABI self-description (no counterpart in the paper; for bindings): the
+ * compiler's layout of every struct declared here, so that a binding can
+ * check its mirrors field by field. Structs in this order: splash_camera,
+ * splash_gaussians, splash_grads, splash_options, splash_param_buffers,
+ * splash_adam_config, splash_state_info, splash_adam_group,
+ * splash_mlp_params, splash_mlp_adam, splash_densify_options,
+ * splash_backscatter_options, splash_backscatter_result; within a struct
+ * its fields in declaration order (an array or struct member counts once).
+ * sizes[s] = sizeof, n_fields[s] = its field count, offsets = every field's
+ * offsetof, struct after struct. Any output may be NULL (call once with
+ * only n_structs and n_offsets to size the arrays). Host only; never fails. */
+splash_status splash_abi_layout(int32_t *sizes, int32_t *n_fields, int32_t *offsets, int32_t *n_structs,
+                                int32_t *n_offsets);
+
 /* Number of kernels this library has launched in this process so far. */
 uint64_t splash_kernel_launches(void);
 
@@ -326,7 +340,9 @@ uint64_t splash_kernel_launches(void);
  * overlap on the GPU (other streams, other host threads) race and must be
  * serialised by the caller. The first call on each device looks up the
  * array's device address (cudaGetSymbolAddress with that device current);
- * make that first call before any stream capture. */
+ * make that first call before any stream capture. The address is kept for
+ * the life of the process: a cudaDeviceReset on a device (which unloads the
+ * module and its array) ends this entry point's use on that device. */
 splash_status splash_sort_pairs_u32_noalloc(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_out,
                                             uint32_t *vals_out, int64_t n, int32_t key_bits, uint32_t *status_out,
                                             void *stream);

@@ -111,7 +111,13 @@ class MlpAdam(ctypes.Structure):
 
 MLP_IN, MLP_ROW, MLP_HIDDEN, MLP_OUT = 3080, 3136, 128, 9
 
+# the mirrors of the header's structs, in the order splash_abi_layout reports them
+LAYOUT_ORDER = (Camera, Gaussians, Grads, Options, ParamBuffers, AdamConfig, StateInfo, AdamGroup, MlpParams, MlpAdam,
+                DensifyOptions, BackscatterOptions, BackscatterResult)
+
 _SIGS = {
+    "splash_abi_layout": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                          ctypes.POINTER(ctypes.c_int32)],
     "splash_create": [ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_void_p)],
     "splash_destroy": [ctypes.c_void_p],
     "splash_state_create": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)],

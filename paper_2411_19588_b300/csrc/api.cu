@@ -6,6 +6,8 @@
 //   -> [read back K] -> emit K (tile, Gaussian) pairs -> tile sort -> ranges
 //   -> blend.
 // Backward: blend adjoint -> preprocess adjoint -> medium reduction.
+#include <cstddef>
+#include <cstring>
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -175,8 +177,9 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
     // the pair count K is the sum of the tile counts: read it back (with the
     // status word) while the depth sort and the scan run, so that the host
     // knows K before the GPU runs out of queued work
-    launch_pair_total(n, st->tt.as<uint32_t>(), dK, s);
-    SPLASH_CUDA_TRY(cudaMemcpyAsync(st->h_small, dK, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    // 64-bit total in dK[0..1] (8-byte aligned) and its pinned copy in h_small[2..3]
+    launch_pair_total(n, st->tt.as<uint32_t>(), reinterpret_cast<uint64_t *>(dK), s);
+    SPLASH_CUDA_TRY(cudaMemcpyAsync(st->h_small + 2, dK, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     SPLASH_CUDA_TRY(cudaMemcpyAsync(st->h_small + 1, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     SPLASH_CUDA_TRY(cudaEventRecord(st->k_ready, s));
     const uint32_t *order = nullptr;
@@ -198,8 +201,12 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
         SPLASH_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), s));
         return status_failure(status);
     }
-    const int64_t K = st->h_small[0];
-    if (K >= ((int64_t)1 << 30)) return fail(SPLASH_ERR_CAPACITY, "more than 2^30 tile/Gaussian pairs");
+    uint64_t K64;
+    std::memcpy(&K64, st->h_small + 2, sizeof K64);
+    // every uint32 offset below is valid only under this bound: nothing that
+    // uses them runs before it is checked
+    if (K64 >= ((uint64_t)1 << 30)) return fail(SPLASH_ERR_CAPACITY, "more than 2^30 tile/Gaussian pairs");
+    const int64_t K = (int64_t)K64;
 
     const int64_t kk = std::max<int64_t>(K, 1);
     ENSURE(st->tk0, 4 * kk);
@@ -551,3 +558,84 @@ splash_status splash_sync_status(splash_ctx *ctx, void *stream)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// ABI self-description: sizeof and offsetof of every struct in splash.h, for
+// bindings to check their mirrors against the compiler's own layout.
+
+#define SPLASH_LAYOUT_STRUCTS(X)                                                                              \
+    X(splash_camera, width, height, fx, fy, cx, cy, world_to_cam, z_near, z_far)                              \
+    X(splash_gaussians, means, log_scales, quats, opacity_logits, sh, n, sh_degree)                           \
+    X(splash_grads, means, log_scales, quats, opacity_logits, sh, medium)                                     \
+    X(splash_options, tile_w, tile_h, spin_limit, test_stall_partition, gaussian_batch)                       \
+    X(splash_param_buffers, means, log_scales, quats, opacity_logits, sh, medium)                             \
+    X(splash_adam_config, m, v, lr_means, lr_log_scales, lr_quats, lr_opacity_logits, lr_sh, lr_medium, beta1, \
+      beta2, eps, step, clamp_medium, medium_min, prior, lambda_est, densify_stats)                           \
+    X(splash_state_info, n_keys, tiles_x, tiles_y, tile_w, tile_h, n_gaussians, tile_ids, gauss_ids, ranges,  \
+      depth_keys, tiles_touched, records, final_T, acc_alpha, n_last, n_walk)                                 \
+    X(splash_adam_group, param, grad, m, v, n, lr, clamp_min, has_clamp)                                      \
+    X(splash_mlp_params, W1, b1, W2, b2, W3, b3)                                                              \
+    X(splash_mlp_adam, lr, beta1, beta2, eps)                                                                 \
+    X(splash_densify_options, grad_threshold, min_opacity, percent_dense, extent)                             \
+    X(splash_backscatter_options, resized_height, edges, intervals, pad, p_dark, b_max, beta_max)             \
+    X(splash_backscatter_result, beta_b, b_inf, residual, n_points, n_dark, width, height, pad, point_z, point_v)
+
+namespace {
+
+struct LayoutSink {
+    int32_t *sizes, *n_fields, *offsets;
+    int32_t ns = 0, no = 0;
+    void begin(size_t size)
+    {
+        if (sizes) sizes[ns] = (int32_t)size;
+        if (n_fields) n_fields[ns] = 0;
+    }
+    void field(size_t off)
+    {
+        if (offsets) offsets[no] = (int32_t)off;
+        if (n_fields) n_fields[ns]++;
+        no++;
+    }
+    void end() { ns++; }
+};
+
+}  // namespace
+
+#define SPLASH_LAYOUT_FIELD(T, f) sink.field(offsetof(T, f));
+
+#define SPLASH_FE_1(M, T, x) M(T, x)
+#define SPLASH_FE_2(M, T, x, ...) M(T, x) SPLASH_FE_1(M, T, __VA_ARGS__)
+#define SPLASH_FE_3(M, T, x, ...) M(T, x) SPLASH_FE_2(M, T, __VA_ARGS__)
+#define SPLASH_FE_4(M, T, x, ...) M(T, x) SPLASH_FE_3(M, T, __VA_ARGS__)
+#define SPLASH_FE_5(M, T, x, ...) M(T, x) SPLASH_FE_4(M, T, __VA_ARGS__)
+#define SPLASH_FE_6(M, T, x, ...) M(T, x) SPLASH_FE_5(M, T, __VA_ARGS__)
+#define SPLASH_FE_7(M, T, x, ...) M(T, x) SPLASH_FE_6(M, T, __VA_ARGS__)
+#define SPLASH_FE_8(M, T, x, ...) M(T, x) SPLASH_FE_7(M, T, __VA_ARGS__)
+#define SPLASH_FE_9(M, T, x, ...) M(T, x) SPLASH_FE_8(M, T, __VA_ARGS__)
+#define SPLASH_FE_10(M, T, x, ...) M(T, x) SPLASH_FE_9(M, T, __VA_ARGS__)
+#define SPLASH_FE_11(M, T, x, ...) M(T, x) SPLASH_FE_10(M, T, __VA_ARGS__)
+#define SPLASH_FE_12(M, T, x, ...) M(T, x) SPLASH_FE_11(M, T, __VA_ARGS__)
+#define SPLASH_FE_13(M, T, x, ...) M(T, x) SPLASH_FE_12(M, T, __VA_ARGS__)
+#define SPLASH_FE_14(M, T, x, ...) M(T, x) SPLASH_FE_13(M, T, __VA_ARGS__)
+#define SPLASH_FE_15(M, T, x, ...) M(T, x) SPLASH_FE_14(M, T, __VA_ARGS__)
+#define SPLASH_FE_16(M, T, x, ...) M(T, x) SPLASH_FE_15(M, T, __VA_ARGS__)
+#define SPLASH_FE_17(M, T, x, ...) M(T, x) SPLASH_FE_16(M, T, __VA_ARGS__)
+#define SPLASH_FE_PICK(_1, _2, _3, _4, _5, _6, _7, _8, _9, _10, _11, _12, _13, _14, _15, _16, _17, NAME, ...) NAME
+#define SPLASH_FOR_EACH(M, T, ...)                                                                                   \
+    SPLASH_FE_PICK(__VA_ARGS__, SPLASH_FE_17, SPLASH_FE_16, SPLASH_FE_15, SPLASH_FE_14, SPLASH_FE_13, SPLASH_FE_12, \
+                   SPLASH_FE_11, SPLASH_FE_10, SPLASH_FE_9, SPLASH_FE_8, SPLASH_FE_7, SPLASH_FE_6, SPLASH_FE_5,     \
+                   SPLASH_FE_4, SPLASH_FE_3, SPLASH_FE_2, SPLASH_FE_1)(M, T, __VA_ARGS__)
+#define SPLASH_LAYOUT_STRUCT(T, ...)                       \
+    sink.begin(sizeof(T));                                 \
+    SPLASH_FOR_EACH(SPLASH_LAYOUT_FIELD, T, __VA_ARGS__) \
+    sink.end();
+
+extern "C" splash_status splash_abi_layout(int32_t *sizes, int32_t *n_fields, int32_t *offsets, int32_t *n_structs,
+                                           int32_t *n_offsets)
+{
+    LayoutSink sink{sizes, n_fields, offsets};
+    SPLASH_LAYOUT_STRUCTS(SPLASH_LAYOUT_STRUCT)
+    if (n_structs) *n_structs = sink.ns;
+    if (n_offsets) *n_offsets = sink.no;
+    return SPLASH_OK;
+}

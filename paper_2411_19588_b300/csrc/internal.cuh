@@ -181,7 +181,7 @@ void launch_count_scan(int64_t n, const uint32_t *order, const uint32_t *tiles_t
 // d_medium[j] = sum over nblocks rows of partials[b][9] (the pixel form's medium gradient)
 void launch_pixel_medium_final(const float *partials, int nblocks, float *d_medium, cudaStream_t s);
 // *total = sum of tt[0..n) (zeroed first)
-void launch_pair_total(int64_t n, const uint32_t *tt, uint32_t *total, cudaStream_t s);
+void launch_pair_total(int64_t n, const uint32_t *tt, uint64_t *total, cudaStream_t s);
 void launch_emit(int64_t n, const uint32_t *order, const uint32_t *offsets, const uint32_t *tt, const uint2 *rect,
                  const TileGeom &tg, uint32_t *tile_ids, uint32_t *gauss_ids, uint64_t capacity, uint32_t *status,
                  cudaStream_t s);

@@ -334,12 +334,21 @@ __global__ void __launch_bounds__(kPreThreads) k_preprocess_fwd(
     sh_basis<DEG>(vx * vinv, vy * vinv, vz * vinv, Y);
     const float *coef = s_sh[warp] + lane * ROW;
     float col[3];
+    // a Gaussian with a non-finite parameter touches no tile (a NaN or an
+    // infinite coefficient makes its colour sum non-finite even where its
+    // basis value is 0)
+    bool finite = isfinite(a) && isfinite(b) && isfinite(c) && isfinite(det) && isfinite(px.hi) && isfinite(py.hi);
 #pragma unroll
     for (int ch = 0; ch < 3; ch++) {
         float acc = 0.5f;
 #pragma unroll
         for (int k = 0; k < K; k++) acc = fmaf(coef[3 * k + ch], Y[k], acc);
+        finite = finite && isfinite(acc);
         col[ch] = fmaxf(acc, 0.f);
+    }
+    if (!finite) {
+        ntiles = 0;
+        rc = make_uint2(0u, 0u);
     }
     // water: ct = c e^{-beta_D d} - B_inf e^{-beta_B d}
     float ct[3];

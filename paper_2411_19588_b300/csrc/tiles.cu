@@ -127,12 +127,11 @@ __global__ void __launch_bounds__(256) k_emit(int64_t n, const uint32_t *__restr
     const int lane = threadIdx.x & 31;
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r - lane >= n) return;  // the whole warp is past the end
-    uint32_t g = 0, cnt = 0, tx0 = 0, ty0 = 0, w = 1, fit = 0;
-    uint32_t off0 = 0;
+    uint32_t g = 0, cnt = 0, tx0 = 0, ty0 = 0, w = 1, fit = 0, off = 0;
     if (r < n) {
         g = order[r];
         cnt = tt[g];
-        const uint32_t off = offsets[r];
+        off = offsets[r];
         if (cnt) {
             const uint2 rc = rect[g];
             tx0 = rc.x & 0xffffu;
@@ -141,9 +140,7 @@ __global__ void __launch_bounds__(256) k_emit(int64_t n, const uint32_t *__restr
             fit = (uint64_t)off + cnt <= capacity;
             if (!fit) atomicOr(status, kStatusCapacity);
         }
-        off0 = off;
     }
-    off0 = __shfl_sync(kFull, off0, 0);  // offsets[first Gaussian of the warp]
     // warp-local start of each lane's run: exclusive scan of the counts
     uint32_t incl = cnt;
 #pragma unroll
@@ -163,10 +160,12 @@ __global__ void __launch_bounds__(256) k_emit(int64_t n, const uint32_t *__restr
         }
         const uint32_t og = __shfl_sync(kFull, g, j), otx0 = __shfl_sync(kFull, tx0, j), oty0 = __shfl_sync(kFull, ty0, j);
         const uint32_t ow = __shfl_sync(kFull, w, j), ofit = __shfl_sync(kFull, fit, j), oloc = __shfl_sync(kFull, loc, j);
+        const uint32_t ooff = __shfl_sync(kFull, off, j);
         if (s < total && ofit) {
+            // the owner's own offset: ofit guarantees ooff + its count <= capacity
             const uint32_t k = s - oloc, dy = k / ow, dx = k - dy * ow;
-            tile_ids[(uint64_t)off0 + s] = (oty0 + dy) * (uint32_t)tiles_x + otx0 + dx;
-            gauss_ids[(uint64_t)off0 + s] = og;
+            tile_ids[(uint64_t)ooff + k] = (oty0 + dy) * (uint32_t)tiles_x + otx0 + dx;
+            gauss_ids[(uint64_t)ooff + k] = og;
         }
     }
 }
@@ -203,30 +202,34 @@ __global__ void __launch_bounds__(256) k_ranges(int64_t k_host, const uint32_t *
 }
 
 // total of the tile counts (the pair count K), one atomic per CTA (all of
-// them land on one address)
-__global__ void __launch_bounds__(256) k_sum_u32(const uint32_t *__restrict__ v, int64_t n, uint32_t *__restrict__ total)
+// them land on one address). Summed in 64 bits: a scene whose counts add up
+// past 2^32 must be reported as over capacity, not wrap to a small count.
+__global__ void __launch_bounds__(256) k_sum_u64(const uint32_t *__restrict__ v, int64_t n,
+                                                 unsigned long long *__restrict__ total)
 {
-    __shared__ uint32_t s_w[8];
-    uint32_t acc = 0;
+    __shared__ unsigned long long s_w[8];
+    unsigned long long acc = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) acc += v[i];
-    acc = __reduce_add_sync(0xffffffffu, acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x < 32) {
-        uint32_t x = threadIdx.x < 8 ? s_w[threadIdx.x] : 0u;
-        x = __reduce_add_sync(0xffffffffu, x);
+        unsigned long long x = threadIdx.x < 8 ? s_w[threadIdx.x] : 0ull;
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
         if (threadIdx.x == 0 && x) atomicAdd(total, x);
     }
 }
 
 }  // namespace
 
-void launch_pair_total(int64_t n, const uint32_t *tt, uint32_t *total, cudaStream_t s)
+void launch_pair_total(int64_t n, const uint32_t *tt, uint64_t *total, cudaStream_t s)
 {
-    cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
+    cudaMemsetAsync(total, 0, sizeof(uint64_t), s);
     if (n <= 0) return;
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 4);
-    k_sum_u32<<<blocks, 256, 0, s>>>(tt, n, total);
+    k_sum_u64<<<blocks, 256, 0, s>>>(tt, n, reinterpret_cast<unsigned long long *>(total));
     count_launch();
 }
 

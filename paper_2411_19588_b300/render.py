@@ -326,12 +326,16 @@ class Batch:
         dev = medium.device
         self.images = [torch.empty((3, c.height, c.width), device=dev) for c in self.cams]
 
-    def forward(self, params: dict, medium: torch.Tensor, images=None):
+    def forward(self, params: dict, medium: torch.Tensor, images=None, depths=None, depth01s=None):
+        """Renders every view into ``images`` (default: the batch's own
+        buffers); ``depths`` / ``depth01s``, lists of [H_v, W_v] device
+        tensors (entries may be None), receive the Eq. 6 depth maps."""
         images = images if images is not None else self.images
-        ptrs = (ctypes.c_void_p * len(images))(*[t.data_ptr() for t in images])
+        V = len(images)
+        arr = lambda ts: None if ts is None else (ctypes.c_void_p * V)(*[_abi.ptr(t) for t in ts])
         g = gaussians_struct(params)
-        _abi.check(_abi.lib().splash_batch_forward(self._h, ctypes.byref(g), medium.data_ptr(), ptrs, None, None,
-                                                   _stream()), "splash_batch_forward")
+        _abi.check(_abi.lib().splash_batch_forward(self._h, ctypes.byref(g), medium.data_ptr(), arr(images),
+                                                   arr(depths), arr(depth01s), _stream()), "splash_batch_forward")
         return images
 
     def backward(self, params: dict, medium: torch.Tensor, dL_dimages: list, grads: dict | None = None) -> dict:

@@ -18,12 +18,26 @@ def test_library_builds_and_exports_every_declared_symbol():
     assert set(syms) - {"splash_last_error", "splash_kernel_launches"} == set(_abi._SIGS)
 
 
-def test_binding_struct_sizes_match_header_layout():
-    # int32 x2 + float x4 + float[12] + float x2
-    assert ctypes.sizeof(_abi.Camera) == 4 * (2 + 4 + 12 + 2)
-    assert ctypes.sizeof(_abi.Gaussians) == 8 * 5 + 8 + 8
-    assert ctypes.sizeof(_abi.Options) == 20
-    assert ctypes.sizeof(_abi.AdamGroup) == 8 * 4 + 8 + 4 + 4 + 4 + 4
+def test_binding_structs_match_the_compilers_layout():
+    """Every ctypes mirror against sizeof / offsetof as the library's own
+    compiler laid the header's structs out (splash_abi_layout), field by
+    field, for all thirteen structs."""
+    L = _abi.lib()
+    ns, no = ctypes.c_int32(), ctypes.c_int32()
+    assert L.splash_abi_layout(None, None, None, ctypes.byref(ns), ctypes.byref(no)) == _abi.OK
+    assert ns.value == len(_abi.LAYOUT_ORDER) == 13
+    sizes, nf = (ctypes.c_int32 * ns.value)(), (ctypes.c_int32 * ns.value)()
+    offs = (ctypes.c_int32 * no.value)()
+    assert L.splash_abi_layout(sizes, nf, offs, ctypes.byref(ns), ctypes.byref(no)) == _abi.OK
+    k = 0
+    for i, T in enumerate(_abi.LAYOUT_ORDER):
+        assert ctypes.sizeof(T) == sizes[i], (T.__name__, ctypes.sizeof(T), sizes[i])
+        fields = [name for name, _ in T._fields_]
+        assert len(fields) == nf[i], (T.__name__, fields, nf[i])
+        for name in fields:
+            assert getattr(T, name).offset == offs[k], (T.__name__, name, getattr(T, name).offset, offs[k])
+            k += 1
+    assert k == no.value
 
 
 def test_library_reports_missing_gpu_as_an_error_not_a_fallback():

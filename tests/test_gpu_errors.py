@@ -56,15 +56,31 @@ def test_invalid_arguments_are_rejected(cuda_lib):
     assert np.isfinite(out["image"]).all()
 
 
-def test_nan_parameters_do_not_break_the_render(cuda_lib):
+def test_nan_parameters_are_culled(cuda_lib):
+    """A Gaussian with a NaN in any parameter group touches no tile, and the
+    rest of the scene renders exactly as the scene without it: same image
+    and depth bit for bit (their relative depth order, ties included, is
+    unchanged by removing others)."""
     r = R.Renderer()
     g, m, cam = scenes.tiny_scene(0)
     g = g.copy()
-    g.means[::7] = np.nan
-    g.log_scales[1::11] = np.nan
+    bad = np.zeros(g.n, bool)
+    for arr, start, step in ((g.means, 0, 7), (g.log_scales, 1, 11), (g.quats, 2, 13), (g.opacity_logits, 3, 17),
+                             (g.sh, 4, 19)):
+        arr[start::step] = np.nan
+        bad[start::step] = True
     out = gpu_forward(r, g, m, cam)
     r.sync_status()
-    assert out["image"].shape == (3, cam.height, cam.width)
+    tt = r.state_array(out["state"], "tiles_touched").cpu().numpy().view(np.uint32)
+    assert (tt[bad] == 0).all()
+    assert (tt[~bad] > 0).sum() > 100
+    keep = np.flatnonzero(~bad)
+    sub = scenes.Gaussians(*(np.ascontiguousarray(a[keep]) for a in (g.means, g.log_scales, g.quats, g.opacity_logits,
+                                                                     g.sh)), g.sh_degree)
+    ref = gpu_forward(R.Renderer(), sub, m, cam)
+    np.testing.assert_array_equal(out["image"], ref["image"])
+    np.testing.assert_array_equal(out["depth"], ref["depth"])
+    assert np.isfinite(out["image"]).all()
 
 
 def test_stalled_lookback_reports_timeout_and_context_survives(cuda_lib):

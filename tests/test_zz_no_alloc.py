@@ -1,8 +1,9 @@
 """splash_sort_pairs_u32_noalloc: the pair sort for callers that cannot
 allocate device memory (its scratch is a static device array). Called
-through the C ABI and compared with the allocating entry point,
-splash_sort_pairs_u32, bit for bit, on two calls in a row. This file is
-collected last so that a failure here leaves every other test already run."""
+through the C ABI and compared bit for bit with the allocating entry point,
+splash_sort_pairs_u32, on two calls in a row, and with numpy's stable
+argsort of the masked keys. This file is collected last so that a failure
+here leaves every other test already run."""
 import ctypes
 
 import numpy as np
@@ -27,6 +28,14 @@ def _noalloc(L, keys, vals, bits):
     return ko, vo, status
 
 
+def _numpy_reference(keys, vals, bits):
+    k = keys.cpu().numpy().view(np.uint32)
+    masked = k & np.uint32((1 << bits) - 1) if bits < 32 else k
+    order = np.argsort(masked, kind="stable")
+    v = np.arange(k.size, dtype=np.uint32) if vals is None else vals.cpu().numpy().view(np.uint32)
+    return k[order], v[order]
+
+
 def test_noalloc_sort_matches_allocating_sort_twice(cuda_lib):
     L = _abi.lib()
     r = R.Renderer()
@@ -42,6 +51,24 @@ def test_noalloc_sort_matches_allocating_sort_twice(cuda_lib):
         torch.cuda.synchronize()
         assert int(status.item()) == 0
         assert torch.equal(ko, ref_k) and torch.equal(vo, ref_v)
+        np_k, np_v = _numpy_reference(keys, vals, bits)
+        np.testing.assert_array_equal(ko.cpu().numpy().view(np.uint32), np_k)
+        np.testing.assert_array_equal(vo.cpu().numpy().view(np.uint32), np_v)
+
+
+@pytest.mark.parametrize("n,bits", [(0, 32), (5_000, 0), (1, 7), (4_097, 9)])
+def test_noalloc_sort_edge_cases(cuda_lib, n, bits):
+    """No pairs; no key bits (the input order is kept and the values are the
+    positions); one pair; a ragged partition with a narrow digit."""
+    L = _abi.lib()
+    rng = np.random.default_rng(n + bits)
+    keys = torch.from_numpy(rng.integers(0, 1 << 32, n, dtype=np.int64).astype(np.uint32).view(np.int32)).cuda()
+    ko, vo, status = _noalloc(L, keys, None, bits)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    np_k, np_v = _numpy_reference(keys, None, bits)
+    np.testing.assert_array_equal(ko.cpu().numpy().view(np.uint32), np_k)
+    np.testing.assert_array_equal(vo.cpu().numpy().view(np.uint32), np_v)
 
 
 def test_noalloc_sort_rejects_sizes_beyond_its_scratch(cuda_lib):
