@@ -48,7 +48,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=N_GAUSS, help="Gaussians (default: the 1.5M workload)")
+    ap.add_argument("--n", "--gaussians", dest="n", type=int, default=N_GAUSS, help="Gaussians (default: the 1.5M workload)")
     ap.add_argument("--tile", default="16x16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -498,7 +498,7 @@ def run_ours(args, world, rank, local):
         "e2e": e2e,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(budget_s=20.0)
+        out["cpu_baseline"] = cpu_baseline(args.n)
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -951,106 +951,103 @@ def run_loop(args, world, rank, local):
         print(json.dumps(out), flush=True)
 
 
-class _OracleStep:
-    """The FP64 oracle (as it stands) on the training workload, timed in pieces
-    and scaled to one full step: projection of all Gaussians (twice: forward
-    and adjoint), forward and adjoint at a random sample of pixels, the loss
-    on a crop and Adam on a sample of elements."""
+ORACLE_BIN = 16  # the oracle's candidate bins (pixels per side); results equal the unbinned scan
 
-    def __init__(self, n: int = N_GAUSS):
+
+class _OracleStep:
+    """The FP64 oracle (as it stands, scanning per pixel only the Gaussians
+    whose widened 3-sigma box meets its 16x16 bin, which leaves every result
+    unchanged) running whole training steps of a workload: the forward at
+    every pixel, the L1 + 0.2 (1 - SSIM) loss and its gradient against a
+    fixed target, the adjoint at every pixel and one Adam step on every
+    parameter. Nothing is sampled or extrapolated."""
+
+    def __init__(self, n: int = N_GAUSS, mid: bool = False):
         import oracle
         from oracle import adam as oadam
         from oracle import loss as oloss
         from paper_2411_19588_b300 import scenes
-        self.oracle = oracle
-        self.n = n
-        self.g, self.m, _ = scenes.patch_scene(n, 3, (2.0, 15.0), 1920, 1280, 1800.0)
-        self.cam = scenes.arc_cameras(N_VIEWS, seed=3)[N_VIEWS // 2]
+        self.oracle, self.oadam, self.oloss = oracle, oadam, oloss
+        if mid:
+            self.g, self.m, self.cam = scenes.mid_scene()
+            self.n = self.g.n
+        else:
+            self.n = n
+            self.g, self.m, _ = scenes.patch_scene(n, 3, (2.0, 15.0), 1920, 1280, 1800.0)
+            self.cam = scenes.arc_cameras(N_VIEWS, seed=3)[N_VIEWS // 2]
         self.H, self.W = self.cam.height, self.cam.width
-        self.rng = np.random.default_rng(0)
-        t = time.perf_counter()
-        oracle.project(self.g, self.m, self.cam)
-        self.t_proj = time.perf_counter() - t
-        self.crop = 256
-        x = self.rng.uniform(0, 1, (3, self.crop, self.crop))
-        t = time.perf_counter()
-        oloss.loss_and_grad(x, x * 0.9, LAMBDA_SSIM)
-        self.t_loss = (time.perf_counter() - t) * (self.H * self.W) / (self.crop * self.crop)
-        self.ne = 1_000_000
-        p = self.rng.standard_normal(self.ne)
-        t = time.perf_counter()
-        oadam.adam_step(p, p, np.zeros(self.ne), np.zeros(self.ne), 1, 1e-3)
-        self.t_adam = (time.perf_counter() - t) * (n * 59 + 9) / self.ne
+        rng = np.random.default_rng(0)
+        self.target = rng.uniform(0, 1, (3, self.H, self.W))
+        self.params = {k: np.asarray(getattr(self.g, k), np.float64) for k in ("means", "log_scales", "quats",
+                                                                               "opacity_logits", "sh")}
+        self.params["medium"] = np.asarray(self.m.as_array(), np.float64)
+        self.mom = {k: (np.zeros_like(v), np.zeros_like(v)) for k, v in self.params.items()}
+        self.t = 0
 
-    def call_seconds(self, S: int) -> float:
-        """Wall time of the oracle's forward + adjoint calls at S random pixels."""
-        pix = self.rng.choice(self.H * self.W, S, replace=False)
+    def forward_adjoint(self) -> float:
+        """Seconds of one forward and one adjoint at every pixel."""
         t = time.perf_counter()
-        self.oracle.render(self.g, self.m, self.cam, pix=pix)
-        self.oracle.backward(self.g, self.m, self.cam, self.rng.standard_normal((3, S)), pix=pix)
+        r = self.oracle.render(self.g, self.m, self.cam, bin=ORACLE_BIN)
+        self.oracle.backward(self.g, self.m, self.cam, r["image"] - self.target, bin=ORACLE_BIN)
         return time.perf_counter() - t
 
-    def pixel_seconds(self, S: int) -> float:
-        """Seconds per pixel of forward + adjoint: an S-pixel call minus the calls'
-        fixed part (their projections and set-up, measured once with one pixel)."""
-        if not hasattr(self, "fixed"):
-            self.fixed = self.call_seconds(1)
-        return max(self.call_seconds(S) - self.fixed, 0.0) / S
+    def step(self) -> float:
+        """Seconds of one whole training step."""
+        t = time.perf_counter()
+        r = self.oracle.render(self.g, self.m, self.cam, bin=ORACLE_BIN)
+        _, dimg = self.oloss.loss_and_grad(r["image"], self.target, LAMBDA_SSIM)
+        gr = self.oracle.backward(self.g, self.m, self.cam, dimg, bin=ORACLE_BIN)
+        self.t += 1
+        for k, p in self.params.items():
+            m, v = self.mom[k]
+            self.params[k], m2, v2 = self.oadam.adam_step(p, gr[k], m, v, self.t, LR[k])
+            self.mom[k] = (m2, v2)
+        return time.perf_counter() - t
 
-    def step_seconds(self, per_pixel: float) -> float:
-        return 2 * self.t_proj + per_pixel * self.H * self.W + self.t_loss + self.t_adam
-
-    def sample(self, S: int) -> str:
-        return (f"projection of all {self.n} Gaussians + forward/adjoint at {S} random pixels (scaled by "
-                f"{self.H * self.W}/{S}) + loss on a {self.crop}x{self.crop} crop and Adam on {self.ne} elements "
-                f"(scaled)")
-
-    def calibrate(self, budget_s: float) -> int:
-        """Pixel-sample size whose per-pixel part takes about budget_s (1024 .. 4096:
-        smaller samples leave the oracle's threads idle and overstate the per-pixel
-        cost)."""
-        S = 1024
-        while S < 4096 and self.pixel_seconds(S) * S < budget_s:
-            S *= 2
-        return S
+    def describe(self) -> str:
+        return (f"whole training steps of the oracle ({self.n} Gaussians, {self.W}x{self.H}; candidate scan in "
+                f"{ORACLE_BIN}x{ORACLE_BIN} bins): forward and adjoint at every pixel, loss and its gradient at full "
+                f"size, Adam on all parameters; not extrapolated")
 
 
-def cpu_baseline(budget_s: float = 20.0, n: int = N_GAUSS) -> dict:
-    """One bounded measurement of the oracle's training step (see _OracleStep)."""
+def cpu_baseline(n: int = N_GAUSS) -> dict:
+    """The oracle on the host cores: one whole training step of the workload,
+    and the mid workload's forward + adjoint in full, median of three runs."""
     o = _OracleStep(n)
-    S = o.calibrate(budget_s * 0.4)
-    t_step = o.step_seconds(o.pixel_seconds(S))
-    return {"value": 1.0 / t_step, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle", "sample": o.sample(S),
-            "seconds_per_step": round(t_step, 1)}
+    t_step = o.step()
+    mid = _OracleStep(mid=True)
+    runs = [mid.forward_adjoint() for _ in range(3)]
+    return {"value": 1.0 / t_step, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle-binned",
+            "extrapolated": False, "sample": o.describe() + "; one step", "seconds_per_step": round(t_step, 2),
+            "mid_scene_fwd_adjoint": {"workload": f"{mid.n} Gaussians, {mid.W}x{mid.H}, forward + adjoint at every "
+                                                  f"pixel", "seconds_median": round(float(np.median(runs)), 2),
+                                      "runs_s": [round(x, 2) for x in runs], "extrapolated": False},
+            "compiler": "gcc -O2 -fopenmp (FP64), OpenMP over pixels"}
 
 
 def run_reference(args, world, rank):
-    """The reference arm: the oracle on the same workload, each of the warm-up and
-    timed steps a bounded pixel sample; the workload, the projection, loss and Adam
-    timings are made once, and the sample is sized so that the whole run takes a few
-    minutes whatever --steps and --warmup are."""
+    """The reference arm: the oracle on the same workload, every step a whole
+    training step (no sampling, no extrapolation). A step takes tens of seconds
+    on the host cores, so at most one untimed warm-up step and three timed steps
+    run whatever --steps and --warmup ask; the line reports the counts run."""
     if rank != 0:
         return
     o = _OracleStep(args.n)
-    # Each step costs the calls' fixed part (about 1.3-2.7 s) plus a 1,024-pixel sample.
-    # Every oracle step is the same work, so at most 20 steps are measured (and at most
-    # two untimed warm-up steps made): the run stays within a few minutes.
-    warm = min(args.warmup, 2)
-    measured = min(args.steps, 20)
-    S = o.calibrate(1.0)
-    vals = []
-    for i in range(warm + measured):
-        v_i = 1.0 / o.step_seconds(o.pixel_seconds(S))
-        if i >= warm:
-            vals.append(v_i)
-    v = float(np.median(vals))
-    out = {"metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+    warm = min(args.warmup, 1)
+    measured = max(1, min(args.steps, 3))
+    for _ in range(warm):
+        o.step()
+    times = [o.step() for _ in range(measured)]
+    t = float(np.median(times))
+    v = 1.0 / t
+    out = {"metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": world, "steps": measured, "warmup": warm,
+           "ms_per_step": 1000.0 * t, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "impl": "reference", "measured_steps": measured,
+           "requested": {"steps": args.steps, "warmup": args.warmup}, "step_seconds": [round(x, 2) for x in times],
            "config": {"workload": "train step: 1.5M Gaussians (SH3, 2-15 m), 1920x1280, 100-view arc, "
                                   "fwd + L1+0.2(1-SSIM) + bwd + Adam", "n_gaussians": args.n},
-           "cpu_baseline": {"value": v, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
-                            "sample": o.sample(S) + f", median of {measured} steps"},
+           "cpu_baseline": {"value": v, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle-binned",
+                            "extrapolated": False, "sample": o.describe() + f"; median of {measured} steps"},
            "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

@@ -47,9 +47,9 @@ def lib():
         ip = ctypes.POINTER(ctypes.c_int64)
         i64, ci, cd = ctypes.c_int64, ctypes.c_int, ctypes.c_double
         L.oracle_project.argtypes = [i64, dp, dp, dp, dp, dp, ci, dp, dp, dp, ci]
-        L.oracle_render.argtypes = [i64, dp, dp, dp, dp, dp, ci, dp, dp, i64, ip, cd, dp, ci]
-        L.oracle_render_branches.argtypes = [i64, dp, dp, dp, dp, dp, ci, dp, dp, i64, ip, cd, dp, ci]
-        L.oracle_backward.argtypes = [i64, dp, dp, dp, dp, dp, ci, dp, dp, i64, ip, dp, ip, cd,
+        L.oracle_render.argtypes = [i64, dp, dp, dp, dp, dp, ci, dp, dp, i64, ip, cd, ci, dp, ci]
+        L.oracle_render_branches.argtypes = [i64, dp, dp, dp, dp, dp, ci, dp, dp, i64, ip, cd, ci, dp, ci]
+        L.oracle_backward.argtypes = [i64, dp, dp, dp, dp, dp, ci, dp, dp, i64, ip, dp, ip, cd, ci,
                                       dp, dp, dp, dp, dp, dp, dp, ci]
         L.oracle_composite.argtypes = [i64, dp, dp, dp, dp, cd, dp]
         L.oracle_sh_basis.argtypes = [ci, dp, dp]
@@ -94,15 +94,17 @@ def _pix(cam, pix):
     return int(p.size), p, p.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
 
 
-def render(g, medium, cam, pix=None, nthreads: int = 0, near: float = NEAR) -> dict:
+def render(g, medium, cam, pix=None, nthreads: int = 0, near: float = NEAR, bin: int = 0) -> dict:
     """Render every pixel (``pix=None``; arrays shaped (H, W), image (3, H, W))
     or the listed linear pixel indices (arrays shaped (npix,), image (3, npix)).
-    ``n_near`` counts each pixel's decisions within ``near`` of a threshold."""
+    ``n_near`` counts each pixel's decisions within ``near`` of a threshold.
+    ``bin`` > 0 scans, per pixel, only the Gaussians whose widened 3-sigma box
+    meets its bin x bin block (same results, much faster on large scenes)."""
     L = lib()
     arrs, med, c = _params(g, medium, cam)
     npix, p, pp = _pix(cam, pix)
     out = np.zeros((npix, _NPIX), np.float64)
-    rc = L.oracle_render(g.n, *[q for _, q in arrs], g.sh_degree, med[1], c[1], npix, pp, float(near),
+    rc = L.oracle_render(g.n, *[q for _, q in arrs], g.sh_degree, med[1], c[1], npix, pp, float(near), int(bin),
                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nthreads)
     if rc != 0:
         raise RuntimeError(f"oracle_render failed: {rc}")
@@ -112,7 +114,7 @@ def render(g, medium, cam, pix=None, nthreads: int = 0, near: float = NEAR) -> d
     return res
 
 
-def branches(g, medium, cam, pix, nthreads: int = 0, near: float = NEAR) -> dict:
+def branches(g, medium, cam, pix, nthreads: int = 0, near: float = NEAR, bin: int = 0) -> dict:
     """Every branch of the listed linear pixel indices: each field shaped
     (npix, NBRANCH). Branch b takes near decision i (in the FP64 walk's order)
     the other way when bit i of b is set; branch 0 is ``render``'s result.
@@ -124,7 +126,7 @@ def branches(g, medium, cam, pix, nthreads: int = 0, near: float = NEAR) -> dict
     nb = L.oracle_nbranch()
     out = np.zeros((p.size, nb, len(BRANCH_FIELDS)), np.float64)
     rc = L.oracle_render_branches(g.n, *[q for _, q in arrs], g.sh_degree, med[1], c[1], p.size,
-                                  p.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), float(near),
+                                  p.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), float(near), int(bin),
                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nthreads)
     if rc != 0:
         raise RuntimeError(f"oracle_render_branches failed: {rc}")
@@ -135,7 +137,7 @@ def branches(g, medium, cam, pix, nthreads: int = 0, near: float = NEAR) -> dict
 
 
 def backward(g, medium, cam, dL_dimage, dL_ddepth=None, dL_ddepth01=None, pix=None, nthreads: int = 0,
-             branch=None, near: float = NEAR) -> dict:
+             branch=None, near: float = NEAR, bin: int = 0) -> dict:
     """Gradients of L = <dL_dimage, C> + <dL_ddepth, z> + <dL_ddepth01, z01>
     with respect to every parameter (FP64 analytic adjoint). Upstream arrays
     are (3, H, W)/(H, W) for ``pix=None`` or (3, npix)/(npix,) otherwise.
@@ -159,7 +161,7 @@ def backward(g, medium, cam, dL_dimage, dL_ddepth=None, dL_ddepth01=None, pix=No
     br = None if branch is None else np.ascontiguousarray(np.asarray(branch).reshape(npix), np.int64)
     bp = None if br is None else br.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
     rc = L.oracle_backward(g.n, *[q for _, q in arrs], g.sh_degree, med[1], c[1], npix, pp, ptr(gout),
-                           bp, float(near), ptr(res["means"]), ptr(res["log_scales"]), ptr(res["quats"]), ptr(res["opacity_logits"]),
+                           bp, float(near), int(bin), ptr(res["means"]), ptr(res["log_scales"]), ptr(res["quats"]), ptr(res["opacity_logits"]),
                            ptr(res["sh"]), ptr(res["medium"]), ptr(res["proj"]), nthreads)
     if rc != 0:
         raise RuntimeError(f"oracle_backward failed: {rc}")

@@ -618,9 +618,87 @@ static void render_pixel(const pg_t *P, const int64_t *vis, int64_t nvis, const 
 /* Render every pixel (pix = NULL) or the npix listed linear pixel indices.
  * near_rel: the relative distance to a threshold that counts a decision as
  * near (the O_NNEAR field). */
+/* Optional binning, a speed-up of the per-pixel candidate scan that leaves
+ * every result unchanged: each visible Gaussian is listed in every
+ * bin x bin block of pixels that its axis-aligned box |dx| <= sqrt(Qb Sxx),
+ * |dy| <= sqrt(Qb Syy) meets, with Qb = 9 (1 + 4 near_rel) + 1e-9. The box
+ * holds every point where q <= Qb, so a pixel's list holds every Gaussian
+ * that can lie inside its 3-sigma ellipse or within near_rel of its edge, in
+ * increasing index order like the unbinned scan. bin = 0: no binning. */
+typedef struct {
+    int bin, bx, by;
+    int64_t *start, *ids;
+} bins_t;
+
+static int bins_build(const pg_t *P, const int64_t *vis, int64_t nvis, const cam_t *c, int bin, double near_rel,
+                      bins_t *b)
+{
+    memset(b, 0, sizeof *b);
+    if (bin <= 0) return 0;
+    b->bin = bin;
+    b->bx = (c->W + bin - 1) / bin;
+    b->by = (c->H + bin - 1) / bin;
+    const int64_t nb = (int64_t)b->bx * b->by;
+    b->start = (int64_t *)calloc((size_t)nb + 1, sizeof(int64_t));
+    int64_t *fill = (int64_t *)calloc((size_t)nb + 1, sizeof(int64_t));
+    if (!b->start || !fill) return -2;
+    const double Qb = Q_MAX * (1.0 + 4.0 * near_rel) + 1e-9;
+    for (int pass = 0; pass < 2; pass++) {
+        for (int64_t k = 0; k < nvis; k++) {
+            const pg_t *g = &P[vis[k]];
+            const double hx = sqrt(Qb * g->S2[0]), hy = sqrt(Qb * g->S2[2]);
+            if (!(isfinite(hx) && isfinite(hy) && isfinite(g->x) && isfinite(g->y))) continue;
+            /* pixel columns and rows whose centres lie in the box */
+            const double fx0 = fmax(ceil(g->x - hx - 0.5), 0.0), fx1 = fmin(floor(g->x + hx - 0.5), c->W - 1.0);
+            const double fy0 = fmax(ceil(g->y - hy - 0.5), 0.0), fy1 = fmin(floor(g->y + hy - 0.5), c->H - 1.0);
+            if (fx0 > fx1 || fy0 > fy1) continue;
+            const int tx0 = (int)fx0 / bin, tx1 = (int)fx1 / bin, ty0 = (int)fy0 / bin, ty1 = (int)fy1 / bin;
+            for (int ty = ty0; ty <= ty1; ty++)
+                for (int tx = tx0; tx <= tx1; tx++) {
+                    const int64_t t = (int64_t)ty * b->bx + tx;
+                    if (pass == 0)
+                        b->start[t + 1]++;
+                    else
+                        b->ids[fill[t]++] = vis[k];
+                }
+        }
+        if (pass == 0) {
+            for (int64_t t = 0; t < nb; t++) b->start[t + 1] += b->start[t];
+            b->ids = (int64_t *)malloc(sizeof(int64_t) * (size_t)(b->start[nb] > 0 ? b->start[nb] : 1));
+            if (!b->ids) {
+                free(fill);
+                return -2;
+            }
+            memcpy(fill, b->start, sizeof(int64_t) * (size_t)nb);
+        }
+    }
+    free(fill);
+    return 0;
+}
+
+static void bins_free(bins_t *b)
+{
+    free(b->start);
+    free(b->ids);
+}
+
+/* the Gaussians pixel p scans: every visible one, or its bin's list */
+static void pixel_candidates(const bins_t *b, const int64_t *vis, int64_t nvis, const cam_t *c, int64_t p,
+                             const int64_t **ids, int64_t *nids)
+{
+    if (b->bin <= 0) {
+        *ids = vis;
+        *nids = nvis;
+        return;
+    }
+    const int64_t t = (p / c->W) / b->bin * b->bx + (p % c->W) / b->bin;
+    *ids = b->ids + b->start[t];
+    *nids = b->start[t + 1] - b->start[t];
+}
+
 int oracle_render(int64_t n, const double *means, const double *ls, const double *quats, const double *ologits,
                   const double *sh, int deg, const double *med, const double *cam, int64_t npix,
-                  const int64_t *pix, double near_rel, double *out, int nthreads)
+                  const int64_t *pix, double near_rel, int bin, double *out, int nthreads)
 {
     if (n < 0 || deg < 0 || deg > 3) return -1;
     cam_t c;
@@ -631,6 +709,8 @@ int oracle_render(int64_t n, const double *means, const double *ls, const double
     project_all(&c, n, means, ls, quats, ologits, sh, deg, med, P, nthreads);
     int64_t nvis;
     int64_t *vis = visible_ids(P, n, &nvis);
+    bins_t bins;
+    if (bins_build(P, vis, nvis, &c, bin, near_rel, &bins) != 0) return -2;
 #ifdef _OPENMP
 #pragma omp parallel num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
 #endif
@@ -643,7 +723,11 @@ int oracle_render(int64_t n, const double *means, const double *ls, const double
             plist_t L;
             near_t nr = {near_rel, 0, {{0, 0}}};
             double res[7];
-            render_pixel(P, vis, nvis, &c, med, pix ? pix[k] : k, NULL, &nr, &b, &L, res);
+            const int64_t p = pix ? pix[k] : k;
+            const int64_t *ids;
+            int64_t nids;
+            pixel_candidates(&bins, vis, nvis, &c, p, &ids, &nids);
+            render_pixel(P, ids, nids, &c, med, p, NULL, &nr, &b, &L, res);
             double *o = out + (size_t)NPIX * k;
             o[O_R] = res[0];
             o[O_G] = res[1];
@@ -663,6 +747,7 @@ int oracle_render(int64_t n, const double *means, const double *ls, const double
         }
         pixbuf_free(&b);
     }
+    bins_free(&bins);
     free(vis);
     free(P);
     return 0;
@@ -677,7 +762,7 @@ int oracle_nbf(void) { return NBF; }
  * 0 alone when it has more). */
 int oracle_render_branches(int64_t n, const double *means, const double *ls, const double *quats,
                            const double *ologits, const double *sh, int deg, const double *med, const double *cam,
-                           int64_t npix, const int64_t *pix, double near_rel, double *out, int nthreads)
+                           int64_t npix, const int64_t *pix, double near_rel, int bin, double *out, int nthreads)
 {
     if (n < 0 || deg < 0 || deg > 3 || npix < 0 || (npix > 0 && !pix)) return -1;
     cam_t c;
@@ -687,6 +772,8 @@ int oracle_render_branches(int64_t n, const double *means, const double *ls, con
     project_all(&c, n, means, ls, quats, ologits, sh, deg, med, P, nthreads);
     int64_t nvis;
     int64_t *vis = visible_ids(P, n, &nvis);
+    bins_t bins;
+    if (bins_build(P, vis, nvis, &c, bin, near_rel, &bins) != 0) return -2;
     memset(out, 0, sizeof(double) * (size_t)npix * NBR * NBF);
 #ifdef _OPENMP
 #pragma omp parallel num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
@@ -700,12 +787,15 @@ int oracle_render_branches(int64_t n, const double *means, const double *ls, con
             plist_t L;
             near_t nr = {near_rel, 0, {{0, 0}}};
             double res[7];
-            render_pixel(P, vis, nvis, &c, med, pix[k], NULL, &nr, &b, &L, res);
+            const int64_t *ids;
+            int64_t nids;
+            pixel_candidates(&bins, vis, nvis, &c, pix[k], &ids, &nids);
+            render_pixel(P, ids, nids, &c, med, pix[k], NULL, &nr, &b, &L, res);
             const int64_t nb = nr.n <= NEAR_MAX ? ((int64_t)1 << nr.n) : 1;
             for (int64_t br = 0; br < nb; br++) {
                 flips_t fl;
                 branch_flips(&nr, br, &fl);
-                render_pixel(P, vis, nvis, &c, med, pix[k], &fl, NULL, &b, &L, res);
+                render_pixel(P, ids, nids, &c, med, pix[k], &fl, NULL, &b, &L, res);
                 double *o = out + ((size_t)k * NBR + (size_t)br) * NBF;
                 o[B_R] = res[0];
                 o[B_G] = res[1];
@@ -719,6 +809,7 @@ int oracle_render_branches(int64_t n, const double *means, const double *ls, con
         }
         pixbuf_free(&b);
     }
+    bins_free(&bins);
     free(vis);
     free(P);
     return 0;
@@ -941,7 +1032,7 @@ static void gaussian_backward(const cam_t *c, const pg_t *g, const double *gp, c
 
 int oracle_backward(int64_t n, const double *means, const double *ls, const double *quats, const double *ologits,
                     const double *sh, int deg, const double *med, const double *cam, int64_t npix,
-                    const int64_t *pix, const double *gout, const int64_t *branch, double near_rel,
+                    const int64_t *pix, const double *gout, const int64_t *branch, double near_rel, int bin,
                     double *g_means, double *g_ls, double *g_quats, double *g_ologits, double *g_sh, double *g_med,
                     double *g_proj, int nthreads)
 {
@@ -956,6 +1047,8 @@ int oracle_backward(int64_t n, const double *means, const double *ls, const doub
     project_all(&c, n, means, ls, quats, ologits, sh, deg, med, P, nthreads);
     int64_t nvis;
     int64_t *vis = visible_ids(P, n, &nvis);
+    bins_t bins;
+    if (bins_build(P, vis, nvis, &c, bin, near_rel, &bins) != 0) return -2;
     double gmed_total[9] = {0};
 #ifdef _OPENMP
 #pragma omp parallel num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
@@ -973,15 +1066,18 @@ int oracle_backward(int64_t n, const double *means, const double *ls, const doub
             const double px = (double)(p % c.W) + 0.5, py = (double)(p / c.W) + 0.5;
             plist_t L;
             const int64_t br = branch ? branch[k] : 0;
+            const int64_t *ids;
+            int64_t nids;
+            pixel_candidates(&bins, vis, nvis, &c, p, &ids, &nids);
             if (br == 0) {
-                pixel_list(P, vis, nvis, px, py, &s, &L, NULL, NULL);
+                pixel_list(P, ids, nids, px, py, &s, &L, NULL, NULL);
             } else {
                 /* the branch's flips name near decisions of the FP64 walk */
                 near_t nr = {near_rel, 0, {{0, 0}}};
                 flips_t fl;
-                pixel_list(P, vis, nvis, px, py, &s, &L, NULL, &nr);
+                pixel_list(P, ids, nids, px, py, &s, &L, NULL, &nr);
                 branch_flips(&nr, br, &fl);
-                pixel_list(P, vis, nvis, px, py, &s, &L, &fl, NULL);
+                pixel_list(P, ids, nids, px, py, &s, &L, &fl, NULL);
             }
             pixel_backward(P, s.lst, L.m, L.Tf, med, c.zfar, G, gp, gmed);
         }
@@ -1012,6 +1108,7 @@ int oracle_backward(int64_t n, const double *means, const double *ls, const doub
         gaussian_backward(&c, &P[i], gpi, sh + 3 * K * i, deg, ologits[i], gmu, gl, gqq, &g_ologits[i], gs);
     }
     if (g_proj) memcpy(g_proj, gp, sizeof(double) * (size_t)NGP * (size_t)n);
+    bins_free(&bins);
     free(vis);
     free(gp);
     free(P);

@@ -50,7 +50,8 @@ def test_rank_helpers_gloo(tmp_path):
 def test_reference_arm_under_torchrun():
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes", "1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), "bench.py", "--impl", "reference",
-           "--gpus", "2", "--steps", "1", "--warmup", "0"]  # the driver's own form of the call
+           "--gpus", "2", "--steps", "1", "--warmup", "0",  # the driver's own form of the call,
+           "--gaussians", "30000"]  # a smaller scene: every oracle step is a whole step
     env = dict(os.environ, OMP_NUM_THREADS="2")
     r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600, env=env)
     assert r.returncode == 0, r.stderr[-2000:]
@@ -59,4 +60,5 @@ def test_reference_arm_under_torchrun():
     out = json.loads(lines[0])
     assert out["impl"] == "reference" and out["n_gpus"] == 2
     assert out["value"] > 0 and out["e2e"]["value"] == out["value"]
-    assert out["cpu_baseline"]["kind"] == "oracle"
+    assert out["cpu_baseline"]["kind"] == "oracle-binned" and out["cpu_baseline"]["extrapolated"] is False
+    assert out["steps"] == out["measured_steps"] == 1

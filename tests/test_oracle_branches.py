@@ -147,3 +147,39 @@ def test_near_decisions_are_rare_at_the_tolerance():
     r = oracle.render(g, m, cam)
     assert (r["n_near"] > 4).sum() == 0
     assert (r["n_near"] > 0).mean() < 1e-3
+
+
+def test_binned_scan_equals_the_full_scan():
+    """The binned candidate scan (bin x bin pixel blocks, widened 3-sigma
+    boxes) gives the unbinned oracle's results bit for bit: images, depths,
+    decision margins, near-decision counts, branches and gradients, on the
+    tiny workload and on a dense ragged scene with large Gaussians."""
+    rng = np.random.default_rng(4)
+    g, m, cam = scenes.tiny_scene(0)
+    cases = [(g, m, cam, 16), (g, m, cam, 7)]
+    n = 1500
+    cam2 = scenes.look_at((0.2, -0.1, -0.3), (0.0, 0.0, 3.5), 91, 67, 80.0, 80.0)
+    g2 = scenes.Gaussians(np.float32(np.c_[rng.uniform(-1.5, 1.5, (n, 2)), rng.uniform(1.5, 6.0, n)]),
+                          np.float32(rng.normal(-1.8, 0.6, (n, 3))), np.float32(rng.standard_normal((n, 4))),
+                          np.float32(rng.normal(0.5, 1.0, n)), np.float32(rng.normal(0, 0.3, (n, 4, 3))), 1)
+    cases.append((g2, m, cam2, 16))
+    for g_, m_, c_, b in cases:
+        full = oracle.render(g_, m_, c_)
+        binned = oracle.render(g_, m_, c_, bin=b)
+        for k in ("image", "depth", "depth01", "T_f", "n_contrib", "n_cand", "n_iter", "n_near", "tie", "gmargin"):
+            np.testing.assert_array_equal(binned[k], full[k], err_msg=k)
+        # a margin beyond the widened boxes (4 near_rel) may come from a Gaussian the bins leave out
+        cap = 4 * oracle.NEAR
+        np.testing.assert_array_equal(np.minimum(binned["margin"], cap), np.minimum(full["margin"], cap))
+        pix = np.flatnonzero(full["n_near"].reshape(-1) > 0)[:20]
+        if pix.size:
+            a, bb = oracle.branches(g_, m_, c_, pix), oracle.branches(g_, m_, c_, pix, bin=b)
+            np.testing.assert_array_equal(a["image"], bb["image"])
+        G = rng.standard_normal((3, c_.height, c_.width))
+        Gz = rng.standard_normal((c_.height, c_.width))
+        ga = oracle.backward(g_, m_, c_, G, Gz, bin=b)
+        gc = oracle.backward(g_, m_, c_, G, Gz)
+        # the same per-pixel terms, summed over threads in another order
+        for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "medium"):
+            np.testing.assert_allclose(ga[k], gc[k], rtol=1e-12, atol=1e-12 * np.abs(gc[k]).max(), err_msg=k)
+        assert np.abs(ga["means"]).sum() > 0
