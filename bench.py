@@ -38,7 +38,12 @@ FLOP_PER_PAIR_FWD = 18
 FLOP_PER_PAIR_BWD = 50
 # DRAM bytes (read + write) of one launch at the default workload (1.5M Gaussians, 1920x1280,
 # 16x16 tiles), from an ncu capture of the current kernel; used for the roofline's `traffic`
-KERNEL_DRAM_BYTES = {"blend_bwd": 80.17e6 + 2.55e6}
+KERNEL_DRAM_BYTES = {"blend_bwd": 80.20e6 + 2.49e6}
+# shared-memory wavefronts per walked pixel-Gaussian pair of the blends
+# (l1tex__data_pipe_lsu_wavefronts_mem_shared.sum / walked pairs of the same
+# launch, from an ncu capture of the current kernels on the 300k-Gaussian
+# 1920x1280 case); the shared-memory peak is one wavefront (128 B) per SM per clock
+KERNEL_SMEM_WAVEFRONTS_PER_PAIR = {"blend_fwd": 0.1026, "blend_bwd": 0.2004}
 SM_COUNT_FALLBACK = 148
 
 
@@ -52,6 +57,7 @@ def parse_args():
     ap.add_argument("--tile", default="16x16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched and warm-start comparisons")
     ap.add_argument("--views", type=int, default=N_VIEWS, help="arc views (targets rendered up front)")
     ap.add_argument("--gemm-size", type=int, default=8192, help="gemm: M = N = K")
     ap.add_argument("--workload", choices=["train", "batch", "warmstart", "gemm", "backscatter", "loop"], default="train",
@@ -262,7 +268,10 @@ def run_ours(args, world, rank, local):
     for cam in cams:
         img, _, _ = r.forward(st_t, gt, med_gt, cam, pixel=pixel)
         targets.append(img.clone())
-    del gt
+    forms = rank == 0 and world == 1 and not args.no_forms and not pixel
+    init = {k: params[k].clone() for k in R.PARAM_NAMES} if forms else None
+    if not forms:
+        del gt
     torch.cuda.synchronize()
 
     tensors = {k: params[k] for k in R.PARAM_NAMES}
@@ -463,6 +472,15 @@ def run_ours(args, world, rank, local):
             a_ = u_ / (per_launch[k] * 1e-3) / (1e12 if un_ == "TFLOP/s" else 1e9)
             p_ = fp32_peak_tflops if un_ == "TFLOP/s" else float(peaks["hbm_gbs"])
             stage_roofline[k] = {"bound": b_, "achieved": round(a_, 2), "unit": un_, "frac": round(a_ / p_, 4)}
+            wpp = KERNEL_SMEM_WAVEFRONTS_PER_PAIR.get(k)
+            if wpp:
+                pairs_k = walk if k == "blend_fwd" else last
+                wf_per_s = wpp * pairs_k / (per_launch[k] * 1e-3)
+                smem_peak = sm_count * f_mhz * 1e6  # wavefronts per second
+                stage_roofline[k].update({"smem_achieved": round(wf_per_s * 128 / 1e9, 1), "smem_unit": "GB/s",
+                                          "smem_peak": round(smem_peak * 128 / 1e9, 1),
+                                          "smem_frac": round(wf_per_s / smem_peak, 4),
+                                          "smem_wavefronts_per_pair": wpp})
 
     out = {
         "metric": METRIC,
@@ -487,7 +505,8 @@ def run_ours(args, world, rank, local):
         "roofline": {"kernel": dom, "bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 2),
                      "unit": unit, "frac": round(achieved / peak, 4),
                      "traffic": KERNEL_DRAM_BYTES.get(dom) if (args.n == N_GAUSS and args.tile == "16x16") else None,
-                     "peak_source": note},
+                     "peak_source": note,
+                     **{k_: v_ for k_, v_ in stage_roofline.get(dom, {}).items() if k_.startswith("smem")}},
         "stages_ms": stages_ms,
         "stages_source": "per-stage CUDA events in a pass of the same length after the timed region; inside "
                          "the timed region only the dominant kernel (blend_bwd) is bracketed",
@@ -497,37 +516,43 @@ def run_ours(args, world, rank, local):
         "clocks": clk,
         "e2e": e2e,
     }
+    if forms:
+        # the two added forms next to the plain one, small enough for the default run
+        # (--workload batch and --workload warmstart run them at full size)
+        from paper_2411_19588_b300 import scenes as S
+        init["sh_degree"] = params["sh_degree"]
+        bc = batch_compare(init, torch.tensor([0.1] * 9, dtype=torch.float32, device="cuda"), gt, med_gt,
+                           S.uneven_cameras(64, seed=4), reps=2, warm=1)
+        del gt
+        ws = warmstart_study(r, init, cams, targets, med_gt, n_scenes=10, views_per_scene=100, epochs=30, iters=300)
+        out["forms"] = {
+            "batch": dict(bc, note="64 uneven views (640..1920 px wide) over the same scene: forward + loss + backward, "
+                                   "plain per-view launches in sequence vs one batched launch each way under a "
+                                   "CUDA graph, tile/staging autotuned on these views; 2 repeats"),
+            "warmstart": dict(ws, note="small study: 1,000 training renders of 10 generated scenes, 300-iteration "
+                                       "fits of this workload from its initial state; iterations and fit time to reach "
+                                       "the plain fit's final PSNR"),
+        }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.n)
     if rank == 0:
         print(json.dumps(out), flush=True)
 
 
-def run_batch(args, world, rank, local):
-    """Batched form: args.batch_views cameras of uneven resolution (640x480
-    .. 1920x1280) over the 1.5M-Gaussian scene; per view forward, the
-    L1 + 0.2 (1 - SSIM) loss against its target and backward, gradients
-    summed over the views. Three ways: the plain per-view path in sequence,
-    the batched path (one persistent blend launch each way), and the batched
-    path replayed from a CUDA graph. Tile shape and staging batch of the
-    batched path come from the autotuner."""
+def batch_compare(params, med, gt, med_gt_t, cams, reps: int, warm: int) -> dict:
+    """The batched form against the plain form on the same views: per view
+    forward, the L1 + 0.2 (1 - SSIM) loss against its target and backward,
+    gradients summed over the views; the plain per-view path in sequence, the
+    batched path (one persistent blend launch each way) eager and replayed from
+    a CUDA graph. Tile shape and staging batch of the batched path come from
+    the autotuner (timed on these views, cached)."""
     import torch
 
     from paper_2411_19588_b300 import autotune
     from paper_2411_19588_b300 import render as R
-    from paper_2411_19588_b300 import scenes
 
-    torch.cuda.set_device(local)
-    g_gt, med_gt, _ = scenes.patch_scene(args.n, 3, (2.0, 15.0), 1920, 1280, 1800.0)
-    cams = scenes.uneven_cameras(args.batch_views, seed=4)
-    fit, _ = scenes.perturb(g_gt, med_gt, seed=1 + rank)
-    params = R.params_to_device(fit)
-    med = torch.tensor([0.1] * 9, dtype=torch.float32, device="cuda")
-    gt = R.params_to_device(g_gt)
-    med_gt_t = torch.tensor(med_gt.as_array(), device="cuda")
     r0 = R.Renderer()
     targets = [r0.render(gt, med_gt_t, c)[0].clone() for c in cams]
-    del gt
     V = len(cams)
     upstream = [torch.full_like(t, 1e-3) for t in targets]
     tune = autotune.autotune(params, med, cams, upstream)
@@ -558,22 +583,21 @@ def run_batch(args, world, rank, local):
             rp.loss(stp, imgp[v], targets[v], LAMBDA_SSIM, loss_out=lossbuf[v], grad_out=gbuf[v])
             rp.backward(stp, params, med, cams[v], gbuf[v], grads=grads)
 
-    def timed(fn, reps):
+    def timed(fn, n):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(reps):
+        for _ in range(n):
             fn()
         e1.record()
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
+        return e0.elapsed_time(e1) / n
 
-    steps = max(1, min(args.steps, 10))
-    for _ in range(max(1, args.warmup // 3)):
+    for _ in range(max(1, warm)):
         plain()
         batched()
-    ms_plain = timed(plain, steps)
-    ms_batched = timed(batched, steps)
+    ms_plain = timed(plain, reps)
+    ms_batched = timed(batched, reps)
     graph = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
@@ -582,30 +606,59 @@ def run_batch(args, world, rank, local):
             batched()
     torch.cuda.current_stream().wait_stream(side)
     graph.replay()
-    ms_graph = timed(graph.replay, steps)
+    ms_graph = timed(graph.replay, reps)
     r.sync_status()
-    ms = max_over_ranks(ms_graph, world)
+    out = {"views": V, "pixels": int(sum(c.width * c.height for c in cams)), "reps": reps,
+           "ms_plain_sequential": round(ms_plain, 3), "ms_batched_eager": round(ms_batched, 3),
+           "ms_batched_graph": round(ms_graph, 3), "speedup_graph_vs_plain": round(ms_plain / ms_graph, 3),
+           "tile": list(tune["tile"]), "gaussian_batch": tune["batch"],
+           "autotune": {"cached": tune["cached"], "table_ms": {k: round(v, 3) for k, v in tune["table"].items()}}}
+    for bb in (b, r, rp, r0):
+        bb.close()
+    return out
+
+
+def run_batch(args, world, rank, local):
+    """Batched form: args.batch_views cameras of uneven resolution (640x480
+    .. 1920x1280) over the 1.5M-Gaussian scene, compared with the plain
+    form on the same views (see batch_compare)."""
+    import torch
+
+    from paper_2411_19588_b300 import render as R
+    from paper_2411_19588_b300 import scenes
+
+    torch.cuda.set_device(local)
+    g_gt, med_gt, _ = scenes.patch_scene(args.n, 3, (2.0, 15.0), 1920, 1280, 1800.0)
+    cams = scenes.uneven_cameras(args.batch_views, seed=4)
+    fit, _ = scenes.perturb(g_gt, med_gt, seed=1 + rank)
+    params = R.params_to_device(fit)
+    med = torch.tensor([0.1] * 9, dtype=torch.float32, device="cuda")
+    gt = R.params_to_device(g_gt)
+    med_gt_t = torch.tensor(med_gt.as_array(), device="cuda")
+    steps = max(1, min(args.steps, 10))
+    res = batch_compare(params, med, gt, med_gt_t, cams, steps, max(1, args.warmup // 3))
+    ms = max_over_ranks(res["ms_batched_graph"], world)
+    V = res["views"]
     out = {"metric": f"batched {V}-view forward+backward (uneven 640x480..1920x1280, 1.5M Gaussians)",
            "value": round(world * V * 1000.0 / ms, 2), "unit": "views/s", "n_gpus": world, "steps": steps,
            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "batch", "views": V, "n_gaussians": args.n,
-                      "pixels": int(sum(c.width * c.height for c in cams)), "tile": list(tune["tile"]),
-                      "gaussian_batch": tune["batch"]},
-           "ms_plain_sequential": round(ms_plain, 3), "ms_batched_eager": round(ms_batched, 3),
-           "ms_batched_graph": round(ms_graph, 3), "speedup_graph_vs_plain": round(ms_plain / ms_graph, 3),
-           "autotune": {"cached": tune["cached"], "table_ms": {k: round(v, 3) for k, v in tune["table"].items()}}}
+           "config": {"workload": "batch", "views": V, "n_gaussians": args.n, "pixels": res["pixels"],
+                      "tile": res["tile"], "gaussian_batch": res["gaussian_batch"]}}
+    out.update({k: v for k, v in res.items() if k.startswith("ms_") or k in ("speedup_graph_vs_plain", "autotune")})
     if rank == 0:
         print(json.dumps(out), flush=True)
 
 
-def run_warmstart(args, world, rank, local):
-    """Learned warm-start form: renders of generated 300k-Gaussian scenes with
-    known water become feature rows; the BF16 MLP trains on them; the 1.5M
-    fit then starts once from the default medium (the plain fit, the yardstick)
-    and once from the medium the network predicts for five target views,
-    and the warm fit counts iterations and fit time until it reaches the
-    plain fit's final PSNR (fallback to the plain fit if it never does)."""
+def warmstart_study(r, params, cams, tgt, med_gt, n_scenes: int, views_per_scene: int, epochs: int,
+                    iters: int) -> dict:
+    """The learned warm-start against the plain fit on the same B300: renders
+    of generated 300k-Gaussian scenes with known water become feature rows;
+    the BF16 MLP trains on them; the fit of the workload then starts once from
+    the default medium (the plain fit, the yardstick) and once from the medium
+    the network predicts for five target views, and the warm fit counts
+    iterations and fit time until it reaches the plain fit's final PSNR
+    (fallback to the plain fit if it never does)."""
     import torch
 
     from paper_2411_19588_b300 import mlp as M
@@ -613,22 +666,18 @@ def run_warmstart(args, world, rank, local):
     from paper_2411_19588_b300 import scenes
     from paper_2411_19588_b300 import warmstart as W
 
-    torch.cuda.set_device(local)
-    r = R.Renderer()
-    # the device scene generator's first call loads torch's linear-algebra libraries
-    # (tens of seconds on a fresh box): make it once, untimed, before the timed generation
-    from paper_2411_19588_b300 import scenes as S
-    S.patch_scene_device(1000, 1, (2.0, 12.0), 1280, 854, 1200.0)
+    # the device scene generator's first call loads libraries: once, untimed
+    scenes.patch_scene_device(1000, 1, (2.0, 12.0), 1280, 854, 1200.0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    bank, targets = W.generate(r, args.ws_scenes, args.ws_views)
+    bank, targets = W.generate(r, n_scenes, views_per_scene)
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t0
     n_rows = bank.shape[0]
     net = M.Mlp(r, 256)
     net.set_params(scenes.mlp_init(5))
-    tr = W.train(net, bank, targets, epochs=args.ws_epochs)
-    # time one training step of the network alone (gather, 8 tensor-core GEMMs, head, Adam)
+    tr = W.train(net, bank, targets, epochs=epochs)
+    # one training step of the network alone (gather, 8 tensor-core GEMMs, head, Adam)
     idx = torch.arange(0, 256, dtype=torch.int32, device="cuda")
     for _ in range(5):
         net.step(bank, targets, idx=idx, lr=1e-6)
@@ -641,17 +690,8 @@ def run_warmstart(args, world, rank, local):
     torch.cuda.synchronize()
     mlp_us = e0.elapsed_time(e1) * 10.0
     mlp_launches = (R.kernel_launches() - l0) // 100
-    # constant predictors on the validation rows, for scale
     tval = targets.double().cpu().numpy()
     default_err = float(np.abs(np.log(0.1) - np.log(tval)).mean())
-
-    params, _, gt, med_gt, cams = build_workload(args.n, rank, args.views)
-    tgt = []
-    st = r.state()
-    for cam in cams:
-        img, _, _ = r.forward(st, gt, med_gt, cam)
-        tgt.append(img.clone())
-    del gt
     nv = len(cams)
     eval_views = sorted(set(int(round(x)) for x in np.linspace(0, nv - 1, 10)))
     pred_views = sorted(set(int(round(x)) for x in np.linspace(0, nv - 1, 5)))
@@ -661,37 +701,59 @@ def run_warmstart(args, world, rank, local):
     torch.cuda.synchronize()
     t_pred = time.perf_counter() - t1
     truth = med_gt.double().cpu().numpy()
-    plain = W.fit_curve(W.Fit(r, params, W.DEFAULT_MEDIUM, cams, tgt), args.ws_iters, 25, eval_views)
-    warm = W.fit_curve(W.Fit(r, params, pred, cams, tgt), args.ws_iters, 25, eval_views,
-                       stop_psnr=plain["final_psnr"])
+    plain = W.fit_curve(W.Fit(r, params, W.DEFAULT_MEDIUM, cams, tgt), iters, 25, eval_views)
+    warm = W.fit_curve(W.Fit(r, params, pred, cams, tgt), iters, 25, eval_views, stop_psnr=plain["final_psnr"])
     r.sync_status()
     fallback = warm["reached_at"] is None
-    value = plain["iters"] if fallback else warm["reached_at"]
+    return {"value": plain["iters"] if fallback else warm["reached_at"],
+            "config": {"train_renders": n_rows, "train_scenes": n_scenes, "train_gaussians": 300_000,
+                       "train_resolution": "1280x854", "mlp": "3080-128-128-9", "epochs": epochs,
+                       "fit_views": nv, "fit_iters": iters},
+            "plain": {"iters": plain["iters"], "fit_s": round(plain["wall_s"], 3),
+                      "final_psnr": round(plain["final_psnr"], 3),
+                      "init_medium_log_err": round(W.log_error(W.DEFAULT_MEDIUM, truth), 4),
+                      "final_medium_log_err": round(W.log_error(np.maximum(plain["medium"], 1e-6), truth), 4)},
+            "warm": {"reached_at": warm["reached_at"], "fit_s": round(warm["wall_s"], 3),
+                     "predict_s": round(t_pred, 4), "final_psnr": round(warm["final_psnr"], 3),
+                     "init_medium_log_err": round(W.log_error(pred, truth), 4),
+                     "predicted": np.round(pred, 4).tolist()},
+            "fallback_to_plain": fallback,
+            "speedup_iters": None if fallback else round(plain["iters"] / max(1, warm["reached_at"]), 3),
+            "speedup_fit_time": None if fallback else round(plain["wall_s"] / max(1e-9, warm["wall_s"] + t_pred), 3),
+            "medium_truth": np.round(truth, 4).tolist(),
+            "training": {"generate_s": round(t_gen, 2), "renders_per_s": round(n_rows / t_gen, 1),
+                         "train_s": round(tr["wall_s"], 2), "steps": tr["steps"],
+                         "val_log_err": round(tr["val_loss"], 4), "default_init_log_err": round(default_err, 4),
+                         "final_train_log_err": round(tr["train_loss"][-1], 4), "mlp_step_us": round(mlp_us, 1),
+                         "mlp_step_launches": int(mlp_launches)},
+            "plain_curve": [(i, round(p, 3)) for i, p in plain["curve"]],
+            "warm_curve": [(i, round(p, 3)) for i, p in warm["curve"]]}
+
+
+def run_warmstart(args, world, rank, local):
+    """Learned warm-start form (see warmstart_study) at the full study's size."""
+    import torch
+
+    from paper_2411_19588_b300 import render as R
+
+    torch.cuda.set_device(local)
+    r = R.Renderer()
+    params, _, gt, med_gt, cams = build_workload(args.n, rank, args.views)
+    tgt = []
+    st = r.state()
+    for cam in cams:
+        img, _, _ = r.forward(st, gt, med_gt, cam)
+        tgt.append(img.clone())
+    del gt
+    res = warmstart_study(r, params, cams, tgt, med_gt, args.ws_scenes, args.ws_views, args.ws_epochs, args.ws_iters)
     out = {"metric": "learned warm-start: fit iterations to reach the plain fit's final PSNR "
                      "(1.5M Gaussians, 1920x1280, 100-view arc)",
-           "value": value, "unit": "iterations", "n_gpus": world, "steps": args.ws_iters, "warmup": 0,
+           "value": res.pop("value"), "unit": "iterations", "n_gpus": world, "steps": args.ws_iters, "warmup": 0,
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 MLP / f32 renderer",
-           "data": "synthetic (generated scenes with known water)",
-           "config": {"workload": "warmstart", "train_renders": n_rows, "train_scenes": args.ws_scenes,
-                      "train_gaussians": 300_000, "train_resolution": "1280x854", "mlp": "3080-128-128-9",
-                      "epochs": args.ws_epochs, "fit_gaussians": args.n, "fit_views": nv},
-           "plain": {"iters": plain["iters"], "fit_s": round(plain["wall_s"], 3), "final_psnr": round(plain["final_psnr"], 3),
-                     "init_medium_log_err": round(W.log_error(W.DEFAULT_MEDIUM, truth), 4),
-                     "final_medium_log_err": round(W.log_error(np.maximum(plain["medium"], 1e-6), truth), 4)},
-           "warm": {"reached_at": warm["reached_at"], "fit_s": round(warm["wall_s"], 3),
-                    "predict_s": round(t_pred, 4), "final_psnr": round(warm["final_psnr"], 3),
-                    "init_medium_log_err": round(W.log_error(pred, truth), 4), "predicted": np.round(pred, 4).tolist()},
-           "fallback_to_plain": fallback,
-           "speedup_iters": None if fallback else round(plain["iters"] / max(1, warm["reached_at"]), 3),
-           "speedup_fit_time": None if fallback else round((plain["wall_s"]) / max(1e-9, warm["wall_s"] + t_pred), 3),
-           "medium_truth": np.round(truth, 4).tolist(),
-           "training": {"generate_s": round(t_gen, 2), "renders_per_s": round(n_rows / t_gen, 1),
-                        "train_s": round(tr["wall_s"], 2), "steps": tr["steps"],
-                        "val_log_err": round(tr["val_loss"], 4), "default_init_log_err": round(default_err, 4),
-                        "final_train_log_err": round(tr["train_loss"][-1], 4), "mlp_step_us": round(mlp_us, 1),
-                        "mlp_step_launches": int(mlp_launches)},
-           "plain_curve": [(i, round(p, 3)) for i, p in plain["curve"]],
-           "warm_curve": [(i, round(p, 3)) for i, p in warm["curve"]]}
+           "data": "synthetic (generated scenes with known water)"}
+    cfg = res.pop("config")
+    out["config"] = dict({"workload": "warmstart", "fit_gaussians": args.n}, **cfg)
+    out.update(res)
     if rank == 0:
         print(json.dumps(out), flush=True)
 

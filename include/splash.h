@@ -208,7 +208,7 @@ typedef struct {
     const uint32_t *tile_ids;    /* [n_keys] sorted tile index of each pair */
     const uint32_t *gauss_ids;   /* [n_keys] Gaussian index of each pair */
     const uint32_t *ranges;      /* [tiles][2] half-open [start, end) into the pairs */
-    const uint32_t *depth_keys;  /* [n] FP32 depth bits, 0xffffffff when culled */
+    const uint32_t *depth_keys;  /* [n] FP32 depth bits minus those of z_near, 0xffffffff when culled */
     const uint32_t *tiles_touched; /* [n] */
     const float *records;        /* [n][12] projected Gaussian: x_hi, y_hi, x_lo, y_lo (centre =
                                     hi + lo), A, B, C (conic scaled by -log2(e)/2, -log2(e),
@@ -217,7 +217,9 @@ typedef struct {
                                     depth_keys != 0xffffffff */
     const float *final_T;        /* [H*W] transmittance after the last contributor */
     const float *acc_alpha;      /* [H*W] sum of alpha T */
-    const uint32_t *n_last;      /* [H*W] 1 + list position of the last contributor */
+    const uint32_t *n_last;      /* [H*W] the backward's walk bound: list entries in front of the
+                                    Gaussian that stopped the pixel (the whole list if none did);
+                                    every contributor lies in front of it */
     const uint32_t *n_walk;      /* [H*W] list entries the pixel walked (its blend work) */
 } splash_state_info;
 splash_status splash_state_get_info(const splash_state *st, splash_state_info *out);
@@ -328,7 +330,7 @@ uint64_t splash_kernel_launches(void);
  * code that cannot take the synchronisation an allocation may imply. This
  * entry point allocates nothing: its scratch (ping-pong pair buffers, digit
  * histograms, look-back flags, a status word) is one static device array of
- * about 9.1 MB that every GPU loading this library holds until the process
+ * about 10 MB that every GPU loading this library holds until the process
  * exits. Same arguments and result as splash_sort_pairs_u32, without the
  * context and state: keys_in/vals_in (device, n; vals_in NULL = 0..n-1) are
  * left unchanged, keys_out/vals_out (device, n) receive the pairs sorted

@@ -186,7 +186,8 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
     if (n > 0) {
         Stage t(ctx->prof, SPLASH_STAGE_DEPTH_SORT, s);
         const int which = sort_pairs(st->depth_key.as<uint32_t>(), nullptr, st->dk0.as<uint32_t>(), st->dv0.as<uint32_t>(),
-                                     st->dk1.as<uint32_t>(), st->dv1.as<uint32_t>(), n, nullptr, 32, ss, ctx->d_status,
+                                     st->dk1.as<uint32_t>(), st->dv1.as<uint32_t>(), n, nullptr,
+                                     depth_key_bits(ck.znear, ck.zfar), ss, ctx->d_status,
                                      ctx->opt.spin_limit, ctx->opt.test_stall_partition, s, kDepthSortItems);
         order = which ? st->dv1.as<uint32_t>() : st->dv0.as<uint32_t>();
     }

@@ -274,7 +274,8 @@ splash_status splash_batch_forward(splash_batch *b, const splash_gaussians *g, c
         if (n > 0) {
             Stage t(ctx->prof, SPLASH_STAGE_DEPTH_SORT, s);
             const int which = sort_pairs(dk, nullptr, b->dk0.as<uint32_t>(), b->dv0.as<uint32_t>(), b->dk1.as<uint32_t>(),
-                                         b->dv1.as<uint32_t>(), n, nullptr, 32, ss, ctx->d_status, ctx->opt.spin_limit,
+                                         b->dv1.as<uint32_t>(), n, nullptr, depth_key_bits(b->ck[v].znear, b->ck[v].zfar),
+                                         ss, ctx->d_status, ctx->opt.spin_limit,
                                          ctx->opt.test_stall_partition, s, kDepthSortItems);
             order = which ? b->dv1.as<uint32_t>() : b->dv0.as<uint32_t>();
         }
@@ -287,7 +288,7 @@ splash_status splash_batch_forward(splash_batch *b, const splash_gaussians *g, c
         }
         // the sorted pairs must end in this view's slice: emit where the pass count puts the result there
         const int bits = bits_for(ntiles);
-        const int passes = (bits + kRadixBits - 1) / kRadixBits;
+        const int passes = digit_plan(bits).passes;
         uint32_t *pk = b->pair_k.as<uint32_t>() + b->cap_off[v], *pv = b->pair_v.as<uint32_t>() + b->cap_off[v];
         uint32_t *tk = b->tmp_k.as<uint32_t>(), *tv = b->tmp_v.as<uint32_t>();
         const bool even = passes > 0 && (passes % 2 == 0);
@@ -357,7 +358,7 @@ splash_status splash_batch_backward(splash_batch *b, const splash_gaussians *g, 
     SPLASH_CUDA_TRY(cudaMemsetAsync(b->gacc.p, 0, sizeof(GAcc) * (size_t)(V * n), s));
     uint32_t *meta = b->item_meta.as<uint32_t>();
     // the forward's queue order is still in the item buffers
-    const int bits_passes = (24 + kRadixBits - 1) / kRadixBits;
+    const int bits_passes = digit_plan(24).passes;
     const uint32_t *items = ((bits_passes - 1) & 1) ? b->items_v.as<uint32_t>() : b->items_v1.as<uint32_t>();
     {
         Stage t(ctx->prof, SPLASH_STAGE_BLEND_BWD, s);

@@ -13,14 +13,19 @@
 // so the inner loop is plain compositing of the effective colour ct (made
 // once per Gaussian in the preprocess) and the water costs one epilogue.
 //
-// Work decomposition: one CTA per tile, kPxFwd / kPxBwd pixels of one row per
-// thread (they share the dy terms and, backward, one warp reduction of the
-// gradient fields per Gaussian). Gaussians are staged in shared
-// memory in batches of NB (64, 128 or 256); the local centre is formed once
-// per (tile, Gaussian) from the doubled-precision record, relative to the
-// 32-pixel-aligned corner that holds the tile (the same corner for every
-// tile shape, so all shapes do identical per-pixel arithmetic). A warp skips
-// a batch once all its pixels are done; the CTA stops when all are.
+// Work decomposition: one CTA per tile, 4 pixels of one row per thread in
+// both passes (they share the dy terms and, backward, one warp reduction of
+// the gradient fields per Gaussian). A thread's pixels run as two FP32x2 lane
+// pairs (packed add / mul / fma, one lane per pixel column) through
+// predicated bodies: a pixel that a Gaussian does not reach gets alpha = 0,
+// which adds nothing. Gaussians are staged in shared memory in batches of NB
+// (64 forward, 128 backward by default) with every per-Gaussian constant
+// stored twice, so one 16-byte load yields a packed operand; the local centre
+// is formed once per (tile, Gaussian) from the doubled-precision record,
+// relative to the 32-pixel-aligned corner that holds the tile (the same
+// corner for every tile shape, so all shapes do identical per-pixel
+// arithmetic). A warp skips a Gaussian that none of its pixels reaches and a
+// batch once all its pixels are done; the CTA stops when all are.
 // Plain launches run one CTA per tile of one view; the persistent launches
 // keep one wave of CTAs that pull (view, tile) items from a queue.
 #include <cuda_runtime.h>
@@ -51,7 +56,7 @@ __device__ __forceinline__ float rcp_approx(float x)
 __device__ __forceinline__ float quad(float dx, float A, float Bdy, float Cdy2) { return fmaf(dx, fmaf(A, dx, Bdy), Cdy2); }
 
 // pixels per thread, forward and backward
-constexpr int kPxFwd = 2;
+constexpr int kPxFwd = 4;
 constexpr int kPxBwd = 4;
 
 template <int TW, int TH, int PX>
@@ -65,26 +70,40 @@ constexpr int fwd_threads() { return Tile<TW, TH, kPxFwd>::NT; }
 template <int TW, int TH>
 constexpr int bwd_threads() { return Tile<TW, TH, kPxBwd>::NT; }
 
-// stage list entry `slot` of the batch: local centre, conic, log-opacity, colour, depth
-__device__ __forceinline__ void stage_rec(const Rec *__restrict__ rec, uint32_t gid, int ox, int oy, float4 *s0, float4 *s1,
-                                          float2 *s2, int slot)
+// Forward staging: every per-Gaussian constant twice, so that one 16-byte
+// shared load yields the packed operand of a thread's two pixel columns
+// (FP32x2 arithmetic, one lane per column). Positions are stored negated:
+// pxl + (-x) rounds exactly as pxl - x.
+__device__ __forceinline__ void stage_fwd(const Rec *__restrict__ rec, uint32_t gid, int ox, int oy, float4 *sx,
+                                          float4 *sy, float4 *sc, float4 *sk, float4 *sb, int slot)
 {
     const Rec r = rec[gid];
     const float xl = (r.r0.x - (float)ox) + r.r0.z;
     const float yl = (r.r0.y - (float)oy) + r.r0.w;
-    s0[slot] = make_float4(xl, yl, r.r1.x, r.r1.y);
-    s1[slot] = make_float4(r.r1.z, r.r1.w, r.r2.y, r.r2.z);
-    s2[slot] = make_float2(r.r2.w, r.r2.x);
+    sx[slot] = make_float4(-xl, -xl, r.r1.x, r.r1.x);          // {-x, -x, A, A}
+    sy[slot] = make_float4(-yl, -yl, r.r1.y, r.r1.y);          // {-y, -y, B, B}
+    sc[slot] = make_float4(r.r1.z, r.r1.z, r.r1.w, r.r1.w);    // {C, C, lo, lo}
+    sk[slot] = make_float4(r.r2.y, r.r2.y, r.r2.z, r.r2.z);    // {ct_r, ct_r, ct_g, ct_g}
+    sb[slot] = make_float4(r.r2.w, r.r2.w, r.r2.x, r.r2.x);    // {ct_b, ct_b, d, d}
 }
 
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
+// Forward. The thread's PX pixels (one row, HW columns apart) run as PX/2
+// FP32x2 lane pairs through one predicated body: a pair that is outside the
+// pixel's 3-sigma ellipse or below 1/255 gets alpha = 0 (adds nothing,
+// leaves T), a finished pixel has a NaN column (its quadratic form is NaN, so
+// it fails the 3-sigma test), and only the rare stop at the transmittance
+// floor branches. Per-lane arithmetic is the scalar IEEE arithmetic of the
+// backward (same dx, quadratic form, exponent and tests), so both passes take
+// identical decisions.
 template <int TW, int TH, int NB>
 __device__ __forceinline__ void blend_tile_fwd(const BlendView &v, int tile, const float *__restrict__ medium)
 {
-    constexpr int PX = kPxFwd;
+    constexpr int PX = kPxFwd, NP = PX / 2;
     constexpr int NT = Tile<TW, TH, PX>::NT, HW = Tile<TW, TH, PX>::HW;
-    __shared__ float4 s0[NB];  // {x_loc, y_loc, A, B}
-    __shared__ float4 s1[NB];  // {C, lo, ct_r, ct_g}
-    __shared__ float2 s2[NB];  // {ct_b, d}
+    __shared__ float4 sx[NB], sy[NB], sc[NB], sk[NB], sb[NB];
     const CamK &cam = v.cam;
     const int tyi = tile / v.tg.tx, txi = tile - tyi * v.tg.tx;
     const int x0 = txi * TW, y0 = tyi * TH;
@@ -96,58 +115,92 @@ __device__ __forceinline__ void blend_tile_fwd(const BlendView &v, int tile, con
     const int gy = y0 + row;
     const uint2 rg = v.ranges[tile];
     const int n = (int)(rg.y - rg.x);
+    const float kNaN = __int_as_float(0x7fffffff);
 
-    float pxl[PX], T[PX], cr[PX], cg[PX], cb[PX], D[PX], A[PX];
-    int last[PX], walk[PX];
-    bool done[PX];
+    float2 pxl[NP], T[NP], cr[NP], cg[NP], cb[NP], D[NP], A[NP];
+    int walk[PX];
+    int live = 0;
 #pragma unroll
-    for (int q = 0; q < PX; q++) {
-        pxl[q] = (float)(x0 - ox + col + q * HW) + 0.5f;
-        T[q] = 1.f;
-        cr[q] = cg[q] = cb[q] = D[q] = A[q] = 0.f;
-        last[q] = 0;
-        done[q] = !(gy < H && x0 + col + q * HW < W);
-        walk[q] = done[q] ? 0 : n;
+    for (int j = 0; j < NP; j++) {
+        float c2[2];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int q = 2 * j + h;
+            const bool in = gy < H && x0 + col + q * HW < W;
+            c2[h] = in ? (float)(x0 - ox + col + q * HW) + 0.5f : kNaN;
+            walk[q] = in ? n : 0;
+            live += in;
+        }
+        pxl[j] = make_float2(c2[0], c2[1]);
+        T[j] = make_float2(1.f, 1.f);
+        cr[j] = cg[j] = cb[j] = D[j] = A[j] = make_float2(0.f, 0.f);
     }
+    const float2 pyl2 = make_float2(pyl, pyl), neg1 = make_float2(-1.f, -1.f);
 
     for (int b0 = 0; b0 < n; b0 += NB) {
-        bool all = true;
-#pragma unroll
-        for (int q = 0; q < PX; q++) all &= done[q];
-        if (__syncthreads_count(!all) == 0) break;
-        for (int sl = tid; sl < NB && b0 + sl < n; sl += NT) stage_rec(v.rec, v.gauss_ids[rg.x + b0 + sl], ox, oy, s0, s1, s2, sl);
+        if (__syncthreads_count(live > 0) == 0) break;
+        for (int sl = tid; sl < NB && b0 + sl < n; sl += NT)
+            stage_fwd(v.rec, v.gauss_ids[rg.x + b0 + sl], ox, oy, sx, sy, sc, sk, sb, sl);
         __syncthreads();
         const int nb = min(NB, n - b0);
-        if (!__any_sync(0xffffffffu, !all)) continue;
+        if (!__any_sync(0xffffffffu, live > 0)) continue;
         for (int k = 0; k < nb; k++) {
-            const float4 a = s0[k];
-            const float4 c = s1[k];
-            const float dy = pyl - a.y;
-            const float Bdy = a.w * dy;
-            const float Cdy2 = c.x * dy * dy;
+            const float4 fx = sx[k], fy = sy[k], fc = sc[k];
+            const float2 dy = __fadd2_rn(pyl2, lo2(fy));
+            const float2 Bdy = __fmul2_rn(hi2(fy), dy);
+            const float2 Cdy2 = __fmul2_rn(__fmul2_rn(lo2(fc), dy), dy);
+            float2 qs[NP];
+            bool inside = false;
 #pragma unroll
-            for (int q = 0; q < PX; q++) {
-                if (done[q]) continue;
-                const float dx = pxl[q] - a.x;
-                const float qs = quad(dx, a.z, Bdy, Cdy2);
-                if (qs < kQsMin) continue;
-                const float alpha = fminf(kAlphaMax, ex2_approx(qs + c.y));
-                if (alpha < kAlphaMin) continue;
-                const float tn = fmaf(-alpha, T[q], T[q]);
-                if (tn < kTStop) {
-                    done[q] = true;
-                    walk[q] = b0 + k + 1;
-                } else {
-                    const float w = alpha * T[q];
-                    const float2 e = s2[k];
-                    cr[q] = fmaf(w, c.z, cr[q]);
-                    cg[q] = fmaf(w, c.w, cg[q]);
-                    cb[q] = fmaf(w, e.x, cb[q]);
-                    D[q] = fmaf(w, e.y, D[q]);
-                    A[q] += w;
-                    T[q] = tn;
-                    last[q] = b0 + k + 1;
+            for (int j = 0; j < NP; j++) {
+                const float2 dx = __fadd2_rn(pxl[j], lo2(fx));
+                qs[j] = __ffma2_rn(dx, __ffma2_rn(hi2(fx), dx, Bdy), Cdy2);
+                inside |= (qs[j].x >= kQsMin) | (qs[j].y >= kQsMin);
+            }
+            // none of the thread's pixels within 3 sigma: nothing to add (a warp
+            // skips the rest when this holds for all its lanes)
+            if (!inside) continue;
+            float2 w[NP], tn[NP];
+            bool stop = false;
+#pragma unroll
+            for (int j = 0; j < NP; j++) {
+                const float2 e = __fadd2_rn(qs[j], hi2(fc));
+                float a0 = fminf(kAlphaMax, ex2_approx(e.x)), a1 = fminf(kAlphaMax, ex2_approx(e.y));
+                a0 = (qs[j].x >= kQsMin && a0 >= kAlphaMin) ? a0 : 0.f;
+                a1 = (qs[j].y >= kQsMin && a1 >= kAlphaMin) ? a1 : 0.f;
+                w[j] = __fmul2_rn(make_float2(a0, a1), T[j]);
+                tn[j] = __ffma2_rn(w[j], neg1, T[j]);  // T - alpha T
+                stop |= (tn[j].x < kTStop) | (tn[j].y < kTStop);
+            }
+            if (stop) {
+                // stop before this Gaussian: it adds nothing, the pixel is finished
+#pragma unroll
+                for (int j = 0; j < NP; j++) {
+                    if (tn[j].x < kTStop) {
+                        w[j].x = 0.f;
+                        tn[j].x = T[j].x;
+                        pxl[j].x = kNaN;
+                        walk[2 * j] = b0 + k + 1;
+                        live--;
+                    }
+                    if (tn[j].y < kTStop) {
+                        w[j].y = 0.f;
+                        tn[j].y = T[j].y;
+                        pxl[j].y = kNaN;
+                        walk[2 * j + 1] = b0 + k + 1;
+                        live--;
+                    }
                 }
+            }
+            const float4 fk = sk[k], fb = sb[k];
+#pragma unroll
+            for (int j = 0; j < NP; j++) {
+                cr[j] = __ffma2_rn(w[j], lo2(fk), cr[j]);
+                cg[j] = __ffma2_rn(w[j], hi2(fk), cg[j]);
+                cb[j] = __ffma2_rn(w[j], lo2(fb), cb[j]);
+                D[j] = __ffma2_rn(w[j], hi2(fb), D[j]);
+                A[j] = __fadd2_rn(A[j], w[j]);
+                T[j] = tn[j];
             }
         }
     }
@@ -165,17 +218,25 @@ __device__ __forceinline__ void blend_tile_fwd(const BlendView &v, int tile, con
     for (int q = 0; q < PX; q++) {
         const int gx = x0 + col + q * HW;
         if (!(gy < H && gx < W)) continue;
+        const int j = q >> 1;
+        const bool h = q & 1;
+        const float Tq = h ? T[j].y : T[j].x, Aq = h ? A[j].y : A[j].x, Dq = h ? D[j].y : D[j].x;
+        const float rq = h ? cr[j].y : cr[j].x, gq = h ? cg[j].y : cg[j].x, bq = h ? cb[j].y : cb[j].x;
+        const bool stopped = isnan(h ? pxl[j].y : pxl[j].x);
         const int p = gy * W + gx;
-        v.image[p] = cr[q] + binf[0] * (1.f - T[q] * bfar[0]);
-        v.image[HWimg + p] = cg[q] + binf[1] * (1.f - T[q] * bfar[1]);
-        v.image[2 * HWimg + p] = cb[q] + binf[2] * (1.f - T[q] * bfar[2]);
-        const float z = A[q] > 0.f ? D[q] / A[q] : zfar;
+        v.image[p] = rq + binf[0] * (1.f - Tq * bfar[0]);
+        v.image[HWimg + p] = gq + binf[1] * (1.f - Tq * bfar[1]);
+        v.image[2 * HWimg + p] = bq + binf[2] * (1.f - Tq * bfar[2]);
+        const float z = Aq > 0.f ? Dq / Aq : zfar;
         if (v.depth) v.depth[p] = z;
         if (v.depth01) v.depth01[p] = 2.f / (1.f + expf(-0.1f * z)) - 1.f;
-        v.final_T[p] = T[q];
-        v.acc_alpha[p] = A[q];
+        v.final_T[p] = Tq;
+        v.acc_alpha[p] = Aq;
         v.zhat[p] = z;
-        v.n_last[p] = (uint32_t)last[q];
+        // the backward's bound: every contributor lies in front of the
+        // Gaussian that stopped the pixel (the entries between the last
+        // contributor and it fail the 3-sigma or 1/255 test in both passes)
+        v.n_last[p] = (uint32_t)(stopped ? walk[q] - 1 : n);
         v.n_walk[p] = (uint32_t)walk[q];
     }
 }
@@ -183,12 +244,13 @@ __device__ __forceinline__ void blend_tile_fwd(const BlendView &v, int tile, con
 // ---------------------------------------------------------------------------
 // Backward.
 
-// Per-pixel state of the back-to-front walk.
-struct PixB {
-    float T;      // transmittance behind the current Gaussian (starts at T_final)
-    float S;      // sum over Gaussians behind: w * (G.ct + gD d + gA), plus the water term
-    float G0, G1, G2, gD, gA;
-    int last;
+// State of the back-to-front walk for a pair of a thread's pixels (one FP32x2
+// lane each).
+struct PairB {
+    float2 T;                 // transmittance behind the current Gaussian (starts at T_final)
+    float2 S;                 // sum over Gaussians behind: w (G.ct + gD d + gA), plus the water term
+    float2 G0, G1, G2, gD, gA;
+    int last0, last1;         // walk bounds (list entries in front of the stop)
 };
 
 // One warp-wide sum of 10 values by recursive halving: after five exchange
@@ -239,46 +301,53 @@ __device__ __forceinline__ int reduce10_field(int lane)
     return nreal > 0 ? base : -1;
 }
 
-// adjoint of one pixel at one Gaussian that contributes to it (alpha = the
-// clamped raw value araw, which is at least 1/255 here; dx its column offset).
-// DG: the loss has a depth term (gD, gA non-zero); without it those terms vanish.
-// The exponent's gradient gqs enters the centre and conic gradients only
-// through its moments: acc[5] = sum gqs, acc[0] = sum gqs dx, acc[2] = sum
-// gqs dx^2 over the thread's pixels (one row, so dy is shared); the dy
-// moments and the conic coefficients are applied once per Gaussian.
+// Adjoint of a pixel pair at one Gaussian, lanes masked by on0 / on1: a lane
+// that does not take part gets alpha = 0 (1 - alpha = 1, so its T, S and
+// every accumulated term stay unchanged). ar: raw alpha per lane; dx: the
+// lanes' column offsets; kc = {ct_r, ct_r, ct_g, ct_g}, kb = {ct_b, ct_b, d, d}.
+// DG: the loss has a depth term (gD, gA non-zero). The exponent's gradient
+// gqs enters the centre and conic gradients only through its moments: a0 =
+// sum gqs dx, a2 = sum gqs dx^2, a5 = sum gqs over the thread's pixels (one
+// row, so dy is shared); the dy moments and the conic coefficients are
+// applied once per Gaussian.
 template <bool DG>
-__device__ __forceinline__ void pix_grad(PixB &p, float dx, float araw, float ctr, float ctg, float ctb, float d, float *acc)
+__device__ __forceinline__ void pair_grad(PairB &p, float2 dx, float2 ar, bool on0, bool on1, float4 kc, float4 kb,
+                                          float2 &a0, float2 &a2, float2 &a5, float2 &a6, float2 &a7, float2 &a8,
+                                          float2 &a9)
 {
-    const float alpha = fminf(kAlphaMax, araw);
-    const float inv = rcp_approx(1.f - alpha);
-    const float Tj = p.T * inv;  // transmittance in front of this Gaussian
-    const float w = alpha * Tj;
-    const float u = DG ? fmaf(p.G0, ctr, fmaf(p.G1, ctg, fmaf(p.G2, ctb, fmaf(p.gD, d, p.gA))))
-                       : fmaf(p.G0, ctr, fmaf(p.G1, ctg, p.G2 * ctb));
+    const float2 neg1 = make_float2(-1.f, -1.f), one = make_float2(1.f, 1.f), ln2 = make_float2(kLn2, kLn2);
+    const float2 al = make_float2(on0 ? fminf(kAlphaMax, ar.x) : 0.f, on1 ? fminf(kAlphaMax, ar.y) : 0.f);
+    const float2 om = __ffma2_rn(al, neg1, one);  // 1 - alpha
+    const float2 inv = make_float2(rcp_approx(om.x), rcp_approx(om.y));
+    const float2 Tj = __fmul2_rn(p.T, inv);       // transmittance in front of this Gaussian
+    const float2 w = __fmul2_rn(al, Tj);
+    const float2 u = DG ? __ffma2_rn(p.G0, lo2(kc), __ffma2_rn(p.G1, hi2(kc), __ffma2_rn(p.G2, lo2(kb),
+                                                                                       __ffma2_rn(p.gD, hi2(kb), p.gA))))
+                        : __ffma2_rn(p.G0, lo2(kc), __ffma2_rn(p.G1, hi2(kc), __fmul2_rn(p.G2, lo2(kb))));
     // dL/dalpha = T_j u - S / (1 - alpha)
-    const float galpha = fmaf(Tj, u, -p.S * inv);
-    const float gqs = araw < kAlphaMax ? galpha * alpha * kLn2 : 0.f;
-    const float gx = gqs * dx;
-    acc[0] += gx;
-    acc[2] = fmaf(gx, dx, acc[2]);
-    acc[5] += gqs;
-    if (DG) acc[6] = fmaf(p.gD, w, acc[6]);
-    acc[7] = fmaf(p.G0, w, acc[7]);
-    acc[8] = fmaf(p.G1, w, acc[8]);
-    acc[9] = fmaf(p.G2, w, acc[9]);
-    p.S = fmaf(w, u, p.S);
+    const float2 galpha = __ffma2_rn(__fmul2_rn(p.S, inv), neg1, __fmul2_rn(Tj, u));
+    float2 gqs = __fmul2_rn(__fmul2_rn(galpha, al), ln2);
+    gqs.x = ar.x < kAlphaMax ? gqs.x : 0.f;  // zero through the alpha clamp
+    gqs.y = ar.y < kAlphaMax ? gqs.y : 0.f;
+    const float2 gx = __fmul2_rn(gqs, dx);
+    a0 = __fadd2_rn(a0, gx);
+    a2 = __ffma2_rn(gx, dx, a2);
+    a5 = __fadd2_rn(a5, gqs);
+    if (DG) a6 = __ffma2_rn(p.gD, w, a6);
+    a7 = __ffma2_rn(p.G0, w, a7);
+    a8 = __ffma2_rn(p.G1, w, a8);
+    a9 = __ffma2_rn(p.G2, w, a9);
+    p.S = __ffma2_rn(w, u, p.S);
     p.T = Tj;
 }
 
 template <int TW, int TH, int NB, bool DG>
 __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, const float *__restrict__ medium)
 {
-    constexpr int PX = kPxBwd;
+    constexpr int PX = kPxBwd, NP = PX / 2;
     constexpr int NT = Tile<TW, TH, PX>::NT, HW = Tile<TW, TH, PX>::HW;
     constexpr int NW = NT / 32;
-    __shared__ float4 s0[NB];
-    __shared__ float4 s1[NB];
-    __shared__ float2 s2[NB];
+    __shared__ float4 sx[NB], sy[NB], sc[NB], sk[NB], sb[NB];
     __shared__ uint32_t s_id[NB];
     __shared__ float s_g[10][NB + 1];  // padded: the ten fields of one Gaussian fall in ten banks
     __shared__ float s_med[NW][6];
@@ -307,44 +376,58 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
     // per-pixel set-up; medium terms that do not go through any Gaussian:
     //   dC/dB_inf = 1 - T_f b_far, dC/dbeta_B = B_inf T_f z_far b_far
     float mB[3] = {0.f, 0.f, 0.f}, mBB[3] = {0.f, 0.f, 0.f};
-    float pxl[PX];
-    PixB P[PX];
+    float2 pxl[NP];
+    PairB P[NP];
     int mylast = 0;
 #pragma unroll
-    for (int q = 0; q < PX; q++) {
-        const int gx = x0 + col + q * HW;
-        pxl[q] = (float)(x0 - ox + col + q * HW) + 0.5f;
-        PixB &p = P[q];
-        p.T = 1.f; p.S = 0.f; p.G0 = p.G1 = p.G2 = p.gD = p.gA = 0.f; p.last = 0;
-        if (!(gy < H && gx < W)) continue;
-        const int pix = gy * W + gx;
-        p.T = v.final_T[pix];
-        p.last = (int)v.n_last[pix];
-        p.G0 = v.dL_dimage[pix];
-        p.G1 = v.dL_dimage[HWimg + pix];
-        p.G2 = v.dL_dimage[2 * HWimg + pix];
-        if (DG) {
-            const float A = v.acc_alpha[pix], z = v.zhat[pix];
-            float gz = v.dL_ddepth ? v.dL_ddepth[pix] : 0.f;
-            if (v.dL_ddepth01) {
-                const float e = expf(-0.1f * z);
-                gz += v.dL_ddepth01[pix] * 0.2f * e / ((1.f + e) * (1.f + e));
-            }
-            if (A > 0.f) {
-                p.gD = gz / A;  // z = D / A
-                p.gA = -gz * z / A;
-            }
-        }
-        const float Gc[3] = {p.G0, p.G1, p.G2};
-        float S = 0.f;
+    for (int jp = 0; jp < NP; jp++) {
+        float T[2] = {1.f, 1.f}, S[2] = {0.f, 0.f}, G0[2] = {0.f, 0.f}, G1[2] = {0.f, 0.f}, G2[2] = {0.f, 0.f};
+        float gD[2] = {0.f, 0.f}, gA[2] = {0.f, 0.f}, px[2];
+        int last[2] = {0, 0};
 #pragma unroll
-        for (int ch = 0; ch < 3; ch++) {
-            mB[ch] += Gc[ch] * (1.f - p.T * bfar[ch]);
-            mBB[ch] += Gc[ch] * binf[ch] * p.T * zfar * bfar[ch];
-            S -= Gc[ch] * binf[ch] * bfar[ch] * p.T;  // the water behind the last Gaussian
+        for (int h = 0; h < 2; h++) {
+            const int q = 2 * jp + h;
+            const int gx = x0 + col + q * HW;
+            px[h] = (float)(x0 - ox + col + q * HW) + 0.5f;
+            if (!(gy < H && gx < W)) continue;
+            const int pix = gy * W + gx;
+            T[h] = v.final_T[pix];
+            last[h] = (int)v.n_last[pix];
+            G0[h] = v.dL_dimage[pix];
+            G1[h] = v.dL_dimage[HWimg + pix];
+            G2[h] = v.dL_dimage[2 * HWimg + pix];
+            if (DG) {
+                const float A = v.acc_alpha[pix], z = v.zhat[pix];
+                float gz = v.dL_ddepth ? v.dL_ddepth[pix] : 0.f;
+                if (v.dL_ddepth01) {
+                    const float e = expf(-0.1f * z);
+                    gz += v.dL_ddepth01[pix] * 0.2f * e / ((1.f + e) * (1.f + e));
+                }
+                if (A > 0.f) {
+                    gD[h] = gz / A;  // z = D / A
+                    gA[h] = -gz * z / A;
+                }
+            }
+            const float Gc[3] = {G0[h], G1[h], G2[h]};
+#pragma unroll
+            for (int ch = 0; ch < 3; ch++) {
+                mB[ch] += Gc[ch] * (1.f - T[h] * bfar[ch]);
+                mBB[ch] += Gc[ch] * binf[ch] * T[h] * zfar * bfar[ch];
+                S[h] -= Gc[ch] * binf[ch] * bfar[ch] * T[h];  // the water behind the last Gaussian
+            }
+            mylast = max(mylast, last[h]);
         }
-        p.S = S;
-        mylast = max(mylast, p.last);
+        pxl[jp] = make_float2(px[0], px[1]);
+        PairB &p = P[jp];
+        p.T = make_float2(T[0], T[1]);
+        p.S = make_float2(S[0], S[1]);
+        p.G0 = make_float2(G0[0], G0[1]);
+        p.G1 = make_float2(G1[0], G1[1]);
+        p.G2 = make_float2(G2[0], G2[1]);
+        p.gD = make_float2(gD[0], gD[1]);
+        p.gA = make_float2(gA[0], gA[1]);
+        p.last0 = last[0];
+        p.last1 = last[1];
     }
     // per-tile medium partials {beta_B[3], B_inf[3]}, reduced now so that the
     // accumulators do not stay live through the main loop
@@ -372,6 +455,7 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
     const int my_field = reduce10_field(lane);
     __syncthreads();
     const int maxlast = s_maxlast;
+    const float2 pyl2 = make_float2(pyl, pyl);
 
     for (int bend = maxlast; bend > 0; bend -= NB) {
         const int b0 = max(0, bend - NB);
@@ -379,7 +463,7 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
         __syncthreads();  // the previous batch's flush has read s_g / s_id
         for (int sl = tid; sl < nb; sl += NT) {
             const uint32_t gid = v.gauss_ids[rg.x + b0 + sl];
-            stage_rec(v.rec, gid, ox, oy, s0, s1, s2, sl);
+            stage_fwd(v.rec, gid, ox, oy, sx, sy, sc, sk, sb, sl);
             s_id[sl] = gid;
         }
         for (int sl = tid; sl < NB; sl += NT)
@@ -389,41 +473,49 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
         if (__any_sync(0xffffffffu, mylast > b0)) {
             for (int k = nb - 1; k >= 0; k--) {
                 const int j = b0 + k;
-                const float4 a = s0[k];
-                const float4 c = s1[k];
-                const float2 e = s2[k];
-                const float dy = pyl - a.y;
-                const float Bdy = a.w * dy;
-                const float Cdy2 = c.x * dy * dy;
-                float acc[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                const float4 fx = sx[k], fy = sy[k], fc = sc[k];
+                const float2 dy = __fadd2_rn(pyl2, lo2(fy));
+                const float2 Bdy = __fmul2_rn(hi2(fy), dy);
+                const float2 Cdy2 = __fmul2_rn(__fmul2_rn(lo2(fc), dy), dy);
                 // the exponent and raw alpha of all the thread's pixels first, without
                 // branches (independent chains the scheduler can overlap); a pixel
-                // takes part if the Gaussian is in front of its last one, within
+                // takes part if the Gaussian is in front of its walk bound, within
                 // 3 sigma and at least 1/255 opaque there
-                float dxv[PX], arv[PX];
-                bool on[PX];
-#pragma unroll
-                for (int q = 0; q < PX; q++) {
-                    dxv[q] = pxl[q] - a.x;
-                    const float qs = quad(dxv[q], a.z, Bdy, Cdy2);
-                    arv[q] = ex2_approx(qs + c.y);
-                    on[q] = (j < P[q].last) & (qs >= kQsMin) & (fminf(kAlphaMax, arv[q]) >= kAlphaMin);
-                }
+                float2 dx[NP], ar[NP];
+                bool on0[NP], on1[NP];
                 bool any = false;
 #pragma unroll
-                for (int q = 0; q < PX; q++) {
-                    if (!on[q]) continue;
-                    pix_grad<DG>(P[q], dxv[q], arv[q], c.z, c.w, e.x, e.y, acc);
-                    any = true;
+                for (int jp = 0; jp < NP; jp++) {
+                    dx[jp] = __fadd2_rn(pxl[jp], lo2(fx));
+                    const float2 qs = __ffma2_rn(dx[jp], __ffma2_rn(hi2(fx), dx[jp], Bdy), Cdy2);
+                    const float2 e = __fadd2_rn(qs, hi2(fc));
+                    ar[jp] = make_float2(ex2_approx(e.x), ex2_approx(e.y));
+                    on0[jp] = (j < P[jp].last0) & (qs.x >= kQsMin) & (fminf(kAlphaMax, ar[jp].x) >= kAlphaMin);
+                    on1[jp] = (j < P[jp].last1) & (qs.y >= kQsMin) & (fminf(kAlphaMax, ar[jp].y) >= kAlphaMin);
+                    any |= on0[jp] | on1[jp];
                 }
-                if (__any_sync(0xffffffffu, any)) {
-                    // moments in y from the row's dy: sum gqs dy, sum gqs dx dy, sum gqs dy^2
-                    acc[1] = acc[5] * dy;
-                    acc[3] = acc[0] * dy;
-                    acc[4] = acc[5] * (dy * dy);
-                    const float r = warp_reduce10(acc, lane);
-                    if (my_field >= 0) atomicAdd(&s_g[my_field][k], r);
-                }
+                if (!__any_sync(0xffffffffu, any)) continue;
+                float2 a0 = make_float2(0.f, 0.f), a2 = a0, a5 = a0, a6 = a0, a7 = a0, a8 = a0, a9 = a0;
+                const float4 kc = sk[k], kb = sb[k];
+                // both pairs, masked, without a branch: their dependency chains overlap
+#pragma unroll
+                for (int jp = 0; jp < NP; jp++)
+                    pair_grad<DG>(P[jp], dx[jp], ar[jp], on0[jp], on1[jp], kc, kb, a0, a2, a5, a6, a7, a8, a9);
+                float acc[10];
+                const float dys = dy.x;
+                acc[0] = a0.x + a0.y;
+                acc[2] = a2.x + a2.y;
+                acc[5] = a5.x + a5.y;
+                acc[6] = DG ? a6.x + a6.y : 0.f;
+                acc[7] = a7.x + a7.y;
+                acc[8] = a8.x + a8.y;
+                acc[9] = a9.x + a9.y;
+                // moments in y from the row's dy: sum gqs dy, sum gqs dx dy, sum gqs dy^2
+                acc[1] = acc[5] * dys;
+                acc[3] = acc[0] * dys;
+                acc[4] = acc[5] * (dys * dys);
+                const float r = warp_reduce10(acc, lane);
+                if (my_field >= 0) atomicAdd(&s_g[my_field][k], r);
             }
         }
         __syncthreads();
@@ -435,7 +527,7 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
             for (int f = 0; f < 10; f++) nz |= g[f] != 0.f;
             if (nz) {
                 // centre gradient from the moments: dqs/dx = 2A dx + B dy, dqs/dy = B dx + 2C dy
-                const float A = s0[sl].z, B = s0[sl].w, C = s1[sl].x;
+                const float A = sx[sl].z, B = sy[sl].z, C = sc[sl].x;
                 const float gmx = -fmaf(2.f * A, g[0], B * g[1]);
                 const float gmy = -fmaf(B, g[0], 2.f * C * g[1]);
                 GAcc *dst = v.gacc + s_id[sl];
@@ -456,10 +548,10 @@ __global__ void __launch_bounds__(fwd_threads<TW, TH>(), 1280 / fwd_threads<TW, 
     blend_tile_fwd<TW, TH, NB>(v, blockIdx.x, medium);
 }
 
-// occupancy target: 14 blocks of 64 threads per SM without the depth terms
-// (72 registers), 12 with them (80)
+// occupancy target: 12 blocks of 64 threads per SM without the depth terms
+// (80 registers, no spills), 11 with them
 template <int TW, int TH, int NB, bool DG>
-__global__ void __launch_bounds__(bwd_threads<TW, TH>(), (DG ? 768 : 896) / bwd_threads<TW, TH>()) k_blend_bwd(BlendView v, const float *__restrict__ medium)
+__global__ void __launch_bounds__(bwd_threads<TW, TH>(), (DG ? 704 : 768) / bwd_threads<TW, TH>()) k_blend_bwd(BlendView v, const float *__restrict__ medium)
 {
     blend_tile_bwd<TW, TH, NB, DG>(v, blockIdx.x, medium);
 }

@@ -152,10 +152,27 @@ constexpr int kDepthSortItems = SPLASH_DEPTH_SORT_ITEMS;
 static_assert(kDepthSortItems >= kSortItems, "the scratch is sized for kSortTile partitions");
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
+constexpr int kRadixBitsMax = 9;                 // widest digit (a sort that saves a pass with it)
+constexpr int kRadixMax = 1 << kRadixBitsMax;
+constexpr int kLookbackPerPart = 3 * kRadixMax;  // the largest sum over a plan's passes of max(256, 2^width)
+
+// Digits of a sort on `bits` key bits: 8-bit passes (the last one narrower),
+// unless 9-bit digits need fewer passes (then the bits are spread evenly, at
+// most 9 per pass).
+struct DigitPlan {
+    int passes;
+    int width[4];
+    int shift[4];
+};
+DigitPlan digit_plan(int bits);
+// Significant bits of the depth keys of a camera: a key is the FP32 depth's
+// bits minus those of z_near (depths lie in (z_near, z_far]; positive floats
+// order like their bit patterns), so the keys span bits(z_far) - bits(z_near).
+int depth_key_bits(float z_near, float z_far);
 
 struct SortScratch {
-    uint32_t *hist;      // [4][256] per-pass digit offsets
-    uint32_t *lookback;  // [4][max_parts][256]
+    uint32_t *hist;      // [4][kRadixMax] per-pass digit offsets
+    uint32_t *lookback;  // per pass [max_parts][max(256, 2^width)], kLookbackPerPart words per partition
     uint32_t *counters;  // [4] partition tickets
     int64_t max_parts;
 };

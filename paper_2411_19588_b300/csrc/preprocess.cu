@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(kPreThreads) k_preprocess_fwd(
     r.r1 = make_float4(A, B, C, lo);
     r.r2 = make_float4(tz, ct[0], ct[1], ct[2]);
     rec[i] = r;
-    depth_key[i] = __float_as_uint(tz);
+    depth_key[i] = __float_as_uint(tz) - __float_as_uint(cam.znear);  // > 0: tz > z_near
     tiles_touched[i] = ntiles;
     rect[i] = rc;
 }

@@ -16,9 +16,9 @@ using namespace splash;
 constexpr int64_t kMaxPairs = 1 << 20;  // largest n this entry point accepts
 constexpr int64_t kPartsMax = (kMaxPairs + kSortTile - 1) / kSortTile + 1;
 constexpr size_t kPairWords = 2 * (size_t)kMaxPairs;                       // temp keys + temp values
-constexpr size_t kScratchWords = 4 * kRadix + 64 + 4 * (size_t)kPartsMax * kRadix;  // sort_scratch_carve layout
+constexpr size_t kScratchWords = 4 * kRadixMax + 64 + (size_t)kLookbackPerPart * kPartsMax;  // sort_scratch_carve layout
 constexpr size_t kStatusWord = kPairWords + kScratchWords;
-constexpr size_t kTotalWords = kStatusWord + 64;  // ~9.1 MB
+constexpr size_t kTotalWords = kStatusWord + 64;  // ~10 MB
 
 // Resident in every device context that loads the library, until exit.
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kTotalWords];

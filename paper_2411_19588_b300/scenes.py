@@ -346,6 +346,14 @@ def view_maps(seed: int, width: int, height: int, z_far: float = 20.0):
     return img, depth
 
 
+def _cross_t(a, b):
+    """Row-wise cross product written out (torch.linalg's first call loads its
+    libraries, tens of seconds on a fresh machine)."""
+    import torch
+    return torch.stack([a[:, 1] * b[:, 2] - a[:, 2] * b[:, 1], a[:, 2] * b[:, 0] - a[:, 0] * b[:, 2],
+                        a[:, 0] * b[:, 1] - a[:, 1] * b[:, 0]], 1)
+
+
 def _rotmat_to_quat_t(R):
     """Torch version of _rotmat_to_quat (Shepperd), for device-side generation."""
     import torch
@@ -407,9 +415,9 @@ def patch_scene_device(n: int, seed: int, z_range=(1.0, 8.0), width=1280, height
     ex = torch.tensor([1.0, 0.0, 0.0], **f64).expand(n_patches, 3)
     ey = torch.tensor([0.0, 1.0, 0.0], **f64).expand(n_patches, 3)
     helper = torch.where(normals[:, :1].abs() < 0.9, ex, ey)
-    t1 = torch.linalg.cross(normals, helper)
+    t1 = _cross_t(normals, helper)
     t1 = t1 / t1.norm(dim=1, keepdim=True)
-    t2 = torch.linalg.cross(normals, t1)
+    t2 = _cross_t(normals, t1)
     u = U(-0.5, 0.5, n_surf) * sides[owner]
     v = U(-0.5, 0.5, n_surf) * sides[owner]
     s_means = centers[owner] + u[:, None] * t1[owner] + v[:, None] * t2[owner]

@@ -166,8 +166,13 @@ def test_binning_and_sort_bit_exact(renderer, n, z_step):
 
 
 @pytest.mark.parametrize("n,bits,distinct", [(1, 32, 10), (4095, 13, 50), (4097, 32, 1 << 30), (100_003, 14, 9600),
-                                             (3_000_001, 32, 1 << 31), (1_234_567, 20, 300), (70_000, 0, 1)])
+                                             (3_000_001, 32, 1 << 31), (1_234_567, 20, 300), (70_000, 0, 1),
+                                             # 9-bit digit plans: 9, 9+8, 9+9+8, 9+9+9 bits
+                                             (5_000, 9, 1 << 9), (300_001, 17, 1 << 17), (1_500_000, 26, 1 << 26),
+                                             (1_000_003, 26, 5000), (70_001, 27, 1 << 32)])
 def test_radix_sort_bit_exact(renderer, n, bits, distinct):
+    """Stable sort on key bits [0, bits) against numpy's stable argsort (keys
+    may carry bits above `bits`: they are ignored)."""
     rng = np.random.default_rng(n)
     keys = rng.integers(0, distinct, n, dtype=np.int64).astype(np.uint32)
     vals = rng.integers(0, 1 << 31, n, dtype=np.int64).astype(np.uint32)
