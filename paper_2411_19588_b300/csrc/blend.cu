@@ -115,10 +115,11 @@ __device__ __forceinline__ void blend_tile_fwd(const BlendView &v, int tile, con
     const int gy = y0 + row;
     const uint2 rg = v.ranges[tile];
     const int n = (int)(rg.y - rg.x);
-    const float kNaN = __int_as_float(0x7fffffff);
+    const float kNaN = __int_as_float(0x7fc00000);
 
+    // a finished pixel's column is a quiet NaN whose payload is its walked
+    // count (the stop position + 1, < 2^22): it fails every 3-sigma test
     float2 pxl[NP], T[NP], cr[NP], cg[NP], cb[NP], D[NP], A[NP];
-    int walk[PX];
     int live = 0;
 #pragma unroll
     for (int j = 0; j < NP; j++) {
@@ -128,7 +129,6 @@ __device__ __forceinline__ void blend_tile_fwd(const BlendView &v, int tile, con
             const int q = 2 * j + h;
             const bool in = gy < H && x0 + col + q * HW < W;
             c2[h] = in ? (float)(x0 - ox + col + q * HW) + 0.5f : kNaN;
-            walk[q] = in ? n : 0;
             live += in;
         }
         pxl[j] = make_float2(c2[0], c2[1]);
@@ -176,18 +176,17 @@ __device__ __forceinline__ void blend_tile_fwd(const BlendView &v, int tile, con
                 // stop before this Gaussian: it adds nothing, the pixel is finished
 #pragma unroll
                 for (int j = 0; j < NP; j++) {
+                    const float done = __int_as_float(0x7fc00000 | (b0 + k + 1));
                     if (tn[j].x < kTStop) {
                         w[j].x = 0.f;
                         tn[j].x = T[j].x;
-                        pxl[j].x = kNaN;
-                        walk[2 * j] = b0 + k + 1;
+                        pxl[j].x = done;
                         live--;
                     }
                     if (tn[j].y < kTStop) {
                         w[j].y = 0.f;
                         tn[j].y = T[j].y;
-                        pxl[j].y = kNaN;
-                        walk[2 * j + 1] = b0 + k + 1;
+                        pxl[j].y = done;
                         live--;
                     }
                 }
@@ -222,7 +221,9 @@ __device__ __forceinline__ void blend_tile_fwd(const BlendView &v, int tile, con
         const bool h = q & 1;
         const float Tq = h ? T[j].y : T[j].x, Aq = h ? A[j].y : A[j].x, Dq = h ? D[j].y : D[j].x;
         const float rq = h ? cr[j].y : cr[j].x, gq = h ? cg[j].y : cg[j].x, bq = h ? cb[j].y : cb[j].x;
-        const bool stopped = isnan(h ? pxl[j].y : pxl[j].x);
+        const float pq = h ? pxl[j].y : pxl[j].x;
+        const bool stopped = isnan(pq);
+        const int walk = stopped ? (__float_as_int(pq) & 0x3fffff) : n;
         const int p = gy * W + gx;
         v.image[p] = rq + binf[0] * (1.f - Tq * bfar[0]);
         v.image[HWimg + p] = gq + binf[1] * (1.f - Tq * bfar[1]);
@@ -236,8 +237,8 @@ __device__ __forceinline__ void blend_tile_fwd(const BlendView &v, int tile, con
         // the backward's bound: every contributor lies in front of the
         // Gaussian that stopped the pixel (the entries between the last
         // contributor and it fail the 3-sigma or 1/255 test in both passes)
-        v.n_last[p] = (uint32_t)(stopped ? walk[q] - 1 : n);
-        v.n_walk[p] = (uint32_t)walk[q];
+        v.n_last[p] = (uint32_t)(stopped ? walk - 1 : n);
+        v.n_walk[p] = (uint32_t)walk;
     }
 }
 
@@ -542,8 +543,9 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
 // ---------------------------------------------------------------------------
 // Kernels.
 
+// occupancy target: 16 blocks of 64 threads per SM (64 registers)
 template <int TW, int TH, int NB>
-__global__ void __launch_bounds__(fwd_threads<TW, TH>(), 1280 / fwd_threads<TW, TH>()) k_blend_fwd(BlendView v, const float *__restrict__ medium)
+__global__ void __launch_bounds__(fwd_threads<TW, TH>(), 1024 / fwd_threads<TW, TH>()) k_blend_fwd(BlendView v, const float *__restrict__ medium)
 {
     blend_tile_fwd<TW, TH, NB>(v, blockIdx.x, medium);
 }
@@ -570,7 +572,7 @@ __device__ __forceinline__ bool next_item(int *counter, const uint32_t *n_items,
 }
 
 template <int TW, int TH, int NB>
-__global__ void __launch_bounds__(fwd_threads<TW, TH>(), 1152 / fwd_threads<TW, TH>()) k_blend_fwd_persistent(const BlendView *__restrict__ views,
+__global__ void __launch_bounds__(fwd_threads<TW, TH>(), 1024 / fwd_threads<TW, TH>()) k_blend_fwd_persistent(const BlendView *__restrict__ views,
                                                                   const uint32_t *__restrict__ items,
                                                                   const uint32_t *__restrict__ n_items, int *counter,
                                                                   const float *__restrict__ medium)
