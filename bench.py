@@ -998,6 +998,22 @@ def run_loop(args, world, rank, local):
     t_dens = (time.perf_counter() - t0) * 1e3
     logits = params["opacity_logits"].clone()
     t_reset = timed(lambda j: R.opacity_reset(logits, None, None, 0.01), 20)
+    # MCMC densification (the form Sec. IV-D adopts): one relocation (about 5 %
+    # of the Gaussians dead) and the per-step position noise
+    mc = {k: v.clone() for k, v in params.items() if isinstance(v, torch.Tensor)}
+    mc["sh_degree"] = params["sh_degree"]
+    mc["opacity_logits"][::20] = -9.0
+    mm = {k: torch.zeros_like(v) for k, v in mc.items() if isinstance(v, torch.Tensor)}
+    mv = {k: torch.zeros_like(v) for k, v in mm.items()}
+    u = torch.rand(args.n, device="cuda")
+    R.mcmc_relocate(r, {**mc}, mm, mv, u)  # warm-up (its scratch)
+    mc["opacity_logits"][::20] = -9.0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n_dead = R.mcmc_relocate(r, mc, mm, mv, u)
+    t_reloc = (time.perf_counter() - t0) * 1e3
+    eta = torch.randn((args.n, 3), device="cuda")
+    t_noise = timed(lambda j: R.mcmc_noise(mc, eta, 1.6e-4), 20)
     clk = clocks.stop()
     r.sync_status()
     out = {"metric": "training-loop schedule pieces at 1.5M Gaussians 1920x1280 (ms)", "value": round(t_stats, 4),
@@ -1005,9 +1021,10 @@ def run_loop(args, world, rank, local):
            "warmup": max(3, args.warmup), "ms_per_step": round(t_stats, 4), "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "loop: fused step +- densification statistics, one densification step, opacity "
-                                  "reset", "n_gaussians": args.n},
+                                  "reset, one MCMC relocation and the MCMC noise", "n_gaussians": args.n},
            "step_ms_without_stats": round(t_plain, 4), "densify_step_ms": round(t_dens, 3),
            "densify_counts": [args.n, int(p2["means"].shape[0])], "opacity_reset_ms": round(t_reset, 4),
+           "mcmc": {"relocate_ms": round(t_reloc, 3), "dead_relocated": n_dead, "noise_ms": round(t_noise, 4)},
            "clocks": clk}
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -449,6 +449,38 @@ splash_status splash_densify_apply(splash_ctx *ctx, const splash_param_buffers *
  * logits[i] = min(logits[i], logit(max_opacity)) for n opacity logits
  * (device), and the opacity group's Adam moments adam_m, adam_v (device,
  * nullable) set to zero. max_opacity in (0, 1); the paper's value is 0.01. */
+/* MCMC densification, the form Sec. IV-D adopts (3DGS-MCMC's sampling in
+ * place of clone / split / prune; Sec. VI ablates it against the 3DGS
+ * procedure above). In place, the Gaussian count unchanged (to grow the set,
+ * append Gaussians with opacity 0 and relocate: they are dead).
+ *
+ * splash_mcmc_relocate: a Gaussian is dead when sigmoid(o) <= min_opacity
+ * (0.005), decided in FP64. Each dead Gaussian d draws a live source with
+ * probability proportional to opacity: the first g with C_g > u_d C_total,
+ * C the FP64 running sum of sigmoid(o) over live Gaussians in index order
+ * and u_d = uniforms[d], which must lie in [0, 1) (device, n floats; only
+ * dead entries are read). A source drawn c times stands for N =
+ * min(c + 1, 51) Gaussians: it and its copies take opacity
+ * o' = 1 - (1 - o)^(1/N) and scales s' = s o / Z, Z = sum_{i=1}^{N}
+ * sum_{k=0}^{i-1} C(i-1,k) (-1)^k o'^(k+1) / sqrt(k+1); each dead Gaussian
+ * then takes every parameter of its source, and the Adam moments (m, v:
+ * same layouts as the parameters) of sources and copies are zeroed. All
+ * buffers are device, caller-owned, read and written in place; quats 16-byte
+ * aligned. n_dead (host, may be NULL) receives the dead count; non-NULL
+ * synchronises the stream. Scratch: about 20 B per Gaussian, owned by the
+ * context (grow-only); calls sharing a context must be stream-ordered.
+ *
+ * splash_mcmc_noise: mu += lambda_noise * lr * sigmoid(-100 (o - 0.005)) *
+ * Sigma eta per Gaussian, Sigma = R diag(exp(2 log_scales)) R^T its
+ * covariance, eta (device [n,3]) standard normals given by the caller
+ * (lambda_noise 5e5 in the cited method, lr the position learning rate).
+ * means written in place; quats 16-byte aligned. */
+splash_status splash_mcmc_relocate(splash_ctx *ctx, const splash_param_buffers *params, const splash_param_buffers *m,
+                                   const splash_param_buffers *v, int64_t n, int32_t sh_degree, const float *uniforms,
+                                   float min_opacity, int64_t *n_dead, void *stream);
+splash_status splash_mcmc_noise(float *means, const float *log_scales, const float *quats, const float *opacity_logits,
+                                const float *eta, int64_t n, float lr, float lambda_noise, void *stream);
+
 splash_status splash_opacity_reset(float *logits, float *adam_m, float *adam_v, int64_t n, float max_opacity,
                                    void *stream);
 

@@ -116,6 +116,11 @@ LAYOUT_ORDER = (Camera, Gaussians, Grads, Options, ParamBuffers, AdamConfig, Sta
                 DensifyOptions, BackscatterOptions, BackscatterResult)
 
 _SIGS = {
+    "splash_mcmc_relocate": [ctypes.c_void_p, ctypes.POINTER(ParamBuffers), ctypes.POINTER(ParamBuffers),
+                             ctypes.POINTER(ParamBuffers), ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                             ctypes.c_float, ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p],
+    "splash_mcmc_noise": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                          ctypes.c_int64, ctypes.c_float, ctypes.c_float, ctypes.c_void_p],
     "splash_abi_layout": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
                           ctypes.POINTER(ctypes.c_int32)],
     "splash_create": [ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_void_p)],

@@ -185,6 +185,8 @@ struct splash_ctx {
     // densification plan: output counts, actions, output offsets (for dens_n Gaussians)
     splash_host::Buf dens_count, dens_action, dens_off, dens_iota, dens_sums, dens_total;
     int64_t dens_n = -1;
+    // MCMC relocation: running sum of the weights, chunk sums, sources, draw counts
+    splash_host::Buf mcmc_c, mcmc_sums, mcmc_src, mcmc_cnt;
 };
 
 struct splash_state {

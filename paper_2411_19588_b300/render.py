@@ -391,6 +391,32 @@ def densify(renderer: "Renderer", params: dict, m: dict, v: dict, stats: torch.T
     return tuple(new)
 
 
+def mcmc_relocate(renderer: "Renderer", params: dict, m: dict, v: dict, uniforms: torch.Tensor,
+                  min_opacity: float = 0.005) -> int:
+    """One MCMC relocation (see splash_mcmc_relocate), in place on the
+    parameter and moment dicts; uniforms: [n] floats in [0, 1). Returns the
+    number of dead Gaussians relocated (synchronises the stream)."""
+    n = params["means"].shape[0]
+    _check_tensor(uniforms, "uniforms", (n,))
+    buf = lambda d: _abi.ParamBuffers(*(d[k].data_ptr() for k in PARAM_NAMES), None)
+    nd = ctypes.c_int64()
+    _abi.check(_abi.lib().splash_mcmc_relocate(renderer._ctx, ctypes.byref(buf(params)), ctypes.byref(buf(m)),
+                                               ctypes.byref(buf(v)), n, int(params["sh_degree"]), uniforms.data_ptr(),
+                                               float(min_opacity), ctypes.byref(nd), _stream()), "splash_mcmc_relocate")
+    return int(nd.value)
+
+
+def mcmc_noise(params: dict, eta: torch.Tensor, lr: float, lambda_noise: float = 5e5):
+    """The MCMC position noise (see splash_mcmc_noise), in place on the means;
+    eta: [n, 3] standard normals."""
+    n = params["means"].shape[0]
+    _check_tensor(eta, "eta", (n, 3))
+    _abi.check(_abi.lib().splash_mcmc_noise(params["means"].data_ptr(), params["log_scales"].data_ptr(),
+                                            params["quats"].data_ptr(), params["opacity_logits"].data_ptr(),
+                                            eta.data_ptr(), n, float(lr), float(lambda_noise), _stream()),
+               "splash_mcmc_noise")
+
+
 def opacity_reset(logits: torch.Tensor, m: torch.Tensor | None = None, v: torch.Tensor | None = None,
                   max_opacity: float = 0.01):
     """The schedule's opacity reset: opacities capped at max_opacity, the

@@ -27,6 +27,9 @@ from . import scenes
 from . import schedule as SCH
 
 DEFAULT_MEDIUM = [0.1] * 9
+# MCMC densification (the cited method's schedule: relocation every 100
+# iterations from 500 to 25,000, dead below opacity 0.005, noise weight 5e5)
+MCMC_DEFAULTS = {"start": 500, "stop": 25_000, "every": 100, "min_opacity": 0.005, "lambda_noise": 5e5}
 # learning rates of the fit (3DGS values the paper keeps, appendix "Experimental Setup")
 FIT_LR = {"means": 1.6e-4, "log_scales": 5e-3, "quats": 1e-3, "opacity_logits": 5e-2, "sh": 2.5e-3, "medium": 2.5e-3}
 
@@ -134,12 +137,16 @@ class Fit:
     grad_threshold, min_opacity, percent_dense; defaults from
     schedule.DENSIFY) the fit gathers the densification statistics while the
     (1-based) iteration is below stop and densifies at every multiple of
-    `every` above start."""
+    `every` above start. With mcmc (a dict: start, stop, every, min_opacity,
+    lambda_noise; defaults MCMC_DEFAULTS) the fit densifies the way Sec. IV-D
+    adopts instead: after every Adam step the position noise, and at every
+    multiple of `every` in [start, stop) a relocation of the dead Gaussians
+    (the count stays fixed)."""
 
     def __init__(self, renderer: R.Renderer, params: dict, medium, cams, targets, lam: float = 0.2, lr=None,
                  lambda_est: float = 0.0, estimate_every: int = 500, schedule: bool = False,
                  reset_every: int = SCH.OPACITY_RESET_EVERY, densify: dict | None = None, seed: int = 0,
-                 pixel: bool = False):
+                 pixel: bool = False, mcmc: dict | None = None):
         self.r = renderer
         self.params = {k: (v.clone() if isinstance(v, torch.Tensor) else v) for k, v in params.items()}
         self.medium = torch.as_tensor(np.asarray(medium, np.float32)).cuda().contiguous()
@@ -165,6 +172,12 @@ class Fit:
         self.densify = None if densify is None else {**SCH.DENSIFY, **densify}
         self.densify_steps, self.counts = 0, [self.params["means"].shape[0]]
         self.stats = None
+        if densify is not None and mcmc is not None:
+            raise ValueError("densify and mcmc are alternatives")
+        self.mcmc = None if mcmc is None else {**MCMC_DEFAULTS, **mcmc}
+        self.relocations, self.dead_relocated = 0, []
+        if self.mcmc is not None:
+            self.gen = torch.Generator(device="cuda").manual_seed(seed)
         if self.densify is not None:
             self.stats = torch.zeros((self.params["means"].shape[0], 2), device="cuda")
             centres = np.stack([-c.world_to_cam[:, :3].T @ c.world_to_cam[:, 3] for c in cams])
@@ -196,6 +209,15 @@ class Fit:
                              pixel=self.pixel)
         if gather and self.it > d["start"] and self.it % d["every"] == 0:
             self._densify()
+        mc = self.mcmc
+        if mc is not None:
+            n = self.params["means"].shape[0]
+            eta = torch.randn((n, 3), generator=self.gen, device="cuda")
+            R.mcmc_noise(self.params, eta, self.lr["means"], mc["lambda_noise"])
+            if mc["start"] <= self.it < mc["stop"] and self.it % mc["every"] == 0:
+                u = torch.rand(n, generator=self.gen, device="cuda")
+                self.dead_relocated.append(R.mcmc_relocate(self.r, self.params, self.m, self.v, u, mc["min_opacity"]))
+                self.relocations += 1
         return loss
 
     def _densify(self):
