@@ -101,3 +101,27 @@ def test_stalled_lookback_reports_timeout_and_context_survives(cuda_lib):
     good.sync_status()
     ref = np.argsort(keys.cpu().numpy().astype(np.int64), kind="stable")
     np.testing.assert_array_equal(vo.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("n", [120_000, 500_000])
+def test_pair_count_beyond_capacity_is_reported(cuda_lib, n):
+    """Screen-filling Gaussians at 1920x1280 (9,600 tiles each): 120k give
+    about 1.15e9 pairs (past the 2^30 limit), 500k about 4.8e9 (past 2^32,
+    where a 32-bit sum would wrap to a small count). The pair count is summed
+    in 64 bits, so both are refused with SPLASH_ERR_CAPACITY before any pair
+    buffer is sized from it, and the context renders correctly afterwards."""
+    r = R.Renderer()
+    cam = scenes.Camera(1920, 1280, 1800.0, 1800.0, 960.0, 640.0, np.concatenate([np.eye(3), np.zeros((3, 1))], 1),
+                        0.2, 20.0)
+    rng = np.random.default_rng(n)
+    g = scenes.Gaussians(np.float32(np.c_[rng.uniform(-0.1, 0.1, (n, 2)), rng.uniform(3.0, 4.0, n)]),
+                         np.full((n, 3), 2.0, np.float32), np.tile(np.float32([1, 0, 0, 0]), (n, 1)),
+                         np.full(n, 2.0, np.float32), np.zeros((n, 1, 3), np.float32), 0)
+    med = scenes.Medium(np.float32([0.1] * 3), np.float32([0.1] * 3), np.float32([0.1] * 3))
+    with pytest.raises(_abi.SplashError) as ei:
+        gpu_forward(r, g, med, cam)
+    assert ei.value.status == _abi.ERR_CAPACITY
+    assert b"2^30" in _abi.lib().splash_last_error()
+    g2, m2, cam2 = scenes.tiny_scene(0)
+    out = gpu_forward(r, g2, m2, cam2)
+    assert np.isfinite(out["image"]).all()
