@@ -55,6 +55,29 @@ BlendView backward_view(splash_state *st, const CamK &ck, const float *gi, const
     return v;
 }
 
+// The backward's per-Gaussian accumulators must be zero when its blend
+// starts. Once this state holds them (a backward ran on it before), the
+// forward blend clears them: each of its CTAs stores its share, which drains
+// under that arithmetic-bound kernel instead of costing a memset pass. The
+// backward clears them itself when the last forward did not.
+void preclear_backward(splash_state *st, int64_t n, BlendView &v)
+{
+    st->gacc_cleared = n > 0 && st->gacc.cap >= sizeof(GAcc) * (size_t)n;
+    if (!st->gacc_cleared) return;
+    v.clear = st->gacc.as<GAcc>();
+    v.clear_n = n;
+    st->gacc_clear_ptr = st->gacc.p;
+    st->gacc_clear_n = n;
+}
+
+splash_status clear_backward(splash_state *st, int64_t n, cudaStream_t s)
+{
+    const bool covered = st->gacc_cleared && st->gacc_clear_ptr == st->gacc.p && st->gacc_clear_n >= n;
+    st->gacc_cleared = false;  // the blend below dirties them
+    if (!covered && n > 0) SPLASH_CUDA_TRY(cudaMemsetAsync(st->gacc.p, 0, sizeof(GAcc) * (size_t)n, s));
+    return SPLASH_OK;
+}
+
 // the failure a non-zero device status word reports
 splash_status status_failure(uint32_t status)
 {
@@ -108,7 +131,11 @@ splash_status splash_state_create(splash_ctx *ctx, splash_state **out)
     if (!ctx || !out) return fail(SPLASH_ERR_INVALID_ARG, "null argument");
     splash_state *s = new splash_state();
     s->ctx = ctx;
-    if (cudaMallocHost(&s->h_small, 16 * sizeof(uint32_t)) != cudaSuccess || !s->small.ensure(64) ||
+    if (cudaHostAlloc(reinterpret_cast<void **>(&s->h_small), 2 * sizeof(uint64_t), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(reinterpret_cast<void **>(&s->h_small_dev), s->h_small, 0) != cudaSuccess ||
+        !s->small.ensure(64) ||
+        !s->pair_part.ensure(kPairTotalScratchBytes) ||
+        cudaMemset(s->pair_part.p, 0, kPairTotalScratchBytes) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->k_ready, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         delete s;
@@ -174,13 +201,12 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
         launch_preprocess_fwd(n, *g, medium, ck, tg, st->rec.as<Rec>(), st->depth_key.as<uint32_t>(),
                               st->tt.as<uint32_t>(), st->rect.as<uint2>(), s);
     }
-    // the pair count K is the sum of the tile counts: read it back (with the
-    // status word) while the depth sort and the scan run, so that the host
+    // the pair count K is the sum of the tile counts: its kernel stores it,
+    // with the status word, into mapped host memory, and the host waits for
+    // that kernel (k_ready) while the depth sort and the scan run, so that it
     // knows K before the GPU runs out of queued work
-    // 64-bit total in dK[0..1] (8-byte aligned) and its pinned copy in h_small[2..3]
-    launch_pair_total(n, st->tt.as<uint32_t>(), reinterpret_cast<uint64_t *>(dK), s);
-    SPLASH_CUDA_TRY(cudaMemcpyAsync(st->h_small + 2, dK, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
-    SPLASH_CUDA_TRY(cudaMemcpyAsync(st->h_small + 1, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    launch_pair_total(n, st->tt.as<uint32_t>(), reinterpret_cast<uint64_t *>(dK), st->pair_part.p, st->h_small_dev,
+                      ctx->d_status, s);
     SPLASH_CUDA_TRY(cudaEventRecord(st->k_ready, s));
     const uint32_t *order = nullptr;
     if (n > 0) {
@@ -198,12 +224,11 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
     }
     SPLASH_CUDA_TRY(cudaGetLastError());
     SPLASH_CUDA_TRY(cudaEventSynchronize(st->k_ready));
-    if (const uint32_t status = st->h_small[1]) {
+    if (const uint32_t status = (uint32_t)st->h_small[0]) {
         SPLASH_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), s));
         return status_failure(status);
     }
-    uint64_t K64;
-    std::memcpy(&K64, st->h_small + 2, sizeof K64);
+    const uint64_t K64 = st->h_small[1];
     // every uint32 offset below is valid only under this bound: nothing that
     // uses them runs before it is checked
     if (K64 >= ((uint64_t)1 << 30)) return fail(SPLASH_ERR_CAPACITY, "more than 2^30 tile/Gaussian pairs");
@@ -253,6 +278,7 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
         v.zhat = st->zh.as<float>();
         v.n_last = st->nlast.as<uint32_t>();
         v.n_walk = st->nwalk.as<uint32_t>();
+        preclear_backward(st, n, v);
         launch_blend_fwd(v, medium, fwd_batch(ctx->opt), s);
     }
     SPLASH_CUDA_TRY(cudaGetLastError());
@@ -294,8 +320,8 @@ splash_status render_backward_impl(splash_ctx *ctx, splash_state *st, const spla
     ENSURE(st->tile_med, 4 * 6 * (size_t)ntiles);
     ENSURE(st->block_med, 4 * 9 * (size_t)nblocks);
     ENSURE(st->red_scratch, 4 * 16 * (size_t)kColsumParts);
-    SPLASH_CUDA_TRY(cudaMemsetAsync(st->gacc.p, 0, sizeof(GAcc) * (size_t)n, s));
-    SPLASH_CUDA_TRY(cudaMemsetAsync(st->block_med.p, 0, 4 * 9 * (size_t)nblocks, s));
+    // (every block of the preprocess adjoint writes its block_med row: no clear)
+    if ((rc = clear_backward(st, n, s)) != SPLASH_OK) return rc;
     const CamK ck = make_cam(*cam);
     {
         Stage t(ctx->prof, SPLASH_STAGE_BLEND_BWD, s);
@@ -363,8 +389,8 @@ splash_status backward_adam_impl(splash_ctx *ctx, splash_state *st, const splash
     ENSURE(st->block_med, 4 * 9 * (size_t)nblocks);
     ENSURE(st->gmed, 4 * 16);
     ENSURE(st->red_scratch, 4 * 16 * (size_t)kColsumParts);
-    SPLASH_CUDA_TRY(cudaMemsetAsync(st->gacc.p, 0, sizeof(GAcc) * (size_t)n, s));
-    SPLASH_CUDA_TRY(cudaMemsetAsync(st->block_med.p, 0, 4 * 9 * (size_t)nblocks, s));
+    // (every block of the fused adjoint writes its block_med row: no clear)
+    if ((rc = clear_backward(st, n, s)) != SPLASH_OK) return rc;
     const CamK ck = make_cam(*cam);
     {
         Stage t(ctx->prof, SPLASH_STAGE_BLEND_BWD, s);

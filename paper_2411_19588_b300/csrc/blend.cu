@@ -116,6 +116,16 @@ __device__ __forceinline__ void blend_tile_fwd(const BlendView &v, int tile, con
     const uint2 rg = v.ranges[tile];
     const int n = (int)(rg.y - rg.x);
     const float kNaN = __int_as_float(0x7fc00000);
+    if (v.clear) {
+        // this tile's share of the backward's accumulators: the stores drain
+        // while the blend below computes
+        const int64_t ntiles = (int64_t)v.tg.tx * v.tg.ty;
+        const int64_t per = (v.clear_n + ntiles - 1) / ntiles;
+        const int64_t b = min((int64_t)tile * per, v.clear_n), e = min(b + per, v.clear_n);
+        float4 *dst = reinterpret_cast<float4 *>(v.clear + b);
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int64_t q = tid; q < 3 * (e - b); q += NT) dst[q] = z;
+    }
 
     // a finished pixel's column is a quiet NaN whose payload is its walked
     // count (the stop position + 1, < 2^22): it fails every 3-sigma test

@@ -206,8 +206,14 @@ struct splash_state {
     splash_host::Buf pixJ, pixG, pixgz, pixmed;
     bool pixel_forward = false;  // the last forward was splash_render_forward_pixel
     splash_host::Buf small;       // [0] = pair count K, [1..] spare
-    uint32_t *h_small = nullptr;  // pinned: K, status
-    cudaEvent_t k_ready = nullptr;  // K and the status word have reached h_small
+    splash_host::Buf pair_part;   // the pair-count sum's partials and ticket (kept zero between calls)
+    // mapped pinned words [status, K] that the pair-count kernel stores (host
+    // and device addresses); k_ready follows that kernel in the stream
+    uint64_t *h_small = nullptr, *h_small_dev = nullptr;
+    cudaEvent_t k_ready = nullptr;
+    bool gacc_cleared = false;  // the last forward blend zeroed gacc[0..gacc_clear_n)
+    const void *gacc_clear_ptr = nullptr;
+    int64_t gacc_clear_n = 0;
     // what the last forward produced
     bool has_forward = false;
     int64_t n = 0;

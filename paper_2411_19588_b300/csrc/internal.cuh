@@ -100,6 +100,8 @@ struct BlendView {
     const float *dL_dimage, *dL_ddepth, *dL_ddepth01;  // backward inputs (last two may be null)
     GAcc *gacc;                           // backward: per-Gaussian accumulators
     float *tile_medium;                   // backward: per-tile medium partials [tiles][6]
+    GAcc *clear;                          // forward (plain launch): zero clear[0..clear_n) for the next backward
+    int64_t clear_n;
 };
 
 // device status word bits
@@ -197,11 +199,19 @@ void launch_count_scan(int64_t n, const uint32_t *order, const uint32_t *tiles_t
                        uint32_t *block_sums, uint32_t *total, cudaStream_t s);
 // d_medium[j] = sum over nblocks rows of partials[b][9] (the pixel form's medium gradient)
 void launch_pixel_medium_final(const float *partials, int nblocks, float *d_medium, cudaStream_t s);
-// *total = sum of tt[0..n) (zeroed first)
-void launch_pair_total(int64_t n, const uint32_t *tt, uint64_t *total, cudaStream_t s);
+// *total = sum of tt[0..n) in 64 bits; with host_out (mapped host memory,
+// device address) also host_out[0] = *status and host_out[1] = the total.
+// CTAs of the pair-count sum; its scratch holds that many 8-byte partials and
+// a ticket word, zero before the first launch (each launch leaves it zero)
+constexpr int kPairTotalBlocksMax = 148 * 4;
+constexpr size_t kPairTotalScratchBytes = 8 * (size_t)(kPairTotalBlocksMax + 1);
+void launch_pair_total(int64_t n, const uint32_t *tt, uint64_t *total, void *scratch, uint64_t *host_out,
+                       const uint32_t *status, cudaStream_t s);
 void launch_emit(int64_t n, const uint32_t *order, const uint32_t *offsets, const uint32_t *tt, const uint2 *rect,
                  const TileGeom &tg, uint32_t *tile_ids, uint32_t *gauss_ids, uint64_t capacity, uint32_t *status,
                  cudaStream_t s);
+// ranges[t] = [first, end) of tile t's run in the sorted tile ids, for every
+// tile (empty ones as [s, s)); nothing needs clearing first
 void launch_ranges(int64_t k_host, const uint32_t *k_dev, const uint32_t *tile_ids, uint2 *ranges, int ntiles,
                    cudaStream_t s);
 // staging batch sizes the blend kernels are built for

@@ -374,11 +374,11 @@ int sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *k0, u
     if (items != kDepthSortItems) items = kSortItems;
     const int64_t tile = (int64_t)kSortThreads * items;
     const int64_t parts = (n_host + tile - 1) / tile;  // at most the scratch's kSortTile-sized count
-    cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * (4 * kRadixMax + 64), stream);
-    // look-back flags of every pass, one block of parts x stride words per pass
+    // histograms, tickets and the look-back flags of every pass (one block of
+    // parts x stride words per pass) are contiguous: one memset clears them
     size_t lb_words = 0;
     for (int p = 0; p < passes; p++) lb_words += (size_t)parts * lookback_stride(plan.width[p]);
-    cudaMemsetAsync(s.lookback, 0, sizeof(uint32_t) * lb_words, stream);
+    cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * (size_t)(s.lookback - s.hist) + sizeof(uint32_t) * lb_words, stream);
     // every CTA flushes its shared counters with global atomics onto the same
     // addresses: 4 CTAs per SM keeps that contention below the cost of reading
     const int hblocks = (int)std::min<int64_t>((n_host / 4 + 255) / 256 + 1, 148 * 4);

@@ -170,66 +170,107 @@ __global__ void __launch_bounds__(256) k_emit(int64_t n, const uint32_t *__restr
     }
 }
 
-__device__ __forceinline__ void range_ends(int64_t i, uint32_t t, uint32_t prev, uint32_t next, int64_t k,
-                                           uint2 *__restrict__ ranges, uint32_t ntiles)
-{
-    if (t >= ntiles) return;  // only after a capacity overflow (reported through the status word)
-    if (i == 0 || prev != t) ranges[t].x = (uint32_t)i;
-    if (i == k - 1 || next != t) ranges[t].y = (uint32_t)(i + 1);
-}
-
-// Starts and ends of the runs of equal tile ids: four ids per thread from one
-// 16-byte load (when the buffer is 16-byte aligned), plus the two neighbours.
+// Start of every tile's run in the sorted pairs, one warp per tile value t
+// in [0, ntiles]: the first index whose tile id is >= t (a 32-way search: each
+// round probes 32 evenly spaced keys, one per lane, and keeps the sub-interval
+// between the last key below t and the first at or above it). Tile t's range
+// is [start(t), start(t + 1)); every tile is written, empty ones as [s, s).
 __global__ void __launch_bounds__(256) k_ranges(int64_t k_host, const uint32_t *__restrict__ k_dev,
                                                 const uint32_t *__restrict__ tile_ids, uint2 *__restrict__ ranges,
                                                 uint32_t ntiles)
 {
+    const int lane = threadIdx.x & 31;
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t > (int64_t)ntiles) return;  // uniform over the warp
     const int64_t k = k_dev ? (int64_t)*k_dev : k_host;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t k4 = (reinterpret_cast<uintptr_t>(tile_ids) & 15) ? 0 : k / 4;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < k4; q += stride) {
-        const uint4 v = reinterpret_cast<const uint4 *>(tile_ids)[q];
-        const int64_t i = 4 * q;
-        const uint32_t prev = i > 0 ? tile_ids[i - 1] : 0u;
-        const uint32_t next = i + 4 < k ? tile_ids[i + 4] : 0u;
-        range_ends(i, v.x, prev, v.y, k, ranges, ntiles);
-        range_ends(i + 1, v.y, v.x, v.z, k, ranges, ntiles);
-        range_ends(i + 2, v.z, v.y, v.w, k, ranges, ntiles);
-        range_ends(i + 3, v.w, v.z, next, k, ranges, ntiles);
+    const uint32_t tv = (uint32_t)t;
+    // invariant: every key before lo is < t; hi == k or key[hi] >= t
+    int64_t lo = 0, hi = k;
+    while (hi - lo > 32) {
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t p = min(lo + (int64_t)(lane + 1) * step - 1, hi - 1);
+        const uint32_t ge = __ballot_sync(0xffffffffu, tile_ids[p] >= tv);
+        if (ge == 0u) {
+            lo = min(lo + 32 * step, hi);  // all 32 probes below t: past the last one
+        } else {
+            const int f = __ffs(ge) - 1;  // first probe at or above t
+            hi = min(lo + (int64_t)(f + 1) * step - 1, hi - 1);
+            if (f > 0) lo = lo + (int64_t)f * step;  // one past the probe before it
+        }
     }
-    for (int64_t i = 4 * k4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride)
-        range_ends(i, tile_ids[i], i > 0 ? tile_ids[i - 1] : 0u, i + 1 < k ? tile_ids[i + 1] : 0u, k, ranges, ntiles);
+    const int64_t q = lo + lane;
+    const uint32_t ge = __ballot_sync(0xffffffffu, q < hi && tile_ids[q] >= tv);
+    const int64_t start = ge ? lo + __ffs(ge) - 1 : hi;
+    if (lane == 0) {
+        if (t < (int64_t)ntiles) ranges[t].x = (uint32_t)start;
+        if (t > 0) ranges[t - 1].y = (uint32_t)start;
+    }
 }
 
-// total of the tile counts (the pair count K), one atomic per CTA (all of
-// them land on one address). Summed in 64 bits: a scene whose counts add up
-// past 2^32 must be reported as over capacity, not wrap to a small count.
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long x, unsigned long long *s_w)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = x;
+    __syncthreads();
+    unsigned long long t = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_w[w];
+    return t;  // valid in thread 0
+}
+
+// Total of the tile counts (the pair count K), summed in 64 bits: a scene
+// whose counts add up past 2^32 must be reported as over capacity, not wrap
+// to a small count. One partial per CTA; the last CTA to finish (a ticket
+// taken after its partial is fenced) adds the partials in CTA order, writes
+// the total and puts the ticket back to zero, so nothing is cleared before
+// the launch. With `host` set it also stores the total (host[1]) and the
+// device status word (host[0]) into mapped host memory, visible to the host
+// once the kernel has completed: no copy has to follow it.
 __global__ void __launch_bounds__(256) k_sum_u64(const uint32_t *__restrict__ v, int64_t n,
-                                                 unsigned long long *__restrict__ total)
+                                                 unsigned long long *__restrict__ part, uint32_t *__restrict__ ticket,
+                                                 unsigned long long *__restrict__ total,
+                                                 unsigned long long *__restrict__ host, const uint32_t *__restrict__ status)
 {
     __shared__ unsigned long long s_w[8];
+    __shared__ uint32_t s_last;
     unsigned long long acc = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) acc += v[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+    acc = block_sum_u64(acc, s_w);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = acc;
+        __threadfence();
+        s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
     __syncthreads();
-    if (threadIdx.x < 32) {
-        unsigned long long x = threadIdx.x < 8 ? s_w[threadIdx.x] : 0ull;
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (threadIdx.x == 0 && x) atomicAdd(total, x);
+    if (!s_last) return;  // uniform over the CTA
+    __threadfence();
+    unsigned long long x = 0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) x += *reinterpret_cast<volatile unsigned long long *>(part + b);
+    __syncthreads();  // s_w is reused
+    x = block_sum_u64(x, s_w);
+    if (threadIdx.x == 0) {
+        *total = x;
+        *ticket = 0u;
+        if (host) {
+            host[0] = *reinterpret_cast<const volatile uint32_t *>(status);
+            host[1] = x;
+            __threadfence_system();
+        }
     }
 }
 
 }  // namespace
 
-void launch_pair_total(int64_t n, const uint32_t *tt, uint64_t *total, cudaStream_t s)
+void launch_pair_total(int64_t n, const uint32_t *tt, uint64_t *total, void *scratch, uint64_t *host_out,
+                       const uint32_t *status, cudaStream_t s)
 {
-    cudaMemsetAsync(total, 0, sizeof(uint64_t), s);
-    if (n <= 0) return;
-    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 4);
-    k_sum_u64<<<blocks, 256, 0, s>>>(tt, n, reinterpret_cast<unsigned long long *>(total));
+    // scratch: kPairTotalBlocksMax partials, then the ticket (zero between launches)
+    unsigned long long *part = static_cast<unsigned long long *>(scratch);
+    uint32_t *ticket = reinterpret_cast<uint32_t *>(part + kPairTotalBlocksMax);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, kPairTotalBlocksMax));
+    k_sum_u64<<<blocks, 256, 0, s>>>(tt, std::max<int64_t>(n, 0), part, ticket, reinterpret_cast<unsigned long long *>(total),
+                                     reinterpret_cast<unsigned long long *>(host_out), status);
     count_launch();
 }
 
@@ -265,10 +306,9 @@ void launch_emit(int64_t n, const uint32_t *order, const uint32_t *offsets, cons
 
 void launch_ranges(int64_t k_host, const uint32_t *k_dev, const uint32_t *tile_ids, uint2 *ranges, int ntiles, cudaStream_t s)
 {
-    cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)ntiles, s);
-    if (k_host <= 0) return;
-    const int blocks = (int)std::min<int64_t>((k_host / 4 + 255) / 256 + 1, 148 * 16);
-    k_ranges<<<blocks, 256, 0, s>>>(k_host, k_dev, tile_ids, ranges, (uint32_t)ntiles);
+    if (ntiles <= 0) return;
+    const int64_t warps = (int64_t)ntiles + 1;
+    k_ranges<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(k_host, k_dev, tile_ids, ranges, (uint32_t)ntiles);
     count_launch();
 }
 
