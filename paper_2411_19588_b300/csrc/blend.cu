@@ -557,6 +557,7 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
 template <int TW, int TH, int NB>
 __global__ void __launch_bounds__(fwd_threads<TW, TH>(), 1024 / fwd_threads<TW, TH>()) k_blend_fwd(BlendView v, const float *__restrict__ medium)
 {
+    pdl_enter();
     blend_tile_fwd<TW, TH, NB>(v, blockIdx.x, medium);
 }
 
@@ -565,6 +566,7 @@ __global__ void __launch_bounds__(fwd_threads<TW, TH>(), 1024 / fwd_threads<TW, 
 template <int TW, int TH, int NB, bool DG>
 __global__ void __launch_bounds__(bwd_threads<TW, TH>(), (DG ? 704 : 768) / bwd_threads<TW, TH>()) k_blend_bwd(BlendView v, const float *__restrict__ medium)
 {
+    pdl_enter();
     blend_tile_bwd<TW, TH, NB, DG>(v, blockIdx.x, medium);
 }
 
@@ -631,7 +633,7 @@ template <int TW, int TH, int NB>
 struct FwdPlain {
     static void run(const BlendView &v, const float *medium, cudaStream_t s)
     {
-        k_blend_fwd<TW, TH, NB><<<v.tg.tx * v.tg.ty, fwd_threads<TW, TH>(), 0, s>>>(v, medium);
+        launch_pdl(k_blend_fwd<TW, TH, NB>, v.tg.tx * v.tg.ty, fwd_threads<TW, TH>(), 0, s, v, medium);
         count_launch();
     }
 };
@@ -640,9 +642,9 @@ struct BwdPlain {
     static void run(const BlendView &v, const float *medium, cudaStream_t s)
     {
         if (v.dL_ddepth || v.dL_ddepth01)
-            k_blend_bwd<TW, TH, NB, true><<<v.tg.tx * v.tg.ty, bwd_threads<TW, TH>(), 0, s>>>(v, medium);
+            launch_pdl(k_blend_bwd<TW, TH, NB, true>, v.tg.tx * v.tg.ty, bwd_threads<TW, TH>(), 0, s, v, medium);
         else
-            k_blend_bwd<TW, TH, NB, false><<<v.tg.tx * v.tg.ty, bwd_threads<TW, TH>(), 0, s>>>(v, medium);
+            launch_pdl(k_blend_bwd<TW, TH, NB, false>, v.tg.tx * v.tg.ty, bwd_threads<TW, TH>(), 0, s, v, medium);
         count_launch();
     }
 };

@@ -264,6 +264,35 @@ size_t ssim_scratch_floats(int C, int H, int W);
 namespace splash {
 // every kernel launch site bumps this (reported by splash_kernel_launches)
 void count_launch(int n = 1);
+
+// Programmatic dependent launch. A kernel started with launch_pdl may be
+// scheduled while the kernel before it in the stream is still finishing; it
+// begins with pdl_enter(), which first lets the kernel after it start
+// launching, then waits until the kernel before it has completed and its
+// stores are visible. Nothing of the previous kernel's output is touched
+// before that wait, so the stream order of the results is unchanged; what
+// overlaps is the launch latency and the previous kernel's last wave.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... P, typename... A>
+inline void launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A &&...args)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<A &&>(args)...);  // errors surface at cudaGetLastError
+}
 }  // namespace splash
 
 // ---- error plumbing shared by the host code

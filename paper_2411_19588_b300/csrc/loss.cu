@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(256) k_ssim_pass1(const float *__restrict__ X,
                                                     float *__restrict__ d_xx, float *__restrict__ d_xy,
                                                     float *__restrict__ partial)
 {
+    pdl_enter();
     __shared__ __align__(16) float sx[kHY][kSX];
     __shared__ __align__(16) float sy[kHY][kSX];
     __shared__ F2 hm[kHY][kTX + 1];   // horizontal (mu_x, mu_y)
@@ -263,6 +264,7 @@ __global__ void __launch_bounds__(256) k_ssim_pass2(const float *__restrict__ X,
                                                     const float *__restrict__ d_xx, const float *__restrict__ d_xy,
                                                     float *__restrict__ grad)
 {
+    pdl_enter();
     __shared__ __align__(16) float s[3][kHY][kSX];
     __shared__ F2 hp[kHY][kTX + 1];     // horizontal (d_mu, d_xx)
     __shared__ float hq[kHY][kTX + 1];  // horizontal d_xy
@@ -387,6 +389,7 @@ __global__ void __launch_bounds__(256) k_ssim_pass2(const float *__restrict__ X,
 // butterfly; the FP64 add chain stays short on this GPU's narrow FP64 pipe
 __global__ void k_loss_final(const float *__restrict__ part, double inv_count, float lam, float *__restrict__ loss)
 {
+    pdl_enter();
     const int lane = threadIdx.x;
     double l1 = 0.0, ss = 0.0;
     for (int p = lane; p < kColsumParts; p += 32) {
@@ -430,14 +433,14 @@ void launch_ssim_loss(const float *img, const float *tgt, int C, int H, int W, f
     float *d_mu = scratch, *d_xx = scratch + n, *d_xy = scratch + 2 * n, *partial = scratch + 3 * n;
     const Win win = make_window();
     const double inv = 1.0 / (double)n;
-    k_ssim_pass1<<<grid, 256, 0, s>>>(img, tgt, W, H, win, (float)(-lam * inv), d_mu, d_xx, d_xy, partial);
+    launch_pdl(k_ssim_pass1, grid, 256, 0, s, img, tgt, W, H, win, (float)(-lam * inv), d_mu, d_xx, d_xy, partial);
     count_launch();
     const int nb = grid.x * grid.y * grid.z;
     float *part2 = partial + 2 * nb;
     launch_colsum_partial(partial, nb, 2, part2, s);
-    k_loss_final<<<1, 32, 0, s>>>(part2, inv, lam, loss);
+    launch_pdl(k_loss_final, 1, 32, 0, s, part2, inv, lam, loss);
     count_launch();
-    if (grad) k_ssim_pass2<<<grid, 256, 0, s>>>(img, tgt, W, H, win, (float)inv, d_mu, d_xx, d_xy, grad);
+    if (grad) launch_pdl(k_ssim_pass2, grid, 256, 0, s, img, tgt, W, H, win, (float)inv, d_mu, d_xx, d_xy, grad);
     if (grad) count_launch();
 }
 

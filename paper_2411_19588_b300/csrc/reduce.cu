@@ -44,6 +44,7 @@ template <int COLS>
 __global__ void __launch_bounds__(kColsumThreads) k_colsum_partial(const float *__restrict__ data, int rows,
                                                                    float *__restrict__ part)
 {
+    pdl_enter();
     colsum_part<COLS>(data, rows, part, blockIdx.x);
 }
 
@@ -54,6 +55,7 @@ __global__ void __launch_bounds__(kColsumThreads) k_colsum_pair(const float *__r
                                                                 float *__restrict__ part_a, const float *__restrict__ b,
                                                                 int rows_b, float *__restrict__ part_b)
 {
+    pdl_enter();
     if (blockIdx.x < kColsumParts)
         colsum_part<CA>(a, rows_a, part_a, blockIdx.x);
     else
@@ -65,16 +67,16 @@ __global__ void __launch_bounds__(kColsumThreads) k_colsum_pair(const float *__r
 void launch_colsum_pair_6_9(const float *a, int rows_a, float *part_a, const float *b, int rows_b, float *part_b,
                             cudaStream_t s)
 {
-    k_colsum_pair<6, 9><<<2 * kColsumParts, kColsumThreads, 0, s>>>(a, rows_a, part_a, b, rows_b, part_b);
+    launch_pdl(k_colsum_pair<6, 9>, 2 * kColsumParts, kColsumThreads, 0, s, a, rows_a, part_a, b, rows_b, part_b);
     count_launch();
 }
 
 void launch_colsum_partial(const float *data, int rows, int cols, float *part, cudaStream_t s)
 {
     switch (cols) {
-    case 2: k_colsum_partial<2><<<kColsumParts, kColsumThreads, 0, s>>>(data, rows, part); break;
-    case 6: k_colsum_partial<6><<<kColsumParts, kColsumThreads, 0, s>>>(data, rows, part); break;
-    default: k_colsum_partial<9><<<kColsumParts, kColsumThreads, 0, s>>>(data, rows, part); break;
+    case 2: launch_pdl(k_colsum_partial<2>, kColsumParts, kColsumThreads, 0, s, data, rows, part); break;
+    case 6: launch_pdl(k_colsum_partial<6>, kColsumParts, kColsumThreads, 0, s, data, rows, part); break;
+    default: launch_pdl(k_colsum_partial<9>, kColsumParts, kColsumThreads, 0, s, data, rows, part); break;
     }
     count_launch();
 }

@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(256) k_hist(const uint32_t *__restrict__ keys,
                                               const uint32_t *__restrict__ n_dev, DigitPlan plan,
                                               uint32_t *__restrict__ hist, uint32_t *__restrict__ done)
 {
+    pdl_enter();
     __shared__ uint32_t s[4][kRadixMax];
     const int passes = plan.passes;
     for (int e = threadIdx.x; e < 4 * kRadixMax; e += blockDim.x) (&s[0][0])[e] = 0u;
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const uint32_t *__restrict__ goff, uint32_t *__restrict__ lookback, uint32_t *__restrict__ counter,
     uint32_t *__restrict__ status, int spin_limit, uint32_t stall_part)
 {
+    pdl_enter();
     // digits per thread in the per-digit steps: RA = max(256, 2^BITS) table entries
     constexpr int RA = (1 << BITS) > kSortThreads ? (1 << BITS) : kSortThreads;
     constexpr int DPT = RA / kSortThreads;
@@ -252,6 +254,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
 __global__ void k_iota_copy(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
                             uint32_t *__restrict__ vout, int64_t n_host, const uint32_t *__restrict__ n_dev)
 {
+    pdl_enter();
     const int64_t n = n_dev ? (int64_t)*n_dev : n_host;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         kout[i] = kin[i];
@@ -367,7 +370,7 @@ int sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *k0, u
     const int passes = plan.passes;
     if (passes == 0) {
         const int blocks = (int)std::min<int64_t>((n_host + 255) / 256, 148 * 16);
-        k_iota_copy<<<blocks, 256, 0, stream>>>(keys_in, vals_in, k0, v0, n_host, n_dev);
+        launch_pdl(k_iota_copy, blocks, 256, 0, stream, keys_in, vals_in, k0, v0, n_host, n_dev);
         count_launch();
         return 0;
     }
@@ -382,7 +385,7 @@ int sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *k0, u
     // every CTA flushes its shared counters with global atomics onto the same
     // addresses: 4 CTAs per SM keeps that contention below the cost of reading
     const int hblocks = (int)std::min<int64_t>((n_host / 4 + 255) / 256 + 1, 148 * 4);
-    k_hist<<<hblocks, 256, 0, stream>>>(keys_in, n_host, n_dev, plan, s.hist, s.counters + 4);  // zeroed above
+    launch_pdl(k_hist, hblocks, 256, 0, stream, keys_in, n_host, n_dev, plan, s.hist, s.counters + 4);  // zeroed above
     count_launch();
     const uint32_t *ki = keys_in, *vi = vals_in;
     uint32_t *lb = s.lookback;
@@ -392,7 +395,7 @@ int sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *k0, u
         const uint32_t mask = (1u << pbits) - 1u;
         size_t smem = 0;
         const OnesweepFn kern = onesweep_kernel(pbits, items, &smem);
-        kern<<<(unsigned)parts, kSortThreads, smem, stream>>>(ki, vi, ko, vo, n_host, n_dev, plan.shift[p], mask,
+        launch_pdl(kern, (unsigned)parts, kSortThreads, smem, stream, ki, vi, ko, vo, n_host, n_dev, plan.shift[p], mask,
                                                               s.hist + kRadixMax * p, lb, s.counters + p, status,
                                                               spin_limit, (uint32_t)stall_part);
         count_launch();

@@ -43,6 +43,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(int64_t n, const uint32_t *__restrict__ order,
                                                             const uint32_t *__restrict__ tt, uint32_t *__restrict__ sums)
 {
+    pdl_enter();
     __shared__ uint32_t s_w[kScanThreads / 32];
     const int64_t base = (int64_t)blockIdx.x * kScanChunk;
     uint32_t acc = 0;
@@ -59,6 +60,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(int64_t n, const u
 // one block: exclusive scan of the chunk sums; total pair count to *total
 __global__ void __launch_bounds__(kScanThreads) k_scan_top(int nchunks, uint32_t *__restrict__ sums, uint32_t *__restrict__ total)
 {
+    pdl_enter();
     __shared__ uint32_t s_w[kScanThreads / 32];
     uint32_t carry = 0;
     for (int b = 0; b < nchunks; b += kScanThreads) {
@@ -82,6 +84,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(int64_t n, const uin
                                                           uint32_t *__restrict__ offsets, int own_prefix,
                                                           uint32_t *__restrict__ total)
 {
+    pdl_enter();
     __shared__ uint32_t s_w[kScanThreads / 32];
     uint32_t pre = 0;
     if (own_prefix) {  // uniform over the grid
@@ -123,6 +126,7 @@ __global__ void __launch_bounds__(256) k_emit(int64_t n, const uint32_t *__restr
                                               uint32_t *__restrict__ tile_ids, uint32_t *__restrict__ gauss_ids,
                                               uint64_t capacity, uint32_t *__restrict__ status)
 {
+    pdl_enter();
     constexpr uint32_t kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -179,6 +183,7 @@ __global__ void __launch_bounds__(256) k_ranges(int64_t k_host, const uint32_t *
                                                 const uint32_t *__restrict__ tile_ids, uint2 *__restrict__ ranges,
                                                 uint32_t ntiles)
 {
+    pdl_enter();
     const int lane = threadIdx.x & 31;
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (t > (int64_t)ntiles) return;  // uniform over the warp
@@ -232,6 +237,7 @@ __global__ void __launch_bounds__(256) k_sum_u64(const uint32_t *__restrict__ v,
                                                  unsigned long long *__restrict__ total,
                                                  unsigned long long *__restrict__ host, const uint32_t *__restrict__ status)
 {
+    pdl_enter();
     __shared__ unsigned long long s_w[8];
     __shared__ uint32_t s_last;
     unsigned long long acc = 0;
@@ -269,7 +275,7 @@ void launch_pair_total(int64_t n, const uint32_t *tt, uint64_t *total, void *scr
     unsigned long long *part = static_cast<unsigned long long *>(scratch);
     uint32_t *ticket = reinterpret_cast<uint32_t *>(part + kPairTotalBlocksMax);
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, kPairTotalBlocksMax));
-    k_sum_u64<<<blocks, 256, 0, s>>>(tt, std::max<int64_t>(n, 0), part, ticket, reinterpret_cast<unsigned long long *>(total),
+    launch_pdl(k_sum_u64, blocks, 256, 0, s, tt, std::max<int64_t>(n, 0), part, ticket, reinterpret_cast<unsigned long long *>(total),
                                      reinterpret_cast<unsigned long long *>(host_out), status);
     count_launch();
 }
@@ -282,15 +288,15 @@ void launch_count_scan(int64_t n, const uint32_t *order, const uint32_t *tt, uin
         cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
         return;
     }
-    k_scan_reduce<<<nchunks, kScanThreads, 0, s>>>(n, order, tt, sums);
+    launch_pdl(k_scan_reduce, nchunks, kScanThreads, 0, s, n, order, tt, sums);
     count_launch();
     // up to 1024 chunks each chunk adds up its predecessors' sums itself
     const int own = nchunks <= 1024;
     if (!own) {
-        k_scan_top<<<1, kScanThreads, 0, s>>>(nchunks, sums, total);
+        launch_pdl(k_scan_top, 1, kScanThreads, 0, s, nchunks, sums, total);
         count_launch();
     }
-    k_scan_down<<<nchunks, kScanThreads, 0, s>>>(n, order, tt, sums, offsets, own, total);
+    launch_pdl(k_scan_down, nchunks, kScanThreads, 0, s, n, order, tt, sums, offsets, own, total);
     count_launch();
 }
 
@@ -299,7 +305,7 @@ void launch_emit(int64_t n, const uint32_t *order, const uint32_t *offsets, cons
                  cudaStream_t s)
 {
     if (n <= 0) return;
-    k_emit<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, order, offsets, tt, rect, tg.tx, tile_ids, gauss_ids, capacity,
+    launch_pdl(k_emit, (unsigned)((n + 255) / 256), 256, 0, s, n, order, offsets, tt, rect, tg.tx, tile_ids, gauss_ids, capacity,
                                                        status);
     count_launch();
 }
@@ -308,7 +314,7 @@ void launch_ranges(int64_t k_host, const uint32_t *k_dev, const uint32_t *tile_i
 {
     if (ntiles <= 0) return;
     const int64_t warps = (int64_t)ntiles + 1;
-    k_ranges<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(k_host, k_dev, tile_ids, ranges, (uint32_t)ntiles);
+    launch_pdl(k_ranges, (unsigned)((warps * 32 + 255) / 256), 256, 0, s, k_host, k_dev, tile_ids, ranges, (uint32_t)ntiles);
     count_launch();
 }
 
