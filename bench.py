@@ -233,6 +233,18 @@ def measured_peaks():
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
 
 
+def super_entries(r, st) -> int:
+    """(Gaussian, super-tile) entries of the last forward's two-level binning:
+    each listed Gaussian's tile rectangle over 8 x 4-tile super-tiles."""
+    import torch
+    tt = r.state_array(st, "tiles_touched")
+    rc = r.state_array(st, "rects").to(torch.int64) & 0xFFFFFFFF
+    vis = tt != 0
+    x0, x1, y0, y1 = rc[:, 0] & 0xFFFF, rc[:, 0] >> 16, rc[:, 1] & 0xFFFF, rc[:, 1] >> 16
+    cnt = (x1 // 8 - x0 // 8 + 1) * (y1 // 4 - y0 // 4 + 1)
+    return int(cnt[vis].sum())
+
+
 def build_workload(n, rank, views, device="cuda"):
     import torch
 
@@ -373,15 +385,17 @@ def run_ours(args, world, rank, local):
     # --- algorithmic work of the blend launches in the timed region: its steps replayed,
     # the walked and last-contributor counts read after each step's forward
     restore()
-    walk, last, n_keys = 0.0, 0.0, 0
+    walk, last, n_keys, n_super = 0.0, 0.0, 0, 0
     for i in range(args.steps):
         step(args.warmup + i)
         walk += float(r.state_array(st, "n_walk").to(torch.int64).sum())
         last += float(r.state_array(st, "n_last").to(torch.int64).sum())
         n_keys += r.info(st)["n_keys"]
+        n_super += super_entries(r, st)
     walk /= args.steps
     last /= args.steps
     n_keys = int(round(n_keys / args.steps))
+    n_super = int(round(n_super / args.steps))
 
     # --- end to end through the public API with host buffers: every step's target comes from
     # pinned host memory (copied on a side stream one step ahead, into one of two device
@@ -448,13 +462,17 @@ def run_ours(args, world, rank, local):
         # fused adjoint + Adam: parameters, both moments and the blend accumulators
         # read; parameters and moments written
         "preprocess_bwd": ("hbm", ((3 * 236 + 48 + 3 * 236) if grads is None else (236 + 48 + 236)) * args.n, "GB/s"),
-        # two-phase sort: 4 passes over the N depth keys, 2 over the K pairs (keys + values read
-        # and written per pass, plus one key read for the histograms)
-        "depth_sort": ("hbm", 4 * 16.0 * args.n + 4.0 * args.n, "GB/s"),
+        # depth sort: 3 passes (9 + 9 + 8 bits) over the N depth keys (key + value read and
+        # written per pass, plus one key read for the histograms)
+        "depth_sort": ("hbm", 3 * 16.0 * args.n + 4.0 * args.n, "GB/s"),
+        # two-level binning: scan of the super-tile counts in depth order; the K_s super-tile
+        # entries emitted (order, offset, count, rectangle read; key + value written); their
+        # one-pass sort, then the tile lists gathered (entries read once, K Gaussian ids
+        # written); the tile counts from the rectangles
         "scan": ("hbm", 8.0 * args.n, "GB/s"),
-        "emit": ("hbm", 16.0 * args.n + 8.0 * n_keys, "GB/s"),
-        "tile_sort": ("hbm", 2 * 16.0 * n_keys + 4.0 * n_keys, "GB/s"),
-        "ranges": ("hbm", 4.0 * n_keys, "GB/s"),
+        "emit": ("hbm", 20.0 * args.n + 8.0 * n_super, "GB/s"),
+        "tile_sort": ("hbm", 16.0 * n_super + 4.0 * n_super + 8.0 * n_super + 4.0 * n_keys, "GB/s"),
+        "ranges": ("hbm", 12.0 * args.n, "GB/s"),
         "loss": ("hbm", 4.0 * 3 * H * W * 9, "GB/s"),
     }
     dom = max((k for k in work if per_launch.get(k, 0) > 0), key=lambda k: per_launch[k])
@@ -511,7 +529,7 @@ def run_ours(args, world, rank, local):
         "stages_source": "per-stage CUDA events in a pass of the same length after the timed region; inside "
                          "the timed region only the dominant kernel (blend_bwd) is bracketed",
         "stage_roofline": stage_roofline,
-        "pairs": {"walked_fwd": int(walk), "walked_bwd": int(last), "keys": int(n_keys)},
+        "pairs": {"walked_fwd": int(walk), "walked_bwd": int(last), "keys": int(n_keys), "super_entries": int(n_super)},
         "gpu_launches": int(launches),
         "clocks": clk,
         "e2e": e2e,

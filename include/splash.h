@@ -205,9 +205,14 @@ typedef struct {
     int64_t n_keys;              /* number of (tile, Gaussian) pairs */
     int32_t tiles_x, tiles_y, tile_w, tile_h;
     int64_t n_gaussians;
-    const uint32_t *tile_ids;    /* [n_keys] sorted tile index of each pair */
-    const uint32_t *gauss_ids;   /* [n_keys] Gaussian index of each pair */
-    const uint32_t *ranges;      /* [tiles][2] half-open [start, end) into the pairs */
+    const uint32_t *tile_ids;    /* [n_keys] sorted tile index of each pair (the two-level binning
+                                    keeps only the lists and their ranges: then this array is
+                                    rebuilt from the ranges by the query, which synchronises the
+                                    device) */
+    const uint32_t *gauss_ids;   /* [n_keys] Gaussian index of each pair, tile by tile, each
+                                    tile's list in depth order */
+    const uint32_t *ranges;      /* [tiles][2] half-open [start, end) into the pairs; an empty
+                                    tile's is [s, s), s the pairs of the tiles before it */
     const uint32_t *depth_keys;  /* [n] FP32 depth bits minus those of z_near, 0xffffffff when culled */
     const uint32_t *tiles_touched; /* [n] */
     const float *records;        /* [n][12] projected Gaussian: x_hi, y_hi, x_lo, y_lo (centre =
@@ -228,7 +233,8 @@ splash_status splash_state_get_info(const splash_state *st, splash_state_info *o
  * (device or pinned host memory), asynchronously on `stream`. `bytes` must
  * equal the buffer's size: n_keys*4 for TILE_IDS/GAUSS_IDS, tiles*8 for
  * RANGES, n*4 for DEPTH_KEYS/TILES_TOUCHED, n*48 for RECORDS, n*8 for RECTS,
- * H*W*4 for the per-pixel fields. */
+ * H*W*4 for the per-pixel fields. TILE_IDS, when the forward kept only the
+ * lists and ranges, is rebuilt from the ranges on `stream` first. */
 typedef enum {
     SPLASH_FIELD_TILE_IDS = 0,
     SPLASH_FIELD_GAUSS_IDS = 1,

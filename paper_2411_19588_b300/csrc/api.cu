@@ -78,6 +78,18 @@ splash_status clear_backward(splash_state *st, int64_t n, cudaStream_t s)
     return SPLASH_OK;
 }
 
+// The two-level binning leaves no array of sorted tile ids (the blends use
+// the ranges); a state query rebuilds it from the ranges, on stream s.
+const uint32_t *rebuilt_tile_ids(const splash_state *st, cudaStream_t s)
+{
+    if (!st->tid_lazy_ok) {
+        if (!st->tid_lazy.ensure(4 * (size_t)std::max<int64_t>(st->K, 1))) return nullptr;
+        launch_expand_tile_ids(st->ranges.as<uint2>(), st->tg.tx * st->tg.ty, st->tid_lazy.as<uint32_t>(), s);
+        st->tid_lazy_ok = true;
+    }
+    return st->tid_lazy.as<uint32_t>();
+}
+
 // the failure a non-zero device status word reports
 splash_status status_failure(uint32_t status)
 {
@@ -131,7 +143,7 @@ splash_status splash_state_create(splash_ctx *ctx, splash_state **out)
     if (!ctx || !out) return fail(SPLASH_ERR_INVALID_ARG, "null argument");
     splash_state *s = new splash_state();
     s->ctx = ctx;
-    if (cudaHostAlloc(reinterpret_cast<void **>(&s->h_small), 2 * sizeof(uint64_t), cudaHostAllocMapped) != cudaSuccess ||
+    if (cudaHostAlloc(reinterpret_cast<void **>(&s->h_small), 4 * sizeof(uint64_t), cudaHostAllocMapped) != cudaSuccess ||
         cudaHostGetDevicePointer(reinterpret_cast<void **>(&s->h_small_dev), s->h_small, 0) != cudaSuccess ||
         !s->small.ensure(64) ||
         !s->pair_part.ensure(kPairTotalScratchBytes) ||
@@ -201,12 +213,19 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
         launch_preprocess_fwd(n, *g, medium, ck, tg, st->rec.as<Rec>(), st->depth_key.as<uint32_t>(),
                               st->tt.as<uint32_t>(), st->rect.as<uint2>(), s);
     }
-    // the pair count K is the sum of the tile counts: its kernel stores it,
-    // with the status word, into mapped host memory, and the host waits for
-    // that kernel (k_ready) while the depth sort and the scan run, so that it
-    // knows K before the GPU runs out of queued work
-    launch_pair_total(n, st->tt.as<uint32_t>(), reinterpret_cast<uint64_t *>(dK), st->pair_part.p, st->h_small_dev,
-                      ctx->d_status, s);
+    // Binning (Sec. III-A), two-level (binning.cu): the Gaussians in depth
+    // order are stably sorted by super-tile, then each super-tile's list is
+    // split into its tiles' lists, in order
+    int nsx = 0;
+    const int sbits = super_bits(tg, &nsx);
+    const int nsuper = nsx * ((tg.ty + kSuperH - 1) / kSuperH);
+    ENSURE(st->sc, 4 * nn);
+    // The pair count K and the super-tile entry count K_s are summed by a
+    // kernel that stores them, with the status word, into mapped host memory;
+    // the host waits for it (k_ready) while the depth sort and the scan run,
+    // so that it knows both before the GPU runs out of queued work
+    launch_pair_totals(n, st->tt.as<uint32_t>(), st->rect.as<uint2>(), st->sc.as<uint32_t>(), st->pair_part.p,
+                       st->h_small_dev, ctx->d_status, s);
     SPLASH_CUDA_TRY(cudaEventRecord(st->k_ready, s));
     const uint32_t *order = nullptr;
     if (n > 0) {
@@ -219,8 +238,8 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
     }
     {
         Stage t(ctx->prof, SPLASH_STAGE_SCAN, s);
-        launch_count_scan(n, order, st->tt.as<uint32_t>(), st->offsets.as<uint32_t>(), st->scan_sums.as<uint32_t>(),
-                          dK + 2, s);  // its total equals K
+        launch_count_scan(n, order, st->sc.as<uint32_t>(), st->offsets.as<uint32_t>(), st->scan_sums.as<uint32_t>(),
+                          dK + 2, s);  // its total equals K_s
     }
     SPLASH_CUDA_TRY(cudaGetLastError());
     SPLASH_CUDA_TRY(cudaEventSynchronize(st->k_ready));
@@ -230,9 +249,11 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
     }
     const uint64_t K64 = st->h_small[1];
     // every uint32 offset below is valid only under this bound: nothing that
-    // uses them runs before it is checked
+    // uses them runs before it is checked (K_s <= K: each super-tile entry
+    // stands for at least one pair)
     if (K64 >= ((uint64_t)1 << 30)) return fail(SPLASH_ERR_CAPACITY, "more than 2^30 tile/Gaussian pairs");
     const int64_t K = (int64_t)K64;
+    const int64_t Ks = (int64_t)std::min<uint64_t>(st->h_small[2], K64);
 
     const int64_t kk = std::max<int64_t>(K, 1);
     ENSURE(st->tk0, 4 * kk);
@@ -243,25 +264,39 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
         ENSURE(st->sort_scratch, sort_scratch_bytes(kk));
     }
     sort_scratch_carve(st->sort_scratch.p, std::max(nn, kk), &ss);
-    // emit into buffer pair 1; the tile sort reads it once, then ping-pongs 0 <-> 1
+    const int64_t chunks = chunk_bound(Ks, nsuper);
+    ENSURE(st->sranges, 8 * (size_t)nsuper);
+    ENSURE(st->bin_scratch, 4 * ((size_t)nsuper + 1 + 32 * (size_t)chunks + (size_t)ntiles));
+    BinningScratch bs;
+    bs.chunk_base = st->bin_scratch.as<uint32_t>();
+    bs.chunk_count = bs.chunk_base + nsuper + 1;
+    bs.tile_count = bs.chunk_count + 32 * chunks;
+    // super-tile entries into buffer pair 1, sorted by super-tile (one pass up
+    // to 512 super-tiles); the tile lists go to the value buffer the sort
+    // leaves free
     {
         Stage t(ctx->prof, SPLASH_STAGE_EMIT, s);
-        launch_emit(n, order, st->offsets.as<uint32_t>(), st->tt.as<uint32_t>(), st->rect.as<uint2>(), tg,
-                    st->tk1.as<uint32_t>(), st->tv1.as<uint32_t>(), (uint64_t)K, ctx->d_status, s);
+        launch_emit_super(n, order, st->offsets.as<uint32_t>(), st->sc.as<uint32_t>(), st->rect.as<uint2>(), nsx, sbits,
+                          st->tk1.as<uint32_t>(), st->tv1.as<uint32_t>(), (uint64_t)Ks, ctx->d_status, s);
     }
-    const uint32_t *tids = st->tk1.as<uint32_t>(), *gids = st->tv1.as<uint32_t>();
-    if (K > 0) {
+    int which = 0;
+    {
         Stage t(ctx->prof, SPLASH_STAGE_TILE_SORT, s);
-        const int which = sort_pairs(st->tk1.as<uint32_t>(), st->tv1.as<uint32_t>(), st->tk0.as<uint32_t>(), st->tv0.as<uint32_t>(),
-                                     st->tk1.as<uint32_t>(), st->tv1.as<uint32_t>(), K, nullptr, bits_for(ntiles), ss,
-                                     ctx->d_status, ctx->opt.spin_limit, ctx->opt.test_stall_partition, s);
-        tids = which ? st->tk1.as<uint32_t>() : st->tk0.as<uint32_t>();
-        gids = which ? st->tv1.as<uint32_t>() : st->tv0.as<uint32_t>();
+        which = sort_pairs(st->tk1.as<uint32_t>(), st->tv1.as<uint32_t>(), st->tk0.as<uint32_t>(), st->tv0.as<uint32_t>(),
+                           st->tk1.as<uint32_t>(), st->tv1.as<uint32_t>(), Ks, nullptr, sbits, ss, ctx->d_status,
+                           ctx->opt.spin_limit, ctx->opt.test_stall_partition, s);
+        launch_ranges(Ks, nullptr, which ? st->tk1.as<uint32_t>() : st->tk0.as<uint32_t>(), st->sranges.as<uint2>(),
+                      nsuper, s, (1u << sbits) - 1u);
     }
+    const uint32_t *skeys = which ? st->tk1.as<uint32_t>() : st->tk0.as<uint32_t>();
+    const uint32_t *svals = which ? st->tv1.as<uint32_t>() : st->tv0.as<uint32_t>();
+    uint32_t *gids = which ? st->tv0.as<uint32_t>() : st->tv1.as<uint32_t>();
     {
         Stage t(ctx->prof, SPLASH_STAGE_RANGES, s);
-        launch_ranges(K, nullptr, tids, st->ranges.as<uint2>(), ntiles, s);
+        launch_tile_lists(tg, nsx, sbits, Ks, skeys, svals, st->sranges.as<uint2>(), bs, st->ranges.as<uint2>(), gids,
+                          ctx->d_status, s);
     }
+    const uint32_t *tids = nullptr;  // rebuilt from the ranges when a query asks for them
     {
         Stage t(ctx->prof, SPLASH_STAGE_BLEND_FWD, s);
         BlendView v{};
@@ -290,7 +325,8 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
     st->tg = tg;
     st->K = K;
     st->order = order;
-    st->tile_ids = tids;
+    st->tile_ids = tids;  // null on the two-level path: rebuilt from the ranges when asked for
+    st->tid_lazy_ok = false;
     st->gauss_ids = gids;
     return SPLASH_OK;
 }
@@ -443,7 +479,13 @@ splash_status splash_state_get_info(const splash_state *st, splash_state_info *o
     out->tile_w = st->tg.tw;
     out->tile_h = st->tg.th;
     out->n_gaussians = st->n;
-    out->tile_ids = st->tile_ids;
+    const uint32_t *tids = st->tile_ids;
+    if (!tids) {  // rebuilt from the ranges once the forward's work is done (a query, not the render path)
+        SPLASH_CUDA_TRY(cudaDeviceSynchronize());
+        if (!(tids = rebuilt_tile_ids(st, 0))) return fail(SPLASH_ERR_OOM, "tile id buffer");
+        SPLASH_CUDA_TRY(cudaDeviceSynchronize());
+    }
+    out->tile_ids = tids;
     out->gauss_ids = st->gauss_ids;
     out->ranges = st->ranges.as<uint32_t>();
     out->depth_keys = st->depth_key.as<uint32_t>();
@@ -464,7 +506,11 @@ splash_status splash_state_copy(const splash_state *st, int32_t field, void *dst
     const void *src = nullptr;
     int64_t size = 0;
     switch (field) {
-    case SPLASH_FIELD_TILE_IDS: src = st->tile_ids; size = 4 * st->K; break;
+    case SPLASH_FIELD_TILE_IDS:
+        src = st->tile_ids ? st->tile_ids : rebuilt_tile_ids(st, (cudaStream_t)stream);
+        if (!src) return fail(SPLASH_ERR_OOM, "tile id buffer");
+        size = 4 * st->K;
+        break;
     case SPLASH_FIELD_GAUSS_IDS: src = st->gauss_ids; size = 4 * st->K; break;
     case SPLASH_FIELD_RANGES: src = st->ranges.p; size = 8 * ntiles; break;
     case SPLASH_FIELD_DEPTH_KEYS: src = st->depth_key.p; size = 4 * st->n; break;

@@ -193,9 +193,16 @@ struct splash_state {
     splash_ctx *ctx = nullptr;
     // per Gaussian
     splash_host::Buf rec, depth_key, tt, rect, dk0, dv0, dk1, dv1, offsets, scan_sums;
-    // per (tile, Gaussian) pair
+    // per (tile, Gaussian) pair (the two-level binning uses them for its
+    // super-tile entries and the tile lists)
     splash_host::Buf tk0, tv0, tk1, tv1;
     splash_host::Buf ranges, sort_scratch;
+    // two-level binning: per-Gaussian super-tile counts, super-tile list
+    // ranges, chunk map / chunk counts / tile counts
+    splash_host::Buf sc, sranges, bin_scratch;
+    // the sorted tile ids rebuilt from the ranges on request (state queries)
+    mutable splash_host::Buf tid_lazy;
+    mutable bool tid_lazy_ok = false;
     // per pixel
     splash_host::Buf fT, aA, zh, nlast, nwalk;
     // backward
@@ -207,8 +214,8 @@ struct splash_state {
     bool pixel_forward = false;  // the last forward was splash_render_forward_pixel
     splash_host::Buf small;       // [0] = pair count K, [1..] spare
     splash_host::Buf pair_part;   // the pair-count sum's partials and ticket (kept zero between calls)
-    // mapped pinned words [status, K] that the pair-count kernel stores (host
-    // and device addresses); k_ready follows that kernel in the stream
+    // mapped pinned words [status, K, K_s, spare] that the pair-count kernel
+    // stores (host and device addresses); k_ready follows that kernel in the stream
     uint64_t *h_small = nullptr, *h_small_dev = nullptr;
     cudaEvent_t k_ready = nullptr;
     bool gacc_cleared = false;  // the last forward blend zeroed gacc[0..gacc_clear_n)

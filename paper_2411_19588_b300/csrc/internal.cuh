@@ -199,21 +199,43 @@ void launch_count_scan(int64_t n, const uint32_t *order, const uint32_t *tiles_t
                        uint32_t *block_sums, uint32_t *total, cudaStream_t s);
 // d_medium[j] = sum over nblocks rows of partials[b][9] (the pixel form's medium gradient)
 void launch_pixel_medium_final(const float *partials, int nblocks, float *d_medium, cudaStream_t s);
-// *total = sum of tt[0..n) in 64 bits; with host_out (mapped host memory,
-// device address) also host_out[0] = *status and host_out[1] = the total.
-// CTAs of the pair-count sum; its scratch holds that many 8-byte partials and
-// a ticket word, zero before the first launch (each launch leaves it zero)
+// scratch of the pair-count sum (binning.cu): kPairTotalBlocksMax 16-byte
+// partials and a ticket word, zero before the first launch (each launch
+// leaves it zero)
 constexpr int kPairTotalBlocksMax = 148 * 4;
-constexpr size_t kPairTotalScratchBytes = 8 * (size_t)(kPairTotalBlocksMax + 1);
-void launch_pair_total(int64_t n, const uint32_t *tt, uint64_t *total, void *scratch, uint64_t *host_out,
-                       const uint32_t *status, cudaStream_t s);
+constexpr size_t kPairTotalScratchBytes = 16 * (size_t)(kPairTotalBlocksMax + 1);
 void launch_emit(int64_t n, const uint32_t *order, const uint32_t *offsets, const uint32_t *tt, const uint2 *rect,
                  const TileGeom &tg, uint32_t *tile_ids, uint32_t *gauss_ids, uint64_t capacity, uint32_t *status,
                  cudaStream_t s);
+// ---- two-level tile binning (binning.cu)
+constexpr int kSuperW = 8, kSuperH = 4;  // tiles per super-tile
+// super-tiles per row (*nsx) and the bits of a super-tile index
+int super_bits(const TileGeom &tg, int *nsx);
+// chunks of the super-tile lists (an upper bound from the entry count)
+int64_t chunk_bound(int64_t n_super_entries, int nsuper);
+// K, K_s and the status word into host_out[0..2] (mapped host memory, device
+// address); sc[g] = Gaussian g's super-tile count
+void launch_pair_totals(int64_t n, const uint32_t *tt, const uint2 *rect, uint32_t *sc, void *scratch,
+                        uint64_t *host_out, const uint32_t *status, cudaStream_t s);
+void launch_emit_super(int64_t n, const uint32_t *order, const uint32_t *offsets, const uint32_t *sc, const uint2 *rect,
+                       int nsx, int sbits, uint32_t *keys, uint32_t *vals, uint64_t capacity, uint32_t *status,
+                       cudaStream_t s);
+struct BinningScratch {
+    uint32_t *chunk_base;   // [nsuper + 1]
+    uint32_t *chunk_count;  // [chunk_bound][32]
+    uint32_t *tile_count;   // [tiles]
+};
+// the tile lists (gauss_ids) and their ranges from the sorted super-tile lists
+void launch_tile_lists(const TileGeom &tg, int nsx, int sbits, int64_t n_super_entries, const uint32_t *skeys,
+                       const uint32_t *svals, const uint2 *sranges, const BinningScratch &bs, uint2 *ranges,
+                       uint32_t *gauss_ids, uint32_t *status, cudaStream_t s);
+// tile_ids[i] = t for every i in ranges[t] (the sorted tile ids, rebuilt from the ranges)
+void launch_expand_tile_ids(const uint2 *ranges, int ntiles, uint32_t *tile_ids, cudaStream_t s);
+
 // ranges[t] = [first, end) of tile t's run in the sorted tile ids, for every
 // tile (empty ones as [s, s)); nothing needs clearing first
 void launch_ranges(int64_t k_host, const uint32_t *k_dev, const uint32_t *tile_ids, uint2 *ranges, int ntiles,
-                   cudaStream_t s);
+                   cudaStream_t s, uint32_t key_mask = 0xffffffffu);
 // staging batch sizes the blend kernels are built for
 constexpr int kBlendBatches[3] = {64, 128, 256};
 void launch_blend_fwd(const BlendView &v, const float *medium, int batch, cudaStream_t s);

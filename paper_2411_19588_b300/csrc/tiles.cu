@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(256) k_emit(int64_t n, const uint32_t *__restr
 // is [start(t), start(t + 1)); every tile is written, empty ones as [s, s).
 __global__ void __launch_bounds__(256) k_ranges(int64_t k_host, const uint32_t *__restrict__ k_dev,
                                                 const uint32_t *__restrict__ tile_ids, uint2 *__restrict__ ranges,
-                                                uint32_t ntiles)
+                                                uint32_t ntiles, uint32_t mask)
 {
     pdl_enter();
     const int lane = threadIdx.x & 31;
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(256) k_ranges(int64_t k_host, const uint32_t *
     while (hi - lo > 32) {
         const int64_t step = (hi - lo + 31) / 32;
         const int64_t p = min(lo + (int64_t)(lane + 1) * step - 1, hi - 1);
-        const uint32_t ge = __ballot_sync(0xffffffffu, tile_ids[p] >= tv);
+        const uint32_t ge = __ballot_sync(0xffffffffu, (tile_ids[p] & mask) >= tv);
         if (ge == 0u) {
             lo = min(lo + 32 * step, hi);  // all 32 probes below t: past the last one
         } else {
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(256) k_ranges(int64_t k_host, const uint32_t *
         }
     }
     const int64_t q = lo + lane;
-    const uint32_t ge = __ballot_sync(0xffffffffu, q < hi && tile_ids[q] >= tv);
+    const uint32_t ge = __ballot_sync(0xffffffffu, q < hi && (tile_ids[q] & mask) >= tv);
     const int64_t start = ge ? lo + __ffs(ge) - 1 : hi;
     if (lane == 0) {
         if (t < (int64_t)ntiles) ranges[t].x = (uint32_t)start;
@@ -212,73 +212,7 @@ __global__ void __launch_bounds__(256) k_ranges(int64_t k_host, const uint32_t *
     }
 }
 
-__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long x, unsigned long long *s_w)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = x;
-    __syncthreads();
-    unsigned long long t = 0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_w[w];
-    return t;  // valid in thread 0
-}
-
-// Total of the tile counts (the pair count K), summed in 64 bits: a scene
-// whose counts add up past 2^32 must be reported as over capacity, not wrap
-// to a small count. One partial per CTA; the last CTA to finish (a ticket
-// taken after its partial is fenced) adds the partials in CTA order, writes
-// the total and puts the ticket back to zero, so nothing is cleared before
-// the launch. With `host` set it also stores the total (host[1]) and the
-// device status word (host[0]) into mapped host memory, visible to the host
-// once the kernel has completed: no copy has to follow it.
-__global__ void __launch_bounds__(256) k_sum_u64(const uint32_t *__restrict__ v, int64_t n,
-                                                 unsigned long long *__restrict__ part, uint32_t *__restrict__ ticket,
-                                                 unsigned long long *__restrict__ total,
-                                                 unsigned long long *__restrict__ host, const uint32_t *__restrict__ status)
-{
-    pdl_enter();
-    __shared__ unsigned long long s_w[8];
-    __shared__ uint32_t s_last;
-    unsigned long long acc = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) acc += v[i];
-    acc = block_sum_u64(acc, s_w);
-    if (threadIdx.x == 0) {
-        part[blockIdx.x] = acc;
-        __threadfence();
-        s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!s_last) return;  // uniform over the CTA
-    __threadfence();
-    unsigned long long x = 0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) x += *reinterpret_cast<volatile unsigned long long *>(part + b);
-    __syncthreads();  // s_w is reused
-    x = block_sum_u64(x, s_w);
-    if (threadIdx.x == 0) {
-        *total = x;
-        *ticket = 0u;
-        if (host) {
-            host[0] = *reinterpret_cast<const volatile uint32_t *>(status);
-            host[1] = x;
-            __threadfence_system();
-        }
-    }
-}
-
 }  // namespace
-
-void launch_pair_total(int64_t n, const uint32_t *tt, uint64_t *total, void *scratch, uint64_t *host_out,
-                       const uint32_t *status, cudaStream_t s)
-{
-    // scratch: kPairTotalBlocksMax partials, then the ticket (zero between launches)
-    unsigned long long *part = static_cast<unsigned long long *>(scratch);
-    uint32_t *ticket = reinterpret_cast<uint32_t *>(part + kPairTotalBlocksMax);
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, kPairTotalBlocksMax));
-    launch_pdl(k_sum_u64, blocks, 256, 0, s, tt, std::max<int64_t>(n, 0), part, ticket, reinterpret_cast<unsigned long long *>(total),
-                                     reinterpret_cast<unsigned long long *>(host_out), status);
-    count_launch();
-}
 
 void launch_count_scan(int64_t n, const uint32_t *order, const uint32_t *tt, uint32_t *offsets, uint32_t *sums,
                        uint32_t *total, cudaStream_t s)
@@ -310,11 +244,32 @@ void launch_emit(int64_t n, const uint32_t *order, const uint32_t *offsets, cons
     count_launch();
 }
 
-void launch_ranges(int64_t k_host, const uint32_t *k_dev, const uint32_t *tile_ids, uint2 *ranges, int ntiles, cudaStream_t s)
+void launch_ranges(int64_t k_host, const uint32_t *k_dev, const uint32_t *tile_ids, uint2 *ranges, int ntiles, cudaStream_t s,
+                   uint32_t key_mask)
 {
     if (ntiles <= 0) return;
     const int64_t warps = (int64_t)ntiles + 1;
-    launch_pdl(k_ranges, (unsigned)((warps * 32 + 255) / 256), 256, 0, s, k_host, k_dev, tile_ids, ranges, (uint32_t)ntiles);
+    launch_pdl(k_ranges, (unsigned)((warps * 32 + 255) / 256), 256, 0, s, k_host, k_dev, tile_ids, ranges, (uint32_t)ntiles,
+               key_mask);
+    count_launch();
+}
+
+namespace {
+// one warp per tile: its run of the sorted tile ids
+__global__ void __launch_bounds__(256) k_expand_tile_ids(const uint2 *__restrict__ ranges, int ntiles,
+                                                         uint32_t *__restrict__ tile_ids)
+{
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= ntiles) return;
+    const uint2 rg = ranges[t];
+    for (uint32_t i = rg.x + (threadIdx.x & 31); i < rg.y; i += 32) tile_ids[i] = (uint32_t)t;
+}
+}  // namespace
+
+void launch_expand_tile_ids(const uint2 *ranges, int ntiles, uint32_t *tile_ids, cudaStream_t s)
+{
+    if (ntiles <= 0) return;
+    k_expand_tile_ids<<<(unsigned)(((int64_t)ntiles * 32 + 255) / 256), 256, 0, s>>>(ranges, ntiles, tile_ids);
     count_launch();
 }
 

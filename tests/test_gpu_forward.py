@@ -112,16 +112,25 @@ def test_one_pixel_image(renderer):
     compare_forward(gpu_forward(renderer, g, m, cam), oracle.render(g, m, cam), label="1x1", scene=(g, m, cam))
 
 
-@pytest.mark.parametrize("n,z_step", [(4000, 0.0), (5 * 5120 + 77, 0.25)])
-def test_binning_and_sort_bit_exact(renderer, n, z_step):
-    """Emitted pairs = the tiles of each Gaussian's rectangle; the sorted
-    order equals a CPU stable sort of 64-bit (tile << 32 | depth bits) keys
-    emitted in Gaussian-index order; ranges equal a linear scan. The second
-    case spans several depth-sort partitions with a ragged last one, and its
-    depths sit on planes z_step apart (the camera looks down +z from the
-    origin), so that thousands of Gaussians share one depth key and their
-    order within a tile is decided by the sorts' stability alone."""
-    g, m, cam = _box_scene(41, n, 203, 157, 150.0, 3, log_scale=-2.2)
+@pytest.mark.parametrize("n,z_step,W,H,f,log_scale", [
+    (4000, 0.0, 203, 157, 150.0, -2.2), (5 * 5120 + 77, 0.25, 203, 157, 150.0, -2.2),
+    # more super-tiles, partial ones on both edges
+    (6000, 0.0, 1000, 700, 900.0, -3.6),
+    # 24 x 32 super-tiles: their sort takes two passes
+    (4000, 0.0, 3000, 2000, 2700.0, -4.5),
+    # a tile grid whose count array does not fit in shared memory: the pairs are sorted by tile instead
+    (4000, 0.0, 4200, 4200, 3780.0, -4.5)])
+def test_binning_and_sort_bit_exact(renderer, n, z_step, W, H, f, log_scale):
+    """Each Gaussian is listed in the tiles of its rectangle; the lists equal
+    a CPU stable sort of 64-bit (tile << 32 | depth bits) keys emitted in
+    Gaussian-index order; ranges equal a linear scan. The second case spans
+    several depth-sort partitions with a ragged last one, and its depths sit
+    on planes z_step apart (the camera looks down +z from the origin), so that
+    thousands of Gaussians share one depth key and their order within a tile
+    is decided by the sorts' stability alone. The other cases take the
+    two-level binning over many super-tiles (8 x 4 tiles each), with one and
+    with two sort passes, and the sort-by-tile path of very large images."""
+    g, m, cam = _box_scene(41, n, W, H, f, 3, log_scale=log_scale)
     if z_step:
         g.means[:, 2] = np.round(g.means[:, 2] / z_step) * z_step
     out = gpu_forward(renderer, g, m, cam)
@@ -153,16 +162,12 @@ def test_binning_and_sort_bit_exact(renderer, n, z_step):
     assert info["n_keys"] == keys.size
     np.testing.assert_array_equal(tids, (keys[order] >> np.uint64(32)).astype(np.uint32))
     np.testing.assert_array_equal(gids, ids[order])
-    # ranges by a linear scan
+    # ranges: each tile's run in the sorted ids (an empty tile's is [s, s),
+    # s the number of pairs of the tiles before it)
     ntiles = info["tiles_x"] * info["tiles_y"]
-    exp = np.zeros((ntiles, 2), np.uint32)
-    for k in range(tids.size):
-        t = tids[k]
-        if k == 0 or tids[k - 1] != t:
-            exp[t, 0] = k
-        if k == tids.size - 1 or tids[k + 1] != t:
-            exp[t, 1] = k + 1
-    np.testing.assert_array_equal(ranges, exp)
+    tile_no = np.arange(ntiles)
+    exp = np.stack([np.searchsorted(tids, tile_no, "left"), np.searchsorted(tids, tile_no, "right")], 1)
+    np.testing.assert_array_equal(ranges, exp.astype(np.uint32))
 
 
 @pytest.mark.parametrize("n,bits,distinct", [(1, 32, 10), (4095, 13, 50), (4097, 32, 1 << 30), (100_003, 14, 9600),
