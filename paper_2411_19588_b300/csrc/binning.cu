@@ -173,6 +173,7 @@ __global__ void __launch_bounds__(256) k_emit_super(int64_t n, const uint32_t *_
 // covers, in entry order.
 constexpr int kChunk = 256;    // entries per chunk (one warp each: 8 groups of 32)
 constexpr int kGroups = kChunk / 32;
+static_assert(kGroups <= 15, "four count planes");
 constexpr int kChunkWarps = 4; // chunks per CTA
 
 __device__ __forceinline__ uint32_t tile_mask(uint32_t lr)
@@ -181,6 +182,22 @@ __device__ __forceinline__ uint32_t tile_mask(uint32_t lr)
     const uint32_t row = (0xffu >> (7u - lx1)) & (0xffu << lx0);                          // columns lx0..lx1
     const uint32_t rows = (0xffffffffu >> (8u * (3u - ly1))) & (0xffffffffu << (8u * ly0));  // bytes ly0..ly1
     return (row * 0x01010101u) & rows;
+}
+
+// Transpose of a 32 x 32 bit matrix held one row per lane (bit c of lane l's
+// word = element (l, c)): returns column `lane` (bit l = element (l, lane)).
+// Five exchange steps swap ever smaller blocks between lane pairs (the
+// recursive block transpose written for a warp).
+__device__ __forceinline__ uint32_t warp_transpose(uint32_t w, int lane)
+{
+    uint32_t m = 0x0000ffffu;
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) {
+        const uint32_t p = __shfl_xor_sync(0xffffffffu, w, j);
+        w = (lane & j) ? w ^ (((p >> j) ^ w) & m) : w ^ ((((w >> j) ^ p) & m) << j);
+        m ^= m << (j >> 1);
+    }
+    return w;
 }
 
 // the super-tile whose chunks contain chunk c: the last s with cb[s] <= c
@@ -230,9 +247,8 @@ __global__ void __launch_bounds__(1024) k_chunk_map(const uint2 *__restrict__ sr
 
 // One warp per chunk, lane t = tile t of the chunk's super-tile. The
 // chunk's groups of 32 entries are loaded first (one entry per lane and
-// group, all loads in flight together) and turned into tile masks; then each
-// group's masks pass round the warp by shuffles and every lane counts the
-// entries covering its tile. cnt[c][t] = that count.
+// group, all loads in flight together) and turned into tile masks.
+// cnt[c][t] = the entries covering tile t.
 __global__ void __launch_bounds__(kChunkWarps * 32) k_super_count(const uint32_t *__restrict__ skeys,
                                                                   const uint2 *__restrict__ sranges,
                                                                   const uint32_t *__restrict__ cb, int nsuper, int sbits,
@@ -253,12 +269,22 @@ __global__ void __launch_bounds__(kChunkWarps * 32) k_super_count(const uint32_t
     }
 #pragma unroll
     for (int g = 0; g < kGroups; g++) m[g] = beg + (uint32_t)(g * 32 + lane) < end ? tile_mask(m[g] >> sbits) : 0u;
-    uint32_t acc = 0;
-#pragma unroll 8
-    for (int k = 0; k < 32; k++) {
+    // per lane, the count over its groups of each tile bit, bit-sliced into
+    // four planes (counts up to 8); the column sums of the planes over the
+    // warp's lanes are the tile counts
+    uint32_t p0 = 0, p1 = 0, p2 = 0, p3 = 0;
 #pragma unroll
-        for (int g = 0; g < kGroups; g++) acc += (__shfl_sync(0xffffffffu, m[g], k) >> lane) & 1u;
+    for (int g = 0; g < kGroups; g++) {
+        const uint32_t c0 = m[g], c1 = p0 & c0;
+        p0 ^= c0;
+        const uint32_t c2 = p1 & c1;
+        p1 ^= c1;
+        const uint32_t c3 = p2 & c2;
+        p2 ^= c2;
+        p3 ^= c3;
     }
+    const uint32_t acc = __popc(warp_transpose(p0, lane)) + 2u * __popc(warp_transpose(p1, lane)) +
+                         4u * __popc(warp_transpose(p2, lane)) + 8u * __popc(warp_transpose(p3, lane));
     cnt[(size_t)c * 32 + lane] = acc;
 }
 
@@ -319,11 +345,12 @@ __global__ void __launch_bounds__(kCountScanThreads) k_tile_scan(const uint32_t 
 }
 
 // One warp per chunk: its entries (keys and values) are loaded first, one
-// per lane and group, then taken tile by tile: the entries covering tile t
-// fill consecutive slots of t's list in entry order, from the tile's start
-// plus the chunk's offset (k_super_prefix); they are gathered in a per-warp
-// shared buffer first, so that each store instruction writes up to 32
-// contiguous slots. A slot past a tile's range is reported and not written.
+// per lane and group, and each group's tile masks transposed (lane t then
+// holds the lanes covering tile t). Tile by tile, the entries covering the
+// tile fill consecutive slots of its list in entry order, from the tile's
+// start plus the chunk's offset (k_super_prefix); they are gathered in a
+// per-warp shared buffer first, so that each store instruction writes up to
+// 32 contiguous slots. A slot past a tile's range is reported and not written.
 __global__ void __launch_bounds__(kChunkWarps * 32) k_super_scatter(
     const uint32_t *__restrict__ skeys, const uint32_t *__restrict__ svals, const uint2 *__restrict__ sranges,
     const uint32_t *__restrict__ cb, int nsuper, int nsx, int sbits, int tiles_x, int tiles_y,
@@ -350,8 +377,11 @@ __global__ void __launch_bounds__(kChunkWarps * 32) k_super_scatter(
         m[g] = in ? skeys[idx] : 0u;
         v[g] = in ? svals[idx] : 0u;
     }
+    // per group, the transpose of the lanes' tile masks: lane t holds the
+    // lanes whose entry covers tile t
 #pragma unroll
-    for (int g = 0; g < kGroups; g++) m[g] = beg + (uint32_t)(g * 32 + lane) < end ? tile_mask(m[g] >> sbits) : 0u;
+    for (int g = 0; g < kGroups; g++)
+        m[g] = warp_transpose(beg + (uint32_t)(g * 32 + lane) < end ? tile_mask(m[g] >> sbits) : 0u, lane);
     bool bad = false;
     const uint32_t lt = (1u << lane) - 1u;
     uint32_t *buf = s_slot[threadIdx.x >> 5];
@@ -364,9 +394,8 @@ __global__ void __launch_bounds__(kChunkWarps * 32) k_super_scatter(
         uint32_t pre = 0;
 #pragma unroll
         for (int g = 0; g < kGroups; g++) {
-            const bool cov = (m[g] >> t) & 1u;
-            const uint32_t b = __ballot_sync(0xffffffffu, cov);
-            if (cov) buf[pre + __popc(b & lt)] = v[g];
+            const uint32_t b = __shfl_sync(0xffffffffu, m[g], t);  // the lanes covering tile t
+            if ((b >> lane) & 1u) buf[pre + __popc(b & lt)] = v[g];
             pre += __popc(b);
         }
         __syncwarp();
