@@ -175,9 +175,10 @@ __device__ __forceinline__ void blend_tile_fwd(const BlendView &v, int tile, con
 #pragma unroll
             for (int j = 0; j < NP; j++) {
                 const float2 e = __fadd2_rn(qs[j], hi2(fc));
-                float a0 = fminf(kAlphaMax, ex2_approx(e.x)), a1 = fminf(kAlphaMax, ex2_approx(e.y));
-                a0 = (qs[j].x >= kQsMin && a0 >= kAlphaMin) ? a0 : 0.f;
-                a1 = (qs[j].y >= kQsMin && a1 >= kAlphaMin) ? a1 : 0.f;
+                // the same tests as the backward's (raw alpha >= 1/255, then the clamp)
+                const float r0 = ex2_approx(e.x), r1 = ex2_approx(e.y);
+                const float a0 = (qs[j].x >= kQsMin && r0 >= kAlphaMin) ? fminf(kAlphaMax, r0) : 0.f;
+                const float a1 = (qs[j].y >= kQsMin && r1 >= kAlphaMin) ? fminf(kAlphaMax, r1) : 0.f;
                 w[j] = __fmul2_rn(make_float2(a0, a1), T[j]);
                 tn[j] = __ffma2_rn(w[j], neg1, T[j]);  // T - alpha T
                 stop |= (tn[j].x < kTStop) | (tn[j].y < kTStop);
@@ -326,7 +327,7 @@ __device__ __forceinline__ void pair_grad(PairB &p, float2 dx, float2 ar, bool o
                                           float2 &a0, float2 &a2, float2 &a5, float2 &a6, float2 &a7, float2 &a8,
                                           float2 &a9)
 {
-    const float2 neg1 = make_float2(-1.f, -1.f), one = make_float2(1.f, 1.f), ln2 = make_float2(kLn2, kLn2);
+    const float2 neg1 = make_float2(-1.f, -1.f), one = make_float2(1.f, 1.f);
     const float2 al = make_float2(on0 ? fminf(kAlphaMax, ar.x) : 0.f, on1 ? fminf(kAlphaMax, ar.y) : 0.f);
     const float2 om = __ffma2_rn(al, neg1, one);  // 1 - alpha
     const float2 inv = make_float2(rcp_approx(om.x), rcp_approx(om.y));
@@ -337,7 +338,9 @@ __device__ __forceinline__ void pair_grad(PairB &p, float2 dx, float2 ar, bool o
                         : __ffma2_rn(p.G0, lo2(kc), __ffma2_rn(p.G1, hi2(kc), __fmul2_rn(p.G2, lo2(kb))));
     // dL/dalpha = T_j u - S / (1 - alpha)
     const float2 galpha = __ffma2_rn(__fmul2_rn(p.S, inv), neg1, __fmul2_rn(Tj, u));
-    float2 gqs = __fmul2_rn(__fmul2_rn(galpha, al), ln2);
+    // the exponent's gradient up to its factor ln 2 (applied once per
+    // Gaussian when the tile's sums are flushed)
+    float2 gqs = __fmul2_rn(galpha, al);
     gqs.x = ar.x < kAlphaMax ? gqs.x : 0.f;  // zero through the alpha clamp
     gqs.y = ar.y < kAlphaMax ? gqs.y : 0.f;
     const float2 gx = __fmul2_rn(gqs, dx);
@@ -501,8 +504,9 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
                     const float2 qs = __ffma2_rn(dx[jp], __ffma2_rn(hi2(fx), dx[jp], Bdy), Cdy2);
                     const float2 e = __fadd2_rn(qs, hi2(fc));
                     ar[jp] = make_float2(ex2_approx(e.x), ex2_approx(e.y));
-                    on0[jp] = (j < P[jp].last0) & (qs.x >= kQsMin) & (fminf(kAlphaMax, ar[jp].x) >= kAlphaMin);
-                    on1[jp] = (j < P[jp].last1) & (qs.y >= kQsMin) & (fminf(kAlphaMax, ar[jp].y) >= kAlphaMin);
+                    // (raw alpha >= 1/255 is the clamped alpha's test: the clamp is above it)
+                    on0[jp] = (j < P[jp].last0) & (qs.x >= kQsMin) & (ar[jp].x >= kAlphaMin);
+                    on1[jp] = (j < P[jp].last1) & (qs.y >= kQsMin) & (ar[jp].y >= kAlphaMin);
                     any |= on0[jp] | on1[jp];
                 }
                 if (!__any_sync(0xffffffffu, any)) continue;
@@ -531,8 +535,9 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
         }
         __syncthreads();
         for (int sl = tid; sl < nb; sl += NT) {
-            const float g[10] = {s_g[0][sl], s_g[1][sl], s_g[2][sl], s_g[3][sl], s_g[4][sl],
-                                 s_g[5][sl], s_g[6][sl], s_g[7][sl], s_g[8][sl], s_g[9][sl]};
+            // fields 0-5 (the exponent moments) carry the factor ln 2 from here
+            const float g[10] = {kLn2 * s_g[0][sl], kLn2 * s_g[1][sl], kLn2 * s_g[2][sl], kLn2 * s_g[3][sl],
+                                 kLn2 * s_g[4][sl], kLn2 * s_g[5][sl], s_g[6][sl], s_g[7][sl], s_g[8][sl], s_g[9][sl]};
             bool nz = false;
 #pragma unroll
             for (int f = 0; f < 10; f++) nz |= g[f] != 0.f;
