@@ -6,16 +6,21 @@
 // super-tile) entries, about a quarter as many as the (tile, Gaussian) pairs
 // on the training views, each entry carrying the Gaussian's tile rectangle
 // clipped to that super-tile. Tile t's list is then the subsequence of its
-// super-tile's list whose rectangle covers t: one CTA per tile keeps those
-// entries, in order (a stable compaction). Every tile's count, and so its
-// list's start, is known beforehand from a 2D difference array of the
-// rectangles, so the lists land in the same compact tile-major layout, with
-// the same ranges, as a stable sort of the (tile, Gaussian) pairs by tile.
-//   k_pair_totals      -- K (pairs), K_s (super entries), per-Gaussian super counts
-//   k_tile_diff        -- per-CTA difference arrays of the rectangles, added up
-//   k_tile_count_scan  -- 2D prefix (the tile counts), then their exclusive scan: ranges
-//   k_emit_super       -- (super-tile | clipped rectangle, Gaussian) entries in depth order
-//   k_tile_gather      -- per tile: the covering entries of its super-tile's list
+// super-tile's list whose rectangle covers t. Each super-tile's list is cut
+// into chunks of kChunk entries (one warp each): the per-(chunk, tile)
+// counts give every chunk's offset within each tile's list and, summed and
+// scanned in tile order, every list's start; a scatter pass then writes each
+// entry into the lists of the tiles it covers, in order. The lists land in
+// the same compact tile-major layout, with the same ranges, as a stable sort
+// of the (tile, Gaussian) pairs by tile.
+//   k_pair_totals    -- K (pairs), K_s (super entries), per-Gaussian super counts
+//   k_emit_super     -- (super-tile | clipped rectangle, Gaussian) entries in depth order
+//   (the super-tile sort and its list ranges: sort.cu, tiles.cu)
+//   k_chunk_map      -- first chunk of every super-tile
+//   k_super_count    -- per chunk and tile: entries covering the tile
+//   k_super_prefix   -- chunk offsets within each tile's list; tile counts
+//   k_tile_scan      -- tile ranges (exclusive scan of the counts)
+//   k_super_scatter  -- the tile lists
 #include <cuda_runtime.h>
 
 #include <algorithm>
