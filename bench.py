@@ -467,12 +467,13 @@ def run_ours(args, world, rank, local):
         "depth_sort": ("hbm", 3 * 16.0 * args.n + 4.0 * args.n, "GB/s"),
         # two-level binning: scan of the super-tile counts in depth order; the K_s super-tile
         # entries emitted (order, offset, count, rectangle read; key + value written); their
-        # one-pass sort, then the tile lists gathered (entries read once, K Gaussian ids
-        # written); the tile counts from the rectangles
+        # one-pass sort (key + value read and written, one key read for the histogram); the
+        # tile lists (keys read by the count pass, keys + values by the scatter, K Gaussian
+        # ids written)
         "scan": ("hbm", 8.0 * args.n, "GB/s"),
         "emit": ("hbm", 20.0 * args.n + 8.0 * n_super, "GB/s"),
-        "tile_sort": ("hbm", 16.0 * n_super + 4.0 * n_super + 8.0 * n_super + 4.0 * n_keys, "GB/s"),
-        "ranges": ("hbm", 12.0 * args.n, "GB/s"),
+        "tile_sort": ("hbm", 16.0 * n_super + 4.0 * n_super, "GB/s"),
+        "ranges": ("hbm", 12.0 * n_super + 4.0 * n_keys, "GB/s"),
         "loss": ("hbm", 4.0 * 3 * H * W * 9, "GB/s"),
     }
     dom = max((k for k in work if per_launch.get(k, 0) > 0), key=lambda k: per_launch[k])
