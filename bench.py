@@ -38,7 +38,7 @@ FLOP_PER_PAIR_FWD = 18
 FLOP_PER_PAIR_BWD = 50
 # DRAM bytes (read + write) of one launch at the default workload (1.5M Gaussians, 1920x1280,
 # 16x16 tiles), from an ncu capture of the current kernel; used for the roofline's `traffic`
-KERNEL_DRAM_BYTES = {"blend_bwd": 80.20e6 + 2.49e6}
+KERNEL_DRAM_BYTES = {"blend_bwd": 80.15e6 + 2.63e6}
 # shared-memory wavefronts per walked pixel-Gaussian pair of the blends
 # (l1tex__data_pipe_lsu_wavefronts_mem_shared.sum / walked pairs of the same
 # launch, from an ncu capture of the current kernels on the 300k-Gaussian
