@@ -205,10 +205,10 @@ typedef struct {
     int64_t n_keys;              /* number of (tile, Gaussian) pairs */
     int32_t tiles_x, tiles_y, tile_w, tile_h;
     int64_t n_gaussians;
-    const uint32_t *tile_ids;    /* [n_keys] sorted tile index of each pair (the two-level binning
-                                    keeps only the lists and their ranges: then this array is
-                                    rebuilt from the ranges by the query, which synchronises the
-                                    device) */
+    const uint32_t *tile_ids;    /* [n_keys] sorted tile index of each pair, or NULL when the
+                                    forward kept only the lists and their ranges (the two-level
+                                    binning): splash_state_copy(SPLASH_FIELD_TILE_IDS) rebuilds
+                                    it from the ranges */
     const uint32_t *gauss_ids;   /* [n_keys] Gaussian index of each pair, tile by tile, each
                                     tile's list in depth order */
     const uint32_t *ranges;      /* [tiles][2] half-open [start, end) into the pairs; an empty

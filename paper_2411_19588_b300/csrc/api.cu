@@ -264,13 +264,9 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
         ENSURE(st->sort_scratch, sort_scratch_bytes(kk));
     }
     sort_scratch_carve(st->sort_scratch.p, std::max(nn, kk), &ss);
-    const int64_t chunks = chunk_bound(Ks, nsuper);
     ENSURE(st->sranges, 8 * (size_t)nsuper);
-    ENSURE(st->bin_scratch, 4 * ((size_t)nsuper + 1 + 32 * (size_t)chunks + (size_t)ntiles));
-    BinningScratch bs;
-    bs.chunk_base = st->bin_scratch.as<uint32_t>();
-    bs.chunk_count = bs.chunk_base + nsuper + 1;
-    bs.tile_count = bs.chunk_count + 32 * chunks;
+    ENSURE(st->bin_scratch, 4 * binning_scratch_words(Ks, nsuper, ntiles));
+    const BinningScratch bs = binning_scratch_carve(st->bin_scratch.as<uint32_t>(), Ks, nsuper);
     // super-tile entries into buffer pair 1, sorted by super-tile (one pass up
     // to 512 super-tiles); the tile lists go to the value buffer the sort
     // leaves free
@@ -294,7 +290,7 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
     {
         Stage t(ctx->prof, SPLASH_STAGE_RANGES, s);
         launch_tile_lists(tg, nsx, sbits, Ks, skeys, svals, st->sranges.as<uint2>(), bs, st->ranges.as<uint2>(), gids,
-                          ctx->d_status, s);
+                          ctx->d_status, s, (uint32_t)K);
     }
     const uint32_t *tids = nullptr;  // rebuilt from the ranges when a query asks for them
     {
@@ -324,6 +320,7 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
     st->H = cam->height;
     st->tg = tg;
     st->K = K;
+    st->Ks = Ks;
     st->order = order;
     st->tile_ids = tids;  // null on the two-level path: rebuilt from the ranges when asked for
     st->tid_lazy_ok = false;
@@ -479,13 +476,7 @@ splash_status splash_state_get_info(const splash_state *st, splash_state_info *o
     out->tile_w = st->tg.tw;
     out->tile_h = st->tg.th;
     out->n_gaussians = st->n;
-    const uint32_t *tids = st->tile_ids;
-    if (!tids) {  // rebuilt from the ranges once the forward's work is done (a query, not the render path)
-        SPLASH_CUDA_TRY(cudaDeviceSynchronize());
-        if (!(tids = rebuilt_tile_ids(st, 0))) return fail(SPLASH_ERR_OOM, "tile id buffer");
-        SPLASH_CUDA_TRY(cudaDeviceSynchronize());
-    }
-    out->tile_ids = tids;
+    out->tile_ids = st->tile_ids;  // null when the forward kept only the lists and their ranges
     out->gauss_ids = st->gauss_ids;
     out->ranges = st->ranges.as<uint32_t>();
     out->depth_keys = st->depth_key.as<uint32_t>();

@@ -6,8 +6,9 @@
 //    stays on the device, clamped to a capacity measured once by
 //    splash_batch_calibrate (overflow sets SPLASH_ERR_CAPACITY, every index
 //    stays in range).
-//  * Per view: preprocess, depth sort, scan, emit, tile sort, ranges (the
-//    same kernels as a single render).
+//  * Per view: preprocess, depth sort, and the two-level binning (super-tile
+//    entries, their sort, the tile lists: the same kernels as a single
+//    render, on device-side counts).
 //  * One work queue of all (view, tile) items, ordered longest list first,
 //    drives ONE persistent blend launch forward and ONE backward.
 //  * The adjoint of the preprocess reads every Gaussian once and sums its
@@ -63,6 +64,7 @@ struct splash_batch {
     std::vector<CamK> ck;
     std::vector<TileGeom> tg;
     std::vector<int64_t> tiles_off, pix_off, cap, cap_off;
+    std::vector<int64_t> scap;  // per view: capacity of the super-tile entries
     int64_t tiles_total = 0, pix_total = 0, cap_total = 0, cap_max = 0;
     int64_t n = -1;
     int64_t ns = 0;  // per-view stride of the depth keys: n rounded up to a multiple of 4 (16-byte aligned slices)
@@ -71,8 +73,12 @@ struct splash_batch {
     int ctas_fwd = 0, ctas_bwd = 0;
     // device
     Buf rec, depth_key, tt, rect, dk0, dv0, dk1, dv1, offsets, scan_sums, sort_scratch;
-    Buf pair_k, pair_v, tmp_k, tmp_v;  // per-view sorted pairs (cap_off), shared ping-pong buffer
-    Buf ranges, counts;                // counts[2v] = pairs emitted, counts[2v+1] = pairs used (clamped)
+    Buf pair_k, pair_v, tmp_k, tmp_v;  // per-view tile lists in pair_v (cap_off); super-tile sort buffers
+    Buf tmp2_v;                        // the super-tile sort's second value buffer (cap_max)
+    Buf ranges, counts;                // counts[2v] = the view's pairs, counts[2v + 1] = its super-tile entries (clamped)
+    Buf sc, sranges, bin_scratch, pair_part, scount;  // two-level binning; scount[v] = super-tile entries emitted
+    int nsuper_max = 0;
+    int64_t bin_words = 0;
     Buf fT, aA, zh, nlast, nwalk;
     Buf items_k, items_v, items_k1, items_v1, item_meta;  // item_meta: [0] = item count, [1] = ticket counter
     Buf views, tiles_off_dev;
@@ -153,6 +159,7 @@ splash_status splash_batch_calibrate(splash_batch *b, const splash_gaussians *g,
         return fail(SPLASH_ERR_OOM, "splash_batch_calibrate: image buffer");
     }
     b->cap.assign(b->V, 0);
+    b->scap.assign(b->V, 0);
     b->cap_off.assign(b->V + 1, 0);
     for (int v = 0; v < b->V; v++) {
         rc = splash_render_forward(b->ctx, st, g, medium, &b->cams[v], img.as<float>(), nullptr, nullptr, s);
@@ -163,6 +170,7 @@ splash_status splash_batch_calibrate(splash_batch *b, const splash_gaussians *g,
         // multiples of 4 keep every view's slice of the pair buffers 16-byte aligned
         b->cap[v] = (((int64_t)((double)st->K * headroom) + 1024) + 3) & ~(int64_t)3;
         b->cap_off[v + 1] = b->cap_off[v] + b->cap[v];
+        b->scap[v] = std::min(b->cap[v], (((int64_t)((double)st->Ks * headroom) + 1024) + 3) & ~(int64_t)3);
     }
     splash_state_destroy(st);
     b->cap_total = b->cap_off.back();
@@ -186,6 +194,26 @@ splash_status splash_batch_calibrate(splash_batch *b, const splash_gaussians *g,
     ENSURE(b->pair_v, 4 * (size_t)b->cap_total);
     ENSURE(b->tmp_k, 4 * (size_t)b->cap_max);
     ENSURE(b->tmp_v, 4 * (size_t)b->cap_max);
+    ENSURE(b->tmp2_v, 4 * (size_t)b->cap_max);
+    // two-level binning per view (the super-tile entry capacity is at most the pair capacity)
+    b->nsuper_max = 0;
+    b->bin_words = 0;
+    for (int v = 0; v < b->V; v++) {
+        int nsx = 0;
+        super_bits(b->tg[v], &nsx);
+        const int nsuper = nsx * ((b->tg[v].ty + kSuperH - 1) / kSuperH);
+        b->nsuper_max = std::max(b->nsuper_max, nsuper);
+        b->bin_words = std::max<int64_t>(b->bin_words, (int64_t)binning_scratch_words(b->scap[v], nsuper,
+                                                                                     b->tg[v].tx * b->tg[v].ty));
+    }
+    ENSURE(b->sc, 4 * nn);
+    ENSURE(b->sranges, 8 * (size_t)b->nsuper_max);
+    ENSURE(b->bin_scratch, 4 * (size_t)b->bin_words);
+    ENSURE(b->scount, 4 * (size_t)V);
+    if (b->pair_part.cap < kPairTotalScratchBytes) {  // its ticket is kept zero by every launch
+        ENSURE(b->pair_part, kPairTotalScratchBytes);
+        SPLASH_CUDA_TRY(cudaMemsetAsync(b->pair_part.p, 0, kPairTotalScratchBytes, s));
+    }
     ENSURE(b->ranges, 8 * (size_t)b->tiles_total);
     ENSURE(b->counts, 8 * (size_t)V);
     ENSURE(b->fT, 4 * (size_t)b->pix_total);
@@ -210,6 +238,7 @@ splash_status splash_batch_calibrate(splash_batch *b, const splash_gaussians *g,
     SPLASH_CUDA_TRY(cudaMemsetAsync(b->pair_v.p, 0, 4 * (size_t)b->cap_total, s));
     SPLASH_CUDA_TRY(cudaMemsetAsync(b->tmp_k.p, 0, 4 * (size_t)b->cap_max, s));
     SPLASH_CUDA_TRY(cudaMemsetAsync(b->tmp_v.p, 0, 4 * (size_t)b->cap_max, s));
+    SPLASH_CUDA_TRY(cudaMemsetAsync(b->tmp2_v.p, 0, 4 * (size_t)b->cap_max, s));
     const uint32_t nitems = (uint32_t)b->tiles_total;
     SPLASH_CUDA_TRY(cudaMemcpyAsync(b->item_meta.p, &nitems, 4, cudaMemcpyHostToDevice, s));
     SPLASH_CUDA_TRY(cudaMemcpyAsync(b->tiles_off_dev.p, b->tiles_off.data(), 8 * (V + 1), cudaMemcpyHostToDevice, s));
@@ -279,37 +308,43 @@ splash_status splash_batch_forward(splash_batch *b, const splash_gaussians *g, c
                                          ctx->opt.test_stall_partition, s, kDepthSortItems);
             order = which ? b->dv1.as<uint32_t>() : b->dv0.as<uint32_t>();
         }
+        // two-level binning, as a single render does, on device-side counts bounded by
+        // the view's capacities (pairs; super-tile entries, measured alike)
+        int nsx = 0;
+        const int sbits = super_bits(tg, &nsx);
+        const int nsuper = nsx * ((tg.ty + kSuperH - 1) / kSuperH);
+        uint32_t *ents = counts + 2 * v + 1;  // super-tile entries in use (clamped)
         {
             Stage t(ctx->prof, SPLASH_STAGE_SCAN, s);
-            launch_count_scan(n, order, b->tt.as<uint32_t>(), b->offsets.as<uint32_t>(), b->scan_sums.as<uint32_t>(),
-                              counts + 2 * v, s);
-            k_clamp_count<<<1, 1, 0, s>>>(counts + 2 * v, (uint32_t)b->cap[v], counts + 2 * v + 1, ctx->d_status);
+            launch_pair_totals(n, b->tt.as<uint32_t>(), b->rect.as<uint2>(), b->sc.as<uint32_t>(), b->pair_part.p,
+                               nullptr, ctx->d_status, s);
+            launch_count_scan(n, order, b->sc.as<uint32_t>(), b->offsets.as<uint32_t>(), b->scan_sums.as<uint32_t>(),
+                              b->scount.as<uint32_t>() + v, s);
+            k_clamp_count<<<1, 1, 0, s>>>(b->scount.as<uint32_t>() + v, (uint32_t)b->scap[v], ents, ctx->d_status);
             count_launch();
         }
-        // the sorted pairs must end in this view's slice: emit where the pass count puts the result there
-        const int bits = bits_for(ntiles);
-        const int passes = digit_plan(bits).passes;
         uint32_t *pk = b->pair_k.as<uint32_t>() + b->cap_off[v], *pv = b->pair_v.as<uint32_t>() + b->cap_off[v];
-        uint32_t *tk = b->tmp_k.as<uint32_t>(), *tv = b->tmp_v.as<uint32_t>();
-        const bool even = passes > 0 && (passes % 2 == 0);
-        uint32_t *ek = even ? pk : tk, *ev = even ? pv : tv;
+        uint32_t *tk = b->tmp_k.as<uint32_t>(), *tv = b->tmp_v.as<uint32_t>(), *tv2 = b->tmp2_v.as<uint32_t>();
         {
             Stage t(ctx->prof, SPLASH_STAGE_EMIT, s);
-            launch_emit(n, order, b->offsets.as<uint32_t>(), b->tt.as<uint32_t>(), b->rect.as<uint2>(), tg, ek, ev,
-                        (uint64_t)b->cap[v], ctx->d_status, s);
+            launch_emit_super(n, order, b->offsets.as<uint32_t>(), b->sc.as<uint32_t>(), b->rect.as<uint2>(), nsx, sbits,
+                              tk, tv, (uint64_t)b->scap[v], ctx->d_status, s);
         }
+        const uint32_t *skeys = tk, *svals = tv;
         {
             Stage t(ctx->prof, SPLASH_STAGE_TILE_SORT, s);
-            if (even)
-                sort_pairs(ek, ev, tk, tv, pk, pv, b->cap[v], counts + 2 * v + 1, bits, ss, ctx->d_status,
-                           ctx->opt.spin_limit, ctx->opt.test_stall_partition, s);
-            else
-                sort_pairs(ek, ev, pk, pv, tk, tv, b->cap[v], counts + 2 * v + 1, bits, ss, ctx->d_status,
-                           ctx->opt.spin_limit, ctx->opt.test_stall_partition, s);
+            const int which = sort_pairs(tk, tv, pk, tv2, tk, tv, b->scap[v], ents, sbits, ss, ctx->d_status,
+                                         ctx->opt.spin_limit, ctx->opt.test_stall_partition, s);
+            skeys = which ? tk : pk;
+            svals = which ? tv : tv2;
+            launch_ranges(b->scap[v], ents, skeys, b->sranges.as<uint2>(), nsuper, s, (1u << sbits) - 1u);
         }
         {
             Stage t(ctx->prof, SPLASH_STAGE_RANGES, s);
-            launch_ranges(b->cap[v], counts + 2 * v + 1, pk, b->ranges.as<uint2>() + b->tiles_off[v], ntiles, s);
+            const BinningScratch bs = binning_scratch_carve(b->bin_scratch.as<uint32_t>(), b->scap[v], nsuper);
+            launch_tile_lists(tg, nsx, sbits, b->scap[v], skeys, svals, b->sranges.as<uint2>(), bs,
+                              b->ranges.as<uint2>() + b->tiles_off[v], pv, ctx->d_status, s, (uint32_t)b->cap[v],
+                              counts + 2 * v);
         }
     }
     // the work queue: every (view, tile), longest list first

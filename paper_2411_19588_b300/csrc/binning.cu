@@ -97,10 +97,12 @@ __global__ void __launch_bounds__(256) k_pair_totals(int64_t n, const uint32_t *
     x = block_sum2(x, s_w);
     if (threadIdx.x == 0) {
         *ticket = 0u;
-        host[0] = *reinterpret_cast<const volatile uint32_t *>(status);
-        host[1] = x.x;
-        host[2] = x.y;
-        __threadfence_system();
+        if (host) {
+            host[0] = *reinterpret_cast<const volatile uint32_t *>(status);
+            host[1] = x.x;
+            host[2] = x.y;
+            __threadfence_system();
+        }
     }
 }
 
@@ -320,9 +322,11 @@ __global__ void __launch_bounds__(256) k_super_prefix(const uint32_t *__restrict
     if (tx < tiles_x && ty < tiles_y) tile_count[ty * tiles_x + tx] = acc;
 }
 
-// one CTA: exclusive scan of the tile counts in tile order: ranges
+// one CTA: exclusive scan of the tile counts in tile order: ranges, clamped
+// to `cap` slots (a total past it is reported); *total = the pairs
 __global__ void __launch_bounds__(kCountScanThreads) k_tile_scan(const uint32_t *__restrict__ tile_count, int ntiles,
-                                                                 uint2 *__restrict__ ranges)
+                                                                 uint2 *__restrict__ ranges, uint32_t cap,
+                                                                 uint32_t *__restrict__ total, uint32_t *__restrict__ status)
 {
     pdl_enter();
     __shared__ uint32_t s_w[kCountScanThreads / 32];
@@ -344,8 +348,12 @@ __global__ void __launch_bounds__(kCountScanThreads) k_tile_scan(const uint32_t 
     uint32_t run = base + x - local;
     for (int t = t0; t < t1; t++) {
         const uint32_t c = tile_count[t];
-        ranges[t] = make_uint2(run, run + c);
+        ranges[t] = make_uint2(min(run, cap), min(run + c, cap));
         run += c;
+    }
+    if (tid == kCountScanThreads - 1) {  // its run ends at the total
+        if (total) *total = run;
+        if (run > cap) atomicOr(status, kStatusCapacity);
     }
 }
 
@@ -426,6 +434,20 @@ int super_bits(const TileGeom &tg, int *nsx)
 
 int64_t chunk_bound(int64_t n_super_entries, int nsuper) { return (n_super_entries + kChunk - 1) / kChunk + nsuper; }
 
+size_t binning_scratch_words(int64_t n_super_entries, int nsuper, int ntiles)
+{
+    return (size_t)nsuper + 1 + 32 * (size_t)chunk_bound(n_super_entries, nsuper) + (size_t)ntiles;
+}
+
+BinningScratch binning_scratch_carve(uint32_t *base, int64_t n_super_entries, int nsuper)
+{
+    BinningScratch bs;
+    bs.chunk_base = base;
+    bs.chunk_count = base + nsuper + 1;
+    bs.tile_count = bs.chunk_count + 32 * chunk_bound(n_super_entries, nsuper);
+    return bs;
+}
+
 void launch_pair_totals(int64_t n, const uint32_t *tt, const uint2 *rect, uint32_t *sc, void *scratch,
                         uint64_t *host_out, const uint32_t *status, cudaStream_t s)
 {
@@ -449,7 +471,7 @@ void launch_emit_super(int64_t n, const uint32_t *order, const uint32_t *offsets
 
 void launch_tile_lists(const TileGeom &tg, int nsx, int sbits, int64_t n_super_entries, const uint32_t *skeys,
                        const uint32_t *svals, const uint2 *sranges, const BinningScratch &bs, uint2 *ranges,
-                       uint32_t *gauss_ids, uint32_t *status, cudaStream_t s)
+                       uint32_t *gauss_ids, uint32_t *status, cudaStream_t s, uint32_t cap, uint32_t *total)
 {
     // plain launches: started early behind one another (programmatic launch)
     // these kernels made the forward 0.17 ms slower on the B300
@@ -463,7 +485,7 @@ void launch_tile_lists(const TileGeom &tg, int nsx, int sbits, int64_t n_super_e
     k_super_prefix<<<(unsigned)(((int64_t)nsuper * 32 + 255) / 256), 256, 0, s>>>(bs.chunk_base, nsuper, nsx, tg.tx,
                tg.ty, bs.chunk_count, bs.tile_count);
     count_launch();
-    k_tile_scan<<<1, kCountScanThreads, 0, s>>>(bs.tile_count, ntiles, ranges);
+    k_tile_scan<<<1, kCountScanThreads, 0, s>>>(bs.tile_count, ntiles, ranges, cap, total, status);
     count_launch();
     k_super_scatter<<<ctas, kChunkWarps * 32, 0, s>>>(skeys, svals, sranges, bs.chunk_base, nsuper, nsx, sbits,
                tg.tx, tg.ty, bs.chunk_count, ranges, gauss_ids, status);

@@ -227,6 +227,7 @@ struct splash_state {
     int W = 0, H = 0;
     splash::TileGeom tg{};
     int64_t K = 0;
+    int64_t Ks = 0;  // super-tile entries of the two-level binning
     const uint32_t *order = nullptr;     // depth-sorted Gaussian indices
     const uint32_t *tile_ids = nullptr;  // sorted pairs
     const uint32_t *gauss_ids = nullptr;

@@ -204,9 +204,6 @@ void launch_pixel_medium_final(const float *partials, int nblocks, float *d_medi
 // leaves it zero)
 constexpr int kPairTotalBlocksMax = 148 * 4;
 constexpr size_t kPairTotalScratchBytes = 16 * (size_t)(kPairTotalBlocksMax + 1);
-void launch_emit(int64_t n, const uint32_t *order, const uint32_t *offsets, const uint32_t *tt, const uint2 *rect,
-                 const TileGeom &tg, uint32_t *tile_ids, uint32_t *gauss_ids, uint64_t capacity, uint32_t *status,
-                 cudaStream_t s);
 // ---- two-level tile binning (binning.cu)
 constexpr int kSuperW = 8, kSuperH = 4;  // tiles per super-tile
 // super-tiles per row (*nsx) and the bits of a super-tile index
@@ -214,7 +211,7 @@ int super_bits(const TileGeom &tg, int *nsx);
 // chunks of the super-tile lists (an upper bound from the entry count)
 int64_t chunk_bound(int64_t n_super_entries, int nsuper);
 // K, K_s and the status word into host_out[0..2] (mapped host memory, device
-// address); sc[g] = Gaussian g's super-tile count
+// address; null: none); sc[g] = Gaussian g's super-tile count
 void launch_pair_totals(int64_t n, const uint32_t *tt, const uint2 *rect, uint32_t *sc, void *scratch,
                         uint64_t *host_out, const uint32_t *status, cudaStream_t s);
 void launch_emit_super(int64_t n, const uint32_t *order, const uint32_t *offsets, const uint32_t *sc, const uint2 *rect,
@@ -225,10 +222,15 @@ struct BinningScratch {
     uint32_t *chunk_count;  // [chunk_bound][32]
     uint32_t *tile_count;   // [tiles]
 };
-// the tile lists (gauss_ids) and their ranges from the sorted super-tile lists
+// the tile lists (gauss_ids) and their ranges from the sorted super-tile
+// lists; n_super_entries bounds the entries (their count is read on the
+// device); the ranges are clamped to `cap` slots of gauss_ids (a longer total
+// is reported); *total (optional, device) = the pair count
+size_t binning_scratch_words(int64_t n_super_entries, int nsuper, int ntiles);
 void launch_tile_lists(const TileGeom &tg, int nsx, int sbits, int64_t n_super_entries, const uint32_t *skeys,
                        const uint32_t *svals, const uint2 *sranges, const BinningScratch &bs, uint2 *ranges,
-                       uint32_t *gauss_ids, uint32_t *status, cudaStream_t s);
+                       uint32_t *gauss_ids, uint32_t *status, cudaStream_t s, uint32_t cap, uint32_t *total = nullptr);
+BinningScratch binning_scratch_carve(uint32_t *base, int64_t n_super_entries, int nsuper);
 // tile_ids[i] = t for every i in ranges[t] (the sorted tile ids, rebuilt from the ranges)
 void launch_expand_tile_ids(const uint2 *ranges, int ntiles, uint32_t *tile_ids, cudaStream_t s);
 

@@ -1,10 +1,9 @@
-// Tile binning (Sec. III-A, "Tiles"): every Gaussian is listed in each tile
-// its 3-sigma bounding box covers. The lists are emitted in depth order (the
-// Gaussians come from the depth sort), so a stable sort by tile index yields
-// per-tile lists sorted by depth with ties broken by Gaussian index.
-//   k_scan_*  -- exclusive scan of the tile counts, taken in depth order
-//   k_emit    -- write (tile index, Gaussian index) pairs
-//   k_ranges  -- [start, end) of every tile's run in the sorted pairs
+// Tile binning helpers (Sec. III-A, "Tiles"): the scan of per-Gaussian
+// counts taken in depth order, and the ranges of runs in a sorted key array.
+//   k_scan_*   -- exclusive scan of counts read through the depth order
+//   k_ranges   -- [start, end) of every key value's run (keys masked to their
+//                 low bits), by a 32-way search per value
+//   k_expand_tile_ids -- the sorted tile id of every pair, from the ranges
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -115,65 +114,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(int64_t n, const uin
     if (own_prefix && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *total = pre + tot;
 }
 
-// One warp per 32 consecutive depth-ordered Gaussians. Their runs of pairs are
-// consecutive in the output, so the warp writes the whole range together with
-// coalesced stores: output slot s belongs to the last lane whose run starts at
-// or before s (a 5-step shuffle search), and is the k-th tile of that lane's
-// rectangle in row-major order. A Gaussian whose run does not fit the
-// capacity writes nothing and is reported.
-__global__ void __launch_bounds__(256) k_emit(int64_t n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ offsets,
-                                              const uint32_t *__restrict__ tt, const uint2 *__restrict__ rect, int tiles_x,
-                                              uint32_t *__restrict__ tile_ids, uint32_t *__restrict__ gauss_ids,
-                                              uint64_t capacity, uint32_t *__restrict__ status)
-{
-    pdl_enter();
-    constexpr uint32_t kFull = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r - lane >= n) return;  // the whole warp is past the end
-    uint32_t g = 0, cnt = 0, tx0 = 0, ty0 = 0, w = 1, fit = 0, off = 0;
-    if (r < n) {
-        g = order[r];
-        cnt = tt[g];
-        off = offsets[r];
-        if (cnt) {
-            const uint2 rc = rect[g];
-            tx0 = rc.x & 0xffffu;
-            ty0 = rc.y & 0xffffu;
-            w = (rc.x >> 16) - tx0 + 1;
-            fit = (uint64_t)off + cnt <= capacity;
-            if (!fit) atomicOr(status, kStatusCapacity);
-        }
-    }
-    // warp-local start of each lane's run: exclusive scan of the counts
-    uint32_t incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += y;
-    }
-    const uint32_t loc = incl - cnt;
-    const uint32_t total = __shfl_sync(kFull, incl, 31);
-    for (uint32_t base = 0; base < total; base += 32) {
-        const uint32_t s = base + lane;
-        int j = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const uint32_t lj = __shfl_sync(kFull, loc, j + step);
-            if (lj <= s) j += step;
-        }
-        const uint32_t og = __shfl_sync(kFull, g, j), otx0 = __shfl_sync(kFull, tx0, j), oty0 = __shfl_sync(kFull, ty0, j);
-        const uint32_t ow = __shfl_sync(kFull, w, j), ofit = __shfl_sync(kFull, fit, j), oloc = __shfl_sync(kFull, loc, j);
-        const uint32_t ooff = __shfl_sync(kFull, off, j);
-        if (s < total && ofit) {
-            // the owner's own offset: ofit guarantees ooff + its count <= capacity
-            const uint32_t k = s - oloc, dy = k / ow, dx = k - dy * ow;
-            tile_ids[(uint64_t)ooff + k] = (oty0 + dy) * (uint32_t)tiles_x + otx0 + dx;
-            gauss_ids[(uint64_t)ooff + k] = og;
-        }
-    }
-}
-
 // Start of every tile's run in the sorted pairs, one warp per tile value t
 // in [0, ntiles]: the first index whose tile id is >= t (a 32-way search: each
 // round probes 32 evenly spaced keys, one per lane, and keeps the sub-interval
@@ -231,16 +171,6 @@ void launch_count_scan(int64_t n, const uint32_t *order, const uint32_t *tt, uin
         count_launch();
     }
     launch_pdl(k_scan_down, nchunks, kScanThreads, 0, s, n, order, tt, sums, offsets, own, total);
-    count_launch();
-}
-
-void launch_emit(int64_t n, const uint32_t *order, const uint32_t *offsets, const uint32_t *tt, const uint2 *rect,
-                 const TileGeom &tg, uint32_t *tile_ids, uint32_t *gauss_ids, uint64_t capacity, uint32_t *status,
-                 cudaStream_t s)
-{
-    if (n <= 0) return;
-    launch_pdl(k_emit, (unsigned)((n + 255) / 256), 256, 0, s, n, order, offsets, tt, rect, tg.tx, tile_ids, gauss_ids, capacity,
-                                                       status);
     count_launch();
 }
 
