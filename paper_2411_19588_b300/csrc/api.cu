@@ -52,6 +52,7 @@ BlendView backward_view(splash_state *st, const CamK &ck, const float *gi, const
     v.dL_ddepth01 = g01;
     v.gacc = st->gacc.as<GAcc>();
     v.tile_medium = st->tile_med.as<float>();
+    v.tile_order = st->tile_order.as<uint32_t>();
     return v;
 }
 
@@ -202,6 +203,7 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
     ENSURE(st->zh, 4 * npix);
     ENSURE(st->nlast, 4 * npix);
     ENSURE(st->nwalk, 4 * npix);
+    ENSURE(st->tile_walk, 4 * (size_t)ntiles);
     ENSURE(st->sort_scratch, sort_scratch_bytes(nn));
     SortScratch ss;
     sort_scratch_carve(st->sort_scratch.p, nn, &ss);
@@ -309,6 +311,7 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
         v.zhat = st->zh.as<float>();
         v.n_last = st->nlast.as<uint32_t>();
         v.n_walk = st->nwalk.as<uint32_t>();
+        v.tile_walk = st->tile_walk.as<uint32_t>();
         preclear_backward(st, n, v);
         launch_blend_fwd(v, medium, fwd_batch(ctx->opt), s);
     }
@@ -353,11 +356,13 @@ splash_status render_backward_impl(splash_ctx *ctx, splash_state *st, const spla
     ENSURE(st->tile_med, 4 * 6 * (size_t)ntiles);
     ENSURE(st->block_med, 4 * 9 * (size_t)nblocks);
     ENSURE(st->red_scratch, 4 * 16 * (size_t)kColsumParts);
+    ENSURE(st->tile_order, 4 * (size_t)ntiles);
     // (every block of the preprocess adjoint writes its block_med row: no clear)
     if ((rc = clear_backward(st, n, s)) != SPLASH_OK) return rc;
     const CamK ck = make_cam(*cam);
     {
         Stage t(ctx->prof, SPLASH_STAGE_BLEND_BWD, s);
+        launch_tile_order(st->tile_walk.as<uint32_t>(), ntiles, st->tile_order.as<uint32_t>(), s);
         launch_blend_bwd(backward_view(st, ck, dL_dimage, dL_ddepth, dL_ddepth01), medium, bwd_batch(ctx->opt), s);
     }
     int nb = 0;
@@ -422,11 +427,13 @@ splash_status backward_adam_impl(splash_ctx *ctx, splash_state *st, const splash
     ENSURE(st->block_med, 4 * 9 * (size_t)nblocks);
     ENSURE(st->gmed, 4 * 16);
     ENSURE(st->red_scratch, 4 * 16 * (size_t)kColsumParts);
+    ENSURE(st->tile_order, 4 * (size_t)ntiles);
     // (every block of the fused adjoint writes its block_med row: no clear)
     if ((rc = clear_backward(st, n, s)) != SPLASH_OK) return rc;
     const CamK ck = make_cam(*cam);
     {
         Stage t(ctx->prof, SPLASH_STAGE_BLEND_BWD, s);
+        launch_tile_order(st->tile_walk.as<uint32_t>(), ntiles, st->tile_order.as<uint32_t>(), s);
         launch_blend_bwd(backward_view(st, ck, dL_dimage, dL_ddepth, dL_ddepth01), chain_medium,
                          bwd_batch(ctx->opt), s);
     }

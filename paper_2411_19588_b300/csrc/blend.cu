@@ -224,6 +224,7 @@ __device__ __forceinline__ void blend_tile_fwd(const BlendView &v, int tile, con
         bfar[ch] = expf(-__ldg(medium + 3 + ch) * zfar);
     }
     const int HWimg = W * H;
+    uint32_t walk_max = 0;  // the tile's largest walk bound, for the backward's tile order
 #pragma unroll
     for (int q = 0; q < PX; q++) {
         const int gx = x0 + col + q * HW;
@@ -248,8 +249,21 @@ __device__ __forceinline__ void blend_tile_fwd(const BlendView &v, int tile, con
         // the backward's bound: every contributor lies in front of the
         // Gaussian that stopped the pixel (the entries between the last
         // contributor and it fail the 3-sigma or 1/255 test in both passes)
-        v.n_last[p] = (uint32_t)(stopped ? walk - 1 : n);
+        const uint32_t bound = (uint32_t)(stopped ? walk - 1 : n);
+        v.n_last[p] = bound;
         v.n_walk[p] = (uint32_t)walk;
+        walk_max = max(walk_max, bound);
+    }
+    if (v.tile_walk) {
+        __shared__ uint32_t s_walk[NT / 32];
+        walk_max = __reduce_max_sync(0xffffffffu, walk_max);
+        if ((tid & 31) == 0) s_walk[tid >> 5] = walk_max;
+        __syncthreads();
+        if (tid == 0) {
+#pragma unroll
+            for (int w = 1; w < NT / 32; w++) walk_max = max(walk_max, s_walk[w]);
+            v.tile_walk[tile] = walk_max;
+        }
     }
 }
 
@@ -572,7 +586,56 @@ template <int TW, int TH, int NB, bool DG>
 __global__ void __launch_bounds__(bwd_threads<TW, TH>(), (DG ? 704 : 768) / bwd_threads<TW, TH>()) k_blend_bwd(BlendView v, const float *__restrict__ medium)
 {
     pdl_enter();
-    blend_tile_bwd<TW, TH, NB, DG>(v, blockIdx.x, medium);
+    blend_tile_bwd<TW, TH, NB, DG>(v, v.tile_order ? (int)v.tile_order[blockIdx.x] : (int)blockIdx.x, medium);
+}
+
+// The backward's tile order: tiles by descending walk bound, so that the
+// longest tiles start in the first wave instead of trailing the last one (one
+// CTA per tile, handed out in launch order). A counting sort over
+// kOrderBuckets walk values in one CTA: histogram, exclusive scan, scatter.
+// Walks past the last bucket share it; the order within a bucket is the order
+// of the scatter's shared-memory atomics (any order is a valid schedule).
+constexpr int kOrderThreads = 1024, kOrderBuckets = 2 * kOrderThreads;
+__global__ void __launch_bounds__(kOrderThreads) k_tile_order(const uint32_t *__restrict__ walk, int ntiles,
+                                                              uint32_t *__restrict__ order)
+{
+    __shared__ uint32_t cnt[kOrderBuckets];
+    __shared__ uint32_t wsum[kOrderThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    cnt[tid] = 0;
+    cnt[tid + kOrderThreads] = 0;
+    __syncthreads();
+    for (int i = tid; i < ntiles; i += kOrderThreads)
+        atomicAdd(&cnt[kOrderBuckets - 1 - min(__ldg(walk + i), (uint32_t)(kOrderBuckets - 1))], 1u);
+    __syncthreads();
+    // thread t owns buckets 2t and 2t + 1
+    const uint32_t c0 = cnt[2 * tid], c1 = cnt[2 * tid + 1];
+    uint32_t incl = c0 + c1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = wsum[lane], wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        wsum[lane] = wi - w;  // exclusive over warps
+    }
+    __syncthreads();
+    const uint32_t excl = wsum[warp] + incl - (c0 + c1);
+    cnt[2 * tid] = excl;
+    cnt[2 * tid + 1] = excl + c0;
+    __syncthreads();
+    for (int i = tid; i < ntiles; i += kOrderThreads) {
+        const uint32_t b = kOrderBuckets - 1 - min(__ldg(walk + i), (uint32_t)(kOrderBuckets - 1));
+        order[atomicAdd(&cnt[b], 1u)] = (uint32_t)i;
+    }
 }
 
 // Persistent: one wave of CTAs; each takes the next (view, tile) item from the
@@ -698,6 +761,13 @@ void launch_blend_fwd(const BlendView &v, const float *medium, int batch, cudaSt
 void launch_blend_bwd(const BlendView &v, const float *medium, int batch, cudaStream_t s)
 {
     dispatch<BwdPlain>(v.tg.tw, batch, v, medium, s);
+}
+
+void launch_tile_order(const uint32_t *tile_walk, int ntiles, uint32_t *order, cudaStream_t s)
+{
+    if (ntiles <= 0) return;
+    k_tile_order<<<1, kOrderThreads, 0, s>>>(tile_walk, ntiles, order);
+    count_launch();
 }
 
 void launch_blend_fwd_persistent(int tw, int th, int batch, const BlendView *views, const uint32_t *items,

@@ -205,6 +205,8 @@ struct splash_state {
     mutable bool tid_lazy_ok = false;
     // per pixel
     splash_host::Buf fT, aA, zh, nlast, nwalk;
+    // per tile: the forward's largest walk bound; the backward's CTA order
+    splash_host::Buf tile_walk, tile_order;
     // backward
     splash_host::Buf gacc, tile_med, block_med, gmed, red_scratch;
     // loss / standalone sort

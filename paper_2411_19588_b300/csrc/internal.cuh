@@ -102,6 +102,8 @@ struct BlendView {
     float *tile_medium;                   // backward: per-tile medium partials [tiles][6]
     GAcc *clear;                          // forward (plain launch): zero clear[0..clear_n) for the next backward
     int64_t clear_n;
+    uint32_t *tile_walk;                  // forward (may be null): per tile, the largest walk bound n_last of its pixels
+    const uint32_t *tile_order;           // backward plain launch (may be null): CTA b blends tile tile_order[b]
 };
 
 // device status word bits
@@ -242,6 +244,9 @@ void launch_ranges(int64_t k_host, const uint32_t *k_dev, const uint32_t *tile_i
 constexpr int kBlendBatches[3] = {64, 128, 256};
 void launch_blend_fwd(const BlendView &v, const float *medium, int batch, cudaStream_t s);
 void launch_blend_bwd(const BlendView &v, const float *medium, int batch, cudaStream_t s);
+// tiles ordered by descending walk bound (a counting sort in one CTA), so that
+// the backward starts its longest tiles first
+void launch_tile_order(const uint32_t *tile_walk, int ntiles, uint32_t *order, cudaStream_t s);
 // Persistent forms: `ctas` CTAs pull work items from a queue (items[k] =
 // view << 24 | tile, taken in order; *counter must be zero on entry) until
 // n_items (read from the device) are done. All views share one tile shape.
