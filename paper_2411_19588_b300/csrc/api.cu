@@ -195,8 +195,8 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
     ENSURE(st->dv0, 4 * nn);
     ENSURE(st->dk1, 4 * nn);
     ENSURE(st->dv1, 4 * nn);
-    ENSURE(st->offsets, 4 * nn);
-    ENSURE(st->scan_sums, 4 * (nn / 4096 + 2));
+    ENSURE(st->scs, 4 * nn);
+    ENSURE(st->scan_sums, 4 * (size_t)(emit_blocks(nn) + 1));
     ENSURE(st->ranges, 8 * (size_t)ntiles);
     ENSURE(st->fT, 4 * npix);
     ENSURE(st->aA, 4 * npix);
@@ -240,7 +240,7 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
     }
     {
         Stage t(ctx->prof, SPLASH_STAGE_SCAN, s);
-        launch_count_scan(n, order, st->sc.as<uint32_t>(), st->offsets.as<uint32_t>(), st->scan_sums.as<uint32_t>(),
+        launch_super_scan(n, order, st->sc.as<uint32_t>(), st->scs.as<uint32_t>(), st->scan_sums.as<uint32_t>(),
                           dK + 2, s);  // its total equals K_s
     }
     SPLASH_CUDA_TRY(cudaGetLastError());
@@ -274,7 +274,7 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
     // leaves free
     {
         Stage t(ctx->prof, SPLASH_STAGE_EMIT, s);
-        launch_emit_super(n, order, st->offsets.as<uint32_t>(), st->sc.as<uint32_t>(), st->rect.as<uint2>(), nsx, sbits,
+        launch_emit_super(n, order, st->scs.as<uint32_t>(), st->scan_sums.as<uint32_t>(), st->rect.as<uint2>(), nsx, sbits,
                           st->tk1.as<uint32_t>(), st->tv1.as<uint32_t>(), (uint64_t)Ks, ctx->d_status, s);
     }
     int which = 0;

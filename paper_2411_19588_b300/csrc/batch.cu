@@ -72,7 +72,7 @@ struct splash_batch {
     bool calibrated = false, has_forward = false;
     int ctas_fwd = 0, ctas_bwd = 0;
     // device
-    Buf rec, depth_key, tt, rect, dk0, dv0, dk1, dv1, offsets, scan_sums, sort_scratch;
+    Buf rec, depth_key, tt, rect, dk0, dv0, dk1, dv1, scs, scan_sums, sort_scratch;  // scs: super-tile counts in depth order
     Buf pair_k, pair_v, tmp_k, tmp_v;  // per-view tile lists in pair_v (cap_off); super-tile sort buffers
     Buf tmp2_v;                        // the super-tile sort's second value buffer (cap_max)
     Buf ranges, counts;                // counts[2v] = the view's pairs, counts[2v + 1] = its super-tile entries (clamped)
@@ -186,8 +186,8 @@ splash_status splash_batch_calibrate(splash_batch *b, const splash_gaussians *g,
     ENSURE(b->dv0, 4 * nn);
     ENSURE(b->dk1, 4 * nn);
     ENSURE(b->dv1, 4 * nn);
-    ENSURE(b->offsets, 4 * nn);
-    ENSURE(b->scan_sums, 4 * (nn / 4096 + 2));
+    ENSURE(b->scs, 4 * nn);
+    ENSURE(b->scan_sums, 4 * (size_t)(emit_blocks(nn) + 1));
     const int64_t sort_n = std::max<int64_t>(std::max<int64_t>(nn, b->cap_max), b->tiles_total);
     ENSURE(b->sort_scratch, sort_scratch_bytes(sort_n));
     ENSURE(b->pair_k, 4 * (size_t)b->cap_total);
@@ -318,7 +318,7 @@ splash_status splash_batch_forward(splash_batch *b, const splash_gaussians *g, c
             Stage t(ctx->prof, SPLASH_STAGE_SCAN, s);
             launch_pair_totals(n, b->tt.as<uint32_t>(), b->rect.as<uint2>(), b->sc.as<uint32_t>(), b->pair_part.p,
                                nullptr, ctx->d_status, s);
-            launch_count_scan(n, order, b->sc.as<uint32_t>(), b->offsets.as<uint32_t>(), b->scan_sums.as<uint32_t>(),
+            launch_super_scan(n, order, b->sc.as<uint32_t>(), b->scs.as<uint32_t>(), b->scan_sums.as<uint32_t>(),
                               b->scount.as<uint32_t>() + v, s);
             k_clamp_count<<<1, 1, 0, s>>>(b->scount.as<uint32_t>() + v, (uint32_t)b->scap[v], ents, ctx->d_status);
             count_launch();
@@ -327,7 +327,7 @@ splash_status splash_batch_forward(splash_batch *b, const splash_gaussians *g, c
         uint32_t *tk = b->tmp_k.as<uint32_t>(), *tv = b->tmp_v.as<uint32_t>(), *tv2 = b->tmp2_v.as<uint32_t>();
         {
             Stage t(ctx->prof, SPLASH_STAGE_EMIT, s);
-            launch_emit_super(n, order, b->offsets.as<uint32_t>(), b->sc.as<uint32_t>(), b->rect.as<uint2>(), nsx, sbits,
+            launch_emit_super(n, order, b->scs.as<uint32_t>(), b->scan_sums.as<uint32_t>(), b->rect.as<uint2>(), nsx, sbits,
                               tk, tv, (uint64_t)b->scap[v], ctx->d_status, s);
         }
         const uint32_t *skeys = tk, *svals = tv;

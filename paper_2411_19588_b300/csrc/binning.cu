@@ -14,6 +14,8 @@
 // the same compact tile-major layout, with the same ranges, as a stable sort
 // of the (tile, Gaussian) pairs by tile.
 //   k_pair_totals    -- K (pairs), K_s (super entries), per-Gaussian super counts
+//   k_gather_counts  -- super counts in depth order, sums per emit block
+//   k_block_prefix   -- exclusive offsets of the emit blocks, total K_s
 //   k_emit_super     -- (super-tile | clipped rectangle, Gaussian) entries in depth order
 //   (the super-tile sort and its list ranges: sort.cu, tiles.cu)
 //   k_chunk_map      -- first chunk of every super-tile
@@ -106,34 +108,116 @@ __global__ void __launch_bounds__(256) k_pair_totals(int64_t n, const uint32_t *
     }
 }
 
+// The emit's offsets come in two small steps, without an offset per
+// Gaussian: k_gather_counts copies the super-tile counts into depth order
+// (coalesced reads for the emit) and sums them per block of kEmitBlock
+// ranks; k_block_prefix (one CTA) turns the block sums into exclusive block
+// offsets and the total. Each emit CTA then scans its own ranks.
+constexpr int kEmitBlock = 256;
+constexpr int kPrefixThreads = 1024, kPrefixItems = 8;
+
+__global__ void __launch_bounds__(kEmitBlock) k_gather_counts(int64_t n, const uint32_t *__restrict__ order,
+                                                              const uint32_t *__restrict__ sc, uint32_t *__restrict__ scs,
+                                                              uint32_t *__restrict__ block_sum)
+{
+    pdl_enter();
+    __shared__ uint32_t s_w[kEmitBlock / 32];
+    const int64_t r = (int64_t)blockIdx.x * kEmitBlock + threadIdx.x;
+    uint32_t c = 0;
+    if (r < n) {
+        c = sc[order[r]];
+        scs[r] = c;
+    }
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+#pragma unroll
+        for (int w = 0; w < kEmitBlock / 32; w++) t += s_w[w];
+        block_sum[blockIdx.x] = t;
+    }
+}
+
+// exclusive scan of nb block sums in place (rounds of kPrefixThreads x
+// kPrefixItems, each thread a run of kPrefixItems), the total to *total
+__global__ void __launch_bounds__(kPrefixThreads) k_block_prefix(int64_t nb, uint32_t *__restrict__ sums,
+                                                                 uint32_t *__restrict__ total)
+{
+    pdl_enter();
+    __shared__ uint32_t s_w[kPrefixThreads / 32];
+    __shared__ uint32_t s_round;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t carry = 0;
+    for (int64_t base = 0; base < nb; base += (int64_t)kPrefixThreads * kPrefixItems) {
+        const int64_t i0 = base + (int64_t)tid * kPrefixItems;
+        uint32_t v[kPrefixItems], acc = 0;
+#pragma unroll
+        for (int j = 0; j < kPrefixItems; j++) {
+            v[j] = i0 + j < nb ? sums[i0 + j] : 0u;
+            acc += v[j];
+        }
+        uint32_t x = acc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_w[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t w = s_w[lane];
+            uint32_t wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            s_w[lane] = wi - w;
+            if (lane == 31) s_round = wi;
+        }
+        __syncthreads();
+        uint32_t run = carry + s_w[warp] + x - acc;
+#pragma unroll
+        for (int j = 0; j < kPrefixItems; j++) {
+            if (i0 + j < nb) sums[i0 + j] = run;
+            run += v[j];
+        }
+        carry += s_round;
+        __syncthreads();  // s_w and s_round are rewritten by the next round
+    }
+    if (tid == 0) *total = carry;
+}
+
 // One warp per 32 consecutive depth-ordered Gaussians writes their
 // super-tile entries (row-major over each Gaussian's super-tile rectangle),
 // with coalesced stores as k_emit does for tile pairs: output slot s belongs
-// to the last lane whose run starts at or before s. Key: the super-tile index
-// in the low `sbits` bits, above it the Gaussian's tile rectangle clipped to
-// that super-tile (x0, x1 in 3 bits each, y0, y1 in 2 bits each).
-__global__ void __launch_bounds__(256) k_emit_super(int64_t n, const uint32_t *__restrict__ order,
-                                                    const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ sc,
-                                                    const uint2 *__restrict__ rect, int nsx, int sbits,
-                                                    uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                                                    uint64_t capacity, uint32_t *__restrict__ status)
+// to the last lane whose run starts at or before s. The CTA's first entry is
+// its block offset; each warp adds the counts of the warps before it. Key:
+// the super-tile index in the low `sbits` bits, above it the Gaussian's tile
+// rectangle clipped to that super-tile (x0, x1 in 3 bits each, y0, y1 in 2
+// bits each). Entries at or past `capacity` are not written (the status
+// word records it), so every entry below it is valid.
+__global__ void __launch_bounds__(kEmitBlock) k_emit_super(int64_t n, const uint32_t *__restrict__ order,
+                                                           const uint32_t *__restrict__ scs,
+                                                           const uint32_t *__restrict__ block_pre,
+                                                           const uint2 *__restrict__ rect, int nsx, int sbits,
+                                                           uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                                                           uint64_t capacity, uint32_t *__restrict__ status)
 {
     pdl_enter();
     constexpr uint32_t kFull = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r - lane >= n) return;  // the whole warp is past the end
-    uint32_t g = 0, cnt = 0, off = 0, fit = 0, rx = 0, ry = 0;
+    __shared__ uint32_t s_w[kEmitBlock / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t r = (int64_t)blockIdx.x * kEmitBlock + threadIdx.x;
+    uint32_t g = 0, cnt = 0, rx = 0, ry = 0;
     if (r < n) {
         g = order[r];
-        cnt = sc[g];
-        off = offsets[r];
+        cnt = scs[r];
         if (cnt) {
             const uint2 rc = rect[g];
             rx = rc.x;
             ry = rc.y;
-            fit = (uint64_t)off + cnt <= capacity;
-            if (!fit) atomicOr(status, kStatusCapacity);
         }
     }
     uint32_t incl = cnt;
@@ -142,8 +226,13 @@ __global__ void __launch_bounds__(256) k_emit_super(int64_t n, const uint32_t *_
         const uint32_t y = __shfl_up_sync(kFull, incl, o);
         if (lane >= o) incl += y;
     }
+    if (lane == 31) s_w[warp] = incl;
+    uint64_t wpre = block_pre[blockIdx.x];
+    __syncthreads();
+    for (int w = 0; w < warp; w++) wpre += s_w[w];
     const uint32_t loc = incl - cnt;
     const uint32_t total = __shfl_sync(kFull, incl, 31);
+    if (wpre + total > capacity && lane == 0) atomicOr(status, kStatusCapacity);
     for (uint32_t base = 0; base < total; base += 32) {
         const uint32_t s = base + lane;
         int j = 0;
@@ -153,9 +242,9 @@ __global__ void __launch_bounds__(256) k_emit_super(int64_t n, const uint32_t *_
             if (lj <= s) j += step;
         }
         const uint32_t og = __shfl_sync(kFull, g, j), orx = __shfl_sync(kFull, rx, j), ory = __shfl_sync(kFull, ry, j);
-        const uint32_t ofit = __shfl_sync(kFull, fit, j), oloc = __shfl_sync(kFull, loc, j);
-        const uint32_t ooff = __shfl_sync(kFull, off, j);
-        if (s < total && ofit) {
+        const uint32_t oloc = __shfl_sync(kFull, loc, j);
+        const uint64_t slot = wpre + s;
+        if (s < total && slot < capacity) {
             const uint32_t tx0 = orx & 0xffffu, tx1 = orx >> 16, ty0 = ory & 0xffffu, ty1 = ory >> 16;
             const uint32_t sx0 = tx0 / kSuperW, sx1 = tx1 / kSuperW, sy0 = ty0 / kSuperH;
             const uint32_t k = s - oloc, sw = sx1 - sx0 + 1, dy = k / sw, dx = k - dy * sw;
@@ -164,12 +253,11 @@ __global__ void __launch_bounds__(256) k_emit_super(int64_t n, const uint32_t *_
             const uint32_t lx0 = max(tx0, bx) - bx, lx1 = min(tx1, bx + kSuperW - 1) - bx;
             const uint32_t ly0 = max(ty0, by) - by, ly1 = min(ty1, by + kSuperH - 1) - by;
             const uint32_t lr = lx0 | (lx1 << 3) | (ly0 << 6) | (ly1 << 8);
-            keys[(uint64_t)ooff + k] = (syi * (uint32_t)nsx + sxi) | (lr << sbits);
-            vals[(uint64_t)ooff + k] = og;
+            keys[slot] = (syi * (uint32_t)nsx + sxi) | (lr << sbits);
+            vals[slot] = og;
         }
     }
 }
-
 
 // ---- tile lists from the sorted super-tile lists. Each list is cut into
 // chunks of kChunk consecutive entries; every entry's clipped rectangle is a
@@ -459,13 +547,27 @@ void launch_pair_totals(int64_t n, const uint32_t *tt, const uint2 *rect, uint32
     count_launch();
 }
 
-void launch_emit_super(int64_t n, const uint32_t *order, const uint32_t *offsets, const uint32_t *sc, const uint2 *rect,
-                       int nsx, int sbits, uint32_t *keys, uint32_t *vals, uint64_t capacity, uint32_t *status,
-                       cudaStream_t s)
+int64_t emit_blocks(int64_t n) { return (std::max<int64_t>(n, 0) + kEmitBlock - 1) / kEmitBlock; }
+
+void launch_super_scan(int64_t n, const uint32_t *order, const uint32_t *sc, uint32_t *scs, uint32_t *block_pre,
+                       uint32_t *total, cudaStream_t s)
+{
+    const int64_t nb = emit_blocks(n);
+    if (nb > 0) {
+        launch_pdl(k_gather_counts, (unsigned)nb, kEmitBlock, 0, s, n, order, sc, scs, block_pre);
+        count_launch();
+    }
+    launch_pdl(k_block_prefix, 1, kPrefixThreads, 0, s, nb, block_pre, total);
+    count_launch();
+}
+
+void launch_emit_super(int64_t n, const uint32_t *order, const uint32_t *scs, const uint32_t *block_pre,
+                       const uint2 *rect, int nsx, int sbits, uint32_t *keys, uint32_t *vals, uint64_t capacity,
+                       uint32_t *status, cudaStream_t s)
 {
     if (n <= 0) return;
-    launch_pdl(k_emit_super, (unsigned)((n + 255) / 256), 256, 0, s, n, order, offsets, sc, rect, nsx, sbits, keys, vals,
-               capacity, status);
+    launch_pdl(k_emit_super, (unsigned)emit_blocks(n), kEmitBlock, 0, s, n, order, scs, block_pre, rect, nsx, sbits,
+               keys, vals, capacity, status);
     count_launch();
 }
 

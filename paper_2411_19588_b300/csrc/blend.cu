@@ -596,17 +596,32 @@ __global__ void __launch_bounds__(bwd_threads<TW, TH>(), (DG ? 704 : 768) / bwd_
 // Walks past the last bucket share it; the order within a bucket is the order
 // of the scatter's shared-memory atomics (any order is a valid schedule).
 constexpr int kOrderThreads = 1024, kOrderBuckets = 2 * kOrderThreads;
+constexpr int kOrderItems = 16;  // walk values per thread and round, all loaded before the first atomic
+__device__ __forceinline__ uint32_t walk_bucket(uint32_t w)
+{
+    return kOrderBuckets - 1 - min(w, (uint32_t)(kOrderBuckets - 1));
+}
 __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const uint32_t *__restrict__ walk, int ntiles,
                                                               uint32_t *__restrict__ order)
 {
     __shared__ uint32_t cnt[kOrderBuckets];
     __shared__ uint32_t wsum[kOrderThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kRound = kOrderThreads * kOrderItems;
     cnt[tid] = 0;
     cnt[tid + kOrderThreads] = 0;
     __syncthreads();
-    for (int i = tid; i < ntiles; i += kOrderThreads)
-        atomicAdd(&cnt[kOrderBuckets - 1 - min(__ldg(walk + i), (uint32_t)(kOrderBuckets - 1))], 1u);
+    for (int base = 0; base < ntiles; base += kRound) {
+        uint32_t b[kOrderItems];
+#pragma unroll
+        for (int j = 0; j < kOrderItems; j++) {
+            const int i = base + j * kOrderThreads + tid;
+            b[j] = i < ntiles ? walk_bucket(__ldg(walk + i)) : 0xffffffffu;
+        }
+#pragma unroll
+        for (int j = 0; j < kOrderItems; j++)
+            if (b[j] != 0xffffffffu) atomicAdd(&cnt[b[j]], 1u);
+    }
     __syncthreads();
     // thread t owns buckets 2t and 2t + 1
     const uint32_t c0 = cnt[2 * tid], c1 = cnt[2 * tid + 1];
@@ -632,9 +647,16 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const uint32_t *__
     cnt[2 * tid] = excl;
     cnt[2 * tid + 1] = excl + c0;
     __syncthreads();
-    for (int i = tid; i < ntiles; i += kOrderThreads) {
-        const uint32_t b = kOrderBuckets - 1 - min(__ldg(walk + i), (uint32_t)(kOrderBuckets - 1));
-        order[atomicAdd(&cnt[b], 1u)] = (uint32_t)i;
+    for (int base = 0; base < ntiles; base += kRound) {
+        uint32_t b[kOrderItems];
+#pragma unroll
+        for (int j = 0; j < kOrderItems; j++) {
+            const int i = base + j * kOrderThreads + tid;
+            b[j] = i < ntiles ? walk_bucket(__ldg(walk + i)) : 0xffffffffu;
+        }
+#pragma unroll
+        for (int j = 0; j < kOrderItems; j++)
+            if (b[j] != 0xffffffffu) order[atomicAdd(&cnt[b[j]], 1u)] = (uint32_t)(base + j * kOrderThreads + tid);
     }
 }
 

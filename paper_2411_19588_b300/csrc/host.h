@@ -192,7 +192,8 @@ struct splash_ctx {
 struct splash_state {
     splash_ctx *ctx = nullptr;
     // per Gaussian
-    splash_host::Buf rec, depth_key, tt, rect, dk0, dv0, dk1, dv1, offsets, scan_sums;
+    // (scs: the super-tile counts in depth order; scan_sums: the emit blocks' offsets)
+    splash_host::Buf rec, depth_key, tt, rect, dk0, dv0, dk1, dv1, scs, scan_sums;
     // per (tile, Gaussian) pair (the two-level binning uses them for its
     // super-tile entries and the tile lists)
     splash_host::Buf tk0, tv0, tk1, tv1;

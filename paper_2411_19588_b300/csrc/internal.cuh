@@ -216,9 +216,16 @@ int64_t chunk_bound(int64_t n_super_entries, int nsuper);
 // address; null: none); sc[g] = Gaussian g's super-tile count
 void launch_pair_totals(int64_t n, const uint32_t *tt, const uint2 *rect, uint32_t *sc, void *scratch,
                         uint64_t *host_out, const uint32_t *status, cudaStream_t s);
-void launch_emit_super(int64_t n, const uint32_t *order, const uint32_t *offsets, const uint32_t *sc, const uint2 *rect,
-                       int nsx, int sbits, uint32_t *keys, uint32_t *vals, uint64_t capacity, uint32_t *status,
-                       cudaStream_t s);
+// blocks of depth-ordered Gaussians the emit takes per CTA (block_pre holds
+// emit_blocks(n) + 1 words)
+int64_t emit_blocks(int64_t n);
+// scs[r] = sc[order[r]]; block_pre[b] = exclusive offset of emit block b;
+// *total = K_s
+void launch_super_scan(int64_t n, const uint32_t *order, const uint32_t *sc, uint32_t *scs, uint32_t *block_pre,
+                       uint32_t *total, cudaStream_t s);
+void launch_emit_super(int64_t n, const uint32_t *order, const uint32_t *scs, const uint32_t *block_pre,
+                       const uint2 *rect, int nsx, int sbits, uint32_t *keys, uint32_t *vals, uint64_t capacity,
+                       uint32_t *status, cudaStream_t s);
 struct BinningScratch {
     uint32_t *chunk_base;   // [nsuper + 1]
     uint32_t *chunk_count;  // [chunk_bound][32]
