@@ -270,6 +270,7 @@ constexpr int kChunk = 256;    // entries per chunk (one warp each: 8 groups of 
 constexpr int kGroups = kChunk / 32;
 static_assert(kGroups <= 15, "four count planes");
 constexpr int kChunkWarps = 4; // chunks per CTA
+constexpr int kRecWords = (kGroups + 2 + 3) / 4 * 4;  // the scatter's per-tile record: masks, position, limit
 
 __device__ __forceinline__ uint32_t tile_mask(uint32_t lr)
 {
@@ -461,6 +462,7 @@ __global__ void __launch_bounds__(kChunkWarps * 32) k_super_scatter(
     pdl_enter();
     const int lane = threadIdx.x & 31;
     __shared__ uint32_t s_slot[kChunkWarps][kChunk];
+    __shared__ __align__(16) uint32_t s_rec[kChunkWarps][32][kRecWords];
     const uint32_t c = blockIdx.x * kChunkWarps + (threadIdx.x >> 5);
     if (c >= cb[nsuper]) return;  // uniform over the warp
     const int s = chunk_super(cb, nsuper, c);
@@ -483,6 +485,23 @@ __global__ void __launch_bounds__(kChunkWarps * 32) k_super_scatter(
 #pragma unroll
     for (int g = 0; g < kGroups; g++)
         m[g] = warp_transpose(beg + (uint32_t)(g * 32 + lane) < end ? tile_mask(m[g] >> sbits) : 0u, lane);
+    // lane t's record for tile t (its masks, list position and limit) goes
+    // to shared memory: the tile loop reads it with broadcast 16-byte loads,
+    // three per tile instead of ten shuffles (the shuffle rate bounds this loop)
+    uint32_t(*rec)[kRecWords] = s_rec[threadIdx.x >> 5];
+    {
+        uint32_t w[kRecWords];
+#pragma unroll
+        for (int g = 0; g < kGroups; g++) w[g] = m[g];
+        w[kGroups] = base;
+        w[kGroups + 1] = rg.y;
+#pragma unroll
+        for (int q = kGroups + 2; q < kRecWords; q++) w[q] = 0u;
+#pragma unroll
+        for (int q = 0; q < kRecWords; q += 4)
+            *reinterpret_cast<uint4 *>(&rec[lane][q]) = make_uint4(w[q], w[q + 1], w[q + 2], w[q + 3]);
+    }
+    __syncwarp();
     bool bad = false;
     const uint32_t lt = (1u << lane) - 1u;
     uint32_t *buf = s_slot[threadIdx.x >> 5];
@@ -490,12 +509,20 @@ __global__ void __launch_bounds__(kChunkWarps * 32) k_super_scatter(
         // the tile's hits in this chunk, in entry order: group g's covering
         // lanes put their values in slots pre_g + rank of the warp's buffer,
         // then the warp stores the slots 32 at a time, contiguously
-        const uint32_t pos = __shfl_sync(0xffffffffu, base, t);
-        const uint32_t lim = __shfl_sync(0xffffffffu, rg.y, t);
+        uint32_t w[kRecWords];
+#pragma unroll
+        for (int q = 0; q < kRecWords; q += 4) {
+            const uint4 u = *reinterpret_cast<const uint4 *>(&rec[t][q]);
+            w[q] = u.x;
+            w[q + 1] = u.y;
+            w[q + 2] = u.z;
+            w[q + 3] = u.w;
+        }
+        const uint32_t pos = w[kGroups], lim = w[kGroups + 1];
         uint32_t pre = 0;
 #pragma unroll
         for (int g = 0; g < kGroups; g++) {
-            const uint32_t b = __shfl_sync(0xffffffffu, m[g], t);  // the lanes covering tile t
+            const uint32_t b = w[g];  // the lanes covering tile t
             if ((b >> lane) & 1u) buf[pre + __popc(b & lt)] = v[g];
             pre += __popc(b);
         }

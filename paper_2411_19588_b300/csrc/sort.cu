@@ -162,8 +162,8 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
         }
         const uint32_t old = wh[d];  // every peer reads the same word (a broadcast)
         __syncwarp();
-        if (lane == 31 - __clz(peers)) wh[d] = old + __popc(peers);
         rank[j] = old + __popc(peers & lt);
+        if ((peers >> lane) == 1u) wh[d] = rank[j] + 1u;  // the last peer: old + the peer count
         __syncwarp();
     }
     __syncthreads();
