@@ -38,7 +38,7 @@ FLOP_PER_PAIR_FWD = 18
 FLOP_PER_PAIR_BWD = 50
 # DRAM bytes (read + write) of one launch at the default workload (1.5M Gaussians, 1920x1280,
 # 16x16 tiles), from an ncu capture of the current kernel; used for the roofline's `traffic`
-KERNEL_DRAM_BYTES = {"blend_bwd": 80.15e6 + 2.63e6}
+KERNEL_DRAM_BYTES = {"blend_bwd": 81.07e6 + 2.86e6}
 # shared-memory wavefronts per walked pixel-Gaussian pair of the blends
 # (l1tex__data_pipe_lsu_wavefronts_mem_shared.sum / walked pairs of the same
 # launch, from an ncu capture of the current kernels on the 300k-Gaussian
@@ -465,13 +465,13 @@ def run_ours(args, world, rank, local):
         # depth sort: 3 passes (9 + 9 + 8 bits) over the N depth keys (key + value read and
         # written per pass, plus one key read for the histograms)
         "depth_sort": ("hbm", 3 * 16.0 * args.n + 4.0 * args.n, "GB/s"),
-        # two-level binning: scan of the super-tile counts in depth order; the K_s super-tile
-        # entries emitted (order, offset, count, rectangle read; key + value written); their
-        # one-pass sort (key + value read and written, one key read for the histogram); the
-        # tile lists (keys read by the count pass, keys + values by the scatter, K Gaussian
-        # ids written)
-        "scan": ("hbm", 8.0 * args.n, "GB/s"),
-        "emit": ("hbm", 20.0 * args.n + 8.0 * n_super, "GB/s"),
+        # two-level binning: the super-tile counts gathered into depth order (order and count
+        # read, the depth-ordered count written); the K_s super-tile entries emitted (order,
+        # depth-ordered count, rectangle read; key + value written); their one-pass sort
+        # (key + value read and written, one key read for the histogram); the tile lists (keys
+        # read by the count pass, keys + values by the scatter, K Gaussian ids written)
+        "scan": ("hbm", 12.0 * args.n, "GB/s"),
+        "emit": ("hbm", 16.0 * args.n + 8.0 * n_super, "GB/s"),
         "tile_sort": ("hbm", 16.0 * n_super + 4.0 * n_super, "GB/s"),
         "ranges": ("hbm", 12.0 * n_super + 4.0 * n_keys, "GB/s"),
         "loss": ("hbm", 4.0 * 3 * H * W * 9, "GB/s"),
