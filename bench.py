@@ -43,7 +43,7 @@ KERNEL_DRAM_BYTES = {"blend_bwd": 81.07e6 + 2.86e6}
 # (l1tex__data_pipe_lsu_wavefronts_mem_shared.sum / walked pairs of the same
 # launch, from an ncu capture of the current kernels on the 300k-Gaussian
 # 1920x1280 case); the shared-memory peak is one wavefront (128 B) per SM per clock
-KERNEL_SMEM_WAVEFRONTS_PER_PAIR = {"blend_fwd": 0.1026, "blend_bwd": 0.2004}
+KERNEL_SMEM_WAVEFRONTS_PER_PAIR = {"blend_fwd": 0.1013, "blend_bwd": 0.2004}
 SM_COUNT_FALLBACK = 148
 
 
