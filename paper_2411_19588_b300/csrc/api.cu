@@ -278,13 +278,17 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
                           st->tk1.as<uint32_t>(), st->tv1.as<uint32_t>(), (uint64_t)Ks, ctx->d_status, s);
     }
     int which = 0;
+    // a one-pass super-tile sort leaves each super-tile's list start in its
+    // digit offsets: the tile lists take the ranges from there
+    const bool one_pass = Ks > 0 && digit_plan(sbits).passes == 1;
     {
         Stage t(ctx->prof, SPLASH_STAGE_TILE_SORT, s);
         which = sort_pairs(st->tk1.as<uint32_t>(), st->tv1.as<uint32_t>(), st->tk0.as<uint32_t>(), st->tv0.as<uint32_t>(),
                            st->tk1.as<uint32_t>(), st->tv1.as<uint32_t>(), Ks, nullptr, sbits, ss, ctx->d_status,
                            ctx->opt.spin_limit, ctx->opt.test_stall_partition, s);
-        launch_ranges(Ks, nullptr, which ? st->tk1.as<uint32_t>() : st->tk0.as<uint32_t>(), st->sranges.as<uint2>(),
-                      nsuper, s, (1u << sbits) - 1u);
+        if (!one_pass)
+            launch_ranges(Ks, nullptr, which ? st->tk1.as<uint32_t>() : st->tk0.as<uint32_t>(), st->sranges.as<uint2>(),
+                          nsuper, s, (1u << sbits) - 1u);
     }
     const uint32_t *skeys = which ? st->tk1.as<uint32_t>() : st->tk0.as<uint32_t>();
     const uint32_t *svals = which ? st->tv1.as<uint32_t>() : st->tv0.as<uint32_t>();
@@ -292,7 +296,7 @@ splash_status splash_render_forward(splash_ctx *ctx, splash_state *st, const spl
     {
         Stage t(ctx->prof, SPLASH_STAGE_RANGES, s);
         launch_tile_lists(tg, nsx, sbits, Ks, skeys, svals, st->sranges.as<uint2>(), bs, st->ranges.as<uint2>(), gids,
-                          ctx->d_status, s, (uint32_t)K);
+                          ctx->d_status, s, (uint32_t)K, nullptr, one_pass ? ss.hist : nullptr);
     }
     const uint32_t *tids = nullptr;  // rebuilt from the ranges when a query asks for them
     {

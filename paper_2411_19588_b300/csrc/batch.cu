@@ -331,20 +331,22 @@ splash_status splash_batch_forward(splash_batch *b, const splash_gaussians *g, c
                               tk, tv, (uint64_t)b->scap[v], ctx->d_status, s);
         }
         const uint32_t *skeys = tk, *svals = tv;
+        // a one-pass super-tile sort's digit offsets are the super-tile list starts
+        const bool one_pass = b->scap[v] > 0 && digit_plan(sbits).passes == 1;
         {
             Stage t(ctx->prof, SPLASH_STAGE_TILE_SORT, s);
             const int which = sort_pairs(tk, tv, pk, tv2, tk, tv, b->scap[v], ents, sbits, ss, ctx->d_status,
                                          ctx->opt.spin_limit, ctx->opt.test_stall_partition, s);
             skeys = which ? tk : pk;
             svals = which ? tv : tv2;
-            launch_ranges(b->scap[v], ents, skeys, b->sranges.as<uint2>(), nsuper, s, (1u << sbits) - 1u);
+            if (!one_pass) launch_ranges(b->scap[v], ents, skeys, b->sranges.as<uint2>(), nsuper, s, (1u << sbits) - 1u);
         }
         {
             Stage t(ctx->prof, SPLASH_STAGE_RANGES, s);
             const BinningScratch bs = binning_scratch_carve(b->bin_scratch.as<uint32_t>(), b->scap[v], nsuper);
             launch_tile_lists(tg, nsx, sbits, b->scap[v], skeys, svals, b->sranges.as<uint2>(), bs,
                               b->ranges.as<uint2>() + b->tiles_off[v], pv, ctx->d_status, s, (uint32_t)b->cap[v],
-                              counts + 2 * v);
+                              counts + 2 * v, one_pass ? ss.hist : nullptr, ents);
         }
     }
     // the work queue: every (view, tile), longest list first

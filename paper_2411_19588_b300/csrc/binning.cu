@@ -17,8 +17,9 @@
 //   k_gather_counts  -- super counts in depth order, sums per emit block
 //   k_block_prefix   -- exclusive offsets of the emit blocks, total K_s
 //   k_emit_super     -- (super-tile | clipped rectangle, Gaussian) entries in depth order
-//   (the super-tile sort and its list ranges: sort.cu, tiles.cu)
-//   k_chunk_map      -- first chunk of every super-tile
+//   (the super-tile sort: sort.cu; its list ranges are its digit offsets, or
+//   come from tiles.cu when the sort takes more than one pass)
+//   k_chunk_map      -- super-tile list ranges; first chunk of every super-tile
 //   k_super_count    -- per chunk and tile: entries covering the tile
 //   k_super_prefix   -- chunk offsets within each tile's list; tile counts
 //   k_tile_scan      -- tile ranges (exclusive scan of the counts)
@@ -309,8 +310,13 @@ __device__ __forceinline__ int chunk_super(const uint32_t *__restrict__ cb, int 
 }
 
 // one CTA: cb[s] = first chunk of super-tile s (exclusive scan of the chunk
-// counts), cb[nsuper] = all chunks
-__global__ void __launch_bounds__(1024) k_chunk_map(const uint2 *__restrict__ sranges, int nsuper, uint32_t *__restrict__ cb)
+// counts), cb[nsuper] = all chunks. With `off` (the one-pass super-tile
+// sort's exclusive digit offsets: the digit is the super-tile index) it first
+// writes every super-tile's list range, [off[s], off[s + 1]), the last one
+// ending at the sorted entry count.
+__global__ void __launch_bounds__(1024) k_chunk_map(uint2 *__restrict__ sranges, const uint32_t *__restrict__ off,
+                                                    int64_t total_host, const uint32_t *__restrict__ total_dev,
+                                                    int nsuper, uint32_t *__restrict__ cb)
 {
     pdl_enter();
     __shared__ uint32_t s_w[32];
@@ -318,9 +324,18 @@ __global__ void __launch_bounds__(1024) k_chunk_map(const uint2 *__restrict__ sr
     const int per = (nsuper + 1023) / 1024;
     const int s0 = min(nsuper, tid * per), s1 = min(nsuper, s0 + per);
     uint32_t local = 0;
-    for (int q = s0; q < s1; q++) {
-        const uint2 r = sranges[q];
-        local += (r.y - r.x + kChunk - 1) / kChunk;
+    if (off) {
+        const uint32_t total = total_dev ? *total_dev : (uint32_t)total_host;
+        for (int q = s0; q < s1; q++) {
+            const uint2 r = make_uint2(off[q], q + 1 < nsuper ? off[q + 1] : total);
+            sranges[q] = r;
+            local += (r.y - r.x + kChunk - 1) / kChunk;
+        }
+    } else {
+        for (int q = s0; q < s1; q++) {
+            const uint2 r = sranges[q];
+            local += (r.y - r.x + kChunk - 1) / kChunk;
+        }
     }
     uint32_t x = local;
 #pragma unroll
@@ -599,14 +614,15 @@ void launch_emit_super(int64_t n, const uint32_t *order, const uint32_t *scs, co
 }
 
 void launch_tile_lists(const TileGeom &tg, int nsx, int sbits, int64_t n_super_entries, const uint32_t *skeys,
-                       const uint32_t *svals, const uint2 *sranges, const BinningScratch &bs, uint2 *ranges,
-                       uint32_t *gauss_ids, uint32_t *status, cudaStream_t s, uint32_t cap, uint32_t *total)
+                       const uint32_t *svals, uint2 *sranges, const BinningScratch &bs, uint2 *ranges,
+                       uint32_t *gauss_ids, uint32_t *status, cudaStream_t s, uint32_t cap, uint32_t *total,
+                       const uint32_t *digit_off, const uint32_t *n_sorted_dev)
 {
     // plain launches: started early behind one another (programmatic launch)
     // these kernels made the forward 0.17 ms slower on the B300
     const int nsuper = nsx * ((tg.ty + kSuperH - 1) / kSuperH), ntiles = tg.tx * tg.ty;
     const unsigned chunks = (unsigned)chunk_bound(n_super_entries, nsuper);
-    k_chunk_map<<<1, 1024, 0, s>>>(sranges, nsuper, bs.chunk_base);
+    k_chunk_map<<<1, 1024, 0, s>>>(sranges, digit_off, n_super_entries, n_sorted_dev, nsuper, bs.chunk_base);
     count_launch();
     const unsigned ctas = (chunks + kChunkWarps - 1) / kChunkWarps;
     k_super_count<<<ctas, kChunkWarps * 32, 0, s>>>(skeys, sranges, bs.chunk_base, nsuper, sbits, bs.chunk_count);

@@ -234,11 +234,15 @@ struct BinningScratch {
 // the tile lists (gauss_ids) and their ranges from the sorted super-tile
 // lists; n_super_entries bounds the entries (their count is read on the
 // device); the ranges are clamped to `cap` slots of gauss_ids (a longer total
-// is reported); *total (optional, device) = the pair count
+// is reported); *total (optional, device) = the pair count. sranges holds the
+// super-tile list ranges, or, with digit_off (the exclusive digit offsets of
+// a one-pass super-tile sort), is filled from them, the last list ending at
+// *n_sorted_dev (or n_super_entries when that is null)
 size_t binning_scratch_words(int64_t n_super_entries, int nsuper, int ntiles);
 void launch_tile_lists(const TileGeom &tg, int nsx, int sbits, int64_t n_super_entries, const uint32_t *skeys,
-                       const uint32_t *svals, const uint2 *sranges, const BinningScratch &bs, uint2 *ranges,
-                       uint32_t *gauss_ids, uint32_t *status, cudaStream_t s, uint32_t cap, uint32_t *total = nullptr);
+                       const uint32_t *svals, uint2 *sranges, const BinningScratch &bs, uint2 *ranges,
+                       uint32_t *gauss_ids, uint32_t *status, cudaStream_t s, uint32_t cap, uint32_t *total = nullptr,
+                       const uint32_t *digit_off = nullptr, const uint32_t *n_sorted_dev = nullptr);
 BinningScratch binning_scratch_carve(uint32_t *base, int64_t n_super_entries, int nsuper);
 // tile_ids[i] = t for every i in ranges[t] (the sorted tile ids, rebuilt from the ranges)
 void launch_expand_tile_ids(const uint2 *ranges, int ntiles, uint32_t *tile_ids, cudaStream_t s);
