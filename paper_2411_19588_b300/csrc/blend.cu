@@ -73,9 +73,15 @@ constexpr int bwd_threads() { return Tile<TW, TH, kPxBwd>::NT; }
 // Forward staging: every per-Gaussian constant twice, so that one 16-byte
 // shared load yields the packed operand of a thread's two pixel columns
 // (FP32x2 arithmetic, one lane per column). Positions are stored negated:
-// pxl + (-x) rounds exactly as pxl - x.
+// pxl + (-x) rounds exactly as pxl - x. sth: the Gaussian's threshold on the
+// exponent qs of a pixel, max(3-sigma cut, log2(1/255) - log2 opacity): a
+// pixel takes part where qs >= it, i.e. within 3 sigma and at least 1/255
+// opaque (both tests in one comparison, in the exponent's domain). The
+// backward forms the same threshold from the staged log2 opacity (null sth).
+__device__ __forceinline__ float exponent_threshold(float log2_opacity) { return fmaxf(kQsMin, kLog2AlphaMin - log2_opacity); }
+
 __device__ __forceinline__ void stage_fwd(const Rec *__restrict__ rec, uint32_t gid, int ox, int oy, float4 *sx,
-                                          float4 *sy, float4 *sc, float4 *sk, float4 *sb, int slot)
+                                          float4 *sy, float4 *sc, float4 *sk, float4 *sb, float *sth, int slot)
 {
     const Rec r = rec[gid];
     const float xl = (r.r0.x - (float)ox) + r.r0.z;
@@ -85,6 +91,7 @@ __device__ __forceinline__ void stage_fwd(const Rec *__restrict__ rec, uint32_t 
     sc[slot] = make_float4(r.r1.z, r.r1.z, r.r1.w, r.r1.w);    // {C, C, lo, lo}
     sk[slot] = make_float4(r.r2.y, r.r2.y, r.r2.z, r.r2.z);    // {ct_r, ct_r, ct_g, ct_g}
     sb[slot] = make_float4(r.r2.w, r.r2.w, r.r2.x, r.r2.x);    // {ct_b, ct_b, d, d}
+    if (sth) sth[slot] = exponent_threshold(r.r1.w);
 }
 
 __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
@@ -104,6 +111,7 @@ __device__ __forceinline__ void blend_tile_fwd(const BlendView &v, int tile, con
     constexpr int PX = kPxFwd, NP = PX / 2;
     constexpr int NT = Tile<TW, TH, PX>::NT, HW = Tile<TW, TH, PX>::HW;
     __shared__ float4 sx[NB], sy[NB], sc[NB], sk[NB], sb[NB];
+    __shared__ float sth[NB];
     const CamK &cam = v.cam;
     const int tyi = tile / v.tg.tx, txi = tile - tyi * v.tg.tx;
     const int x0 = txi * TW, y0 = tyi * TH;
@@ -150,12 +158,13 @@ __device__ __forceinline__ void blend_tile_fwd(const BlendView &v, int tile, con
     for (int b0 = 0; b0 < n; b0 += NB) {
         if (__syncthreads_count(live > 0) == 0) break;
         for (int sl = tid; sl < NB && b0 + sl < n; sl += NT)
-            stage_fwd(v.rec, v.gauss_ids[rg.x + b0 + sl], ox, oy, sx, sy, sc, sk, sb, sl);
+            stage_fwd(v.rec, v.gauss_ids[rg.x + b0 + sl], ox, oy, sx, sy, sc, sk, sb, sth, sl);
         __syncthreads();
         const int nb = min(NB, n - b0);
         if (!__any_sync(0xffffffffu, live > 0)) continue;
         for (int k = 0; k < nb; k++) {
             const float4 fx = sx[k], fy = sy[k], fc = sc[k];
+            const float th = sth[k];
             const float2 dy = __fadd2_rn(pyl2, lo2(fy));
             const float2 Bdy = __fmul2_rn(hi2(fy), dy);
             const float2 Cdy2 = __fmul2_rn(__fmul2_rn(lo2(fc), dy), dy);
@@ -165,20 +174,21 @@ __device__ __forceinline__ void blend_tile_fwd(const BlendView &v, int tile, con
             for (int j = 0; j < NP; j++) {
                 const float2 dx = __fadd2_rn(pxl[j], lo2(fx));
                 qs[j] = __ffma2_rn(dx, __ffma2_rn(hi2(fx), dx, Bdy), Cdy2);
-                inside |= (qs[j].x >= kQsMin) | (qs[j].y >= kQsMin);
+                inside |= (qs[j].x >= th) | (qs[j].y >= th);
             }
-            // none of the thread's pixels within 3 sigma: nothing to add (a warp
-            // skips the rest when this holds for all its lanes)
+            // none of the thread's pixels within 3 sigma and 1/255 opaque:
+            // nothing to add (a warp skips the rest when this holds for all
+            // its lanes)
             if (!inside) continue;
             float2 w[NP], tn[NP];
             bool stop = false;
 #pragma unroll
             for (int j = 0; j < NP; j++) {
                 const float2 e = __fadd2_rn(qs[j], hi2(fc));
-                // the same tests as the backward's (raw alpha >= 1/255, then the clamp)
+                // the same test as the backward's (qs against the threshold), then the clamp
                 const float r0 = ex2_approx(e.x), r1 = ex2_approx(e.y);
-                const float a0 = (qs[j].x >= kQsMin && r0 >= kAlphaMin) ? fminf(kAlphaMax, r0) : 0.f;
-                const float a1 = (qs[j].y >= kQsMin && r1 >= kAlphaMin) ? fminf(kAlphaMax, r1) : 0.f;
+                const float a0 = qs[j].x >= th ? fminf(kAlphaMax, r0) : 0.f;
+                const float a1 = qs[j].y >= th ? fminf(kAlphaMax, r1) : 0.f;
                 w[j] = __fmul2_rn(make_float2(a0, a1), T[j]);
                 tn[j] = __ffma2_rn(w[j], neg1, T[j]);  // T - alpha T
                 stop |= (tn[j].x < kTStop) | (tn[j].y < kTStop);
@@ -491,7 +501,7 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
         __syncthreads();  // the previous batch's flush has read s_g / s_id
         for (int sl = tid; sl < nb; sl += NT) {
             const uint32_t gid = v.gauss_ids[rg.x + b0 + sl];
-            stage_fwd(v.rec, gid, ox, oy, sx, sy, sc, sk, sb, sl);
+            stage_fwd(v.rec, gid, ox, oy, sx, sy, sc, sk, sb, nullptr, sl);
             s_id[sl] = gid;
         }
         for (int sl = tid; sl < NB; sl += NT)
@@ -502,13 +512,15 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
             for (int k = nb - 1; k >= 0; k--) {
                 const int j = b0 + k;
                 const float4 fx = sx[k], fy = sy[k], fc = sc[k];
+                const float th = exponent_threshold(fc.z);  // as the forward staged it
                 const float2 dy = __fadd2_rn(pyl2, lo2(fy));
                 const float2 Bdy = __fmul2_rn(hi2(fy), dy);
                 const float2 Cdy2 = __fmul2_rn(__fmul2_rn(lo2(fc), dy), dy);
                 // the exponent and raw alpha of all the thread's pixels first, without
                 // branches (independent chains the scheduler can overlap); a pixel
-                // takes part if the Gaussian is in front of its walk bound, within
-                // 3 sigma and at least 1/255 opaque there
+                // takes part if the Gaussian is in front of its walk bound and its
+                // exponent reaches the threshold (within 3 sigma, at least 1/255
+                // opaque)
                 float2 dx[NP], ar[NP];
                 bool on0[NP], on1[NP];
                 bool any = false;
@@ -518,9 +530,8 @@ __device__ __forceinline__ void blend_tile_bwd(const BlendView &v, int tile, con
                     const float2 qs = __ffma2_rn(dx[jp], __ffma2_rn(hi2(fx), dx[jp], Bdy), Cdy2);
                     const float2 e = __fadd2_rn(qs, hi2(fc));
                     ar[jp] = make_float2(ex2_approx(e.x), ex2_approx(e.y));
-                    // (raw alpha >= 1/255 is the clamped alpha's test: the clamp is above it)
-                    on0[jp] = (j < P[jp].last0) & (qs.x >= kQsMin) & (ar[jp].x >= kAlphaMin);
-                    on1[jp] = (j < P[jp].last1) & (qs.y >= kQsMin) & (ar[jp].y >= kAlphaMin);
+                    on0[jp] = (j < P[jp].last0) & (qs.x >= th);
+                    on1[jp] = (j < P[jp].last1) & (qs.y >= th);
                     any |= on0[jp] | on1[jp];
                 }
                 if (!__any_sync(0xffffffffu, any)) continue;

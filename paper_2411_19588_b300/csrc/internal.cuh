@@ -23,6 +23,7 @@ constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 // q <= 9 (3 sigma) expressed on the scaled form qs = -log2(e)/2 * q
 constexpr float kQsMin = -4.5f * kLog2e;
+constexpr float kLog2AlphaMin = -7.99435329f;  // log2(1/255), rounded to FP32
 
 // ---- camera as the kernels see it
 struct CamK {
