@@ -37,8 +37,10 @@ LR = {"means": 1.6e-4, "log_scales": 5e-3, "quats": 1e-3, "opacity_logits": 5e-2
 FLOP_PER_PAIR_FWD = 18
 FLOP_PER_PAIR_BWD = 50
 # DRAM bytes (read + write) of one launch at the default workload (1.5M Gaussians, 1920x1280,
-# 16x16 tiles), from an ncu capture of the current kernel; used for the roofline's `traffic`
-KERNEL_DRAM_BYTES = {"blend_bwd": 81.07e6 + 2.86e6}
+# 16x16 tiles), from an ncu capture of the current kernel; used for the roofline's `traffic`.
+# Empty: both candidates changed after their last captures (k_blend_bwd's 81.07 + 2.86 MB was
+# taken before its combined exponent threshold), so `traffic` is null until recaptured.
+KERNEL_DRAM_BYTES: dict = {}
 # stages bracketed by events inside the timed region (the candidates for the dominant kernel)
 TIMED_STAGES = ["blend_bwd", "preprocess_bwd"]
 # shared-memory wavefronts per walked pixel-Gaussian pair of the blends
